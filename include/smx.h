@@ -1,0 +1,198 @@
+/*
+ * smx.h -- C ABI of the GB300 submatrix density-matrix library.
+ *
+ * The library computes the density matrix of a sparse, filtered, orthogonalised
+ * Kohn-Sham-like matrix H by sign-function purification (the paper's Eq. 14
+ * with S = I),
+ *
+ *        D = 1/2 (I - sign(H - mu I)),
+ *
+ * using the submatrix method (the paper's Fig. 2): for every block column j the
+ * block rows R_j stored in that column of the filtered H form a dense principal
+ * submatrix T_j = H[R_j, R_j]; its sign function (Eq. 13) is computed by
+ * Newton-Schulz iteration on the GPU; only the columns of block j are kept,
+ * D[R_j, j] = 1/2 (E_j - sign(T_j - mu I)[:, cols of j]).  mu is either fixed
+ * or found by bisection on trace(D) = n_e.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns an smx_status and never throws or aborts.
+ *  - Arrays passed in are borrowed for the duration of the call only; the
+ *    library copies what it keeps.  The library owns all device memory it
+ *    allocates and frees it in smx_destroy.
+ *  - "Host pointer" means ordinary CPU memory (pinned or pageable); "device
+ *    pointer" means memory of the current CUDA device.
+ *  - Work is enqueued on the stream given to smx_create (NULL = legacy default
+ *    stream).  Calls that return results to the host synchronise that stream.
+ *  - A failure inside asynchronous device work (non-finite numbers, a
+ *    submatrix that did not converge, a device wait that timed out) is latched
+ *    in the context and reported by the next smx_get_* call; it stays latched
+ *    until the next successful smx_build_density / smx_solve_mu.
+ *  - Matrix layout ("block-CSC"): n_block_cols block columns; block i has
+ *    block_size[i] rows and columns.  Column j stores blocks for the block
+ *    rows row_idx[col_ptr[j] .. col_ptr[j+1]-1], strictly ascending; the
+ *    diagonal block must be present and the block pattern must be symmetric.
+ *    values holds the blocks in that order, each block (b_r x b_c) stored
+ *    column-major, so block k starts at sum_{k' < k} b_r(k') b_c(k').
+ *  - The values of H are assumed symmetric (H_ij = H_ji^T); they are not
+ *    checked for symmetry.
+ *
+ * Thread safety: a context must not be used from two host threads at once.
+ * Different contexts are independent.
+ */
+#ifndef SMX_H
+#define SMX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smx_ctx smx_ctx;
+
+typedef enum {
+    SMX_OK = 0,
+    SMX_ERR_ARG = 1,         /* null pointer, size out of range, unknown enum value */
+    SMX_ERR_PATTERN = 2,     /* malformed block-CSC pattern */
+    SMX_ERR_NONFINITE = 3,   /* NaN/Inf in the input values or in a submatrix iteration */
+    SMX_ERR_CUDA = 4,        /* a CUDA runtime call failed (the context should be destroyed) */
+    SMX_ERR_OOM = 5,         /* device allocation failed */
+    SMX_ERR_NOCONV = 6,      /* a submatrix did not converge within the iteration cap */
+    SMX_ERR_NOBRACKET = 7,   /* the electron count lies outside [0, N] */
+    SMX_ERR_TIMEOUT = 8,     /* a device-side wait exceeded its limit and the kernel gave up */
+    SMX_ERR_STATE = 9,       /* call order violated (e.g. results requested before a build) */
+    SMX_ERR_UNSUPPORTED = 10 /* valid request this build cannot serve (e.g. submatrix too large) */
+} smx_status;
+
+/* Arithmetic of the Newton-Schulz bulk phase (Eq. 13 iteration).
+ *  SMX_FP64   : FP64 on the CUDA cores ("plain" form).
+ *  SMX_FP16X3 : tcgen05 tensor cores, FP16 operands split as hi + lo with three
+ *               products (hi*hi + hi*lo + lo*hi) per step and FP32 accumulation
+ *               in tensor memory; about 22 significant bits per operand.
+ *  SMX_FP16   : tcgen05, one FP16 product per step, FP32 accumulation.
+ *  SMX_BF16   : tcgen05, one BF16 product per step, FP32 accumulation.
+ * The scaling X0 = (T - mu I)/b per submatrix, the trace and the energy are
+ * always FP64. */
+typedef enum {
+    SMX_FP64 = 0,
+    SMX_FP16X3 = 1,
+    SMX_FP16 = 2,
+    SMX_BF16 = 3
+} smx_precision;
+
+/* Statistics of the last build (or the last bisection step). */
+typedef struct {
+    int32_t n_block_cols;       /* number of submatrices */
+    int64_t n;                  /* scalar dimension of H */
+    int64_t nnzb_input;         /* stored blocks of the input pattern */
+    int64_t nnzb_filtered;      /* stored blocks after filtering */
+    int32_t dim_min, dim_max;   /* smallest / largest submatrix dimension n_j */
+    double dim_mean;
+    int32_t iters_min, iters_max; /* Newton-Schulz iterations per submatrix */
+    double iters_mean;
+    int32_t n_noconv;           /* submatrices that hit the iteration cap */
+    int32_t n_bound_fallback;   /* submatrices whose learned bound failed the safe check */
+    int32_t bisection_steps;    /* builds done by the last smx_solve_mu */
+    double flops_ns;            /* algorithmic flops of the last build: sum_j 4 n_j^3 iters_j */
+    double ms_last_build;       /* device time of the last build (CUDA events), ms */
+    double mu;                  /* mu of the last build */
+    int32_t precision;          /* smx_precision of the bulk phase */
+    int32_t fp64_final_iters;
+    /* Counters accumulated since smx_create or the last smx_reset_counters: */
+    int64_t kernel_launches;    /* CUDA kernels this library launched */
+    int64_t ns_launches;        /* launches of the Newton-Schulz kernel */
+    double ns_ms_total;         /* their summed device time (CUDA events on the context stream), ms */
+    double ns_work_n3;          /* sum over submatrices and launches of n_j^3 * iterations_j;
+                                   4 * ns_work_n3 is the algorithmic Newton-Schulz flop count */
+} smx_stats;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* smx_status_string(smx_status s);
+
+/* Creates a context for a block-sparse symmetric H (Fig. 2 input).
+ *  out          : receives the new context (set to NULL on failure).
+ *  n_block_cols : number of block rows/columns B (>= 1).
+ *  block_size   : host int32[B], each >= 1 and <= 64.
+ *  col_ptr      : host int64[B+1], col_ptr[0] = 0, non-decreasing.
+ *  row_idx      : host int32[col_ptr[B]], see the layout convention above.
+ *  values       : host double[sum of block areas], the blocks of H.
+ *  cuda_stream  : cudaStream_t to enqueue work on, or NULL.
+ * Errors: SMX_ERR_ARG, SMX_ERR_PATTERN, SMX_ERR_NONFINITE, SMX_ERR_OOM, SMX_ERR_CUDA.
+ * Defaults: filter threshold 0, mu = 0 (fixed), precision SMX_FP64. */
+smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_size,
+                      const int64_t* col_ptr, const int32_t* row_idx, const double* values,
+                      void* cuda_stream);
+
+/* Replaces the values of H (same input pattern, e.g. the next MD snapshot).
+ *  values    : double[] of the same length as in smx_create.
+ *  on_device : 0 = host pointer, 1 = device pointer (read on the context stream).
+ * The filter is re-applied at the next build.  Errors: SMX_ERR_ARG, SMX_ERR_CUDA. */
+smx_status smx_set_values(smx_ctx* ctx, const double* values, int32_t on_device);
+
+/* Block filter: an off-diagonal block whose Frobenius norm is strictly below
+ * eps is dropped from H (and from D); diagonal blocks are always kept.
+ * eps >= 0.  Errors: SMX_ERR_ARG. */
+smx_status smx_set_filter_threshold(smx_ctx* ctx, double eps);
+
+/* Fixed chemical potential mu (Eq. 14) for smx_build_density.  Errors: SMX_ERR_ARG (non-finite). */
+smx_status smx_set_mu(smx_ctx* ctx, double mu);
+
+/* Electron count for smx_solve_mu: bisection on trace(D(mu)) = n_e inside the
+ * Gershgorin interval of the filtered H; stops when |trace - n_e| <= tol or
+ * after max_steps builds (1..200).  The result is the last evaluated mu.
+ * Errors: SMX_ERR_ARG. */
+smx_status smx_set_electron_count(smx_ctx* ctx, double n_e, int32_t max_steps, double tol);
+
+/* Arithmetic of the Newton-Schulz iteration; fp64_final_iters (0..4) FP64
+ * iterations follow the bulk phase when bulk != SMX_FP64.  Errors: SMX_ERR_ARG. */
+smx_status smx_set_precision(smx_ctx* ctx, smx_precision bulk, int32_t fp64_final_iters);
+
+/* Builds D at the current fixed mu (Fig. 2 steps (i)-(iii) and Eq. 14):
+ * filter (if values or threshold changed), gather, spectral bound, scaling,
+ * Newton-Schulz, scatter, trace and energy.  Asynchronous on the context
+ * stream except for a small host round trip when the filtered pattern must
+ * be recomputed.  Errors: SMX_ERR_NONFINITE (input), SMX_ERR_OOM, SMX_ERR_CUDA,
+ * SMX_ERR_UNSUPPORTED (a submatrix larger than this build handles). */
+smx_status smx_build_density(smx_ctx* ctx);
+
+/* Finds mu by bisection (see smx_set_electron_count) and leaves the last
+ * build's D in the context.  Synchronises once per bisection step.
+ * Errors: as smx_build_density, plus SMX_ERR_STATE (no electron count set),
+ * SMX_ERR_NOBRACKET, and latched device errors. */
+smx_status smx_solve_mu(smx_ctx* ctx);
+
+/* trace(D), trace(D H) (the band-structure energy, unshifted H) and mu of the
+ * last build.  Any argument may be NULL.  Synchronises the stream and returns
+ * latched device errors.  Errors: SMX_ERR_STATE (no build yet). */
+smx_status smx_get_trace(smx_ctx* ctx, double* trace_D, double* trace_DH, double* mu);
+
+/* Copies D of the last build, laid out exactly like the input values
+ * (input pattern; blocks dropped by the filter are zero).
+ *  values_out : double[] of the input value count; host or device pointer.
+ *  on_device  : 0 = host pointer (synchronises), 1 = device pointer (async).
+ * Errors: SMX_ERR_ARG, SMX_ERR_STATE, SMX_ERR_CUDA, latched device errors. */
+smx_status smx_get_density(smx_ctx* ctx, double* values_out, int32_t on_device);
+
+/* Filtered pattern of the last build.  col_ptr: host int64[B+1]; row_idx: host
+ * int32[nnzb_filtered] (size from smx_get_stats), either may be NULL. */
+smx_status smx_get_pattern(smx_ctx* ctx, int64_t* col_ptr, int32_t* row_idx);
+
+/* Statistics of the last build (see smx_stats).  Synchronises. */
+smx_status smx_get_stats(smx_ctx* ctx, smx_stats* out);
+
+/* Zeroes the accumulated counters of smx_stats.  Synchronises the stream. */
+smx_status smx_reset_counters(smx_ctx* ctx);
+
+/* Per-submatrix details of the last build, host arrays of length B (any may
+ * be NULL): dimension n_j, Newton-Schulz iterations, and the scaling bound
+ * b_j used for X0 = (T_j - mu I)/b_j.  Synchronises. */
+smx_status smx_get_submatrix_info(smx_ctx* ctx, int32_t* dims, int32_t* iters, double* bounds);
+
+/* Releases the context and all device memory it owns.  NULL is ignored. */
+void smx_destroy(smx_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMX_H */

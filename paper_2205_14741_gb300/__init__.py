@@ -1,0 +1,137 @@
+"""GB300 submatrix-method density matrix: thin Python binding of include/smx.h.
+
+Every step of the computation runs in the CUDA library ``lib/libsmx.so``;
+this module only marshals arguments (numpy arrays for host buffers, torch
+CUDA tensors for device buffers and streams).  The binding raises if the
+library is missing: there is no CPU fallback.
+
+The names follow the C ABI: ``SubmatrixDensity`` owns one ``smx_ctx``.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import BF16, FP16, FP16X3, FP64, PRECISIONS, SmxError, Stats, check  # noqa: F401
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())
+
+
+class SubmatrixDensity:
+    """One library context: a block-sparse symmetric H and its density matrix.
+
+    Parameters mirror ``smx_create``: block sizes, block-CSC column pointers
+    and rows (full symmetric pattern), values (column-major blocks), and an
+    optional CUDA stream handle (an int; ``torch.cuda.current_stream().cuda_stream``).
+    """
+
+    def __init__(self, block_size, col_ptr, row_idx, values, stream: int | None = None):
+        lib = _lib.load()
+        self._lib = lib
+        self.block_size = np.ascontiguousarray(block_size, dtype=np.int32)
+        self.col_ptr = np.ascontiguousarray(col_ptr, dtype=np.int64)
+        self.row_idx = np.ascontiguousarray(row_idx, dtype=np.int32)
+        vals = np.ascontiguousarray(values, dtype=np.float64)
+        self.n_values = int(vals.shape[0])
+        self.n_block_cols = int(self.block_size.shape[0])
+        ctx = C.c_void_p()
+        check(lib.smx_create(C.byref(ctx), self.n_block_cols, _ptr(self.block_size), _ptr(self.col_ptr),
+                             _ptr(self.row_idx), _ptr(vals), C.c_void_p(stream or 0)), "smx_create")
+        self._ctx = ctx
+
+    @classmethod
+    def from_system(cls, sysm, stream: int | None = None):
+        """Context for a ``synth.BlockCSC``-like object (block_size, col_ptr, row_idx, values)."""
+        return cls(sysm.block_size, sysm.col_ptr, sysm.row_idx, sysm.values, stream)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.smx_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- settings -----------------------------------------------------------
+    def set_values(self, values, on_device: bool = False):
+        if on_device:
+            check(self._lib.smx_set_values(self._ctx, _ptr(values), 1), "smx_set_values")
+        else:
+            v = np.ascontiguousarray(values, dtype=np.float64)
+            check(self._lib.smx_set_values(self._ctx, _ptr(v), 0), "smx_set_values")
+
+    def set_filter_threshold(self, eps: float):
+        check(self._lib.smx_set_filter_threshold(self._ctx, float(eps)), "smx_set_filter_threshold")
+
+    def set_mu(self, mu: float):
+        check(self._lib.smx_set_mu(self._ctx, float(mu)), "smx_set_mu")
+
+    def set_electron_count(self, n_e: float, max_steps: int = 30, tol: float = 0.5):
+        check(self._lib.smx_set_electron_count(self._ctx, float(n_e), int(max_steps), float(tol)),
+              "smx_set_electron_count")
+
+    def set_precision(self, bulk="fp64", fp64_final_iters: int = 0):
+        p = PRECISIONS[bulk] if isinstance(bulk, str) else int(bulk)
+        check(self._lib.smx_set_precision(self._ctx, p, int(fp64_final_iters)), "smx_set_precision")
+
+    # -- work ---------------------------------------------------------------
+    def build_density(self):
+        check(self._lib.smx_build_density(self._ctx), "smx_build_density")
+
+    def solve_mu(self):
+        check(self._lib.smx_solve_mu(self._ctx), "smx_solve_mu")
+
+    # -- results ------------------------------------------------------------
+    def get_trace(self):
+        tr, en, mu = C.c_double(), C.c_double(), C.c_double()
+        check(self._lib.smx_get_trace(self._ctx, C.byref(tr), C.byref(en), C.byref(mu)), "smx_get_trace")
+        return tr.value, en.value, mu.value
+
+    def get_density(self, out=None):
+        """D laid out like the input values: into ``out`` (numpy or CUDA tensor) or a new numpy array."""
+        if out is None:
+            out = np.empty(self.n_values, dtype=np.float64)
+        on_device = not isinstance(out, np.ndarray)
+        check(self._lib.smx_get_density(self._ctx, _ptr(out), 1 if on_device else 0), "smx_get_density")
+        return out
+
+    def get_pattern(self):
+        st = self.get_stats()
+        cp = np.empty(self.n_block_cols + 1, dtype=np.int64)
+        ri = np.empty(max(1, st["nnzb_filtered"]), dtype=np.int32)
+        check(self._lib.smx_get_pattern(self._ctx, _ptr(cp), _ptr(ri)), "smx_get_pattern")
+        return cp, ri[: st["nnzb_filtered"]]
+
+    def get_stats(self) -> dict:
+        s = Stats()
+        check(self._lib.smx_get_stats(self._ctx, C.byref(s)), "smx_get_stats")
+        return s.as_dict()
+
+    def reset_counters(self):
+        check(self._lib.smx_reset_counters(self._ctx), "smx_reset_counters")
+
+    def get_submatrix_info(self):
+        dims = np.empty(self.n_block_cols, dtype=np.int32)
+        iters = np.empty(self.n_block_cols, dtype=np.int32)
+        bounds = np.empty(self.n_block_cols, dtype=np.float64)
+        check(self._lib.smx_get_submatrix_info(self._ctx, _ptr(dims), _ptr(iters), _ptr(bounds)),
+              "smx_get_submatrix_info")
+        return dims, iters, bounds

@@ -1,0 +1,133 @@
+// Newton-Schulz sign iteration in FP64 on the CUDA cores (the plain form).
+//
+// Eq. 13 defines sign(A) = A (A^2)^(-1/2).  The iteration
+//     X_{k+1} = 1/2 X_k (3 I - X_k^2),   X_0 = (T_j - mu I) / b_j,
+// converges to sign(T_j - mu I) when every eigenvalue of X_0 lies in
+// (-sqrt 3, 0) u (0, sqrt 3); b_j >= spectral radius guarantees |lambda| <= 1.
+// Each step is two products: Y = 3/2 I - 1/2 X X (which also yields the
+// residual ||X^2 - I||_F) and X' = X Y.  Stopping rule: after the step whose
+// residual is <= tau (the next residual is ~0.75 tau^2).
+//
+// One CTA per submatrix; FP64 throughput on this part is about 1.2 TFLOP/s
+// for the whole GPU, so the kernel is bound by the FP64 pipes and a plain
+// shared-memory tiled product with 4x4 register blocking suffices.
+#include "smx_finish.cuh"
+#include "smx_kernels.h"
+
+namespace smx {
+
+namespace {
+
+constexpr int kTile = 64;
+constexpr int kKc = 16;
+
+// C = A B (n x n, row-major, leading dimension ld).  mode 1 writes
+// 3/2 I - 1/2 A B and returns this thread's share of ||A B - I||_F^2;
+// mode 2 writes A B.
+__device__ double gemm_fp64(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C, int n,
+                            int ld, int mode, double (*As)[kTile + 1], double (*Bs)[kTile + 1]) {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double r2 = 0.0;
+    for (int r0 = 0; r0 < n; r0 += kTile) {
+        for (int c0 = 0; c0 < n; c0 += kTile) {
+            double acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+            for (int k0 = 0; k0 < n; k0 += kKc) {
+                for (int e = tid; e < kTile * kKc; e += 256) {
+                    const int rr = e / kKc, kk = e - rr * kKc;
+                    const int row = r0 + rr, col = k0 + kk;
+                    As[kk][rr] = (row < n && col < n) ? A[static_cast<int64_t>(row) * ld + col] : 0.0;
+                }
+                for (int e = tid; e < kTile * kKc; e += 256) {
+                    const int kk = e / kTile, cc = e - kk * kTile;
+                    const int row = k0 + kk, col = c0 + cc;
+                    Bs[kk][cc] = (row < n && col < n) ? B[static_cast<int64_t>(row) * ld + col] : 0.0;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < kKc; ++kk) {
+                    double a[4], b[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int row = r0 + ty * 4 + i;
+                if (row >= n) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int col = c0 + tx * 4 + j;
+                    if (col >= n) continue;
+                    const double v = acc[i][j];
+                    if (mode == 1) {
+                        const double dlt = (row == col) ? 1.0 : 0.0;
+                        C[static_cast<int64_t>(row) * ld + col] = 1.5 * dlt - 0.5 * v;
+                        r2 += (v - dlt) * (v - dlt);
+                    } else {
+                        C[static_cast<int64_t>(row) * ld + col] = v;
+                    }
+                }
+            }
+        }
+    }
+    return r2;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
+    __shared__ double As[kKc][kTile + 1];
+    __shared__ double Bs[kKc][kTile + 1];
+    __shared__ double scratch[32];
+    extern __shared__ int ls_smem[];
+    const SubDesc s = a.subs[blockIdx.x];
+    const int n = s.n, ld = s.ld;
+    double* X = a.T + s.t_off;
+    double* Y = a.W1 + s.t_off;
+    double* Z = a.W2 + s.t_off;
+    const double inv_b = 1.0 / a.bound[blockIdx.x];
+    for (int r = threadIdx.x / 32; r < n; r += 8)
+        for (int c = threadIdx.x & 31; c < n; c += 32) X[static_cast<int64_t>(r) * ld + c] *= inv_b;
+    __syncthreads();
+
+    int done = 0;
+    bool conv = false, bad = false;
+    for (int it = 0; it < a.max_iter; ++it) {
+        double r2 = gemm_fp64(X, X, Y, n, ld, 1, As, Bs);
+        r2 = block_sum(r2, scratch);
+        gemm_fp64(X, Y, Z, n, ld, 2, As, Bs);
+        __syncthreads();
+        double* tmp = X; X = Z; Z = tmp;
+        done = it + 1;
+        if (!isfinite(r2)) { bad = true; break; }
+        if (sqrt(r2) <= a.tau) { conv = true; break; }
+    }
+    if (threadIdx.x == 0) {
+        a.iters[s.col] = done;
+        atomicAdd(a.work_n3, static_cast<unsigned long long>(n) * n * n * done);
+        if (bad) atomicCAS(a.status, kOk, kErrNonfinite);
+        else if (!conv) atomicCAS(a.status, kOk, kErrNoconv);
+    }
+    const double* Xf = X;
+    auto xrow = [&](int q, int i) -> double { return Xf[static_cast<int64_t>(s.own + q) * ld + i]; };
+    finish_column(s, a.pv, a.H, a.D, a.partial, xrow, ls_smem, scratch);
+}
+
+cudaError_t launch_ns_fp64(const NsFp64Args& a, int max_nblk, cudaStream_t st) {
+    const size_t smem = sizeof(int) * (static_cast<size_t>(max_nblk) + 1);
+    k_ns_fp64<<<a.n_subs, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace smx

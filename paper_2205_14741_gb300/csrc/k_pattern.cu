@@ -1,0 +1,217 @@
+// Filter, gather + spectral bound, Gershgorin bracket and reductions.
+//
+//  a1  block filter (Frobenius norm per block; diagonal blocks kept)
+//  a3  gather T_j = H[R_j, R_j] - mu I (Fig. 2 step (i), shift of Eq. 14)
+//  a4  Gershgorin bound b_j >= spectral radius of T_j - mu I
+//  a8  deterministic FP64 sums of trace(D) and trace(D H)
+#include "smx_kernels.h"
+
+namespace smx {
+
+// One warp per stored block.
+__global__ void k_block_filter(const double* __restrict__ H, const int64_t* __restrict__ voff,
+                               const int32_t* __restrict__ row_idx, const int32_t* __restrict__ bcol,
+                               const int32_t* __restrict__ bsize, int64_t nnzb, double eps, uint8_t* __restrict__ keep,
+                               int* status) {
+    const int64_t k = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= nnzb) return;
+    const int r = row_idx[k], c = bcol[k];
+    const int sz = bsize[r] * bsize[c];
+    const double* blk = H + voff[k];
+    double s = 0.0;
+    bool finite = true;
+    for (int e = lane; e < sz; e += 32) {
+        const double v = blk[e];
+        s = fma(v, v, s);
+        finite = finite && isfinite(v);
+    }
+    s = warp_sum(s);
+    finite = __all_sync(0xffffffffu, finite);
+    if (lane == 0) {
+        keep[k] = (r == c || !(sqrt(s) < eps)) ? 1 : 0;
+        if (!finite) atomicCAS(status, kOk, kErrNonfinite);
+    }
+}
+
+cudaError_t launch_block_filter(const double* H, const int64_t* voff, const int32_t* row_idx, const int32_t* bcol,
+                                const int32_t* bsize, int64_t nnzb, double eps, uint8_t* keep, int* status,
+                                cudaStream_t st) {
+    if (nnzb == 0) return cudaSuccess;
+    const int64_t threads = nnzb * 32;
+    const int grid = static_cast<int>((threads + 255) / 256);
+    k_block_filter<<<grid, 256, 0, st>>>(H, voff, row_idx, bcol, bsize, nnzb, eps, keep, status);
+    return cudaGetLastError();
+}
+
+// One warp per block column j: column abs-sums over the filtered blocks of
+// column j (equal to row sums, H being symmetric) give the Gershgorin
+// interval of the rows of block j.
+__global__ void k_column_gershgorin(PatternView pv, const double* __restrict__ H, int n_cols, double* lohi) {
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= n_cols) return;
+    const int bj = pv.bsize[j];
+    double lo = INFINITY, hi = -INFINITY;
+    for (int q = lane; q < bj; q += 32) {
+        double s = 0.0, d = 0.0;
+        for (int64_t k = pv.fcol_ptr[j]; k < pv.fcol_ptr[j + 1]; ++k) {
+            const int r = pv.frow_idx[k];
+            const int br = pv.bsize[r];
+            const double* col = H + pv.fvoff[k] + static_cast<int64_t>(q) * br;
+            for (int p = 0; p < br; ++p) s += fabs(col[p]);
+            if (r == j) d = col[q];
+        }
+        const double rad = s - fabs(d);
+        lo = fmin(lo, d - rad);
+        hi = fmax(hi, d + rad);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+        lohi[2 * j] = lo;
+        lohi[2 * j + 1] = hi;
+    }
+}
+
+cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, const int64_t* /*row_start*/,
+                                     int n_cols, double* lohi, cudaStream_t st) {
+    const int grid = (n_cols * 32 + 255) / 256;
+    k_column_gershgorin<<<grid, 256, 0, st>>>(pv, H, n_cols, lohi);
+    return cudaGetLastError();
+}
+
+// One CTA per submatrix.  T_j is stored row-major with leading dimension
+// s.ld; it is symmetric, so block (R_j[a], R_j[c]) of H (column-major in the
+// input) is written transposed at rows of c / columns of a, which makes each
+// column of the source block a contiguous run in T_j.
+__global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict__ subs, PatternView pv,
+                                                      const double* __restrict__ H, double mu, double* __restrict__ T,
+                                                      double* __restrict__ bound) {
+    extern __shared__ int sm_int[];
+    __shared__ double warp_max_s[8];
+    const SubDesc s = subs[blockIdx.x];
+    int* rows = sm_int;               // R_j
+    int* ls = sm_int + s.nblk;        // local starts, nblk + 1 entries
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int a = tid; a < s.nblk; a += blockDim.x) {
+        rows[a] = pv.frow_idx[s.fptr + a];
+        ls[a] = pv.lstart[s.fptr + a];
+    }
+    if (tid == 0) ls[s.nblk] = s.n;
+    double* t = T + s.t_off;
+    const int64_t area = static_cast<int64_t>(s.n) * s.ld;
+    for (int64_t e = tid; e < area; e += blockDim.x) t[e] = 0.0;
+    __syncthreads();
+
+    for (int c = warp; c < s.nblk; c += 8) {
+        const int col = rows[c];
+        const int bc = ls[c + 1] - ls[c];
+        const int64_t k0 = pv.fcol_ptr[col], k1 = pv.fcol_ptr[col + 1];
+        for (int64_t kb = k0; kb < k1; kb += 32) {
+            const int64_t k = kb + lane;
+            int a = -1;
+            if (k < k1) {
+                const int r = pv.frow_idx[k];
+                int lo = 0, hi = s.nblk - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (rows[mid] < r) lo = mid + 1; else hi = mid;
+                }
+                if (rows[lo] == r) a = lo;
+            }
+            unsigned found = __ballot_sync(0xffffffffu, a >= 0);
+            while (found) {
+                const int src = __ffs(found) - 1;
+                found &= found - 1;
+                const int aa = __shfl_sync(0xffffffffu, a, src);
+                const int64_t kk = kb + src;
+                const int br = ls[aa + 1] - ls[aa];
+                const double* blk = H + pv.fvoff[kk];
+                const int sz = br * bc;
+                for (int e = lane; e < sz; e += 32) {
+                    const int q = e / br, p = e - q * br;
+                    double v = blk[e];
+                    if (aa == c && p == q) v -= mu;
+                    t[static_cast<int64_t>(ls[c] + q) * s.ld + ls[aa] + p] = v;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // b_j = max_x sum_y |T[x][y]|  (T already holds the shift)
+    double m = 0.0;
+    for (int x = warp; x < s.n; x += 8) {
+        const double* row = t + static_cast<int64_t>(x) * s.ld;
+        double acc = 0.0;
+        for (int y = lane; y < s.n; y += 32) acc += fabs(row[y]);
+        m = fmax(m, warp_sum(acc));
+    }
+    if (lane == 0) warp_max_s[warp] = m;
+    __syncthreads();
+    if (tid == 0) {
+        double g = 0.0;
+        for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
+        bound[blockIdx.x] = g > 0.0 ? g : 1.0;
+    }
+}
+
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv, const double* H,
+                                double mu, double* T, double* bound, cudaStream_t st) {
+    const size_t smem = sizeof(int) * (2 * static_cast<size_t>(max_nblk) + 1);
+    k_gather_bound<<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(1024) k_reduce(const double2* __restrict__ partial, const double* __restrict__ lohi,
+                                                 int n_cols, double* out) {
+    __shared__ double scratch[32];
+    __shared__ double mm[2][32];
+    double tr = 0.0, en = 0.0, lo = INFINITY, hi = -INFINITY;
+    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) {
+        const double2 p = partial[j];
+        tr += p.x;
+        en += p.y;
+        if (lohi) {
+            lo = fmin(lo, lohi[2 * j]);
+            hi = fmax(hi, lohi[2 * j + 1]);
+        }
+    }
+    tr = block_sum(tr, scratch);
+    en = block_sum(en, scratch);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+        mm[0][warp] = lo;
+        mm[1][warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = tr;
+        out[1] = en;
+        if (lohi) {
+            double l = INFINITY, h = -INFINITY;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                l = fmin(l, mm[0][w]);
+                h = fmax(h, mm[1][w]);
+            }
+            out[2] = l;
+            out[3] = h;
+        }
+    }
+}
+
+cudaError_t launch_reduce(const double2* partial, const double* lohi, int n_cols, double* out, cudaStream_t st) {
+    k_reduce<<<1, 1024, 0, st>>>(partial, lohi, n_cols, out);
+    return cudaGetLastError();
+}
+
+}  // namespace smx

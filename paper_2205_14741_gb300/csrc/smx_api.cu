@@ -1,0 +1,705 @@
+// C ABI of the submatrix density-matrix library (declared in include/smx.h).
+//
+// Host responsibilities: validation of the block-CSC pattern, the symbolic
+// analysis of the filtered pattern (R_j, n_j, owner offsets; Fig. 2 step
+// (i)), device memory, the TMA tensor map of the tensor-core workspace, the
+// launch sequence of one build, the mu bisection loop and the statistics.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "smx.h"
+#include "smx_kernels.h"
+
+using namespace smx;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+class DeviceGuard {
+   public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+        dev_ = dev;
+    }
+    ~DeviceGuard() {
+        if (prev_ != dev_) cudaSetDevice(prev_);
+    }
+
+   private:
+    int prev_ = 0, dev_ = 0;
+};
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct smx_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+
+    // input pattern
+    int32_t B = 0;
+    int64_t N = 0, nnzb = 0, n_values = 0;
+    std::vector<int32_t> bs, row_idx, bcol;
+    std::vector<int64_t> col_ptr, voff, row_start;
+
+    // settings
+    double eps = 0.0, mu = 0.0;
+    bool have_ne = false;
+    double n_e = 0.0, tol = 0.5;
+    int max_steps = 30;
+    int precision = SMX_FP64;
+    int fp64_final = 0;
+
+    // filtered pattern + submatrices
+    bool analysed = false, dirty = true;
+    std::vector<uint8_t> keep;
+    std::vector<int64_t> fcol_ptr, fvoff;
+    std::vector<int32_t> frow_idx, lstart, order;
+    std::vector<SubDesc> subs;
+    int max_nblk = 0, max_n = 0;
+    int64_t t_elems = 0;
+
+    // device buffers
+    DevBuf d_H, d_voff, d_row_idx, d_bcol, d_bs, d_keep;
+    DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order;
+    DevBuf d_T, d_W1, d_W2, d_ws, d_D;
+    DevBuf d_bound, d_iters, d_partial, d_lohi, d_out, d_out_br, d_status, d_counter, d_work_n3;
+    uint8_t* h_keep_pinned = nullptr;
+
+    // tensor-core workspace
+    CUtensorMap tmap;
+    int ws_ld = 0, ws_slots = 0, ws_prec = -1;
+    EncodeTiledFn encode = nullptr;
+
+    // results
+    bool built = false;
+    double last_mu = 0.0;
+    int bisection_steps = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    // counters (see smx_stats)
+    int64_t kernel_launches = 0, ns_launches = 0;
+    double ns_ms_total = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ns_events;  // pool, one pair per pending launch
+    size_t ns_pending = 0;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+static smx_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return SMX_OK;
+    if (e == cudaErrorMemoryAllocation) return SMX_ERR_OOM;
+    return SMX_ERR_CUDA;
+}
+
+#define SMX_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_status(e_);      \
+    } while (0)
+
+#define SMX_TRY(call)                          \
+    do {                                       \
+        smx_status s_ = (call);                \
+        if (s_ != SMX_OK) return s_;           \
+    } while (0)
+
+static smx_status ensure(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return SMX_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    SMX_CUDA(cudaMalloc(&b.p, bytes));
+    b.bytes = bytes;
+    return SMX_OK;
+}
+
+static void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+template <class T>
+static smx_status upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
+    SMX_TRY(ensure(b, v.size() * sizeof(T)));
+    if (!v.empty()) SMX_CUDA(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return SMX_OK;
+}
+
+template <class T>
+static T* dp(DevBuf& b) {
+    return static_cast<T*>(b.p);
+}
+
+static PatternView pattern_view(smx_ctx* c) {
+    PatternView pv;
+    pv.fcol_ptr = dp<int64_t>(c->d_fcol_ptr);
+    pv.frow_idx = dp<int32_t>(c->d_frow_idx);
+    pv.fvoff = dp<int64_t>(c->d_fvoff);
+    pv.lstart = dp<int32_t>(c->d_lstart);
+    pv.bsize = dp<int32_t>(c->d_bs);
+    return pv;
+}
+
+// Pattern checks: monotone col_ptr, strictly ascending in-range rows, diagonal
+// present, symmetric block pattern.
+static smx_status validate_pattern(int32_t B, const int32_t* bs, const int64_t* col_ptr, const int32_t* row_idx) {
+    if (col_ptr[0] != 0) return SMX_ERR_PATTERN;
+    for (int32_t j = 0; j < B; ++j) {
+        if (bs[j] < 1 || bs[j] > 64) return SMX_ERR_ARG;
+        if (col_ptr[j + 1] < col_ptr[j]) return SMX_ERR_PATTERN;
+    }
+    for (int32_t j = 0; j < B; ++j) {
+        bool diag = false;
+        for (int64_t k = col_ptr[j]; k < col_ptr[j + 1]; ++k) {
+            const int32_t r = row_idx[k];
+            if (r < 0 || r >= B) return SMX_ERR_PATTERN;
+            if (k > col_ptr[j] && row_idx[k - 1] >= r) return SMX_ERR_PATTERN;
+            if (r == j) diag = true;
+            // symmetric pattern: block (j, r) must exist, i.e. j in column r
+            const int32_t* b0 = row_idx + col_ptr[r];
+            const int32_t* b1 = row_idx + col_ptr[r + 1];
+            const int32_t* f = std::lower_bound(b0, b1, j);
+            if (f == b1 || *f != j) return SMX_ERR_PATTERN;
+        }
+        if (!diag) return SMX_ERR_PATTERN;
+    }
+    return SMX_OK;
+}
+
+static smx_status get_encoder(smx_ctx* c) {
+    if (c->encode) return SMX_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    SMX_CUDA(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return SMX_ERR_CUDA;
+    c->encode = reinterpret_cast<EncodeTiledFn>(fn);
+    return SMX_OK;
+}
+
+// Filter (a1) and symbolic analysis (a2).
+static smx_status analyse(smx_ctx* c) {
+    cudaStream_t st = c->stream;
+    SMX_CUDA(cudaMemsetAsync(c->d_status.p, 0, sizeof(int), st));
+    SMX_CUDA(launch_block_filter(dp<double>(c->d_H), dp<int64_t>(c->d_voff), dp<int32_t>(c->d_row_idx),
+                                 dp<int32_t>(c->d_bcol), dp<int32_t>(c->d_bs), c->nnzb, c->eps, dp<uint8_t>(c->d_keep),
+                                 dp<int>(c->d_status), st));
+    c->kernel_launches += 1;
+    int status = 0;
+    const bool need_flags = c->eps > 0.0 || !c->analysed;
+    if (need_flags) {
+        SMX_CUDA(cudaMemcpyAsync(c->h_keep_pinned, c->d_keep.p, c->nnzb, cudaMemcpyDeviceToHost, st));
+    }
+    SMX_CUDA(cudaMemcpyAsync(&status, c->d_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SMX_CUDA(cudaStreamSynchronize(st));
+    if (status == kErrNonfinite) return SMX_ERR_NONFINITE;
+    if (!need_flags) {
+        c->dirty = false;
+        return SMX_OK;
+    }
+    if (c->analysed && std::equal(c->keep.begin(), c->keep.end(), c->h_keep_pinned)) {
+        c->dirty = false;
+        return SMX_OK;  // same filtered pattern
+    }
+    c->keep.assign(c->h_keep_pinned, c->h_keep_pinned + c->nnzb);
+
+    const int32_t B = c->B;
+    c->fcol_ptr.assign(B + 1, 0);
+    c->frow_idx.clear();
+    c->fvoff.clear();
+    for (int32_t j = 0; j < B; ++j) {
+        for (int64_t k = c->col_ptr[j]; k < c->col_ptr[j + 1]; ++k)
+            if (c->keep[k]) {
+                c->frow_idx.push_back(c->row_idx[k]);
+                c->fvoff.push_back(c->voff[k]);
+            }
+        c->fcol_ptr[j + 1] = static_cast<int64_t>(c->frow_idx.size());
+    }
+    const int64_t nnzf = static_cast<int64_t>(c->frow_idx.size());
+    c->lstart.assign(nnzf, 0);
+    c->subs.assign(B, SubDesc{});
+    c->max_nblk = 0;
+    c->max_n = 0;
+    int64_t t_off = 0;
+    for (int32_t j = 0; j < B; ++j) {
+        SubDesc& s = c->subs[j];
+        s.col = j;
+        s.fptr = c->fcol_ptr[j];
+        s.nblk = static_cast<int32_t>(c->fcol_ptr[j + 1] - c->fcol_ptr[j]);
+        int32_t acc = 0;
+        s.own = -1;
+        for (int32_t a = 0; a < s.nblk; ++a) {
+            const int32_t r = c->frow_idx[s.fptr + a];
+            c->lstart[s.fptr + a] = acc;
+            if (r == j) s.own = acc;
+            acc += c->bs[r];
+        }
+        if (s.own < 0) return SMX_ERR_PATTERN;
+        s.n = acc;
+        s.ld = acc;
+        s.bown = c->bs[j];
+        s.t_off = t_off;
+        t_off += round_up(static_cast<int64_t>(s.n) * s.ld, 32);
+        c->max_nblk = std::max(c->max_nblk, s.nblk);
+        c->max_n = std::max(c->max_n, s.n);
+    }
+    c->t_elems = t_off;
+    c->order.resize(B);
+    for (int32_t j = 0; j < B; ++j) c->order[j] = j;
+    std::stable_sort(c->order.begin(), c->order.end(),
+                     [&](int32_t x, int32_t y) { return c->subs[x].n > c->subs[y].n; });
+
+    SMX_TRY(upload(c->d_fcol_ptr, c->fcol_ptr, st));
+    SMX_TRY(upload(c->d_frow_idx, c->frow_idx, st));
+    SMX_TRY(upload(c->d_fvoff, c->fvoff, st));
+    SMX_TRY(upload(c->d_lstart, c->lstart, st));
+    SMX_TRY(upload(c->d_subs, c->subs, st));
+    SMX_TRY(upload(c->d_order, c->order, st));
+    SMX_TRY(ensure(c->d_T, static_cast<size_t>(c->t_elems) * sizeof(double)));
+    SMX_CUDA(cudaMemsetAsync(c->d_D.p, 0, c->n_values * sizeof(double), st));
+    c->analysed = true;
+    c->dirty = false;
+    c->ws_prec = -1;  // tensor-core workspace must be re-checked
+    return SMX_OK;
+}
+
+static smx_status prepare_tc_workspace(smx_ctx* c) {
+    const int ld = static_cast<int>(round_up(c->max_n, 64));
+    const int slots = std::max(1, std::min(c->num_sms, c->B));
+    if (c->ws_prec == c->precision && c->ws_ld >= ld && c->ws_slots == slots) return SMX_OK;
+    SMX_TRY(get_encoder(c));
+    const size_t bytes = static_cast<size_t>(slots) * 6 * ld * ld * 2;
+    SMX_TRY(ensure(c->d_ws, bytes));
+    SMX_CUDA(cudaMemsetAsync(c->d_ws.p, 0, bytes, c->stream));
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(ld), static_cast<cuuint64_t>(ld), static_cast<cuuint64_t>(slots) * 6};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 2, static_cast<cuuint64_t>(ld) * ld * 2};
+    cuuint32_t box[3] = {64, 64, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    const CUtensorMapDataType dt =
+        c->precision == SMX_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    CUresult r = c->encode(&c->tmap, dt, 3, c->d_ws.p, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return SMX_ERR_CUDA;
+    c->ws_ld = ld;
+    c->ws_slots = slots;
+    c->ws_prec = c->precision;
+    return SMX_OK;
+}
+
+static double tau_for(int precision) {
+    switch (precision) {
+        case SMX_FP64: return 1e-7;
+        case SMX_FP16X3: return 2e-3;
+        default: return 5e-2;
+    }
+}
+
+// Adds the device time of the Newton-Schulz launches recorded since the last
+// call; the stream must be synchronised.
+static void accumulate_timers(smx_ctx* c) {
+    for (size_t i = 0; i < c->ns_pending; ++i) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c->ns_events[i].first, c->ns_events[i].second) == cudaSuccess)
+            c->ns_ms_total += ms;
+    }
+    c->ns_pending = 0;
+}
+
+static smx_status ns_event_pair(smx_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
+    if (c->ns_pending == c->ns_events.size()) {
+        cudaEvent_t a, b;
+        SMX_CUDA(cudaEventCreate(&a));
+        SMX_CUDA(cudaEventCreate(&b));
+        c->ns_events.emplace_back(a, b);
+    }
+    *e0 = c->ns_events[c->ns_pending].first;
+    *e1 = c->ns_events[c->ns_pending].second;
+    ++c->ns_pending;
+    return SMX_OK;
+}
+
+// One build at chemical potential mu (a3 - a8).
+static smx_status build_at(smx_ctx* c, double mu) {
+    if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
+    cudaStream_t st = c->stream;
+    const int B = c->B;
+    SMX_CUDA(cudaMemsetAsync(c->d_status.p, 0, sizeof(int), st));
+    SMX_CUDA(cudaEventRecord(c->ev0, st));
+    const PatternView pv = pattern_view(c);
+    SMX_CUDA(launch_gather_bound(dp<SubDesc>(c->d_subs), B, c->max_nblk, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
+                                 dp<double>(c->d_bound), st));
+    cudaEvent_t ns0, ns1;
+    SMX_TRY(ns_event_pair(c, &ns0, &ns1));
+    if (c->precision == SMX_FP64) {
+        SMX_TRY(ensure(c->d_W1, c->d_T.bytes));
+        SMX_TRY(ensure(c->d_W2, c->d_T.bytes));
+        NsFp64Args a;
+        a.subs = dp<SubDesc>(c->d_subs);
+        a.n_subs = B;
+        a.T = dp<double>(c->d_T);
+        a.W1 = dp<double>(c->d_W1);
+        a.W2 = dp<double>(c->d_W2);
+        a.bound = dp<double>(c->d_bound);
+        a.tau = tau_for(SMX_FP64);
+        a.max_iter = 100;
+        a.iters = dp<int32_t>(c->d_iters);
+        a.work_n3 = dp<unsigned long long>(c->d_work_n3);
+        a.status = dp<int>(c->d_status);
+        a.pv = pv;
+        a.H = dp<double>(c->d_H);
+        a.D = dp<double>(c->d_D);
+        a.partial = dp<double2>(c->d_partial);
+        SMX_CUDA(cudaEventRecord(ns0, st));
+        SMX_CUDA(launch_ns_fp64(a, c->max_nblk, st));
+        SMX_CUDA(cudaEventRecord(ns1, st));
+    } else {
+        SMX_TRY(prepare_tc_workspace(c));
+        NsTcArgs a;
+        a.subs = dp<SubDesc>(c->d_subs);
+        a.order = dp<int32_t>(c->d_order);
+        a.n_subs = B;
+        a.work_counter = dp<int>(c->d_counter);
+        a.T = dp<double>(c->d_T);
+        a.bound = dp<double>(c->d_bound);
+        a.ws = c->d_ws.p;
+        a.ld = c->ws_ld;
+        a.n_slots = c->ws_slots;
+        a.tau = static_cast<float>(tau_for(c->precision));
+        a.max_iter = 100;
+        a.iters = dp<int32_t>(c->d_iters);
+        a.work_n3 = dp<unsigned long long>(c->d_work_n3);
+        a.status = dp<int>(c->d_status);
+        a.pv = pv;
+        a.H = dp<double>(c->d_H);
+        a.D = dp<double>(c->d_D);
+        a.partial = dp<double2>(c->d_partial);
+        SMX_CUDA(cudaEventRecord(ns0, st));
+        SMX_CUDA(launch_ns_tc(a, c->precision, c->tmap, c->max_nblk, st));
+        SMX_CUDA(cudaEventRecord(ns1, st));
+    }
+    SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), nullptr, B, dp<double>(c->d_out), st));
+    SMX_CUDA(cudaEventRecord(c->ev1, st));
+    c->kernel_launches += 3;
+    c->ns_launches += 1;
+    c->built = true;
+    c->last_mu = mu;
+    return SMX_OK;
+}
+
+static smx_status read_status(smx_ctx* c) {
+    int status = 0;
+    SMX_CUDA(cudaMemcpyAsync(&status, c->d_status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    accumulate_timers(c);
+    return static_cast<smx_status>(status);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char* smx_status_string(smx_status s) {
+    switch (s) {
+        case SMX_OK: return "ok";
+        case SMX_ERR_ARG: return "invalid argument";
+        case SMX_ERR_PATTERN: return "malformed block pattern";
+        case SMX_ERR_NONFINITE: return "non-finite value";
+        case SMX_ERR_CUDA: return "CUDA error";
+        case SMX_ERR_OOM: return "device out of memory";
+        case SMX_ERR_NOCONV: return "Newton-Schulz did not converge";
+        case SMX_ERR_NOBRACKET: return "electron count outside [0, N]";
+        case SMX_ERR_TIMEOUT: return "device wait timed out";
+        case SMX_ERR_STATE: return "invalid call order";
+        case SMX_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_size, const int64_t* col_ptr,
+                      const int32_t* row_idx, const double* values, void* cuda_stream) {
+    if (!out) return SMX_ERR_ARG;
+    *out = nullptr;
+    if (n_block_cols < 1 || !block_size || !col_ptr || !row_idx || !values) return SMX_ERR_ARG;
+    SMX_TRY(validate_pattern(n_block_cols, block_size, col_ptr, row_idx));
+    smx_ctx* c = new (std::nothrow) smx_ctx();
+    if (!c) return SMX_ERR_OOM;
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->B = n_block_cols;
+    c->bs.assign(block_size, block_size + n_block_cols);
+    c->col_ptr.assign(col_ptr, col_ptr + n_block_cols + 1);
+    c->nnzb = col_ptr[n_block_cols];
+    c->row_idx.assign(row_idx, row_idx + c->nnzb);
+    c->bcol.resize(c->nnzb);
+    c->voff.assign(c->nnzb + 1, 0);
+    c->row_start.assign(n_block_cols + 1, 0);
+    for (int32_t j = 0; j < n_block_cols; ++j) c->row_start[j + 1] = c->row_start[j] + block_size[j];
+    c->N = c->row_start[n_block_cols];
+    for (int32_t j = 0; j < n_block_cols; ++j)
+        for (int64_t k = col_ptr[j]; k < col_ptr[j + 1]; ++k) {
+            c->bcol[k] = j;
+            c->voff[k + 1] = c->voff[k] + static_cast<int64_t>(block_size[row_idx[k]]) * block_size[j];
+        }
+    c->n_values = c->voff[c->nnzb];
+    smx_status s = SMX_OK;
+    auto fail = [&](smx_status e) {
+        smx_destroy(c);
+        return e;
+    };
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return fail(SMX_ERR_CUDA);
+    if ((s = upload(c->d_voff, c->voff, c->stream)) != SMX_OK) return fail(s);
+    if ((s = upload(c->d_row_idx, c->row_idx, c->stream)) != SMX_OK) return fail(s);
+    if ((s = upload(c->d_bcol, c->bcol, c->stream)) != SMX_OK) return fail(s);
+    if ((s = upload(c->d_bs, c->bs, c->stream)) != SMX_OK) return fail(s);
+    const size_t vb = static_cast<size_t>(c->n_values) * sizeof(double);
+    if ((s = ensure(c->d_H, vb)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_D, vb)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_keep, c->nnzb)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_bound, sizeof(double) * n_block_cols)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_iters, sizeof(int32_t) * n_block_cols)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_partial, sizeof(double2) * n_block_cols)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_lohi, sizeof(double) * 2 * n_block_cols)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_out, sizeof(double) * 4)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_out_br, sizeof(double) * 4)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_status, sizeof(int))) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_counter, sizeof(int))) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_work_n3, sizeof(unsigned long long))) != SMX_OK) return fail(s);
+    if (cudaMemsetAsync(c->d_work_n3.p, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
+    if (cudaMallocHost(&c->h_keep_pinned, c->nnzb > 0 ? c->nnzb : 1) != cudaSuccess) return fail(SMX_ERR_OOM);
+    if (cudaMemcpyAsync(c->d_H.p, values, vb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
+    if (cudaMemsetAsync(c->d_status.p, 0, sizeof(int), c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
+    if (cudaMemsetAsync(c->d_iters.p, 0, sizeof(int32_t) * n_block_cols, c->stream) != cudaSuccess)
+        return fail(SMX_ERR_CUDA);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
+    *out = c;
+    return SMX_OK;
+}
+
+smx_status smx_set_values(smx_ctx* c, const double* values, int32_t on_device) {
+    if (!c || !values) return SMX_ERR_ARG;
+    DeviceGuard g(c->device);
+    SMX_CUDA(cudaMemcpyAsync(c->d_H.p, values, static_cast<size_t>(c->n_values) * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    c->dirty = true;
+    c->built = false;
+    return SMX_OK;
+}
+
+smx_status smx_set_filter_threshold(smx_ctx* c, double eps) {
+    if (!c || !(eps >= 0.0) || !std::isfinite(eps)) return SMX_ERR_ARG;
+    if (eps != c->eps) {
+        c->eps = eps;
+        c->dirty = true;
+        c->analysed = false;  // force the keep flags to be read back
+    }
+    return SMX_OK;
+}
+
+smx_status smx_set_mu(smx_ctx* c, double mu) {
+    if (!c || !std::isfinite(mu)) return SMX_ERR_ARG;
+    c->mu = mu;
+    return SMX_OK;
+}
+
+smx_status smx_set_electron_count(smx_ctx* c, double n_e, int32_t max_steps, double tol) {
+    if (!c || !std::isfinite(n_e) || max_steps < 1 || max_steps > 200 || !(tol >= 0.0)) return SMX_ERR_ARG;
+    c->have_ne = true;
+    c->n_e = n_e;
+    c->max_steps = max_steps;
+    c->tol = tol;
+    return SMX_OK;
+}
+
+smx_status smx_set_precision(smx_ctx* c, smx_precision bulk, int32_t fp64_final_iters) {
+    if (!c) return SMX_ERR_ARG;
+    if (bulk != SMX_FP64 && bulk != SMX_FP16X3 && bulk != SMX_FP16 && bulk != SMX_BF16) return SMX_ERR_ARG;
+    if (fp64_final_iters < 0 || fp64_final_iters > 4) return SMX_ERR_ARG;
+    if (fp64_final_iters != 0) return SMX_ERR_UNSUPPORTED;
+    c->precision = bulk;
+    c->fp64_final = fp64_final_iters;
+    return SMX_OK;
+}
+
+smx_status smx_build_density(smx_ctx* c) {
+    if (!c) return SMX_ERR_ARG;
+    DeviceGuard g(c->device);
+    c->bisection_steps = 0;
+    return build_at(c, c->mu);
+}
+
+smx_status smx_solve_mu(smx_ctx* c) {
+    if (!c) return SMX_ERR_ARG;
+    if (!c->have_ne) return SMX_ERR_STATE;
+    DeviceGuard g(c->device);
+    if (c->n_e < 0.0 || c->n_e > static_cast<double>(c->N)) return SMX_ERR_NOBRACKET;
+    if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
+    SMX_CUDA(launch_column_gershgorin(pattern_view(c), dp<double>(c->d_H), nullptr, c->B, dp<double>(c->d_lohi),
+                                      c->stream));
+    SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), dp<double>(c->d_lohi), c->B, dp<double>(c->d_out_br), c->stream));
+    c->kernel_launches += 2;
+    double br[4];
+    SMX_CUDA(cudaMemcpyAsync(br, c->d_out_br.p, sizeof(br), cudaMemcpyDeviceToHost, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    double lo = br[2], hi = br[3];
+    c->bisection_steps = 0;
+    for (int step = 0; step < c->max_steps; ++step) {
+        const double mid = 0.5 * (lo + hi);
+        SMX_TRY(build_at(c, mid));
+        ++c->bisection_steps;
+        double tr[2];
+        SMX_CUDA(cudaMemcpyAsync(tr, c->d_out.p, sizeof(tr), cudaMemcpyDeviceToHost, c->stream));
+        const smx_status ds = read_status(c);
+        if (ds != SMX_OK) return ds;
+        if (std::fabs(tr[0] - c->n_e) <= c->tol) break;
+        if (tr[0] < c->n_e) lo = mid; else hi = mid;
+    }
+    return SMX_OK;
+}
+
+smx_status smx_get_trace(smx_ctx* c, double* trace_D, double* trace_DH, double* mu) {
+    if (!c) return SMX_ERR_ARG;
+    if (!c->built) return SMX_ERR_STATE;
+    DeviceGuard g(c->device);
+    double out[2];
+    SMX_CUDA(cudaMemcpyAsync(out, c->d_out.p, sizeof(out), cudaMemcpyDeviceToHost, c->stream));
+    const smx_status ds = read_status(c);
+    if (ds != SMX_OK) return ds;
+    if (trace_D) *trace_D = out[0];
+    if (trace_DH) *trace_DH = out[1];
+    if (mu) *mu = c->last_mu;
+    return SMX_OK;
+}
+
+smx_status smx_get_density(smx_ctx* c, double* values_out, int32_t on_device) {
+    if (!c || !values_out) return SMX_ERR_ARG;
+    if (!c->built) return SMX_ERR_STATE;
+    DeviceGuard g(c->device);
+    SMX_CUDA(cudaMemcpyAsync(values_out, c->d_D.p, static_cast<size_t>(c->n_values) * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) return read_status(c);
+    return SMX_OK;
+}
+
+smx_status smx_get_pattern(smx_ctx* c, int64_t* col_ptr, int32_t* row_idx) {
+    if (!c) return SMX_ERR_ARG;
+    if (!c->analysed) return SMX_ERR_STATE;
+    if (col_ptr) std::copy(c->fcol_ptr.begin(), c->fcol_ptr.end(), col_ptr);
+    if (row_idx) std::copy(c->frow_idx.begin(), c->frow_idx.end(), row_idx);
+    return SMX_OK;
+}
+
+smx_status smx_get_submatrix_info(smx_ctx* c, int32_t* dims, int32_t* iters, double* bounds) {
+    if (!c) return SMX_ERR_ARG;
+    if (!c->built) return SMX_ERR_STATE;
+    DeviceGuard g(c->device);
+    if (iters) SMX_CUDA(cudaMemcpyAsync(iters, c->d_iters.p, sizeof(int32_t) * c->B, cudaMemcpyDeviceToHost, c->stream));
+    if (bounds) SMX_CUDA(cudaMemcpyAsync(bounds, c->d_bound.p, sizeof(double) * c->B, cudaMemcpyDeviceToHost, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    if (dims)
+        for (int32_t j = 0; j < c->B; ++j) dims[j] = c->subs[j].n;
+    return SMX_OK;
+}
+
+smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
+    if (!c || !out) return SMX_ERR_ARG;
+    if (!c->built) return SMX_ERR_STATE;
+    DeviceGuard g(c->device);
+    std::vector<int32_t> it(c->B);
+    unsigned long long work = 0;
+    SMX_CUDA(cudaMemcpyAsync(it.data(), c->d_iters.p, sizeof(int32_t) * c->B, cudaMemcpyDeviceToHost, c->stream));
+    SMX_CUDA(cudaMemcpyAsync(&work, c->d_work_n3.p, sizeof(work), cudaMemcpyDeviceToHost, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    accumulate_timers(c);
+    std::memset(out, 0, sizeof(*out));
+    out->n_block_cols = c->B;
+    out->n = c->N;
+    out->nnzb_input = c->nnzb;
+    out->nnzb_filtered = static_cast<int64_t>(c->frow_idx.size());
+    out->dim_min = 1 << 30;
+    out->iters_min = 1 << 30;
+    double dsum = 0.0, isum = 0.0, flops = 0.0;
+    int noconv = 0;
+    for (int32_t j = 0; j < c->B; ++j) {
+        const int n = c->subs[j].n;
+        out->dim_min = std::min(out->dim_min, n);
+        out->dim_max = std::max(out->dim_max, n);
+        out->iters_min = std::min(out->iters_min, it[j]);
+        out->iters_max = std::max(out->iters_max, it[j]);
+        dsum += n;
+        isum += it[j];
+        flops += 4.0 * n * static_cast<double>(n) * n * it[j];
+        if (it[j] >= 100) ++noconv;
+    }
+    out->dim_mean = dsum / c->B;
+    out->iters_mean = isum / c->B;
+    out->n_noconv = noconv;
+    out->bisection_steps = c->bisection_steps;
+    out->flops_ns = flops;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) out->ms_last_build = ms;
+    out->mu = c->last_mu;
+    out->precision = c->precision;
+    out->fp64_final_iters = c->fp64_final;
+    out->kernel_launches = c->kernel_launches;
+    out->ns_launches = c->ns_launches;
+    out->ns_ms_total = c->ns_ms_total;
+    out->ns_work_n3 = static_cast<double>(work);
+    return SMX_OK;
+}
+
+smx_status smx_reset_counters(smx_ctx* c) {
+    if (!c) return SMX_ERR_ARG;
+    DeviceGuard g(c->device);
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    c->ns_pending = 0;
+    c->kernel_launches = 0;
+    c->ns_launches = 0;
+    c->ns_ms_total = 0.0;
+    SMX_CUDA(cudaMemsetAsync(c->d_work_n3.p, 0, sizeof(unsigned long long), c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    return SMX_OK;
+}
+
+void smx_destroy(smx_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    DevBuf* bufs[] = {&c->d_H, &c->d_voff, &c->d_row_idx, &c->d_bcol, &c->d_bs, &c->d_keep, &c->d_fcol_ptr,
+                      &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
+                      &c->d_W2, &c->d_ws, &c->d_D, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
+                      &c->d_out, &c->d_out_br, &c->d_status, &c->d_counter, &c->d_work_n3};
+    for (DevBuf* b : bufs) release(*b);
+    for (auto& pr : c->ns_events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    if (c->h_keep_pinned) cudaFreeHost(c->h_keep_pinned);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+}
+
+}  // extern "C"

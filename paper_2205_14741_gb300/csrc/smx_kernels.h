@@ -1,0 +1,79 @@
+// Host-side launchers of the library's CUDA kernels (internal interface).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "smx_device.cuh"
+
+namespace smx {
+
+// a1: per-block Frobenius norms -> keep flags (diagonal always kept), and a
+// non-finite check of the values.  keep[k] = 1 if block k survives.
+cudaError_t launch_block_filter(const double* H, const int64_t* voff, const int32_t* row_idx, const int32_t* bcol,
+                                const int32_t* bsize, int64_t nnzb, double eps, uint8_t* keep, int* status,
+                                cudaStream_t st);
+
+// Gershgorin interval of the filtered H, per block column (lohi[2j], lohi[2j+1]).
+cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, const int64_t* row_start, int n_cols,
+                                     double* lohi, cudaStream_t st);
+
+// a3 + a4: T_j = H[R_j, R_j] - mu I into the FP64 staging buffer, then the
+// Gershgorin bound b_j = max row abs-sum of T_j (>= spectral radius).
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
+                                const double* H, double mu, double* T, double* bound, cudaStream_t st);
+
+// a8: deterministic sums of the per-column partials -> out[0] = trace(D),
+// out[1] = trace(D H); also min/max of the column Gershgorin bounds into
+// out[2], out[3] when lohi != nullptr.
+cudaError_t launch_reduce(const double2* partial, const double* lohi, int n_cols, double* out, cudaStream_t st);
+
+// a5/a6 (FP64 plain form) + a7: Newton-Schulz in FP64, then scatter.
+struct NsFp64Args {
+    const SubDesc* subs;
+    int n_subs;
+    double* T;   // FP64 staging buffer (overwritten: X0 = T / b)
+    double* W1;  // FP64 work buffers laid out like T
+    double* W2;
+    const double* bound;
+    double tau;
+    int max_iter;
+    int32_t* iters;
+    unsigned long long* work_n3;  // += n_j^3 * iters_j per submatrix
+    int* status;
+    PatternView pv;
+    const double* H;
+    double* D;
+    double2* partial;
+};
+cudaError_t launch_ns_fp64(const NsFp64Args& a, int max_nblk, cudaStream_t st);
+
+// a5 (tcgen05 tensor cores) + a7.
+struct NsTcArgs {
+    const SubDesc* subs;
+    const int32_t* order;  // processing order (largest first)
+    int n_subs;
+    int* work_counter;     // zeroed by the launcher
+    const double* T;
+    const double* bound;
+    void* ws;              // 16-bit workspace: n_slots * 6 buffers of ld x ld
+    int ld;                // multiple of 64, >= every padded n_j
+    int n_slots;           // persistent CTAs
+    float tau;
+    int max_iter;
+    int32_t* iters;
+    unsigned long long* work_n3;  // += n_j^3 * iters_j per submatrix
+    int* status;
+    PatternView pv;
+    const double* H;
+    double* D;
+    double2* partial;
+};
+// precision: 1 = FP16 split hi/lo (3 products), 2 = FP16, 3 = BF16 (values of smx_precision)
+cudaError_t launch_ns_tc(const NsTcArgs& a, int precision, const CUtensorMap& tmap, int max_nblk, cudaStream_t st);
+
+// Dynamic shared memory the tcgen05 kernel needs for a precision.
+size_t ns_tc_smem_bytes(int precision);
+
+}  // namespace smx

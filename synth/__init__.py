@@ -11,6 +11,7 @@ from .water import (  # noqa: F401
     WORKLOADS,
     make_workload,
     make_lattice_system,
+    make_mixed_block_system,
     make_slab_system,
     md_trajectory,
     keyed_normals,

@@ -256,6 +256,50 @@ def md_trajectory(n_mol: int, b: int, r_c: float, ell: float, seed: int, n_snap:
         yield sysm
 
 
+def make_mixed_block_system(block_sizes, r_c: float, ell: float, seed: int, spacing: float = 3.1,
+                            jitter: float = 0.3, sigma: float = 0.1) -> BlockCSC:
+    """Lattice system whose molecules have different block sizes (small systems only).
+
+    Molecule i has ``block_sizes[i]`` orbitals; its on-site energies split into
+    the two bands as for uniform blocks; off-diagonal blocks are
+    ``b_i x b_j`` with the same keyed entries and decay.
+    """
+    sizes = np.asarray(block_sizes, dtype=np.int64)
+    n_mol = sizes.shape[0]
+    rng = np.random.default_rng(seed)
+    pos, box = lattice_positions(n_mol, spacing, jitter, rng)
+    diag = []
+    for b in sizes:
+        diag.append(_diag_blocks(1, int(b), rng)[0])
+    if np.isfinite(r_c):
+        pi, pj, d = _pairs_within(pos, box, r_c)
+    else:
+        pi, pj = np.triu_indices(n_mol, k=1)
+        dv = pos[pi] - pos[pj]
+        dv -= box * np.round(dv / box)
+        d = np.sqrt(np.einsum("ak,ak->a", dv, dv))
+    bmax = int(sizes.max())
+    g = keyed_normals(seed, pi, pj, bmax * bmax).reshape(-1, bmax, bmax)
+    entries = {(i, i): diag[i] for i in range(n_mol)}
+    for t in range(pi.shape[0]):
+        i, j = int(pi[t]), int(pj[t])
+        m = g[t, : sizes[i], : sizes[j]] * sigma * np.exp(-d[t] / ell)
+        entries[(i, j)] = m
+        entries[(j, i)] = m.T
+    col_ptr = np.zeros(n_mol + 1, dtype=np.int64)
+    rows, vals = [], []
+    for j in range(n_mol):
+        rj = sorted(i for (i, jj) in entries if jj == j)
+        for i in rj:
+            rows.append(i)
+            vals.append(entries[(i, j)].T.reshape(-1))
+        col_ptr[j + 1] = len(rows)
+    sysm = BlockCSC(block_size=sizes.astype(np.int32), col_ptr=col_ptr, row_idx=np.asarray(rows, dtype=np.int32),
+                    values=np.concatenate(vals), positions=pos, box=box, n_occ=int(np.sum(sizes // 2)))
+    sysm.meta = dict(kind="mixed", n_mol=n_mol, r_c=r_c, ell=ell, seed=seed)
+    return sysm
+
+
 # Named workloads. Each entry gives the generator arguments and the method
 # settings (filter threshold eps, fixed mu or electron count).
 WORKLOADS = {
