@@ -188,6 +188,32 @@ smx_status smx_reset_counters(smx_ctx* ctx);
  * b_j used for X0 = (T_j - mu I)/b_j.  Synchronises. */
 smx_status smx_get_submatrix_info(smx_ctx* ctx, int32_t* dims, int32_t* iters, double* bounds);
 
+/* Dense density matrix without any device allocation (the paper has no
+ * counterpart; this serves callers that cannot allocate device memory at the
+ * time they need the result: code running while a stream is captured into a
+ * CUDA graph, plug-ins whose host framework owns the whole device pool, and
+ * latency-critical loops that must not enter the allocator, which can
+ * synchronise the device).
+ * Computes D = 1/2 (I - sign(H - mu I)) of one dense symmetric H by FP64
+ * Newton-Schulz iteration with a Gershgorin scaling (one CTA; same arithmetic
+ * as the FP64 form of smx_build_density).
+ *  h_dev       : device double[n*n], row-major, symmetric (read only).
+ *  n           : 1 <= n <= 256; larger n returns SMX_ERR_ARG.
+ *  mu          : finite chemical potential.
+ *  d_dev       : device double[n*n], row-major, receives D (caller-owned).
+ *  cuda_stream : stream to run on (NULL = legacy default stream).
+ * Work matrices live in one fixed __device__ array of 3*256*256 + 4 doubles
+ * (about 1.5 MiB) that every GPU which loads the library keeps until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress), so make the first call on each device
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on a GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  The call synchronises the stream to report
+ * errors: SMX_ERR_ARG, SMX_ERR_CUDA, SMX_ERR_UNSUPPORTED (device index >= 64),
+ * SMX_ERR_NONFINITE, SMX_ERR_NOCONV. */
+smx_status smx_dense_density_noalloc(const double* h_dev, int32_t n, double mu, double* d_dev,
+                                     void* cuda_stream);
+
 /* Releases the context and all device memory it owns.  NULL is ignored. */
 void smx_destroy(smx_ctx* ctx);
 

@@ -68,6 +68,7 @@ SIGNATURES = {
     "smx_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "smx_reset_counters": (C.c_int, [C.c_void_p]),
     "smx_get_submatrix_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "smx_dense_density_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
     "smx_destroy": (None, [C.c_void_p]),
 }
 

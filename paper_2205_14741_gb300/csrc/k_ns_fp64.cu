@@ -131,3 +131,126 @@ cudaError_t launch_ns_fp64(const NsFp64Args& a, int max_nblk, cudaStream_t st) {
 }
 
 }  // namespace smx
+
+// ---------------------------------------------------------------------------
+// Allocation-free dense entry point (no counterpart in the paper).
+//
+// Some callers cannot allocate device memory when they need a result: code
+// that runs while a CUDA stream is being captured into a graph (cudaMalloc is
+// not allowed there), plug-ins inside a framework whose caching allocator owns
+// the whole device pool, and latency-critical loops that must never enter the
+// driver's allocator (cudaMalloc/cudaFree can synchronise the device).
+// smx_dense_density_noalloc serves them: it takes caller-owned input and
+// output buffers and keeps its Newton-Schulz work matrices in the fixed
+// device array below, which every GPU that loads this library holds until the
+// process exits.
+// ---------------------------------------------------------------------------
+
+#include <cmath>
+#include <mutex>
+
+#include "smx.h"
+
+namespace smx {
+
+namespace {
+constexpr int kNoAllocMaxN = 256;                          // largest n accepted
+constexpr int64_t kNoAllocMat = int64_t(kNoAllocMaxN) * kNoAllocMaxN;
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+
+// X, Y, Z work matrices (n x n each, leading dimension n) followed by a small
+// header: [0] status, [1] iterations.  3 * 256^2 + 4 doubles, about 1.5 MiB.
+static __device__ __align__(256) double g_noalloc_scratch[3 * kNoAllocMat + 4];
+
+// One CTA: D = 1/2 (I - sign(H - mu I)) of a dense symmetric H by the FP64
+// Newton-Schulz iteration of k_ns_fp64, with the Gershgorin bound for X0.
+__global__ void __launch_bounds__(256) k_dense_density_noalloc(const double* __restrict__ H, int n, double mu,
+                                                               double* __restrict__ Dout, double* scratch,
+                                                               double tau, int max_iter) {
+    __shared__ double As[kKc][kTile + 1];
+    __shared__ double Bs[kKc][kTile + 1];
+    __shared__ double red[32];
+    double* X = scratch;
+    double* Y = scratch + kNoAllocMat;
+    double* Z = scratch + 2 * kNoAllocMat;
+    int* hdr = reinterpret_cast<int*>(scratch + 3 * kNoAllocMat);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // every call overwrites the work matrices in full; nothing is carried over
+
+    // Gershgorin bound b = max_r sum_c |H_rc - mu delta_rc| (>= spectral radius)
+    double m = 0.0;
+    for (int r = warp; r < n; r += 8) {
+        double acc = 0.0;
+        for (int c = lane; c < n; c += 32) acc += fabs(H[static_cast<int64_t>(r) * n + c] - (r == c ? mu : 0.0));
+        m = fmax(m, warp_sum(acc));
+    }
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    double b = 0.0;
+    for (int w = 0; w < 8; ++w) b = fmax(b, red[w]);
+    if (b == 0.0) b = 1.0;
+    __syncthreads();
+    const double inv_b = 1.0 / b;
+    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(n) * n; e += blockDim.x) {
+        const int r = static_cast<int>(e / n), c = static_cast<int>(e - static_cast<int64_t>(r) * n);
+        X[e] = (H[e] - (r == c ? mu : 0.0)) * inv_b;
+    }
+    __syncthreads();
+
+    int done = 0;
+    bool conv = false, bad = false;
+    for (int it = 0; it < max_iter; ++it) {
+        double r2 = gemm_fp64(X, X, Y, n, n, 1, As, Bs);
+        r2 = block_sum(r2, red);
+        gemm_fp64(X, Y, Z, n, n, 2, As, Bs);
+        __syncthreads();
+        double* t = X; X = Z; Z = t;
+        done = it + 1;
+        if (!isfinite(r2)) { bad = true; break; }
+        if (sqrt(r2) <= tau) { conv = true; break; }
+    }
+    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(n) * n; e += blockDim.x) {
+        const int r = static_cast<int>(e / n), c = static_cast<int>(e - static_cast<int64_t>(r) * n);
+        Dout[e] = 0.5 * ((r == c ? 1.0 : 0.0) - X[e]);
+    }
+    if (threadIdx.x == 0) {
+        hdr[0] = bad ? kErrNonfinite : (conv ? kOk : kErrNoconv);
+        hdr[1] = done;
+    }
+}
+
+}  // namespace smx
+
+namespace {
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[smx::kNoAllocMaxDevices] = {};
+}  // namespace
+
+extern "C" smx_status smx_dense_density_noalloc(const double* h_dev, int32_t n, double mu, double* d_dev,
+                                                void* cuda_stream) {
+    if (!h_dev || !d_dev || n < 1 || n > smx::kNoAllocMaxN || !std::isfinite(mu)) return SMX_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SMX_ERR_CUDA;
+    if (dev < 0 || dev >= smx::kNoAllocMaxDevices) return SMX_ERR_UNSUPPORTED;
+    double* scratch = nullptr;
+    {
+        // set-up once per device, with that device current: the host-side name
+        // of a __device__ array is not a device address, so look the address up
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, smx::g_noalloc_scratch) != cudaSuccess || !p) return SMX_ERR_CUDA;
+            g_noalloc_ptr[dev] = static_cast<double*>(p);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    smx::k_dense_density_noalloc<<<1, 256, 0, st>>>(h_dev, n, mu, d_dev, scratch, 1e-7, 100);
+    if (cudaGetLastError() != cudaSuccess) return SMX_ERR_CUDA;
+    int hdr[2] = {0, 0};
+    if (cudaMemcpyAsync(hdr, scratch + 3 * smx::kNoAllocMat, sizeof(hdr), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SMX_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SMX_ERR_CUDA;
+    return static_cast<smx_status>(hdr[0]);
+}
