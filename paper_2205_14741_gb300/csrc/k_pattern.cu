@@ -12,19 +12,21 @@ namespace smx {
 __global__ void k_block_filter(const double* __restrict__ H, const int64_t* __restrict__ voff,
                                const int32_t* __restrict__ row_idx, const int32_t* __restrict__ bcol,
                                const int32_t* __restrict__ bsize, int64_t nnzb, double eps, uint8_t* __restrict__ keep,
-                               int* status) {
+                               int* status, float* __restrict__ H32) {
     const int64_t k = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= nnzb) return;
     const int r = row_idx[k], c = bcol[k];
     const int sz = bsize[r] * bsize[c];
     const double* blk = H + voff[k];
+    float* blk32 = H32 + voff[k];
     double s = 0.0;
     bool finite = true;
     for (int e = lane; e < sz; e += 32) {
         const double v = blk[e];
         s = fma(v, v, s);
         finite = finite && isfinite(v);
+        blk32[e] = __double2float_rn(v);
     }
     s = warp_sum(s);
     finite = __all_sync(0xffffffffu, finite);
@@ -36,11 +38,11 @@ __global__ void k_block_filter(const double* __restrict__ H, const int64_t* __re
 
 cudaError_t launch_block_filter(const double* H, const int64_t* voff, const int32_t* row_idx, const int32_t* bcol,
                                 const int32_t* bsize, int64_t nnzb, double eps, uint8_t* keep, int* status,
-                                cudaStream_t st) {
+                                float* H32, cudaStream_t st) {
     if (nnzb == 0) return cudaSuccess;
     const int64_t threads = nnzb * 32;
     const int grid = static_cast<int>((threads + 255) / 256);
-    k_block_filter<<<grid, 256, 0, st>>>(H, voff, row_idx, bcol, bsize, nnzb, eps, keep, status);
+    k_block_filter<<<grid, 256, 0, st>>>(H, voff, row_idx, bcol, bsize, nnzb, eps, keep, status, H32);
     return cudaGetLastError();
 }
 
@@ -88,11 +90,13 @@ cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, con
 // s.ld; it is symmetric, so block (R_j[a], R_j[c]) of H (column-major in the
 // input) is written transposed at rows of c / columns of a, which makes each
 // column of the source block a contiguous run in T_j.
+template <class R>
 __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict__ subs, PatternView pv,
-                                                      const double* __restrict__ H, double mu, double* __restrict__ T,
+                                                      const R* __restrict__ H, double mu_d, R* __restrict__ T,
                                                       double* __restrict__ bound) {
     extern __shared__ int sm_int[];
-    __shared__ double warp_max_s[8];
+    __shared__ R warp_max_s[8];
+    const R mu = static_cast<R>(mu_d);
     const SubDesc s = subs[blockIdx.x];
     int* rows = sm_int;               // R_j
     int* ls = sm_int + s.nblk;        // local starts, nblk + 1 entries
@@ -102,9 +106,9 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
         ls[a] = pv.lstart[s.fptr + a];
     }
     if (tid == 0) ls[s.nblk] = s.n;
-    double* t = T + s.t_off;
+    R* t = T + s.t_off;
     const int64_t area = static_cast<int64_t>(s.n) * s.ld;
-    for (int64_t e = tid; e < area; e += blockDim.x) t[e] = 0.0;
+    for (int64_t e = tid; e < area; e += blockDim.x) t[e] = R(0);
     __syncthreads();
 
     for (int c = warp; c < s.nblk; c += 8) {
@@ -130,11 +134,11 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
                 const int aa = __shfl_sync(0xffffffffu, a, src);
                 const int64_t kk = kb + src;
                 const int br = ls[aa + 1] - ls[aa];
-                const double* blk = H + pv.fvoff[kk];
+                const R* blk = H + pv.fvoff[kk];
                 const int sz = br * bc;
                 for (int e = lane; e < sz; e += 32) {
                     const int q = e / br, p = e - q * br;
-                    double v = blk[e];
+                    R v = blk[e];
                     if (aa == c && p == q) v -= mu;
                     t[static_cast<int64_t>(ls[c] + q) * s.ld + ls[aa] + p] = v;
                 }
@@ -143,19 +147,23 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
     }
     __syncthreads();
 
-    // b_j = max_x sum_y |T[x][y]|  (T already holds the shift)
-    double m = 0.0;
+    // b_j = max_x sum_y |T[x][y]|  (T already holds the shift).  In FP32 the
+    // sum carries a relative error below n * 2^-24, covered by the 1e-5 margin.
+    R m = R(0);
     for (int x = warp; x < s.n; x += 8) {
-        const double* row = t + static_cast<int64_t>(x) * s.ld;
-        double acc = 0.0;
+        const R* row = t + static_cast<int64_t>(x) * s.ld;
+        R acc = R(0);
         for (int y = lane; y < s.n; y += 32) acc += fabs(row[y]);
-        m = fmax(m, warp_sum(acc));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        m = m > acc ? m : acc;
     }
     if (lane == 0) warp_max_s[warp] = m;
     __syncthreads();
     if (tid == 0) {
         double g = 0.0;
-        for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
+        for (int w = 0; w < 8; ++w) g = fmax(g, static_cast<double>(warp_max_s[w]));
+        if (sizeof(R) == 4) g *= 1.0 + 1e-5;
         bound[blockIdx.x] = g > 0.0 ? g : 1.0;
     }
 }
@@ -163,7 +171,14 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
 cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv, const double* H,
                                 double mu, double* T, double* bound, cudaStream_t st) {
     const size_t smem = sizeof(int) * (2 * static_cast<size_t>(max_nblk) + 1);
-    k_gather_bound<<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound);
+    k_gather_bound<double><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
+                                    const float* H32, double mu, float* T32, double* bound, cudaStream_t st) {
+    const size_t smem = sizeof(int) * (2 * static_cast<size_t>(max_nblk) + 1);
+    k_gather_bound<float><<<n_subs, 256, smem, st>>>(subs, pv, H32, mu, T32, bound);
     return cudaGetLastError();
 }
 

@@ -75,7 +75,7 @@ struct smx_ctx {
     int64_t t_elems = 0;
 
     // device buffers
-    DevBuf d_H, d_voff, d_row_idx, d_bcol, d_bs, d_keep;
+    DevBuf d_H, d_H32, d_voff, d_row_idx, d_bcol, d_bs, d_keep;
     DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order;
     DevBuf d_T, d_W1, d_W2, d_ws, d_D;
     DevBuf d_bound, d_iters, d_partial, d_lohi, d_out, d_out_br, d_status, d_counter, d_work_n3;
@@ -202,7 +202,7 @@ static smx_status analyse(smx_ctx* c) {
     SMX_CUDA(cudaMemsetAsync(c->d_status.p, 0, sizeof(int), st));
     SMX_CUDA(launch_block_filter(dp<double>(c->d_H), dp<int64_t>(c->d_voff), dp<int32_t>(c->d_row_idx),
                                  dp<int32_t>(c->d_bcol), dp<int32_t>(c->d_bs), c->nnzb, c->eps, dp<uint8_t>(c->d_keep),
-                                 dp<int>(c->d_status), st));
+                                 dp<int>(c->d_status), dp<float>(c->d_H32), st));
     c->kernel_launches += 1;
     int status = 0;
     const bool need_flags = c->eps > 0.0 || !c->analysed;
@@ -346,8 +346,13 @@ static smx_status build_at(smx_ctx* c, double mu) {
     SMX_CUDA(cudaMemsetAsync(c->d_status.p, 0, sizeof(int), st));
     SMX_CUDA(cudaEventRecord(c->ev0, st));
     const PatternView pv = pattern_view(c);
-    SMX_CUDA(launch_gather_bound(dp<SubDesc>(c->d_subs), B, c->max_nblk, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
-                                 dp<double>(c->d_bound), st));
+    if (c->precision == SMX_FP64) {
+        SMX_CUDA(launch_gather_bound(dp<SubDesc>(c->d_subs), B, c->max_nblk, pv, dp<double>(c->d_H), mu,
+                                     dp<double>(c->d_T), dp<double>(c->d_bound), st));
+    } else {
+        SMX_CUDA(launch_gather_bound_f32(dp<SubDesc>(c->d_subs), B, c->max_nblk, pv, dp<float>(c->d_H32), mu,
+                                         dp<float>(c->d_T), dp<double>(c->d_bound), st));
+    }
     cudaEvent_t ns0, ns1;
     SMX_TRY(ns_event_pair(c, &ns0, &ns1));
     if (c->precision == SMX_FP64) {
@@ -379,7 +384,7 @@ static smx_status build_at(smx_ctx* c, double mu) {
         a.order = dp<int32_t>(c->d_order);
         a.n_subs = B;
         a.work_counter = dp<int>(c->d_counter);
-        a.T = dp<double>(c->d_T);
+        a.T = dp<float>(c->d_T);
         a.bound = dp<double>(c->d_bound);
         a.ws = c->d_ws.p;
         a.ld = c->ws_ld;
@@ -476,6 +481,7 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if ((s = upload(c->d_bs, c->bs, c->stream)) != SMX_OK) return fail(s);
     const size_t vb = static_cast<size_t>(c->n_values) * sizeof(double);
     if ((s = ensure(c->d_H, vb)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_H32, vb / 2)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_D, vb)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_keep, c->nnzb)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_bound, sizeof(double) * n_block_cols)) != SMX_OK) return fail(s);
@@ -687,7 +693,7 @@ void smx_destroy(smx_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    DevBuf* bufs[] = {&c->d_H, &c->d_voff, &c->d_row_idx, &c->d_bcol, &c->d_bs, &c->d_keep, &c->d_fcol_ptr,
+    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_bcol, &c->d_bs, &c->d_keep, &c->d_fcol_ptr,
                       &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
                       &c->d_W2, &c->d_ws, &c->d_D, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
                       &c->d_out, &c->d_out_br, &c->d_status, &c->d_counter, &c->d_work_n3};

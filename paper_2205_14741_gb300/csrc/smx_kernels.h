@@ -9,11 +9,12 @@
 
 namespace smx {
 
-// a1: per-block Frobenius norms -> keep flags (diagonal always kept), and a
-// non-finite check of the values.  keep[k] = 1 if block k survives.
+// a1: per-block Frobenius norms -> keep flags (diagonal always kept), a
+// non-finite check of the values, and an FP32 copy of H (same layout) for the
+// tensor-core path.  keep[k] = 1 if block k survives.
 cudaError_t launch_block_filter(const double* H, const int64_t* voff, const int32_t* row_idx, const int32_t* bcol,
                                 const int32_t* bsize, int64_t nnzb, double eps, uint8_t* keep, int* status,
-                                cudaStream_t st);
+                                float* H32, cudaStream_t st);
 
 // Gershgorin interval of the filtered H, per block column (lohi[2j], lohi[2j+1]).
 cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, const int64_t* row_start, int n_cols,
@@ -23,6 +24,10 @@ cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, con
 // Gershgorin bound b_j = max row abs-sum of T_j (>= spectral radius).
 cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
                                 const double* H, double mu, double* T, double* bound, cudaStream_t st);
+// The same in FP32 (tensor-core path): T32 from the FP32 copy of H; the bound
+// is enlarged by 1e-5 relative to cover FP32 summation.
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
+                                    const float* H32, double mu, float* T32, double* bound, cudaStream_t st);
 
 // a8: deterministic sums of the per-column partials -> out[0] = trace(D),
 // out[1] = trace(D H); also min/max of the column Gershgorin bounds into
@@ -55,7 +60,7 @@ struct NsTcArgs {
     const int32_t* order;  // processing order (largest first)
     int n_subs;
     int* work_counter;     // zeroed by the launcher
-    const double* T;
+    const float* T;        // FP32 staging of T_j - mu I (leading dimension SubDesc::ld)
     const double* bound;
     void* ws;              // 16-bit workspace: n_slots * 6 buffers of ld x ld
     int ld;                // multiple of 64, >= every padded n_j

@@ -90,9 +90,13 @@ def test_multi_tile_submatrices(prec):
     h = O.to_dense(s.block_size, s.col_ptr, s.row_idx, s.values)
     err = np.max(np.abs(O.to_dense(s.block_size, s.col_ptr, s.row_idx, d) - O.dense_density(h, 0.1)))
     assert err <= TOL_D[prec]
-    # the bound is the Gershgorin bound of T_j - mu I
+    # the bound is the Gershgorin bound of T_j - mu I (FP32 sums, enlarged by 1e-5, in the tensor-core form)
     lo, hi = O.gershgorin_bounds(h - 0.1 * np.eye(h.shape[0]))
-    assert np.allclose(bounds, max(abs(lo), abs(hi)), rtol=1e-12)
+    g = max(abs(lo), abs(hi))
+    if prec == "fp64":
+        assert np.allclose(bounds, g, rtol=1e-12)
+    else:
+        assert np.all(bounds >= g) and np.all(bounds <= g * (1 + 2e-5))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp16x3"])
