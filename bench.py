@@ -99,6 +99,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _profiled_traffic(workload: str, precision: str):
+    """DRAM bytes per launch of the Newton-Schulz kernel from the committed ncu
+    record, or None when that record was taken on a different kernel source."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "ns_tc_traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, rec["kernel_source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except Exception:
+        return None, "no ncu record"
+    if sha != rec["sha256_16"] or workload != rec["workload"] or precision != "fp16x3":
+        return None, "kernel changed since the ncu capture"
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"], "ncu dram__bytes_read+write of one launch"
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -240,6 +257,7 @@ def run_ours(args):
                 + (" / 3 (three fp16 products per multiply-add in the split form)" if passes == 3 else ""),
         "ns_share_of_step": (st["ns_ms_total"] / ms) if ms > 0 else None,
     }
+    roofline["traffic"], roofline["traffic_note"] = _profiled_traffic(args.workload, args.precision)
     gpu_launches = int(st["kernel_launches"])
 
     # -- e2e through the C ABI with host buffers -------------------------------

@@ -7,9 +7,7 @@
 // paper's low-precision tensor-unit work (Section 3): FP16 (or BF16) operands,
 // FP32 accumulation in tensor memory.  In the split form each operand is held
 // as hi + lo (two FP16 numbers, about 22 significant bits) and every product
-// is hi*hi + hi*lo + lo*hi; hi*hi and the two cross products go to separate
-// TMEM accumulators (the tensor core rounds its FP32 accumulator after every
-// instruction, so the small cross terms are kept away from the large sums).
+// is hi*hi + hi*lo + lo*hi, all accumulated in one FP32 TMEM accumulator.
 //
 // Operand layout: both factors of C = A B are read from row-major matrices in
 // the CTA's workspace slot.  A (rows of the left factor) is loaded K-major,
@@ -20,8 +18,9 @@
 //
 // CTA layout (384 threads):
 //   warp 0       TMA producer (one lane): 64-wide K chunks of A (128 rows)
-//                and B (N <= 128 split / 256 single-pass columns) into a ring
-//                of shared-memory stages (128-byte swizzle)
+//                and B (all columns of the tile, N <= 256) into a ring of
+//                shared-memory stages (128-byte swizzle); a row tile spans
+//                the whole padded width when n <= 256, so A is read once
 //   warp 1       MMA issuer (one lane): tcgen05.mma M=128, K=16 into one of
 //                two TMEM accumulator buffers of 256 FP32 columns
 //   warps 2..3   help with the per-submatrix prologue and scatter
@@ -42,9 +41,9 @@ constexpr uint32_t kABytes = 128 * 128;  // 128 rows x 64 K x 2 B
 template <int PREC>
 struct TcCfg {
     static constexpr int kNb = (PREC == 1) ? 2 : 1;        // operand buffers per matrix (hi[, lo])
-    static constexpr int kNmax = (PREC == 1) ? 128 : 256;  // columns per N tile
+    static constexpr int kNmax = 256;                      // columns per N tile
     static constexpr uint32_t kBBytes = kNmax * 128;       // 64 K rows x kNmax columns x 2 B
-    static constexpr int kStages = (PREC == 1) ? 3 : 4;    // smem ring depth
+    static constexpr int kStages = (PREC == 1) ? 2 : 4;    // smem ring depth
     static constexpr uint32_t kStage = kNb * (kABytes + kBBytes);
     static constexpr int kFmt = (PREC == 3) ? 1 : 0;       // 0 = FP16, 1 = BF16
     static constexpr size_t kDynSmem = 1024 + static_cast<size_t>(kStages) * kStage;
@@ -85,17 +84,42 @@ __device__ __forceinline__ float from16(uint16_t h) {
     else return __half2float(__ushort_as_half(h));
 }
 
-// (a, b) -> hi pair and lo pair with a = hi.x + lo.x, b = hi.y + lo.y
+// x rounded to the significand width of the 16-bit format (11 bits for FP16,
+// 8 for BF16), half away from zero, as an FP32 number: exactly representable
+// in the 16-bit format except in the FP16 subnormal range (|x| < 2^-14), where
+// the conversion below rounds it once more (absolute error < 2^-25).
+template <int PREC>
+__device__ __forceinline__ float round16(float x) {
+    constexpr uint32_t half_ulp = (PREC == 3) ? 0x8000u : 0x1000u;
+    constexpr uint32_t mask = (PREC == 3) ? 0xFFFF0000u : 0xFFFFE000u;
+    return __uint_as_float((__float_as_uint(x) + half_ulp) & mask);
+}
+
+// (a, b) -> hi pair and lo pair with a ~ hi.x + lo.x, b ~ hi.y + lo.y
 template <int PREC, int NB>
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hw, uint32_t& lw) {
-    hw = pack2<PREC>(a, b);
     if constexpr (NB == 2) {
-        const float2 h = unpack2<PREC>(hw);
-        lw = pack2<PREC>(a - h.x, b - h.y);
+        const float ha = round16<PREC>(a), hb = round16<PREC>(b);
+        hw = pack2<PREC>(ha, hb);
+        lw = pack2<PREC>(a - ha, b - hb);
     } else {
+        hw = pack2<PREC>(a, b);
         lw = 0;
     }
 }
+
+// two TMEM loads (32 columns each), one wait
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%"
+        "20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ bool mbar_wait_plain(uint64_t* bar, uint32_t parity, uint32_t limit) {
     for (uint32_t i = 0; i < limit; ++i)
@@ -187,8 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                         const uint32_t abuf = m_tile & 1, around = m_tile >> 1;
                         if (around > 0 && !mbar_wait(&tempty[abuf], (around - 1) & 1, &abort_s, a.status)) break;
                         tc_fence_after();
-                        const uint32_t d = tmem_base + abuf * 256;  // main accumulator
-                        const uint32_t dx = d + 128;                // cross terms (split form)
+                        const uint32_t d = tmem_base + abuf * 256;
                         const uint32_t idesc = idesc_f16(128, nn, C::kFmt) | idesc_b_mn;
                         bool ok = true;
                         for (int kc = 0; kc < kchunks; ++kc) {
@@ -205,8 +228,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                 const uint64_t ah = sdesc_sw128(a_hi + kk * 32), bh = sdesc_mn_sw128(b_hi + kk * 2048);
                                 tc_mma_f16(d, ah, bh, idesc, acc);
                                 if constexpr (NB == 2) {
-                                    tc_mma_f16(dx, ah, sdesc_mn_sw128(b_lo + kk * 2048), idesc, acc);
-                                    tc_mma_f16(dx, sdesc_sw128(a_lo + kk * 32), bh, idesc, 1u);
+                                    tc_mma_f16(d, ah, sdesc_mn_sw128(b_lo + kk * 2048), idesc, 1u);
+                                    tc_mma_f16(d, sdesc_sw128(a_lo + kk * 32), bh, idesc, 1u);
                                 }
                             }
                             tc_commit(&empty_bar[stage]);
@@ -236,36 +259,48 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     uint16_t* out_hi = ws + static_cast<int64_t>(zo) * buf + static_cast<int64_t>(row) * a.ld;
                     uint16_t* out_lo = out_hi + buf;
                     for (int c0 = 32 * half; c0 < nn; c0 += 64) {
-                        float v[32];
-                        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + abuf * 256 + c0;
-                        tmem_ld32(taddr, v);
-                        if constexpr (NB == 2) {
-                            float vx[32];
-                            tmem_ld32(taddr + 128, vx);
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) v[i] += vx[i];
-                        }
+                        uint32_t raw[32];
+                        tmem_ld32_issue(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + abuf * 256 + c0, raw);
+                        tmem_wait_ld();
                         if (row < kpad) {
                             const int col0 = NT * nt + c0;
-                            uint32_t hw[16], lw[16];
+                            const bool interior = row < n && col0 + 32 <= n;
+                            const int i0 = row - col0;  // position of the diagonal in this chunk, if 0 <= i0 < 32
+                            float y[32];
+                            if (interior) {
+                                if (mode == 1) {
+                                    float sq = 0.0f, dv = 0.0f;
 #pragma unroll
-                            for (int i = 0; i < 32; i += 2) {
-                                float y[2];
+                                    for (int i = 0; i < 32; ++i) {
+                                        const float v = __uint_as_float(raw[i]);
+                                        sq = fmaf(v, v, sq);
+                                        y[i] = -0.5f * v;
+                                        if (i == i0) { y[i] += 1.5f; dv = v; }
+                                    }
+                                    // sum (v - delta)^2 = sum v^2 - 2 v_diag + 1 when the diagonal is here
+                                    r2 += (i0 >= 0 && i0 < 32) ? sq - 2.0f * dv + 1.0f : sq;
+                                } else {
 #pragma unroll
-                                for (int u = 0; u < 2; ++u) {
-                                    const int col = col0 + i + u;
-                                    const bool valid = row < n && col < n;
+                                    for (int i = 0; i < 32; ++i) y[i] = __uint_as_float(raw[i]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 32; ++i) {
+                                    const float v = __uint_as_float(raw[i]);
+                                    const bool valid = row < n && col0 + i < n;
                                     if (mode == 1) {
-                                        const float dl = (row == col) ? 1.0f : 0.0f;
-                                        const float e = v[i + u] - dl;
-                                        y[u] = valid ? fmaf(-0.5f, v[i + u], 1.5f * dl) : 0.0f;
+                                        const float dl = (i == i0) ? 1.0f : 0.0f;
+                                        const float e = v - dl;
+                                        y[i] = valid ? fmaf(-0.5f, v, 1.5f * dl) : 0.0f;
                                         r2 = valid ? fmaf(e, e, r2) : r2;
                                     } else {
-                                        y[u] = valid ? v[i + u] : 0.0f;
+                                        y[i] = valid ? v : 0.0f;
                                     }
                                 }
-                                split2<PREC, NB>(y[0], y[1], hw[i >> 1], lw[i >> 1]);
                             }
+                            uint32_t hw[16], lw[16];
+#pragma unroll
+                            for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
                             uint4* dh = reinterpret_cast<uint4*>(out_hi + col0);
 #pragma unroll
                             for (int u = 0; u < 4; ++u) dh[u] = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
