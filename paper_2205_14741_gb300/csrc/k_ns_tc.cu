@@ -9,6 +9,10 @@
 // as hi + lo (two FP16 numbers, about 22 significant bits) and every product
 // is hi*hi + hi*lo + lo*hi, all accumulated in one FP32 TMEM accumulator.
 //
+// Submatrices are padded to multiples of 32 for the MMA (K steps and N);
+// TMA moves 64-wide boxes, whose columns beyond the padded size are never
+// multiplied.
+//
 // Operand layout: both factors of C = A B are read from row-major matrices in
 // the CTA's workspace slot.  A (rows of the left factor) is loaded K-major,
 // B in its true orientation (MN-major: rows of B are K), so the kernel forms
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     // C = A * B over K in [0, kpad), written to buffer zo (rows and columns < kpad).
     // mode 1: zo = 3/2 I - 1/2 A A, residual ||A A - I||_F^2 accumulated; mode 2: zo = A B.
     auto gemm = [&](int kpad, int n, int mode, int za, int zb, int zo) {
-        const int mtiles = (kpad + 127) / 128, ntiles = (kpad + NT - 1) / NT, kchunks = kpad / 64;
+        const int mtiles = (kpad + 127) / 128, ntiles = (kpad + NT - 1) / NT, kchunks = (kpad + 63) / 64;
         if (warp == 0) {
             if (lane == 0) {
                 for (int mt = 0; mt < mtiles && !*abortp; ++mt)
@@ -188,13 +192,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                             const uint32_t round = p_it / S;
                             if (round > 0 && !mbar_wait(&empty_bar[stage], (round - 1) & 1, &abort_s, a.status)) break;
                             uint8_t* st = smem + stage * C::kStage;
-                            mbar_arrive_expect_tx(&full_bar[stage], NB * (kABytes + static_cast<uint32_t>(nn) * 128));
+                            const int nboxes = (nn + 63) / 64;
+                            mbar_arrive_expect_tx(&full_bar[stage], NB * (kABytes + static_cast<uint32_t>(nboxes) * 8192));
                             for (int b = 0; b < NB; ++b) {
                                 uint8_t* sa = st + b * kABytes;
                                 tma_load_3d(sa, &tmap, kc * 64, 128 * mt, za + b, &full_bar[stage]);
                                 tma_load_3d(sa + 8192, &tmap, kc * 64, 128 * mt + 64, za + b, &full_bar[stage]);
                                 uint8_t* sb = st + NB * kABytes + b * C::kBBytes;
-                                for (int h = 0; h < nn / 64; ++h)
+                                for (int h = 0; h < nboxes; ++h)
                                     tma_load_3d(sb + h * 8192, &tmap, NT * nt + 64 * h, kc * 64, zb + b, &full_bar[stage]);
                             }
                             ++p_it;
@@ -222,8 +227,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                             const uint32_t base = smem_u32(smem + stage * C::kStage);
                             const uint32_t a_hi = base, a_lo = base + kABytes;
                             const uint32_t b_hi = base + NB * kABytes, b_lo = b_hi + C::kBBytes;
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
+                            // K steps beyond kpad (the tail of the last 64-wide chunk) are not issued
+                            const int ksteps = min(4, (kpad - 64 * kc) / 16);
+                            for (int kk = 0; kk < ksteps; ++kk) {
                                 const uint32_t acc = (kc | kk) ? 1u : 0u;
                                 const uint64_t ah = sdesc_sw128(a_hi + kk * 32), bh = sdesc_mn_sw128(b_hi + kk * 2048);
                                 tc_mma_f16(d, ah, bh, idesc, acc);
@@ -331,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         if (job >= a.n_subs || *abortp) break;
         const int j = a.order[job];
         const SubDesc s = a.subs[j];
-        const int kpad = (s.n + 63) & ~63;
+        const int kpad = (s.n + 31) & ~31;  // MMA extent; TMA moves 64-wide boxes
         const int zx0 = slot_z + 0, zx1 = slot_z + 2, zy = slot_z + 4;
 
         // prologue: X0 = (T_j - mu I) / b_j in FP32, zero-padded to kpad x kpad, split hi/lo
@@ -343,17 +349,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             const int per_row = kpad / 8;
             for (int e = tid; e < kpad * per_row; e += blockDim.x) {
                 const int r = e / per_row, c0 = (e - r * per_row) * 8;
+                // rows of T are 16-byte aligned (ld is a multiple of 4) and zero in [n, ld)
+                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+                if (r < s.n) {
+                    const float4* src = reinterpret_cast<const float4*>(t + static_cast<int64_t>(r) * s.ld + c0);
+                    if (c0 + 4 <= s.ld) v0 = src[0];
+                    if (c0 + 8 <= s.ld) v1 = src[1];
+                }
+                const float x[8] = {v0.x * inv_b, v0.y * inv_b, v0.z * inv_b, v0.w * inv_b,
+                                    v1.x * inv_b, v1.y * inv_b, v1.z * inv_b, v1.w * inv_b};
                 uint32_t hw[4], lw[4];
 #pragma unroll
-                for (int i = 0; i < 8; i += 2) {
-                    float x[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int c = c0 + i + u;
-                        x[u] = (r < s.n && c < s.n) ? t[static_cast<int64_t>(r) * s.ld + c] * inv_b : 0.0f;
-                    }
-                    split2<PREC, NB>(x[0], x[1], hw[i >> 1], lw[i >> 1]);
-                }
+                for (int i = 0; i < 8; i += 2) split2<PREC, NB>(x[i], x[i + 1], hw[i >> 1], lw[i >> 1]);
                 *reinterpret_cast<uint4*>(xh + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                 if constexpr (NB == 2)
                     *reinterpret_cast<uint4*>(xl + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -385,18 +392,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             if (bad_s) atomicCAS(a.status, kOk, kErrNonfinite);
             else if (!conv_s) atomicCAS(a.status, kOk, kErrNoconv);
         }
-        const uint16_t* fh = ws + static_cast<int64_t>(cur ? zx1 : zx0) * buf;
-        const uint16_t* fl = fh + buf;
-        const int ld = a.ld;
-        // column own + q of X (the iterate is symmetric up to rounding; the
-        // method keeps the columns)
-        auto xcol = [&](int q, int i) -> double {
-            const int64_t o = static_cast<int64_t>(i) * ld + s.own + q;
-            float x = from16<PREC>(fh[o]);
-            if constexpr (NB == 2) x += from16<PREC>(fl[o]);
-            return static_cast<double>(x);
-        };
-        finish_column(s, a.pv, a.H, a.D, a.partial, xcol, ls_smem, scratch);
+        // save columns own .. own + b_j of the final X (the method keeps the
+        // columns; the iterate is symmetric only up to rounding) for the scatter
+        {
+            const uint16_t* fh = ws + static_cast<int64_t>(cur ? zx1 : zx0) * buf;
+            const uint16_t* fl = fh + buf;
+            float* dst = a.xown + s.x_off;
+            for (int e = tid; e < s.n * s.bown; e += blockDim.x) {
+                const int q = e / s.n, i = e - q * s.n;
+                const int64_t o = static_cast<int64_t>(i) * a.ld + s.own + q;
+                float x = from16<PREC>(fh[o]);
+                if constexpr (NB == 2) x += from16<PREC>(fl[o]);
+                dst[e] = x;
+            }
+        }
         __syncthreads();
     }
 

@@ -4,6 +4,7 @@
 //  a3  gather T_j = H[R_j, R_j] - mu I (Fig. 2 step (i), shift of Eq. 14)
 //  a4  Gershgorin bound b_j >= spectral radius of T_j - mu I
 //  a8  deterministic FP64 sums of trace(D) and trace(D H)
+#include "smx_finish.cuh"
 #include "smx_kernels.h"
 
 namespace smx {
@@ -179,6 +180,25 @@ cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nbl
                                     const float* H32, double mu, float* T32, double* bound, cudaStream_t st) {
     const size_t smem = sizeof(int) * (2 * static_cast<size_t>(max_nblk) + 1);
     k_gather_bound<float><<<n_subs, 256, smem, st>>>(subs, pv, H32, mu, T32, bound);
+    return cudaGetLastError();
+}
+
+// One CTA per submatrix: scatter of the saved owner columns (Fig. 2 step (iii)).
+__global__ void __launch_bounds__(256) k_scatter_owner(const SubDesc* __restrict__ subs, PatternView pv,
+                                                       const float* __restrict__ xown, const double* __restrict__ H,
+                                                       double* __restrict__ D, double2* __restrict__ partial) {
+    extern __shared__ int ls_smem[];
+    __shared__ double scratch[32];
+    const SubDesc s = subs[blockIdx.x];
+    const float* x = xown + s.x_off;
+    auto xcol = [&](int q, int i) -> double { return static_cast<double>(x[static_cast<int64_t>(q) * s.n + i]); };
+    finish_column(s, pv, H, D, partial, xcol, ls_smem, scratch);
+}
+
+cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
+                                 const float* xown, const double* H, double* D, double2* partial, cudaStream_t st) {
+    const size_t smem = sizeof(int) * (static_cast<size_t>(max_nblk) + 1);
+    k_scatter_owner<<<n_subs, 256, smem, st>>>(subs, pv, xown, H, D, partial);
     return cudaGetLastError();
 }
 

@@ -72,12 +72,12 @@ struct smx_ctx {
     std::vector<int32_t> frow_idx, lstart, order;
     std::vector<SubDesc> subs;
     int max_nblk = 0, max_n = 0;
-    int64_t t_elems = 0;
+    int64_t t_elems = 0, x_elems = 0;
 
     // device buffers
     DevBuf d_H, d_H32, d_voff, d_row_idx, d_bcol, d_bs, d_keep;
     DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order;
-    DevBuf d_T, d_W1, d_W2, d_ws, d_D;
+    DevBuf d_T, d_W1, d_W2, d_ws, d_D, d_xown;
     DevBuf d_bound, d_iters, d_partial, d_lohi, d_out, d_out_br, d_status, d_counter, d_work_n3;
     uint8_t* h_keep_pinned = nullptr;
 
@@ -239,7 +239,7 @@ static smx_status analyse(smx_ctx* c) {
     c->subs.assign(B, SubDesc{});
     c->max_nblk = 0;
     c->max_n = 0;
-    int64_t t_off = 0;
+    int64_t t_off = 0, x_off = 0;
     for (int32_t j = 0; j < B; ++j) {
         SubDesc& s = c->subs[j];
         s.col = j;
@@ -255,14 +255,17 @@ static smx_status analyse(smx_ctx* c) {
         }
         if (s.own < 0) return SMX_ERR_PATTERN;
         s.n = acc;
-        s.ld = acc;
+        s.ld = static_cast<int32_t>(round_up(acc, 4));  // 16-byte aligned FP32 rows
         s.bown = c->bs[j];
         s.t_off = t_off;
+        s.x_off = x_off;
         t_off += round_up(static_cast<int64_t>(s.n) * s.ld, 32);
+        x_off += round_up(static_cast<int64_t>(s.n) * s.bown, 32);
         c->max_nblk = std::max(c->max_nblk, s.nblk);
         c->max_n = std::max(c->max_n, s.n);
     }
     c->t_elems = t_off;
+    c->x_elems = x_off;
     c->order.resize(B);
     for (int32_t j = 0; j < B; ++j) c->order[j] = j;
     std::stable_sort(c->order.begin(), c->order.end(),
@@ -398,9 +401,14 @@ static smx_status build_at(smx_ctx* c, double mu) {
         a.H = dp<double>(c->d_H);
         a.D = dp<double>(c->d_D);
         a.partial = dp<double2>(c->d_partial);
+        SMX_TRY(ensure(c->d_xown, static_cast<size_t>(c->x_elems) * sizeof(float)));
+        a.xown = dp<float>(c->d_xown);
         SMX_CUDA(cudaEventRecord(ns0, st));
         SMX_CUDA(launch_ns_tc(a, c->precision, c->tmap, c->max_nblk, st));
         SMX_CUDA(cudaEventRecord(ns1, st));
+        SMX_CUDA(launch_scatter_owner(dp<SubDesc>(c->d_subs), B, c->max_nblk, pv, dp<float>(c->d_xown),
+                                      dp<double>(c->d_H), dp<double>(c->d_D), dp<double2>(c->d_partial), st));
+        c->kernel_launches += 1;
     }
     SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), nullptr, B, dp<double>(c->d_out), st));
     SMX_CUDA(cudaEventRecord(c->ev1, st));
@@ -695,7 +703,7 @@ void smx_destroy(smx_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_bcol, &c->d_bs, &c->d_keep, &c->d_fcol_ptr,
                       &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
-                      &c->d_W2, &c->d_ws, &c->d_D, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
+                      &c->d_W2, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
                       &c->d_out, &c->d_out_br, &c->d_status, &c->d_counter, &c->d_work_n3};
     for (DevBuf* b : bufs) release(*b);
     for (auto& pr : c->ns_events) {

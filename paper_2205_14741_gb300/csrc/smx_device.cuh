@@ -23,7 +23,8 @@ struct SubDesc {
     int32_t bown;   // block size of j
     int32_t nblk;   // |R_j|
     int64_t fptr;   // first filtered block of column j (R_j = frow_idx[fptr .. fptr + nblk))
-    int64_t t_off;  // offset of T_j (doubles) in the FP64 staging buffer
+    int64_t t_off;  // offset of T_j (elements) in the staging buffer
+    int64_t x_off;  // offset of the saved owner columns (n x bown, column by column)
 };
 
 // Filtered pattern and value addressing shared by gather and scatter.

@@ -64,7 +64,7 @@ struct NsTcArgs {
     const double* bound;
     void* ws;              // 16-bit workspace: n_slots * 6 buffers of ld x ld
     int ld;                // multiple of 64, >= every padded n_j
-    int n_slots;           // persistent CTAs
+    int n_slots;           // persistent CTAs (one per SM)
     float tau;
     int max_iter;
     int32_t* iters;
@@ -74,9 +74,15 @@ struct NsTcArgs {
     const double* H;
     double* D;
     double2* partial;
+    float* xown;           // receives columns own .. own + bown of each final X
 };
 // precision: 1 = FP16 split hi/lo (3 products), 2 = FP16, 3 = BF16 (values of smx_precision)
 cudaError_t launch_ns_tc(const NsTcArgs& a, int precision, const CUtensorMap& tmap, int max_nblk, cudaStream_t st);
+
+// a7 + a8 for the tensor-core path: D[R_j, j] = 1/2 (E_j - X[:, own]) from the
+// saved owner columns, with the per-column trace / energy partials (FP64).
+cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
+                                 const float* xown, const double* H, double* D, double2* partial, cudaStream_t st);
 
 // Dynamic shared memory the tcgen05 kernel needs for a precision.
 size_t ns_tc_smem_bytes(int precision);
