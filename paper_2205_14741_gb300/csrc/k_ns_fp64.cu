@@ -23,9 +23,9 @@ constexpr int kKc = 16;
 
 // C = A B (n x n, row-major, leading dimension ld).  mode 1 writes
 // 3/2 I - 1/2 A B and returns this thread's share of ||A B - I||_F^2;
-// mode 2 writes A B.
+// mode 2 writes oscale * A B.
 __device__ double gemm_fp64(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C, int n,
-                            int ld, int mode, double (*As)[kTile + 1], double (*Bs)[kTile + 1]) {
+                            int ld, int mode, double (*As)[kTile + 1], double (*Bs)[kTile + 1], double oscale = 1.0) {
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     double r2 = 0.0;
     for (int r0 = 0; r0 < n; r0 += kTile) {
@@ -75,7 +75,7 @@ __device__ double gemm_fp64(const double* __restrict__ A, const double* __restri
                         C[static_cast<int64_t>(row) * ld + col] = 1.5 * dlt - 0.5 * v;
                         r2 += (v - dlt) * (v - dlt);
                     } else {
-                        C[static_cast<int64_t>(row) * ld + col] = v;
+                        C[static_cast<int64_t>(row) * ld + col] = oscale * v;
                     }
                 }
             }
@@ -104,14 +104,44 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
     int done = 0;
     bool conv = false, bad = false;
     for (int it = 0; it < a.max_iter; ++it) {
-        double r2 = gemm_fp64(X, X, Y, n, ld, 1, As, Bs);
-        r2 = block_sum(r2, scratch);
-        gemm_fp64(X, Y, Z, n, ld, 2, As, Bs);
+        double r2 = 1.0, oscale = 1.0;
+        if (it == 0) {
+            // a-posteriori scaling (as in the tensor-core kernel): with Y = X0^2,
+            // rho(X0)^2 <= s^2 = max_r sum_c |Y_rc|; continue from X0' = (1.2/s) X0
+            gemm_fp64(X, X, Y, n, ld, 2, As, Bs);
+            __syncthreads();
+            double rmax = 0.0;
+            for (int r = threadIdx.x / 32; r < n; r += 8) {
+                double acc = 0.0;
+                for (int c = threadIdx.x & 31; c < n; c += 32) acc += fabs(Y[static_cast<int64_t>(r) * ld + c]);
+                rmax = fmax(rmax, warp_sum(acc));
+            }
+            if ((threadIdx.x & 31) == 0) scratch[threadIdx.x / 32] = rmax;
+            __syncthreads();
+            double smax = 0.0;
+            for (int w = 0; w < 8; ++w) smax = fmax(smax, scratch[w]);
+            smax = sqrt(smax);
+            __syncthreads();
+            const double scale = smax > 0.0 ? 1.2 / smax : 1.0;
+            const double sc2 = scale * scale;
+            for (int r = threadIdx.x / 32; r < n; r += 8)
+                for (int c = threadIdx.x & 31; c < n; c += 32) {
+                    double& y = Y[static_cast<int64_t>(r) * ld + c];
+                    y = (r == c ? 1.5 : 0.0) - 0.5 * sc2 * y;
+                }
+            if (threadIdx.x == 0) a.bound[blockIdx.x] = a.bound[blockIdx.x] * smax / 1.2;
+            __syncthreads();
+            oscale = scale;
+        } else {
+            r2 = gemm_fp64(X, X, Y, n, ld, 1, As, Bs);
+            r2 = block_sum(r2, scratch);
+        }
+        gemm_fp64(X, Y, Z, n, ld, 2, As, Bs, oscale);
         __syncthreads();
         double* tmp = X; X = Z; Z = tmp;
         done = it + 1;
         if (!isfinite(r2)) { bad = true; break; }
-        if (sqrt(r2) <= a.tau) { conv = true; break; }
+        if (it > 0 && sqrt(r2) <= a.tau) { conv = true; break; }
     }
     if (threadIdx.x == 0) {
         a.iters[s.col] = done;

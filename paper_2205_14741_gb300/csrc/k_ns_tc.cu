@@ -179,8 +179,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     const uint32_t idesc_b_mn = 1u << 16;  // B operand MN-major
 
     // C = A * B over K in [0, kpad), written to buffer zo (rows and columns < kpad).
-    // mode 1: zo = 3/2 I - 1/2 A A, residual ||A A - I||_F^2 accumulated; mode 2: zo = A B.
-    auto gemm = [&](int kpad, int n, int mode, int za, int zb, int zo) {
+    // mode 1: zo = 3/2 I - 1/2 A A, residual ||A A - I||_F^2 accumulated;
+    // mode 2: zo = oscale * A B.
+    auto gemm = [&](int kpad, int n, int mode, int za, int zb, int zo, float oscale) {
         const int mtiles = (kpad + 127) / 128, ntiles = (kpad + NT - 1) / NT, kchunks = (kpad + 63) / 64;
         if (warp == 0) {
             if (lane == 0) {
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                     r2 += (i0 >= 0 && i0 < 32) ? sq - 2.0f * dv + 1.0f : sq;
                                 } else {
 #pragma unroll
-                                    for (int i = 0; i < 32; ++i) y[i] = __uint_as_float(raw[i]);
+                                    for (int i = 0; i < 32; ++i) y[i] = oscale * __uint_as_float(raw[i]);
                                 }
                             } else {
 #pragma unroll
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                         y[i] = valid ? fmaf(-0.5f, v, 1.5f * dl) : 0.0f;
                                         r2 = valid ? fmaf(e, e, r2) : r2;
                                     } else {
-                                        y[i] = valid ? v : 0.0f;
+                                        y[i] = valid ? oscale * v : 0.0f;
                                     }
                                 }
                             }
@@ -373,14 +374,78 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         int cur = 0, done = 0;
         for (int it = 0; it < a.max_iter; ++it) {
             const int zx = cur ? zx1 : zx0, zn = cur ? zx0 : zx1;
-            gemm(kpad, s.n, 1, zx, zx, zy);  // Y = 3/2 I - 1/2 X^2
-            if (tid == 0) {
-                double r2 = 0.0;
-                for (int w = 0; w < kEpiWarps; ++w) r2 += resid_s[w];
-                if (!isfinite(r2)) bad_s = 1;
-                else if (sqrt(r2) <= a.tau) conv_s = 1;
+            float oscale = 1.0f;
+            if (it == 0) {
+                // A-posteriori scaling.  Z = X0^2; every eigenvalue of X0 satisfies
+                // |lambda|^2 <= max_r sum_c |Z_rc| =: s^2 (Gershgorin on Z), so
+                // X0' = (c/s) X0 has all |lambda| <= c = 1.2 < sqrt(3) and the
+                // iteration from X0' is guaranteed to converge.  The step is then
+                // X1 = X0' (3/2 I - 1/2 X0'^2) = (c/s) X0 (3/2 I - 1/2 (c/s)^2 Z).
+                gemm(kpad, s.n, 2, zx, zx, zy, 1.0f);  // Z = X0^2
+                float rmax = 0.0f;
+                const uint16_t* zh = ws + static_cast<int64_t>(zy) * buf;
+                const uint16_t* zl = zh + buf;
+                for (int r = warp; r < s.n; r += kThreads / 32) {
+                    float acc = 0.0f;
+                    for (int c = lane; c < s.n; c += 32) {
+                        float z = from16<PREC>(zh[static_cast<int64_t>(r) * a.ld + c]);
+                        if constexpr (NB == 2) z += from16<PREC>(zl[static_cast<int64_t>(r) * a.ld + c]);
+                        acc += fabsf(z);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    rmax = fmaxf(rmax, acc);
+                }
+                if (lane == 0) resid_s[warp < kEpiWarps ? warp : 0] = 0.0f;
+                __syncthreads();
+                if (lane == 0) atomicMax(reinterpret_cast<int*>(&resid_s[0]), __float_as_int(rmax));  // rmax >= 0
+                __syncthreads();
+                const float smax = sqrtf(resid_s[0] * (1.0f + 1e-5f));  // margin for FP32 summation
+                const float scale = smax > 0.0f ? 1.2f / smax : 1.0f;
+                const float sc2 = scale * scale;
+                // Y' = 3/2 I - 1/2 scale^2 Z, in place
+                uint16_t* yh = ws + static_cast<int64_t>(zy) * buf;
+                uint16_t* yl = yh + buf;
+                const int per_row = kpad / 8;
+                for (int e = tid; e < kpad * per_row; e += blockDim.x) {
+                    const int r = e / per_row, c0 = (e - r * per_row) * 8;
+                    const int64_t o = static_cast<int64_t>(r) * a.ld + c0;
+                    const uint4 hv = *reinterpret_cast<const uint4*>(yh + o);
+                    uint4 lv = make_uint4(0, 0, 0, 0);
+                    if constexpr (NB == 2) lv = *reinterpret_cast<const uint4*>(yl + o);
+                    const uint32_t hin[4] = {hv.x, hv.y, hv.z, hv.w}, lin[4] = {lv.x, lv.y, lv.z, lv.w};
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float2 z = unpack2<PREC>(hin[i]);
+                        if constexpr (NB == 2) {
+                            const float2 zl2 = unpack2<PREC>(lin[i]);
+                            z.x += zl2.x;
+                            z.y += zl2.y;
+                        }
+                        const int c = c0 + 2 * i;
+                        const bool v0 = r < s.n && c < s.n, v1 = r < s.n && c + 1 < s.n;
+                        const float y0 = v0 ? fmaf(-0.5f * sc2, z.x, r == c ? 1.5f : 0.0f) : 0.0f;
+                        const float y1 = v1 ? fmaf(-0.5f * sc2, z.y, r == c + 1 ? 1.5f : 0.0f) : 0.0f;
+                        split2<PREC, NB>(y0, y1, hw[i], lw[i]);
+                    }
+                    *reinterpret_cast<uint4*>(yh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    if constexpr (NB == 2) *reinterpret_cast<uint4*>(yl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+                fence_proxy_async_global();
+                if (tid == 0) a.bound[j] = a.bound[j] * static_cast<double>(smax) / 1.2;  // effective scaling of X0'
+                __syncthreads();
+                oscale = scale;
+            } else {
+                gemm(kpad, s.n, 1, zx, zx, zy, 1.0f);  // Y = 3/2 I - 1/2 X^2
+                if (tid == 0) {
+                    double r2 = 0.0;
+                    for (int w = 0; w < kEpiWarps; ++w) r2 += resid_s[w];
+                    if (!isfinite(r2)) bad_s = 1;
+                    else if (sqrt(r2) <= a.tau) conv_s = 1;
+                }
             }
-            gemm(kpad, s.n, 2, zx, zy, zn);  // X' = X Y
+            gemm(kpad, s.n, 2, zx, zy, zn, oscale);  // X' = X Y
             cur ^= 1;
             done = it + 1;
             if (conv_s || bad_s || *abortp) break;

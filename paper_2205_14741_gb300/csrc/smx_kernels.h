@@ -41,7 +41,7 @@ struct NsFp64Args {
     double* T;   // FP64 staging buffer (overwritten: X0 = T / b)
     double* W1;  // FP64 work buffers laid out like T
     double* W2;
-    const double* bound;
+    double* bound;  // in: initial bound b_j; out: effective bound after the a-posteriori rescale
     double tau;
     int max_iter;
     int32_t* iters;
@@ -61,7 +61,7 @@ struct NsTcArgs {
     int n_subs;
     int* work_counter;     // zeroed by the launcher
     const float* T;        // FP32 staging of T_j - mu I (leading dimension SubDesc::ld)
-    const double* bound;
+    double* bound;         // in: initial bound b_j (X0 = T_j / b_j); out: effective bound after rescaling
     void* ws;              // 16-bit workspace: n_slots * 6 buffers of ld x ld
     int ld;                // multiple of 64, >= every padded n_j
     int n_slots;           // persistent CTAs (one per SM)
