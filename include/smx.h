@@ -180,6 +180,74 @@ smx_status smx_get_pattern(smx_ctx* ctx, int64_t* col_ptr, int32_t* row_idx);
 /* Statistics of the last build (see smx_stats).  Synchronises. */
 smx_status smx_get_stats(smx_ctx* ctx, smx_stats* out);
 
+/* ---------------------------------------------------------------------------
+ * Learned spectral bound (the paper's Section 4: a network trained on data the
+ * simulation itself produces, consulted during the run).
+ *
+ * Per submatrix A = T_j - mu I the model maps nine features (all over the
+ * Gershgorin bound G = max_r sum_c |A_rc|, except f6 and f8):
+ *   f0 ||A||_F/sqrt(n)  f1 max|A_rr|  f2 mean|A_rr|  f3 std(A_rr)  f4 max_r R_r
+ *   f5 mean_r R_r  f6 n/256  f7 mean A_rr  f8 previous-step ratio
+ * (R_r = sum_{c != r} |A_rc|; f8 = sqrt(max_r sum_c |(A^2)_rc|)/G of the same
+ * block column at the build before the last smx_set_values, 0 before any)
+ * through
+ * 9 -> 64 -> 64 -> 2 (tanh hidden layers) to predictions of rho/G and delta/G
+ * (rho = max |lambda(A)|, delta = min |lambda(A)|).  When enabled, a build
+ * starts Newton-Schulz from X0 = A / b with b = rho_hat (1.05) / 1.2; the first
+ * product Z = X0^2 gives the guaranteed bound s >= rho(X0) (s^2 =
+ * max_r (|Z| w)_r / w_r, the smallest over w = 1 and two power steps of |Z|
+ * from it: a Collatz-Wielandt bound on rho(Z)) and the prediction is kept
+ * only if s <= 1.6 (the iteration converges for rho(X0) < sqrt 3), otherwise
+ * X0 is rescaled by 1.2/s as without the model (counted in n_bound_fallback).
+ * Parameters: SMX_BOUND_MODEL_PARAMS floats, layout W1 (64 x 9, row-major),
+ * b1 (64), W2 (64 x 64), b2 (64), W3 (2 x 64), b3 (2).  Inference uses the
+ * parameters rounded to FP16; training keeps FP32 master weights (Adam,
+ * beta1 0.9, beta2 0.999, eps 1e-8) and minimises 1/(2m) sum (y - t)^2.
+ * ------------------------------------------------------------------------- */
+#define SMX_BOUND_MODEL_FEATURES 9
+#define SMX_BOUND_MODEL_PARAMS 4930
+
+/* Initialises the parameters (uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from a
+ * counter-based generator seeded by seed, zero biases) and clears the Adam
+ * state and the collected samples. */
+smx_status smx_bound_model_init(smx_ctx* ctx, uint64_t seed);
+
+/* Copies count (= SMX_BOUND_MODEL_PARAMS) parameters from / to host memory.
+ * Setting parameters clears the Adam state.  Errors: SMX_ERR_ARG. */
+smx_status smx_bound_model_set_params(smx_ctx* ctx, const float* params, int32_t count);
+smx_status smx_bound_model_get_params(smx_ctx* ctx, float* params, int32_t count);
+
+/* Appends one training sample per submatrix of the current H at the fixed mu
+ * of smx_set_mu: the features and Lanczos labels (lanczos_steps 8..64 steps on
+ * A for rho and on A^2 for delta).  Synchronises. */
+smx_status smx_bound_model_collect(smx_ctx* ctx, int32_t lanczos_steps);
+
+/* Trains on the collected samples: epochs passes of contiguous mini-batches of
+ * batch samples, Adam with learning rate lr; final_loss (may be NULL) receives
+ * the loss of the last mini-batch.  Synchronises. */
+smx_status smx_bound_model_train(smx_ctx* ctx, int32_t epochs, int32_t batch, float lr, double* final_loss);
+
+/* steps full-batch Adam steps on caller data (host x[m*9], t[m*2]); grad (host,
+ * SMX_BOUND_MODEL_PARAMS floats, may be NULL) receives the gradient at the
+ * parameters before the first step, loss (may be NULL) the loss there.
+ * steps = 0 only evaluates loss and gradient.  Synchronises. */
+smx_status smx_bound_model_fit(smx_ctx* ctx, const float* x, const float* t, int32_t m, int32_t steps, float lr,
+                               float* grad, double* loss);
+
+/* For the current H at the fixed mu: host arrays features[B*9], pred[B*2] and
+ * Lanczos labels[B*2] (any may be NULL; labels cost lanczos_steps steps).
+ * Synchronises. */
+smx_status smx_bound_model_predict(smx_ctx* ctx, float* features, float* pred, float* labels, int32_t lanczos_steps);
+
+/* Enables (1) or disables (0) the model in builds; weights_path, if not NULL,
+ * loads parameters saved by smx_bound_model_save.  Errors: SMX_ERR_ARG (bad
+ * file), SMX_ERR_STATE (enabling a model that was never initialised). */
+smx_status smx_set_bound_model(smx_ctx* ctx, int32_t enable, const char* weights_path);
+
+/* Writes the parameters to a binary file: 8-byte magic "SMXBNDM1", int32
+ * count, count floats, uint64 checksum (FNV-1a of the float bytes). */
+smx_status smx_bound_model_save(smx_ctx* ctx, const char* path);
+
 /* Zeroes the accumulated counters of smx_stats.  Synchronises the stream. */
 smx_status smx_reset_counters(smx_ctx* ctx);
 

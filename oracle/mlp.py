@@ -14,8 +14,9 @@ Definitions shared with the GPU path (both sides implement them separately):
     f0 = ||A||_F / sqrt(n)        f1 = max_r |A_rr|       f2 = mean_r |A_rr|
     f3 = std_r(A_rr)              f4 = max_r R_r          f5 = mean_r R_r
     f6 = n / 256                  f7 = mean_r A_rr        f8 = previous-step ratio
-  where f8 is sqrt(max_r sum_c |(A^2)_rc|) / G of the same block column at
-  the previous snapshot (0 when there is none).
+  where f8 is square_bound_ratio(A) of the same block column at the previous
+  snapshot (0 when there is none).  power_bound_ratio is the tighter bound the
+  Newton-Schulz start is checked against when the model is on.
 * Labels: rho / G and delta / G with rho = max |lambda(A)|, delta = min |lambda(A)|.
 * Network: h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = W3 h2 + b3,
   widths F -> 64 -> 64 -> 2; loss L = 1/(2m) sum_i sum_k (y_ik - t_ik)^2.
@@ -121,6 +122,24 @@ def features(a: np.ndarray, prev_ratio: float = 0.0) -> np.ndarray:
 def square_bound_ratio(a: np.ndarray) -> float:
     """sqrt(max_r sum_c |(A^2)_rc|) / G: a guaranteed bound on rho / G from A^2."""
     return float(np.sqrt(gershgorin_radius(a @ a)) / gershgorin_radius(a))
+
+
+def power_bound_ratio(a: np.ndarray, steps: int = 2) -> float:
+    """Guaranteed bound on rho(A) / G from Z = A^2 (Collatz-Wielandt).
+
+    For every positive vector w, rho(Z) <= rho(|Z|) <= max_r (|Z| w)_r / w_r.
+    The bound is the smallest of these over w = 1 (the row sums: the
+    Gershgorin bound of Z) and ``steps`` power steps of |Z| from it; its
+    square root over G bounds rho(A) / G.
+    """
+    z = np.abs(a @ a)
+    w = np.ones(a.shape[0])
+    best = np.inf
+    for _ in range(steps + 1):
+        zw = z @ w
+        best = min(best, float(np.max(zw / w)))
+        w = np.maximum(zw / np.max(zw), 1e-300)  # stays positive where a row of Z is zero
+    return float(np.sqrt(best) / gershgorin_radius(a))
 
 
 def labels(a: np.ndarray) -> np.ndarray:

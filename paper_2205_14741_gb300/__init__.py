@@ -15,7 +15,8 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import BF16, FP16, FP16X3, FP64, PRECISIONS, SmxError, Stats, check  # noqa: F401
+from ._lib import (BF16, BOUND_MODEL_FEATURES, BOUND_MODEL_PARAMS, FP16, FP16X3, FP64, PRECISIONS,  # noqa: F401
+                   SmxError, Stats, check)
 
 
 def _ptr(a):
@@ -150,3 +151,54 @@ class SubmatrixDensity:
         check(self._lib.smx_get_submatrix_info(self._ctx, _ptr(dims), _ptr(iters), _ptr(bounds)),
               "smx_get_submatrix_info")
         return dims, iters, bounds
+
+    # learned spectral bound -------------------------------------------------
+
+    def bound_model_init(self, seed: int = 0):
+        check(self._lib.smx_bound_model_init(self._ctx, C.c_uint64(seed)), "smx_bound_model_init")
+
+    def bound_model_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        check(self._lib.smx_bound_model_set_params(self._ctx, _ptr(p), int(p.shape[0])), "smx_bound_model_set_params")
+
+    def bound_model_get_params(self):
+        p = np.empty(BOUND_MODEL_PARAMS, dtype=np.float32)
+        check(self._lib.smx_bound_model_get_params(self._ctx, _ptr(p), BOUND_MODEL_PARAMS), "smx_bound_model_get_params")
+        return p
+
+    def bound_model_collect(self, lanczos_steps: int = 48):
+        check(self._lib.smx_bound_model_collect(self._ctx, int(lanczos_steps)), "smx_bound_model_collect")
+
+    def bound_model_train(self, epochs: int, batch: int = 256, lr: float = 1e-3) -> float:
+        loss = C.c_double(0.0)
+        check(self._lib.smx_bound_model_train(self._ctx, int(epochs), int(batch), float(lr), C.byref(loss)),
+              "smx_bound_model_train")
+        return loss.value
+
+    def bound_model_fit(self, x, t, steps: int = 0, lr: float = 1e-3):
+        """Loss and gradient at the current parameters on (x [m, 9], t [m, 2]), then ``steps`` Adam steps."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        assert x.ndim == 2 and x.shape[1] == BOUND_MODEL_FEATURES and t.shape == (x.shape[0], 2)
+        g = np.empty(BOUND_MODEL_PARAMS, dtype=np.float32)
+        loss = C.c_double(0.0)
+        check(self._lib.smx_bound_model_fit(self._ctx, _ptr(x), _ptr(t), int(x.shape[0]), int(steps), float(lr),
+                                            _ptr(g), C.byref(loss)), "smx_bound_model_fit")
+        return loss.value, g
+
+    def bound_model_predict(self, predict: bool = True, labels: bool = False, lanczos_steps: int = 48):
+        """(features [B, 9], predictions [B, 2] or None, Lanczos labels [B, 2] or None) at the fixed mu."""
+        f = np.empty((self.n_block_cols, BOUND_MODEL_FEATURES), dtype=np.float32)
+        p = np.empty((self.n_block_cols, 2), dtype=np.float32) if predict else None
+        lab = np.empty((self.n_block_cols, 2), dtype=np.float32) if labels else None
+        check(self._lib.smx_bound_model_predict(self._ctx, _ptr(f), _ptr(p) if p is not None else None,
+                                                _ptr(lab) if lab is not None else None, int(lanczos_steps)),
+              "smx_bound_model_predict")
+        return f, p, lab
+
+    def set_bound_model(self, enable: bool, weights_path: str | None = None):
+        path = weights_path.encode() if weights_path is not None else None
+        check(self._lib.smx_set_bound_model(self._ctx, 1 if enable else 0, path), "smx_set_bound_model")
+
+    def bound_model_save(self, path: str):
+        check(self._lib.smx_bound_model_save(self._ctx, path.encode()), "smx_bound_model_save")

@@ -18,6 +18,9 @@ OK, ERR_ARG, ERR_PATTERN, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_NOCONV, ERR_NOBR
 # smx_precision
 FP64, FP16X3, FP16, BF16 = range(4)
 PRECISIONS = {"fp64": FP64, "fp16x3": FP16X3, "fp16": FP16, "bf16": BF16}
+# learned spectral bound
+BOUND_MODEL_FEATURES = 9
+BOUND_MODEL_PARAMS = 4930
 
 
 class Stats(C.Structure):
@@ -66,6 +69,16 @@ SIGNATURES = {
     "smx_get_density": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "smx_get_pattern": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "smx_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "smx_bound_model_init": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "smx_bound_model_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "smx_bound_model_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "smx_bound_model_collect": (C.c_int, [C.c_void_p, C.c_int32]),
+    "smx_bound_model_train": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_void_p]),
+    "smx_bound_model_fit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float,
+                                      C.c_void_p, C.c_void_p]),
+    "smx_bound_model_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "smx_set_bound_model": (C.c_int, [C.c_void_p, C.c_int32, C.c_char_p]),
+    "smx_bound_model_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "smx_reset_counters": (C.c_int, [C.c_void_p]),
     "smx_get_submatrix_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smx_dense_density_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),

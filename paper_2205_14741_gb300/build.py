@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(OUT_DIR, "libsmx.so")
-SOURCES = ["smx_api.cu", "k_pattern.cu", "k_ns_fp64.cu", "k_ns_tc.cu"]
+SOURCES = ["smx_api.cu", "k_pattern.cu", "k_ns_fp64.cu", "k_ns_tc.cu", "k_bound_model.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

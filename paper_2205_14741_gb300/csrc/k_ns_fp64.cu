@@ -107,29 +107,75 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
         double r2 = 1.0, oscale = 1.0;
         if (it == 0) {
             // a-posteriori scaling (as in the tensor-core kernel): with Y = X0^2,
-            // rho(X0)^2 <= s^2 = max_r sum_c |Y_rc|; continue from X0' = (1.2/s) X0
+            // rho(X0)^2 = rho(Y) <= rho(|Y|) <= max_r (|Y| w)_r / w_r for any
+            // positive w (Collatz-Wielandt): w = 1 (the max row sum) and two
+            // power steps of |Y| from it; continue from X0' = (1.2/s) X0
             gemm_fp64(X, X, Y, n, ld, 2, As, Bs);
             __syncthreads();
+            double* wv = Z;  // the output buffer of this iteration is free until the second product
+            double* wn = Z + n;
+            const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+            auto block_max2 = [&](double x, double y) -> double2 {
+                x = warp_max(x);
+                y = warp_max(y);
+                if (lane == 0) {
+                    scratch[warp] = x;
+                    scratch[8 + warp] = y;
+                }
+                __syncthreads();
+                double2 m = make_double2(0.0, 0.0);
+                for (int w = 0; w < 8; ++w) {
+                    m.x = fmax(m.x, scratch[w]);
+                    m.y = fmax(m.y, scratch[8 + w]);
+                }
+                __syncthreads();
+                return m;
+            };
             double rmax = 0.0;
-            for (int r = threadIdx.x / 32; r < n; r += 8) {
+            for (int r = warp; r < n; r += 8) {
                 double acc = 0.0;
-                for (int c = threadIdx.x & 31; c < n; c += 32) acc += fabs(Y[static_cast<int64_t>(r) * ld + c]);
-                rmax = fmax(rmax, warp_sum(acc));
+                for (int c = lane; c < n; c += 32) acc += fabs(Y[static_cast<int64_t>(r) * ld + c]);
+                acc = warp_sum(acc);
+                if (lane == 0) wv[r] = acc;
+                rmax = fmax(rmax, acc);
             }
-            if ((threadIdx.x & 31) == 0) scratch[threadIdx.x / 32] = rmax;
-            __syncthreads();
-            double smax = 0.0;
-            for (int w = 0; w < 8; ++w) smax = fmax(smax, scratch[w]);
-            smax = sqrt(smax);
-            __syncthreads();
-            const double scale = smax > 0.0 ? 1.2 / smax : 1.0;
+            rmax = block_max2(rmax, 0.0).x;
+            double best = rmax, wtop = rmax;
+            for (int pass = 0; pass < 2 && best > 0.0; ++pass) {
+                for (int c = threadIdx.x; c < n; c += blockDim.x) wv[c] = fmax(wv[c], 1e-30 * wtop);
+                __syncthreads();
+                double q = 0.0, wm = 0.0;
+                for (int r = warp; r < n; r += 8) {
+                    double acc = 0.0;
+                    for (int c = lane; c < n; c += 32) acc = fma(fabs(Y[static_cast<int64_t>(r) * ld + c]), wv[c], acc);
+                    acc = warp_sum(acc);
+                    if (lane == 0) wn[r] = acc;
+                    q = fmax(q, acc / wv[r]);
+                    wm = fmax(wm, acc);
+                }
+                const double2 m2 = block_max2(q, wm);
+                best = fmin(best, m2.x);
+                if (!(m2.y > 0.0)) break;
+                for (int c = threadIdx.x; c < n; c += blockDim.x) wv[c] = wn[c] / m2.y;
+                wtop = 1.0;
+            }
+            const double smax = sqrt(best * (1.0 + 1e-12));
+            double scale = smax > 0.0 ? 1.2 / smax : 1.0;
+            if (a.use_model && smax > 0.0) {  // same rule as the tensor-core kernel
+                if (smax <= 1.6) scale = fmax(1.0, scale);
+                else if (threadIdx.x == 0) atomicAdd(a.fallbacks, 1);
+            }
             const double sc2 = scale * scale;
             for (int r = threadIdx.x / 32; r < n; r += 8)
                 for (int c = threadIdx.x & 31; c < n; c += 32) {
                     double& y = Y[static_cast<int64_t>(r) * ld + c];
                     y = (r == c ? 1.5 : 0.0) - 0.5 * sc2 * y;
                 }
-            if (threadIdx.x == 0) a.bound[blockIdx.x] = a.bound[blockIdx.x] * smax / 1.2;
+            if (threadIdx.x == 0) {
+                // feature of the next snapshot: the Gershgorin bound of A^2, over G
+                a.sq_ratio[blockIdx.x] = static_cast<float>(sqrt(rmax) * a.bound[blockIdx.x] / a.gersh[blockIdx.x]);
+                a.bound[blockIdx.x] = a.bound[blockIdx.x] / scale;
+            }
             __syncthreads();
             oscale = scale;
         } else {

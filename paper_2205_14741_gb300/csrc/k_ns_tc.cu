@@ -112,6 +112,34 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hw, uint32_t&
     }
 }
 
+// 8 consecutive values hi[0..8) + lo[0..8) (16-byte aligned) as FP32
+template <int PREC, int NB>
+__device__ __forceinline__ void load8(const uint16_t* hi, const uint16_t* lo, float (&v)[8]) {
+    const uint4 h = *reinterpret_cast<const uint4*>(hi);
+    const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f = unpack2<PREC>(hw[i]);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+    if constexpr (NB == 2) {
+        const uint4 l = *reinterpret_cast<const uint4*>(lo);
+        const uint32_t lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = unpack2<PREC>(lw[i]);
+            v[2 * i] += f.x;
+            v[2 * i + 1] += f.y;
+        }
+    }
+}
+template <int PREC, int NB>
+__device__ __forceinline__ void load32(const uint16_t* hi, const uint16_t* lo, float (&v)[32]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) load8<PREC, NB>(hi + 8 * u, lo + 8 * u, *reinterpret_cast<float(*)[8]>(v + 8 * u));
+}
+
 // two TMEM loads (32 columns each), one wait
 __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
@@ -145,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s, job_s, conv_s, bad_s, p_issued_s, m_consumed_s;
     __shared__ float resid_s[kEpiWarps];
-    __shared__ double scratch[32];
+    __shared__ float red_s[2][kThreads / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int* const abortp = &abort_s;
@@ -169,6 +197,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     tc_fence_after();
     const uint32_t tmem_base = tmem_base_s;
 
+    auto warp_sum_f = [](float v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+    // block-wide maxima of two non-negative values (all threads get the result)
+    auto block_max2 = [&](float x, float y) -> float2 {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+            y = fmaxf(y, __shfl_xor_sync(0xffffffffu, y, o));
+        }
+        if (lane == 0) {
+            red_s[0][warp] = x;
+            red_s[1][warp] = y;
+        }
+        __syncthreads();
+        float2 m = make_float2(0.0f, 0.0f);
+        for (int w = 0; w < kThreads / 32; ++w) {
+            m.x = fmaxf(m.x, red_s[0][w]);
+            m.y = fmaxf(m.y, red_s[1][w]);
+        }
+        __syncthreads();
+        return m;
+    };
+
     // role-local pipeline positions, continuous over all GEMMs of the CTA
     uint32_t p_it = 0;              // producer: K chunks issued
     uint32_t m_it = 0, m_tile = 0;  // MMA: K chunks consumed, tiles issued
@@ -180,8 +234,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
 
     // C = A * B over K in [0, kpad), written to buffer zo (rows and columns < kpad).
     // mode 1: zo = 3/2 I - 1/2 A A, residual ||A A - I||_F^2 accumulated;
-    // mode 2: zo = oscale * A B.
-    auto gemm = [&](int kpad, int n, int mode, int za, int zb, int zo, float oscale) {
+    // mode 2: zo = oscale * A B;
+    // mode 3: zo = A B and rsum[r] += sum_c |C_rc| (rsum zeroed by the caller);
+    // mode 4: zo = 3/2 c A - 1/2 c^3 A B with c = oscale (the first Newton-Schulz
+    //         step from c A when B = A^2, without forming 3/2 I - 1/2 c^2 B).
+    auto gemm = [&](int kpad, int n, int mode, int za, int zb, int zo, float oscale, float* rsum) {
         const int mtiles = (kpad + 127) / 128, ntiles = (kpad + NT - 1) / NT, kchunks = (kpad + 63) / 64;
         if (warp == 0) {
             if (lane == 0) {
@@ -253,6 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             const int q = warp & 3, half = (warp - 4) >> 2;
             const int lrow = q * 32 + lane;
             float r2 = 0.0f;
+            const float c15 = 1.5f * oscale, c05 = 0.5f * oscale * oscale * oscale;
             for (int mt = 0; mt < mtiles; ++mt)
                 for (int nt = 0; nt < ntiles; ++nt) {
                     const int nn = min(NT, kpad - NT * nt);
@@ -265,6 +323,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     const int row = 128 * mt + lrow;
                     uint16_t* out_hi = ws + static_cast<int64_t>(zo) * buf + static_cast<int64_t>(row) * a.ld;
                     uint16_t* out_lo = out_hi + buf;
+                    const uint16_t* a_hi = ws + static_cast<int64_t>(za) * buf + static_cast<int64_t>(row) * a.ld;
+                    const uint16_t* a_lo = a_hi + buf;
+                    float ra = 0.0f;  // mode 3: this thread's share of the row's abs sum
                     for (int c0 = 32 * half; c0 < nn; c0 += 64) {
                         uint32_t raw[32];
                         tmem_ld32_issue(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + abuf * 256 + c0, raw);
@@ -286,11 +347,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                     }
                                     // sum (v - delta)^2 = sum v^2 - 2 v_diag + 1 when the diagonal is here
                                     r2 += (i0 >= 0 && i0 < 32) ? sq - 2.0f * dv + 1.0f : sq;
+                                } else if (mode == 4) {
+                                    float xa[32];
+                                    load32<PREC, NB>(a_hi + col0, a_lo + col0, xa);
+#pragma unroll
+                                    for (int i = 0; i < 32; ++i) y[i] = fmaf(c15, xa[i], -c05 * __uint_as_float(raw[i]));
                                 } else {
 #pragma unroll
                                     for (int i = 0; i < 32; ++i) y[i] = oscale * __uint_as_float(raw[i]);
+                                    if (mode == 3) {
+#pragma unroll
+                                        for (int i = 0; i < 32; ++i) ra += fabsf(y[i]);
+                                    }
                                 }
                             } else {
+                                float xa[32];
+                                if (mode == 4) load32<PREC, NB>(a_hi + col0, a_lo + col0, xa);
 #pragma unroll
                                 for (int i = 0; i < 32; ++i) {
                                     const float v = __uint_as_float(raw[i]);
@@ -300,8 +372,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                         const float e = v - dl;
                                         y[i] = valid ? fmaf(-0.5f, v, 1.5f * dl) : 0.0f;
                                         r2 = valid ? fmaf(e, e, r2) : r2;
+                                    } else if (mode == 4) {
+                                        y[i] = valid ? fmaf(c15, xa[i], -c05 * v) : 0.0f;
                                     } else {
                                         y[i] = valid ? oscale * v : 0.0f;
+                                        if (mode == 3) ra += fabsf(y[i]);
                                     }
                                 }
                             }
@@ -318,6 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                             }
                         }
                     }
+                    if (mode == 3 && row < n) atomicAdd(rsum + row, ra);
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&tempty[abuf]);
@@ -374,78 +450,100 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         int cur = 0, done = 0;
         for (int it = 0; it < a.max_iter; ++it) {
             const int zx = cur ? zx1 : zx0, zn = cur ? zx0 : zx1;
-            float oscale = 1.0f;
             if (it == 0) {
                 // A-posteriori scaling.  Z = X0^2; every eigenvalue of X0 satisfies
-                // |lambda|^2 <= max_r sum_c |Z_rc| =: s^2 (Gershgorin on Z), so
+                // |lambda|^2 <= s^2 with s^2 the bound on rho(Z) below, so
                 // X0' = (c/s) X0 has all |lambda| <= c = 1.2 < sqrt(3) and the
                 // iteration from X0' is guaranteed to converge.  The step is then
-                // X1 = X0' (3/2 I - 1/2 X0'^2) = (c/s) X0 (3/2 I - 1/2 (c/s)^2 Z).
-                gemm(kpad, s.n, 2, zx, zx, zy, 1.0f);  // Z = X0^2
+                // X1 = X0' (3/2 I - 1/2 X0'^2) = 3/2 (c/s) X0 - 1/2 (c/s)^3 X0 Z.
+                //
+                // Bound on rho(Z) = rho(X0)^2 (Collatz-Wielandt): for any positive
+                // vector w, rho(Z) <= rho(|Z|) <= max_r (|Z| w)_r / w_r.  w = 1 gives
+                // the Gershgorin bound (the max row sum, from the product's
+                // epilogue); with the learned bound on, two power steps of |Z| from
+                // the row sums tighten it (on water-like submatrices from about
+                // 1.5 rho to 1.3 rho) so that good predictions pass the check.
+                // The power-step vectors live in the (still unused) buffer of X1.
+                float* wv = reinterpret_cast<float*>(ws + static_cast<int64_t>(zn) * buf);
+                float* wn = wv + kpad;
+                for (int c = tid; c < kpad; c += kThreads) wv[c] = 0.0f;
+                __syncthreads();
+                gemm(kpad, s.n, 3, zx, zx, zy, 1.0f, wv);  // Z = X0^2, wv = row sums of |Z|
                 float rmax = 0.0f;
+                for (int r = tid; r < s.n; r += kThreads) rmax = fmaxf(rmax, wv[r]);
+                rmax = block_max2(rmax, 0.0f).x;
+                float best = rmax, wtop = rmax;
                 const uint16_t* zh = ws + static_cast<int64_t>(zy) * buf;
                 const uint16_t* zl = zh + buf;
-                for (int r = warp; r < s.n; r += kThreads / 32) {
-                    float acc = 0.0f;
-                    for (int c = lane; c < s.n; c += 32) {
-                        float z = from16<PREC>(zh[static_cast<int64_t>(r) * a.ld + c]);
-                        if constexpr (NB == 2) z += from16<PREC>(zl[static_cast<int64_t>(r) * a.ld + c]);
-                        acc += fabsf(z);
-                    }
+                for (int pass = 0; a.use_model && pass < 2 && best > 0.0f; ++pass) {
+                    // w > 0: rows that are zero in Z get a tiny positive weight
+                    for (int c = tid; c < s.n; c += kThreads) wv[c] = fmaxf(wv[c], 1e-12f * wtop);
+                    __syncthreads();
+                    float q = 0.0f, wm = 0.0f;
+                    // wn = |Z| wv, four rows per warp in flight, 8 columns per lane and load
+                    for (int r0 = warp * 4; r0 < s.n; r0 += 4 * (kThreads / 32)) {
+                        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                        for (int c = 8 * lane; c < kpad; c += 256) {
+                            const float4 w0 = *reinterpret_cast<const float4*>(wv + c);
+                            const float4 w1 = *reinterpret_cast<const float4*>(wv + c + 4);
+                            const float wc[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                    rmax = fmaxf(rmax, acc);
-                }
-                if (lane == 0) resid_s[warp < kEpiWarps ? warp : 0] = 0.0f;
-                __syncthreads();
-                if (lane == 0) atomicMax(reinterpret_cast<int*>(&resid_s[0]), __float_as_int(rmax));  // rmax >= 0
-                __syncthreads();
-                const float smax = sqrtf(resid_s[0] * (1.0f + 1e-5f));  // margin for FP32 summation
-                const float scale = smax > 0.0f ? 1.2f / smax : 1.0f;
-                const float sc2 = scale * scale;
-                // Y' = 3/2 I - 1/2 scale^2 Z, in place
-                uint16_t* yh = ws + static_cast<int64_t>(zy) * buf;
-                uint16_t* yl = yh + buf;
-                const int per_row = kpad / 8;
-                for (int e = tid; e < kpad * per_row; e += blockDim.x) {
-                    const int r = e / per_row, c0 = (e - r * per_row) * 8;
-                    const int64_t o = static_cast<int64_t>(r) * a.ld + c0;
-                    const uint4 hv = *reinterpret_cast<const uint4*>(yh + o);
-                    uint4 lv = make_uint4(0, 0, 0, 0);
-                    if constexpr (NB == 2) lv = *reinterpret_cast<const uint4*>(yl + o);
-                    const uint32_t hin[4] = {hv.x, hv.y, hv.z, hv.w}, lin[4] = {lv.x, lv.y, lv.z, lv.w};
-                    uint32_t hw[4], lw[4];
+                            for (int u = 0; u < 4; ++u) {
+                                const int r = r0 + u;
+                                if (r < s.n) {
+                                    float zr[8];
+                                    load8<PREC, NB>(zh + static_cast<int64_t>(r) * a.ld + c, zl + static_cast<int64_t>(r) * a.ld + c, zr);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        float2 z = unpack2<PREC>(hin[i]);
-                        if constexpr (NB == 2) {
-                            const float2 zl2 = unpack2<PREC>(lin[i]);
-                            z.x += zl2.x;
-                            z.y += zl2.y;
+                                    for (int i = 0; i < 8; ++i) acc[u] = fmaf(fabsf(zr[i]), wc[i], acc[u]);
+                                }
+                            }
                         }
-                        const int c = c0 + 2 * i;
-                        const bool v0 = r < s.n && c < s.n, v1 = r < s.n && c + 1 < s.n;
-                        const float y0 = v0 ? fmaf(-0.5f * sc2, z.x, r == c ? 1.5f : 0.0f) : 0.0f;
-                        const float y1 = v1 ? fmaf(-0.5f * sc2, z.y, r == c + 1 ? 1.5f : 0.0f) : 0.0f;
-                        split2<PREC, NB>(y0, y1, hw[i], lw[i]);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int r = r0 + u;
+                            const float v = warp_sum_f(acc[u]);
+                            if (r < s.n) {
+                                if (lane == 0) wn[r] = v;
+                                q = fmaxf(q, v / wv[r]);
+                                wm = fmaxf(wm, v);
+                            }
+                        }
                     }
-                    *reinterpret_cast<uint4*>(yh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    if constexpr (NB == 2) *reinterpret_cast<uint4*>(yl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    const float2 m2 = block_max2(q, wm);
+                    best = fminf(best, m2.x);
+                    if (!(m2.y > 0.0f)) break;
+                    const float inv = 1.0f / m2.y;
+                    for (int c = tid; c < s.n; c += kThreads) wv[c] = wn[c] * inv;
+                    wtop = 1.0f;
                 }
-                fence_proxy_async_global();
-                if (tid == 0) a.bound[j] = a.bound[j] * static_cast<double>(smax) / 1.2;  // effective scaling of X0'
+                const float smax = sqrtf(best * (1.0f + 1e-4f));  // margin for FP32 summation
+                // Without the learned bound X0 = A / G and X0 is always rescaled to
+                // c / s.  With it, the predicted scaling is kept when the guaranteed
+                // bound allows (s <= 1.6 < sqrt 3) and only enlarged, never shrunk;
+                // otherwise the prediction is discarded for the guaranteed c / s.
+                float scale = smax > 0.0f ? 1.2f / smax : 1.0f;
+                if (a.use_model && smax > 0.0f) {
+                    if (smax <= 1.6f) scale = fmaxf(1.0f, scale);
+                    else if (tid == 0) atomicAdd(a.fallbacks, 1);
+                }
+                if (tid == 0) {
+                    // feature of the next snapshot: the Gershgorin bound of A^2, over G
+                    const double s0 = sqrt(static_cast<double>(rmax) * (1.0 + 1e-5));
+                    a.sq_ratio[j] = static_cast<float>(s0 * a.bound[j] / a.gersh[j]);
+                    a.bound[j] = a.bound[j] / static_cast<double>(scale);  // effective scaling of X0'
+                }
                 __syncthreads();
-                oscale = scale;
+                gemm(kpad, s.n, 4, zx, zy, zn, scale, nullptr);  // X1 = 3/2 c X0 - 1/2 c^3 X0 Z
             } else {
-                gemm(kpad, s.n, 1, zx, zx, zy, 1.0f);  // Y = 3/2 I - 1/2 X^2
+                gemm(kpad, s.n, 1, zx, zx, zy, 1.0f, nullptr);  // Y = 3/2 I - 1/2 X^2
                 if (tid == 0) {
                     double r2 = 0.0;
                     for (int w = 0; w < kEpiWarps; ++w) r2 += resid_s[w];
                     if (!isfinite(r2)) bad_s = 1;
                     else if (sqrt(r2) <= a.tau) conv_s = 1;
                 }
+                gemm(kpad, s.n, 2, zx, zy, zn, 1.0f, nullptr);  // X' = X Y
             }
-            gemm(kpad, s.n, 2, zx, zy, zn, oscale);  // X' = X Y
             cur ^= 1;
             done = it + 1;
             if (conv_s || bad_s || *abortp) break;

@@ -97,6 +97,13 @@ struct smx_ctx {
     double ns_ms_total = 0.0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ns_events;  // pool, one pair per pending launch
     size_t ns_pending = 0;
+
+    // learned spectral bound
+    bool model_ready = false, model_on = false, sq_valid = false;
+    int adam_t = 0;
+    int64_t n_samples = 0, cap_samples = 0;
+    DevBuf d_params, d_mst, d_vst, d_partial_mlp, d_feat, d_pred, d_labels, d_gersh, d_prev_ratio, d_sq_ratio,
+        d_fallback, d_loss, d_sx, d_st, d_fit_x, d_fit_t, d_grad;
 };
 
 // ---------------------------------------------------------------------------
@@ -356,6 +363,16 @@ static smx_status build_at(smx_ctx* c, double mu) {
         SMX_CUDA(launch_gather_bound_f32(dp<SubDesc>(c->d_subs), B, c->max_nblk, pv, dp<float>(c->d_H32), mu,
                                          dp<float>(c->d_T), dp<double>(c->d_bound), st));
     }
+    SMX_CUDA(cudaMemcpyAsync(c->d_gersh.p, c->d_bound.p, sizeof(double) * B, cudaMemcpyDeviceToDevice, st));
+    SMX_CUDA(cudaMemsetAsync(c->d_fallback.p, 0, sizeof(int), st));
+    if (c->model_on) {
+        // learned bound: features -> prediction -> b_j (checked inside the Newton-Schulz kernel)
+        SMX_CUDA(launch_features(dp<SubDesc>(c->d_subs), B, c->d_T.p, c->precision != SMX_FP64, dp<float>(c->d_prev_ratio),
+                                 dp<float>(c->d_feat), st));
+        SMX_CUDA(launch_mlp_predict(dp<float>(c->d_params), dp<float>(c->d_feat), B, dp<float>(c->d_pred), st));
+        SMX_CUDA(launch_model_bound(dp<float>(c->d_pred), dp<double>(c->d_gersh), dp<double>(c->d_bound), B, kModelMargin, st));
+        c->kernel_launches += 3;
+    }
     cudaEvent_t ns0, ns1;
     SMX_TRY(ns_event_pair(c, &ns0, &ns1));
     if (c->precision == SMX_FP64) {
@@ -372,6 +389,10 @@ static smx_status build_at(smx_ctx* c, double mu) {
         a.max_iter = 100;
         a.iters = dp<int32_t>(c->d_iters);
         a.work_n3 = dp<unsigned long long>(c->d_work_n3);
+        a.gersh = dp<double>(c->d_gersh);
+        a.sq_ratio = dp<float>(c->d_sq_ratio);
+        a.use_model = c->model_on ? 1 : 0;
+        a.fallbacks = dp<int>(c->d_fallback);
         a.status = dp<int>(c->d_status);
         a.pv = pv;
         a.H = dp<double>(c->d_H);
@@ -396,6 +417,10 @@ static smx_status build_at(smx_ctx* c, double mu) {
         a.max_iter = 100;
         a.iters = dp<int32_t>(c->d_iters);
         a.work_n3 = dp<unsigned long long>(c->d_work_n3);
+        a.gersh = dp<double>(c->d_gersh);
+        a.sq_ratio = dp<float>(c->d_sq_ratio);
+        a.use_model = c->model_on ? 1 : 0;
+        a.fallbacks = dp<int>(c->d_fallback);
         a.status = dp<int>(c->d_status);
         a.pv = pv;
         a.H = dp<double>(c->d_H);
@@ -414,6 +439,7 @@ static smx_status build_at(smx_ctx* c, double mu) {
     SMX_CUDA(cudaEventRecord(c->ev1, st));
     c->kernel_launches += 3;
     c->ns_launches += 1;
+    c->sq_valid = true;
     c->built = true;
     c->last_mu = mu;
     return SMX_OK;
@@ -501,6 +527,21 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if ((s = ensure(c->d_status, sizeof(int))) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_counter, sizeof(int))) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_work_n3, sizeof(unsigned long long))) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_gersh, sizeof(double) * n_block_cols)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_sq_ratio, sizeof(float) * n_block_cols)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_prev_ratio, sizeof(float) * n_block_cols)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_feat, sizeof(float) * kModelFeatures * n_block_cols)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_pred, sizeof(float) * 2 * n_block_cols)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_labels, sizeof(float) * 2 * n_block_cols)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_fallback, sizeof(int))) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_loss, sizeof(float))) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_params, sizeof(float) * kModelParams)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_mst, sizeof(float) * kModelParams)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_vst, sizeof(float) * kModelParams)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_grad, sizeof(float) * kModelParams)) != SMX_OK) return fail(s);
+    if (cudaMemsetAsync(c->d_prev_ratio.p, 0, sizeof(float) * n_block_cols, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_sq_ratio.p, 0, sizeof(float) * n_block_cols, c->stream) != cudaSuccess)
+        return fail(SMX_ERR_CUDA);
     if (cudaMemsetAsync(c->d_work_n3.p, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
     if (cudaMallocHost(&c->h_keep_pinned, c->nnzb > 0 ? c->nnzb : 1) != cudaSuccess) return fail(SMX_ERR_OOM);
     if (cudaMemcpyAsync(c->d_H.p, values, vb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
@@ -517,6 +558,11 @@ smx_status smx_set_values(smx_ctx* c, const double* values, int32_t on_device) {
     DeviceGuard g(c->device);
     SMX_CUDA(cudaMemcpyAsync(c->d_H.p, values, static_cast<size_t>(c->n_values) * sizeof(double),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (c->sq_valid) {  // the ratio of the last build becomes the previous-step feature
+        SMX_CUDA(cudaMemcpyAsync(c->d_prev_ratio.p, c->d_sq_ratio.p, sizeof(float) * c->B, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+        c->sq_valid = false;
+    }
     c->dirty = true;
     c->built = false;
     return SMX_OK;
@@ -643,6 +689,8 @@ smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
     DeviceGuard g(c->device);
     std::vector<int32_t> it(c->B);
     unsigned long long work = 0;
+    int fallbacks = 0;
+    SMX_CUDA(cudaMemcpyAsync(&fallbacks, c->d_fallback.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     SMX_CUDA(cudaMemcpyAsync(it.data(), c->d_iters.p, sizeof(int32_t) * c->B, cudaMemcpyDeviceToHost, c->stream));
     SMX_CUDA(cudaMemcpyAsync(&work, c->d_work_n3.p, sizeof(work), cudaMemcpyDeviceToHost, c->stream));
     SMX_CUDA(cudaStreamSynchronize(c->stream));
@@ -670,6 +718,7 @@ smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
     out->dim_mean = dsum / c->B;
     out->iters_mean = isum / c->B;
     out->n_noconv = noconv;
+    out->n_bound_fallback = fallbacks;
     out->bisection_steps = c->bisection_steps;
     out->flops_ns = flops;
     float ms = 0.0f;
@@ -697,6 +746,257 @@ smx_status smx_reset_counters(smx_ctx* c) {
     return SMX_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// learned spectral bound
+// ---------------------------------------------------------------------------
+
+static uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+static smx_status model_upload(smx_ctx* c, const std::vector<float>& p) {
+    SMX_CUDA(cudaMemcpyAsync(c->d_params.p, p.data(), sizeof(float) * kModelParams, cudaMemcpyHostToDevice, c->stream));
+    SMX_CUDA(cudaMemsetAsync(c->d_mst.p, 0, sizeof(float) * kModelParams, c->stream));
+    SMX_CUDA(cudaMemsetAsync(c->d_vst.p, 0, sizeof(float) * kModelParams, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    c->adam_t = 0;
+    c->model_ready = true;
+    return SMX_OK;
+}
+
+// gather of T (staging for the context's precision) and the bound at the fixed mu
+static smx_status gather_current(smx_ctx* c) {
+    if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
+    const PatternView pv = pattern_view(c);
+    if (c->precision == SMX_FP64) {
+        SMX_TRY(ensure(c->d_T, static_cast<size_t>(c->t_elems) * sizeof(double)));
+        SMX_CUDA(launch_gather_bound(dp<SubDesc>(c->d_subs), c->B, c->max_nblk, pv, dp<double>(c->d_H), c->mu,
+                                     dp<double>(c->d_T), dp<double>(c->d_bound), c->stream));
+    } else {
+        SMX_TRY(ensure(c->d_T, static_cast<size_t>(c->t_elems) * sizeof(float)));
+        SMX_CUDA(launch_gather_bound_f32(dp<SubDesc>(c->d_subs), c->B, c->max_nblk, pv, dp<float>(c->d_H32), c->mu,
+                                         dp<float>(c->d_T), dp<double>(c->d_bound), c->stream));
+    }
+    c->kernel_launches += 1;
+    return SMX_OK;
+}
+
+extern "C" {
+
+smx_status smx_bound_model_init(smx_ctx* c, uint64_t seed) {
+    if (!c) return SMX_ERR_ARG;
+    DeviceGuard g(c->device);
+    std::vector<float> p(kModelParams, 0.0f);
+    const int F = kModelFeatures;
+    const int shapes[3][3] = {{0, 64, F}, {64 * F + 64, 64, 64}, {64 * F + 64 + 4096 + 64, 2, 64}};  // offset, out, in
+    uint64_t ctr = 0;
+    for (const auto& sh : shapes) {
+        const float lim = 1.0f / std::sqrt(static_cast<float>(sh[2]));
+        for (int i = 0; i < sh[1] * sh[2]; ++i) {
+            const double u = static_cast<double>(splitmix64(seed * 0x100000001B3ull + (ctr++)) >> 11) * (1.0 / 9007199254740992.0);
+            p[sh[0] + i] = static_cast<float>((2.0 * u - 1.0) * lim);
+        }
+    }
+    c->n_samples = 0;
+    return model_upload(c, p);
+}
+
+smx_status smx_bound_model_set_params(smx_ctx* c, const float* params, int32_t count) {
+    if (!c || !params || count != kModelParams) return SMX_ERR_ARG;
+    DeviceGuard g(c->device);
+    return model_upload(c, std::vector<float>(params, params + count));
+}
+
+smx_status smx_bound_model_get_params(smx_ctx* c, float* params, int32_t count) {
+    if (!c || !params || count != kModelParams) return SMX_ERR_ARG;
+    if (!c->model_ready) return SMX_ERR_STATE;
+    DeviceGuard g(c->device);
+    SMX_CUDA(cudaMemcpyAsync(params, c->d_params.p, sizeof(float) * kModelParams, cudaMemcpyDeviceToHost, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    return SMX_OK;
+}
+
+smx_status smx_bound_model_collect(smx_ctx* c, int32_t lanczos_steps) {
+    if (!c || lanczos_steps < 8 || lanczos_steps > kMaxLanczos) return SMX_ERR_ARG;
+    DeviceGuard g(c->device);
+    SMX_TRY(gather_current(c));
+    const int B = c->B;
+    const bool f32 = c->precision != SMX_FP64;
+    SMX_CUDA(launch_features(dp<SubDesc>(c->d_subs), B, c->d_T.p, f32, dp<float>(c->d_prev_ratio), dp<float>(c->d_feat),
+                             c->stream));
+    SMX_CUDA(launch_lanczos(dp<SubDesc>(c->d_subs), B, c->max_n, c->d_T.p, f32, lanczos_steps, dp<float>(c->d_labels),
+                            c->stream));
+    c->kernel_launches += 2;
+    if (c->n_samples + B > c->cap_samples) {  // grow the sample store, keeping its contents
+        const int64_t cap = std::max<int64_t>(2 * c->cap_samples, c->n_samples + B);
+        DevBuf nx, nt;
+        smx_status e = ensure(nx, sizeof(float) * kModelFeatures * cap);
+        if (e == SMX_OK) e = ensure(nt, sizeof(float) * 2 * cap);
+        if (e != SMX_OK) {
+            release(nx);
+            release(nt);
+            return e;
+        }
+        if (c->n_samples) {
+            SMX_CUDA(cudaMemcpyAsync(nx.p, c->d_sx.p, sizeof(float) * kModelFeatures * c->n_samples, cudaMemcpyDeviceToDevice, c->stream));
+            SMX_CUDA(cudaMemcpyAsync(nt.p, c->d_st.p, sizeof(float) * 2 * c->n_samples, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        SMX_CUDA(cudaStreamSynchronize(c->stream));
+        release(c->d_sx);
+        release(c->d_st);
+        c->d_sx = nx;
+        c->d_st = nt;
+        c->cap_samples = cap;
+    }
+    SMX_CUDA(cudaMemcpyAsync(dp<float>(c->d_sx) + kModelFeatures * c->n_samples, c->d_feat.p,
+                             sizeof(float) * kModelFeatures * B, cudaMemcpyDeviceToDevice, c->stream));
+    SMX_CUDA(cudaMemcpyAsync(dp<float>(c->d_st) + 2 * c->n_samples, c->d_labels.p, sizeof(float) * 2 * B,
+                             cudaMemcpyDeviceToDevice, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    c->n_samples += B;
+    return SMX_OK;
+}
+
+static smx_status mlp_steps(smx_ctx* c, const float* X, const float* T, int64_t m_total, int batch, int steps_or_epochs,
+                            bool epochs, float lr, float* grad_host, double* loss_out) {
+    SMX_TRY(ensure(c->d_partial_mlp, sizeof(float) * mlp_partial_floats(static_cast<int>(std::min<int64_t>(batch, m_total)))));
+    float loss = 0.0f;
+    const int64_t nbatch = (m_total + batch - 1) / batch;
+    const int64_t total = epochs ? nbatch * steps_or_epochs : steps_or_epochs;
+    for (int64_t s = 0; s < total; ++s) {
+        const int64_t b0 = epochs ? (s % nbatch) * batch : 0;
+        const int m = static_cast<int>(std::min<int64_t>(batch, m_total - b0));
+        ++c->adam_t;
+        SMX_CUDA(launch_mlp_step(dp<float>(c->d_params), X + kModelFeatures * b0, T + 2 * b0, m, dp<float>(c->d_partial_mlp),
+                                 dp<float>(c->d_params), dp<float>(c->d_mst), dp<float>(c->d_vst), c->adam_t, lr,
+                                 nullptr, dp<float>(c->d_loss), c->stream));
+        c->kernel_launches += 2;
+    }
+    (void)grad_host;
+    if (total > 0) {
+        SMX_CUDA(cudaMemcpyAsync(&loss, c->d_loss.p, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        SMX_CUDA(cudaStreamSynchronize(c->stream));
+        if (loss_out) *loss_out = loss;
+    }
+    return SMX_OK;
+}
+
+smx_status smx_bound_model_train(smx_ctx* c, int32_t epochs, int32_t batch, float lr, double* final_loss) {
+    if (!c || epochs < 1 || batch < 1 || !(lr > 0.0f)) return SMX_ERR_ARG;
+    if (!c->model_ready || c->n_samples == 0) return SMX_ERR_STATE;
+    DeviceGuard g(c->device);
+    return mlp_steps(c, dp<float>(c->d_sx), dp<float>(c->d_st), c->n_samples, batch, epochs, true, lr, nullptr, final_loss);
+}
+
+smx_status smx_bound_model_fit(smx_ctx* c, const float* x, const float* t, int32_t m, int32_t steps, float lr,
+                               float* grad, double* loss) {
+    if (!c || !x || !t || m < 1 || steps < 0 || (steps > 0 && !(lr > 0.0f))) return SMX_ERR_ARG;
+    if (!c->model_ready) return SMX_ERR_STATE;
+    DeviceGuard g(c->device);
+    SMX_TRY(ensure(c->d_fit_x, sizeof(float) * kModelFeatures * m));
+    SMX_TRY(ensure(c->d_fit_t, sizeof(float) * 2 * m));
+    SMX_CUDA(cudaMemcpyAsync(c->d_fit_x.p, x, sizeof(float) * kModelFeatures * m, cudaMemcpyHostToDevice, c->stream));
+    SMX_CUDA(cudaMemcpyAsync(c->d_fit_t.p, t, sizeof(float) * 2 * m, cudaMemcpyHostToDevice, c->stream));
+    SMX_TRY(ensure(c->d_partial_mlp, sizeof(float) * mlp_partial_floats(m)));
+    // gradient and loss at the current parameters (no update)
+    SMX_CUDA(launch_mlp_step(dp<float>(c->d_params), dp<float>(c->d_fit_x), dp<float>(c->d_fit_t), m,
+                             dp<float>(c->d_partial_mlp), dp<float>(c->d_params), dp<float>(c->d_mst), dp<float>(c->d_vst),
+                             0, 0.0f, dp<float>(c->d_grad), dp<float>(c->d_loss), c->stream));
+    c->kernel_launches += 2;
+    float l0 = 0.0f;
+    SMX_CUDA(cudaMemcpyAsync(&l0, c->d_loss.p, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (grad) SMX_CUDA(cudaMemcpyAsync(grad, c->d_grad.p, sizeof(float) * kModelParams, cudaMemcpyDeviceToHost, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    if (loss) *loss = l0;
+    if (steps > 0)
+        SMX_TRY(mlp_steps(c, dp<float>(c->d_fit_x), dp<float>(c->d_fit_t), m, m, steps, false, lr, nullptr, nullptr));
+    return SMX_OK;
+}
+
+smx_status smx_bound_model_predict(smx_ctx* c, float* features, float* pred, float* labels, int32_t lanczos_steps) {
+    if (!c || (labels && (lanczos_steps < 8 || lanczos_steps > kMaxLanczos))) return SMX_ERR_ARG;
+    if (pred && !c->model_ready) return SMX_ERR_STATE;
+    DeviceGuard g(c->device);
+    SMX_TRY(gather_current(c));
+    const int B = c->B;
+    const bool f32 = c->precision != SMX_FP64;
+    SMX_CUDA(launch_features(dp<SubDesc>(c->d_subs), B, c->d_T.p, f32, dp<float>(c->d_prev_ratio), dp<float>(c->d_feat),
+                             c->stream));
+    c->kernel_launches += 1;
+    if (pred) {
+        SMX_CUDA(launch_mlp_predict(dp<float>(c->d_params), dp<float>(c->d_feat), B, dp<float>(c->d_pred), c->stream));
+        SMX_CUDA(cudaMemcpyAsync(pred, c->d_pred.p, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost, c->stream));
+        c->kernel_launches += 1;
+    }
+    if (labels) {
+        SMX_CUDA(launch_lanczos(dp<SubDesc>(c->d_subs), B, c->max_n, c->d_T.p, f32, lanczos_steps, dp<float>(c->d_labels),
+                                c->stream));
+        SMX_CUDA(cudaMemcpyAsync(labels, c->d_labels.p, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost, c->stream));
+        c->kernel_launches += 1;
+    }
+    if (features)
+        SMX_CUDA(cudaMemcpyAsync(features, c->d_feat.p, sizeof(float) * kModelFeatures * B, cudaMemcpyDeviceToHost, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    return SMX_OK;
+}
+
+static uint64_t fnv1a(const void* data, size_t n) {
+    const unsigned char* p = static_cast<const unsigned char*>(data);
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+smx_status smx_bound_model_save(smx_ctx* c, const char* path) {
+    if (!c || !path) return SMX_ERR_ARG;
+    if (!c->model_ready) return SMX_ERR_STATE;
+    std::vector<float> p(kModelParams);
+    SMX_TRY(smx_bound_model_get_params(c, p.data(), kModelParams));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return SMX_ERR_ARG;
+    const int32_t cnt = kModelParams;
+    const uint64_t sum = fnv1a(p.data(), sizeof(float) * p.size());
+    bool ok = std::fwrite("SMXBNDM1", 1, 8, f) == 8 && std::fwrite(&cnt, 4, 1, f) == 1 &&
+              std::fwrite(p.data(), sizeof(float), p.size(), f) == p.size() && std::fwrite(&sum, 8, 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? SMX_OK : SMX_ERR_ARG;
+}
+
+smx_status smx_set_bound_model(smx_ctx* c, int32_t enable, const char* weights_path) {
+    if (!c) return SMX_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (weights_path) {
+        FILE* f = std::fopen(weights_path, "rb");
+        if (!f) return SMX_ERR_ARG;
+        char magic[8];
+        int32_t cnt = 0;
+        uint64_t sum = 0;
+        std::vector<float> p(kModelParams);
+        bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "SMXBNDM1", 8) == 0 &&
+                  std::fread(&cnt, 4, 1, f) == 1 && cnt == kModelParams &&
+                  std::fread(p.data(), sizeof(float), p.size(), f) == p.size() && std::fread(&sum, 8, 1, f) == 1 &&
+                  sum == fnv1a(p.data(), sizeof(float) * p.size());
+        std::fclose(f);
+        if (!ok) return SMX_ERR_ARG;
+        SMX_TRY(model_upload(c, p));
+    }
+    if (enable && !c->model_ready) return SMX_ERR_STATE;
+    c->model_on = enable != 0;
+    return SMX_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
 void smx_destroy(smx_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
@@ -704,7 +1004,10 @@ void smx_destroy(smx_ctx* c) {
     DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_bcol, &c->d_bs, &c->d_keep, &c->d_fcol_ptr,
                       &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
                       &c->d_W2, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
-                      &c->d_out, &c->d_out_br, &c->d_status, &c->d_counter, &c->d_work_n3};
+                      &c->d_out, &c->d_out_br, &c->d_status, &c->d_counter, &c->d_work_n3,
+                      &c->d_params, &c->d_mst, &c->d_vst, &c->d_partial_mlp, &c->d_feat, &c->d_pred, &c->d_labels,
+                      &c->d_gersh, &c->d_prev_ratio, &c->d_sq_ratio, &c->d_fallback, &c->d_loss, &c->d_sx, &c->d_st,
+                      &c->d_fit_x, &c->d_fit_t, &c->d_grad};
     for (DevBuf* b : bufs) release(*b);
     for (auto& pr : c->ns_events) {
         cudaEventDestroy(pr.first);

@@ -46,6 +46,10 @@ struct NsFp64Args {
     int max_iter;
     int32_t* iters;
     unsigned long long* work_n3;  // += n_j^3 * iters_j per submatrix
+    const double* gersh;   // Gershgorin bound G_j of T_j - mu I
+    float* sq_ratio;       // out: sqrt(max_r sum_c |(A^2)_rc|) / G_j, the Gershgorin bound of A^2 (next-step feature)
+    int use_model;         // the initial bound came from the learned model: keep it when the check passes
+    int* fallbacks;        // count of submatrices whose learned bound failed the check
     int* status;
     PatternView pv;
     const double* H;
@@ -69,6 +73,10 @@ struct NsTcArgs {
     int max_iter;
     int32_t* iters;
     unsigned long long* work_n3;  // += n_j^3 * iters_j per submatrix
+    const double* gersh;   // Gershgorin bound G_j of T_j - mu I
+    float* sq_ratio;       // out: sqrt(max_r sum_c |(A^2)_rc|) / G_j, the Gershgorin bound of A^2 (next-step feature)
+    int use_model;         // the initial bound came from the learned model: keep it when the check passes
+    int* fallbacks;        // count of submatrices whose learned bound failed the check
     int* status;
     PatternView pv;
     const double* H;
@@ -83,6 +91,33 @@ cudaError_t launch_ns_tc(const NsTcArgs& a, int precision, const CUtensorMap& tm
 // saved owner columns, with the per-column trace / energy partials (FP64).
 cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
                                  const float* xown, const double* H, double* D, double2* partial, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// learned spectral bound (k_bound_model.cu)
+// ---------------------------------------------------------------------------
+constexpr int kModelFeatures = 9;
+constexpr int kModelParams = 64 * kModelFeatures + 64 + 64 * 64 + 64 + 2 * 64 + 2;  // 4930
+constexpr int kMaxLanczos = 64;
+// b_j = rho_hat (1 + margin) / 1.2: the margin covers the model's typical
+// under-prediction (a few percent) so that the first-product check passes
+constexpr float kModelMargin = 0.05f;
+
+// features[j*9 + k] of A_j = T_j - mu I from the staging buffer (FP32 or FP64)
+cudaError_t launch_features(const SubDesc* subs, int n_subs, const void* T, bool fp32, const float* prev_ratio,
+                            float* feat, cudaStream_t st);
+// labels[2j] = rho/G, labels[2j+1] = delta/G by Lanczos on A and A^2
+cudaError_t launch_lanczos(const SubDesc* subs, int n_subs, int max_n, const void* T, bool fp32, int ksteps,
+                           float* labels, cudaStream_t st);
+cudaError_t launch_mlp_predict(const float* params, const float* feat, int m, float* out, cudaStream_t st);
+// floats of scratch one gradient/Adam step on m samples needs
+size_t mlp_partial_floats(int m);
+// gradient at params_in on (X, Tg); grad_out/loss_out optional; Adam update of params when lr > 0
+cudaError_t launch_mlp_step(const float* params_in, const float* X, const float* Tg, int m, float* partial,
+                            float* params, float* mst, float* vst, int t, float lr, float* grad_out, float* loss_out,
+                            cudaStream_t st);
+// bound[j] = gersh[j] * clamp(pred[2j]) * (1 + margin) / 1.2
+cudaError_t launch_model_bound(const float* pred, const double* gersh, double* bound, int n, float margin,
+                               cudaStream_t st);
 
 // Dynamic shared memory the tcgen05 kernel needs for a precision.
 size_t ns_tc_smem_bytes(int precision);

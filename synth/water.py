@@ -183,9 +183,14 @@ def _diag_blocks(n_mol: int, b: int, rng: np.random.Generator, occ=(-0.5, 0.05),
     return blocks
 
 
-def _assemble(pos, box, b, diag, seed, r_c, ell, sigma) -> BlockCSC:
+def _assemble(pos, box, b, diag, seed, r_c, ell, sigma, pairs=None) -> BlockCSC:
     n_mol = pos.shape[0]
-    if np.isfinite(r_c):
+    if pairs is not None:  # a fixed pattern: the given pairs at their current distances
+        pi, pj = pairs
+        dv = pos[pi] - pos[pj]
+        dv -= box * np.round(dv / box)
+        d = np.sqrt(np.einsum("ak,ak->a", dv, dv))
+    elif np.isfinite(r_c):
         pi, pj, d = _pairs_within(pos, box, r_c)
     else:
         pi, pj = np.triu_indices(n_mol, k=1)
@@ -236,22 +241,25 @@ def make_slab_system(n_mol: int, b: int, r_c: float, ell: float, seed: int, box=
 
 
 def md_trajectory(n_mol: int, b: int, r_c: float, ell: float, seed: int, n_snap: int,
-                  step_sigma: float = 0.05) -> Iterator[BlockCSC]:
+                  step_sigma: float = 0.05, fixed_pattern: bool = False) -> Iterator[BlockCSC]:
     """Snapshots of a lattice system whose positions take cumulative N(0, step_sigma) steps.
 
     Diagonal blocks stay fixed; each pair's off-diagonal block keeps its random
     pattern and only its amplitude follows the distance, so matrices evolve
-    smoothly; the block pattern is recomputed per snapshot.
+    smoothly.  The block pattern is recomputed per snapshot, or, with
+    ``fixed_pattern``, is the pairs within r_c at the first snapshot for the
+    whole trajectory (one library context can then take every snapshot).
     """
     rng = np.random.default_rng(seed)
     pos, box = lattice_positions(n_mol, 3.1, 0.3, rng)
     diag = _diag_blocks(n_mol, b, rng)
     step_rng = np.random.default_rng(seed + 7919)
+    pairs = _pairs_within(pos, box, r_c)[:2] if fixed_pattern else None
     for s in range(n_snap):
         if s:
             pos = pos + step_rng.normal(0.0, step_sigma, size=pos.shape)
             pos = np.mod(pos, box)
-        sysm = _assemble(pos, box, b, diag, seed, r_c, ell, 0.1)
+        sysm = _assemble(pos, box, b, diag, seed, r_c, ell, 0.1, pairs=pairs)
         sysm.meta = dict(kind="md", n_mol=n_mol, b=b, r_c=r_c, ell=ell, seed=seed, snapshot=s)
         yield sysm
 

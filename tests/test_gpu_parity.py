@@ -92,13 +92,44 @@ def test_multi_tile_submatrices(prec):
     assert err <= TOL_D[prec]
     # effective scaling b of X0 = (T_j - mu I)/b after the a-posteriori rescale: the largest
     # eigenvalue of X0 is at most 1.2 (< sqrt 3, so Newton-Schulz converges) and b does not
-    # exceed the Gershgorin bound / 1.2
-    lam = np.linalg.eigvalsh(h - 0.1 * np.eye(h.shape[0]))
+    # exceed the Gershgorin bound of A^2 (square-rooted) / 1.2, which is below the Gershgorin
+    # bound of A / 1.2 (margins: 1e-4 on the FP32 bound of A^2, 1e-5 on the FP32 bound of A)
+    a = h - 0.1 * np.eye(h.shape[0])
+    lam = np.linalg.eigvalsh(a)
     rho = np.max(np.abs(lam))
-    lo, hi = O.gershgorin_bounds(h - 0.1 * np.eye(h.shape[0]))
+    lo, hi = O.gershgorin_bounds(a)
     g = max(abs(lo), abs(hi))
+    g2 = np.sqrt(np.max(np.sum(np.abs(a @ a), axis=1)))
     assert np.all(rho / bounds <= 1.2 * (1 + 1e-6))
-    assert np.all(bounds <= g / 1.2 * (1 + 2e-5))
+    assert np.all(bounds <= g2 / 1.2 * (1 + 1e-4)) and g2 <= g * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x3"])
+def test_first_product_bound_per_submatrix(prec):
+    # the effective scaling b_j after the first product, against the oracle's bounds:
+    # FP64 form: the Collatz-Wielandt bound (two power steps of |A^2|); tensor-core
+    # form without the learned bound: the Gershgorin bound of A^2 (1e-4 margin on it)
+    import oracle.mlp as M
+
+    s = make_workload("water32")
+    mu = 0.1
+    with _ctx(s, prec) as c:
+        c.set_mu(mu)
+        c.build_density()
+        _, _, bounds = c.get_submatrix_info()
+    blocks = [O.gather_submatrix(s.block_size, s.col_ptr, s.row_idx, s.values, j, mu=mu)[0]
+              for j in range(s.block_size.shape[0])]
+    g = np.array([M.gershgorin_radius(a) for a in blocks])
+    rho = np.array([np.max(np.abs(np.linalg.eigvalsh(a))) for a in blocks])
+    if prec == "fp64":
+        ref = np.array([M.power_bound_ratio(a) for a in blocks]) * g / 1.2
+        rel = bounds / ref - 1.0
+        assert np.all(np.abs(rel) <= 1e-10), (rel.min(), rel.max())
+    else:
+        ref = np.array([M.square_bound_ratio(a) for a in blocks]) * g / 1.2
+        rel = bounds / ref - 1.0
+        assert np.all((rel >= 5e-5 - 2e-5) & (rel <= 5e-5 + 2e-5)), (rel.min(), rel.max())
+    assert np.all(rho / bounds <= 1.2)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp16x3"])

@@ -74,6 +74,7 @@ def test_features_and_labels_of_a_diagonal_matrix():
                            0.0, 0.0, 4 / 256, np.mean(d) / g, 0.7])
     assert np.allclose(M.labels(a), [1.0, 0.3 / 0.9])
     assert abs(M.square_bound_ratio(a) - 1.0) < 1e-15  # diagonal: the bound from A^2 is exact
+    assert abs(M.power_bound_ratio(a) - 1.0) < 1e-15
 
 
 def test_labels_and_bound_ratios_are_ordered():
@@ -94,3 +95,26 @@ def test_init_is_seeded_and_scaled():
     assert np.array_equal(a, b)
     w1, b1, w2, b2, w3, b3 = M.unpack(a)
     assert np.all(np.abs(w1) <= 1 / 3) and np.all(b1 == 0) and np.all(np.abs(w2) <= 1 / 8)
+
+
+def test_power_bound_is_between_rho_and_the_square_bound():
+    rng = np.random.default_rng(8)
+    for n in [5, 40, 120]:
+        eigs = np.concatenate([-rng.uniform(0.1, 1.0, n // 2), rng.uniform(0.1, 1.0, n - n // 2)])
+        a = spectrum_matrix(n, eigs, seed=3 * n)
+        g = M.gershgorin_radius(a)
+        rho = np.max(np.abs(eigs)) / g
+        p0, p2 = M.power_bound_ratio(a, steps=0), M.power_bound_ratio(a)
+        assert abs(p0 - M.square_bound_ratio(a)) < 1e-14   # w = 1 alone is the Gershgorin bound of A^2
+        assert rho <= p2 * (1 + 1e-12) and p2 <= p0 * (1 + 1e-12)
+        # many power steps converge to the Perron root of |A^2| (brute force by eigvalsh)
+        perron = np.sqrt(np.max(np.linalg.eigvalsh(np.abs(a @ a)))) / g
+        assert abs(M.power_bound_ratio(a, steps=400) - perron) <= 1e-6 * perron
+        assert perron <= p2 * (1 + 1e-12)
+
+
+def test_power_bound_with_a_zero_row():
+    a = np.zeros((3, 3))
+    a[0, 1] = a[1, 0] = 0.5
+    # A^2 = diag(0.25, 0.25, 0): rho(A) = 0.5 = G, the bound is exact
+    assert abs(M.power_bound_ratio(a) - 1.0) < 1e-15
