@@ -136,6 +136,99 @@ def _oracle_sample(sysm, eps, mu, n_cols, workers, seed=0):
     return dt, cols, res, (cp, ri)
 
 
+def learned_scaling(args, stream):
+    """MD-like trajectory: train the bound model on the first snapshots, compare on the rest.
+
+    The 1024-molecule system takes cumulative N(0, 0.05 A) position steps; one
+    context holds the trajectory (the pair pattern of the first snapshot, the
+    block filter prunes per snapshot).  Training snapshots: solve mu, then
+    collect features and Lanczos labels at that mu.  Evaluation snapshots are
+    timed (values already on the device) with the model off and on.
+    """
+    import torch
+
+    import oracle as O
+    from paper_2205_14741_gb300 import SubmatrixDensity
+    from synth import WORKLOADS, md_trajectory
+
+    w = WORKLOADS["md1024"]
+    n_snap = args.learned_snapshots
+    n_train = n_snap // 2
+    t0 = time.perf_counter()
+    snaps = list(md_trajectory(w["n_mol"], w["b"], w["r_c"], w["ell"], w["seed"], n_snap, fixed_pattern=True))
+    t_gen = time.perf_counter() - t0
+    ctx = SubmatrixDensity.from_system(snaps[0], stream=stream.cuda_stream)
+    ctx.set_filter_threshold(w["eps"])
+    ctx.set_precision(args.precision)
+    ctx.set_electron_count(w["n_e"], max_steps=30, tol=1e-2)
+    ctx.bound_model_init(w["seed"])
+    t0 = time.perf_counter()
+    for sysm in snaps[:n_train]:
+        ctx.set_values(sysm.values)
+        ctx.solve_mu()
+        ctx.set_mu(ctx.get_trace()[2])
+        ctx.bound_model_collect(48)
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = ctx.bound_model_train(epochs=args.learned_epochs, batch=256, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    vals = [torch.from_numpy(sysm.values).to("cuda") for sysm in snaps[n_train:]]
+
+    def evaluate(model_on):
+        ctx.set_bound_model(model_on)
+        ctx.set_values(snaps[n_train - 1].values)
+        ctx.solve_mu()
+        torch.cuda.synchronize()
+        ms, its, fb, ns_ms, builds = 0.0, [], 0, 0.0, 0
+        for v in vals:
+            ctx.reset_counters()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.set_values(v, on_device=True)
+            ctx.solve_mu()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            st = ctx.get_stats()
+            its.append(ctx.get_submatrix_info()[1].copy())
+            fb += st["n_bound_fallback"]
+            ns_ms += st["ns_ms_total"]
+            builds += st["bisection_steps"]
+        its = np.concatenate(its)
+        return {"dm_per_s": len(vals) / (ms / 1e3), "ms_per_step": ms / len(vals), "ns_ms_per_step": ns_ms / len(vals),
+                "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+                "fallback_rate": fb / its.shape[0], "builds_per_step": builds / len(vals)}, ctx.get_density()
+
+    off, d_off = evaluate(False)
+    on, d_on = evaluate(True)
+    mu = ctx.get_trace()[2]
+    last = snaps[-1]
+    _, cols, res, _ = _oracle_sample(last, w["eps"], mu, 32, os.cpu_count() or 1)
+    offs = O.block_value_offsets(last.block_size, last.col_ptr, last.row_idx)
+    cp_f, ri_f, _, keep = O.filter_blocks(last.block_size, last.col_ptr, last.row_idx, last.values, w["eps"])
+    off_f = O.block_value_offsets(last.block_size, cp_f, ri_f)
+    kf = np.cumsum(keep) - 1
+    err = 0.0
+    for j in cols:  # compare the kept blocks of each sampled column (dropped blocks are zero on both sides)
+        for k in range(last.col_ptr[j], last.col_ptr[j + 1]):
+            a = d_on[offs[k]:offs[k + 1]]
+            b = res.values[off_f[kf[k]]:off_f[kf[k] + 1]] if keep[k] else np.zeros_like(a)
+            err = max(err, float(np.max(np.abs(a - b))))
+    ctx.close()
+    return {
+        "workload": f"{w['n_mol']}-molecule trajectory, {n_snap} snapshots, cumulative N(0, 0.05 A) steps; "
+                    f"model trained on the first {n_train} (features and 48-step Lanczos labels at the solved mu), "
+                    f"evaluated on the last {n_snap - n_train}",
+        "train_loss": loss, "train_samples": n_train * w["n_mol"], "epochs": args.learned_epochs,
+        "seconds": {"generate": t_gen, "collect": t_collect, "train": t_train},
+        "without_model": off, "with_model": on,
+        "iters_saved_frac": 1.0 - on["iters_mean"] / off["iters_mean"],
+        "speedup_with_model": on["dm_per_s"] / off["dm_per_s"],
+        "d_max_abs_err_vs_oracle_last_snapshot": err, "oracle_columns": len(cols),
+        "max_abs_diff_with_vs_without": float(np.max(np.abs(d_on - d_off))),
+    }
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -321,6 +414,10 @@ def run_ours(args):
                "sample": f"{len(cols)} of {sysm.n_blocks} block columns at the GPU's final mu, "
                          f"time x{sysm.n_blocks}/{len(cols)} x{builds} bisection build(s)"}
 
+    learned = None
+    if rank == 0 and world == 1 and args.learned_snapshots > 0:
+        learned = learned_scaling(args, stream)
+
     if rank == 0:
         out = {
             "metric": METRIC,
@@ -342,6 +439,7 @@ def run_ours(args):
             "gpu_launches": gpu_launches,
             "iters": {"min": st["iters_min"], "max": st["iters_max"], "mean": st["iters_mean"]},
             "dims": {"min": st["dim_min"], "max": st["dim_max"], "mean": st["dim_mean"]},
+            "learned_scaling": learned,
         }
         print(json.dumps(out))
     ctx.close()
@@ -362,6 +460,9 @@ def main():
     ap.add_argument("--ref-columns", type=int, default=128)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--learned-snapshots", type=int, default=200,
+                    help="trajectory length of the learned-bound report (0 skips it)")
+    ap.add_argument("--learned-epochs", type=int, default=40)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
