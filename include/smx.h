@@ -195,10 +195,11 @@ smx_status smx_get_stats(smx_ctx* ctx, smx_stats* out);
  * (rho = max |lambda(A)|, delta = min |lambda(A)|).  When enabled, a build
  * starts Newton-Schulz from X0 = A / b with b = rho_hat (1.05) / 1.2; the first
  * product Z = X0^2 gives the guaranteed bound s >= rho(X0) (s^2 =
- * max_r (|Z| w)_r / w_r, the smallest over w = 1 and two power steps of |Z|
- * from it: a Collatz-Wielandt bound on rho(Z)) and the prediction is kept
- * only if s <= 1.6 (the iteration converges for rho(X0) < sqrt 3), otherwise
- * X0 is rescaled by 1.2/s as without the model (counted in n_bound_fallback).
+ * max_r (|Z| w)_r / w_r, the smallest over w = 1 and power steps of |Z| from
+ * it, one in the tensor-core forms and two in FP64: a Collatz-Wielandt bound
+ * on rho(Z)) and the prediction is kept only if s <= 1.7 (the iteration
+ * converges for rho(X0) < sqrt 3 = 1.732), otherwise X0 is rescaled by 1.2/s
+ * as without the model (counted in n_bound_fallback).
  * Parameters: SMX_BOUND_MODEL_PARAMS floats, layout W1 (64 x 9, row-major),
  * b1 (64), W2 (64 x 64), b2 (64), W3 (2 x 64), b3 (2).  Inference uses the
  * parameters rounded to FP16; training keeps FP32 master weights (Adam,

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
             const double smax = sqrt(best * (1.0 + 1e-12));
             double scale = smax > 0.0 ? 1.2 / smax : 1.0;
             if (a.use_model && smax > 0.0) {  // same rule as the tensor-core kernel
-                if (smax <= 1.6) scale = fmax(1.0, scale);
+                if (smax <= 1.7) scale = fmax(1.0, scale);
                 else if (threadIdx.x == 0) atomicAdd(a.fallbacks, 1);
             }
             const double sc2 = scale * scale;

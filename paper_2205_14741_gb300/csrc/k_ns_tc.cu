@@ -83,6 +83,11 @@ __device__ __forceinline__ float2 unpack2(uint32_t w) {
     else return __half22float2(*reinterpret_cast<__half2*>(&w));
 }
 template <int PREC>
+__device__ __forceinline__ uint16_t to16(float x) {
+    if constexpr (PREC == 3) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    else return __half_as_ushort(__float2half_rn(x));
+}
+template <int PREC>
 __device__ __forceinline__ float from16(uint16_t h) {
     if constexpr (PREC == 3) return __bfloat162float(__ushort_as_bfloat16(h));
     else return __half2float(__ushort_as_half(h));
@@ -133,11 +138,6 @@ __device__ __forceinline__ void load8(const uint16_t* hi, const uint16_t* lo, fl
             v[2 * i + 1] += f.y;
         }
     }
-}
-template <int PREC, int NB>
-__device__ __forceinline__ void load32(const uint16_t* hi, const uint16_t* lo, float (&v)[32]) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) load8<PREC, NB>(hi + 8 * u, lo + 8 * u, *reinterpret_cast<float(*)[8]>(v + 8 * u));
 }
 
 // two TMEM loads (32 columns each), one wait
@@ -235,9 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     // C = A * B over K in [0, kpad), written to buffer zo (rows and columns < kpad).
     // mode 1: zo = 3/2 I - 1/2 A A, residual ||A A - I||_F^2 accumulated;
     // mode 2: zo = oscale * A B;
-    // mode 3: zo = A B and rsum[r] += sum_c |C_rc| (rsum zeroed by the caller);
-    // mode 4: zo = 3/2 c A - 1/2 c^3 A B with c = oscale (the first Newton-Schulz
-    //         step from c A when B = A^2, without forming 3/2 I - 1/2 c^2 B).
+    // mode 3: zo = A B and rsum[r] += sum_c |C_rc| (rsum zeroed by the caller).
     auto gemm = [&](int kpad, int n, int mode, int za, int zb, int zo, float oscale, float* rsum) {
         const int mtiles = (kpad + 127) / 128, ntiles = (kpad + NT - 1) / NT, kchunks = (kpad + 63) / 64;
         if (warp == 0) {
@@ -310,7 +308,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             const int q = warp & 3, half = (warp - 4) >> 2;
             const int lrow = q * 32 + lane;
             float r2 = 0.0f;
-            const float c15 = 1.5f * oscale, c05 = 0.5f * oscale * oscale * oscale;
             for (int mt = 0; mt < mtiles; ++mt)
                 for (int nt = 0; nt < ntiles; ++nt) {
                     const int nn = min(NT, kpad - NT * nt);
@@ -323,8 +320,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     const int row = 128 * mt + lrow;
                     uint16_t* out_hi = ws + static_cast<int64_t>(zo) * buf + static_cast<int64_t>(row) * a.ld;
                     uint16_t* out_lo = out_hi + buf;
-                    const uint16_t* a_hi = ws + static_cast<int64_t>(za) * buf + static_cast<int64_t>(row) * a.ld;
-                    const uint16_t* a_lo = a_hi + buf;
                     float ra = 0.0f;  // mode 3: this thread's share of the row's abs sum
                     for (int c0 = 32 * half; c0 < nn; c0 += 64) {
                         uint32_t raw[32];
@@ -347,11 +342,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                     }
                                     // sum (v - delta)^2 = sum v^2 - 2 v_diag + 1 when the diagonal is here
                                     r2 += (i0 >= 0 && i0 < 32) ? sq - 2.0f * dv + 1.0f : sq;
-                                } else if (mode == 4) {
-                                    float xa[32];
-                                    load32<PREC, NB>(a_hi + col0, a_lo + col0, xa);
-#pragma unroll
-                                    for (int i = 0; i < 32; ++i) y[i] = fmaf(c15, xa[i], -c05 * __uint_as_float(raw[i]));
                                 } else {
 #pragma unroll
                                     for (int i = 0; i < 32; ++i) y[i] = oscale * __uint_as_float(raw[i]);
@@ -361,8 +351,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                     }
                                 }
                             } else {
-                                float xa[32];
-                                if (mode == 4) load32<PREC, NB>(a_hi + col0, a_lo + col0, xa);
 #pragma unroll
                                 for (int i = 0; i < 32; ++i) {
                                     const float v = __uint_as_float(raw[i]);
@@ -372,8 +360,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                         const float e = v - dl;
                                         y[i] = valid ? fmaf(-0.5f, v, 1.5f * dl) : 0.0f;
                                         r2 = valid ? fmaf(e, e, r2) : r2;
-                                    } else if (mode == 4) {
-                                        y[i] = valid ? fmaf(c15, xa[i], -c05 * v) : 0.0f;
                                     } else {
                                         y[i] = valid ? oscale * v : 0.0f;
                                         if (mode == 3) ra += fabsf(y[i]);
@@ -415,6 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         const int j = a.order[job];
         const SubDesc s = a.subs[j];
         const int kpad = (s.n + 31) & ~31;  // MMA extent; TMA moves 64-wide boxes
+
         const int zx0 = slot_z + 0, zx1 = slot_z + 2, zy = slot_z + 4;
 
         // prologue: X0 = (T_j - mu I) / b_j in FP32, zero-padded to kpad x kpad, split hi/lo
@@ -423,24 +410,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             const float* t = a.T + s.t_off;
             uint16_t* xh = ws + static_cast<int64_t>(zx0) * buf;
             uint16_t* xl = xh + buf;
-            const int per_row = kpad / 8;
-            for (int e = tid; e < kpad * per_row; e += blockDim.x) {
-                const int r = e / per_row, c0 = (e - r * per_row) * 8;
-                // rows of T are 16-byte aligned (ld is a multiple of 4) and zero in [n, ld)
-                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-                if (r < s.n) {
-                    const float4* src = reinterpret_cast<const float4*>(t + static_cast<int64_t>(r) * s.ld + c0);
-                    if (c0 + 4 <= s.ld) v0 = src[0];
-                    if (c0 + 8 <= s.ld) v1 = src[1];
-                }
-                const float x[8] = {v0.x * inv_b, v0.y * inv_b, v0.z * inv_b, v0.w * inv_b,
-                                    v1.x * inv_b, v1.y * inv_b, v1.z * inv_b, v1.w * inv_b};
-                uint32_t hw[4], lw[4];
+            const int per_row = kpad / 8, total = kpad * per_row;
+            constexpr int kU = 4;  // loads in flight per thread
+            for (int e0 = tid; e0 < total; e0 += kU * kThreads) {
+                float4 v[kU][2];
 #pragma unroll
-                for (int i = 0; i < 8; i += 2) split2<PREC, NB>(x[i], x[i + 1], hw[i >> 1], lw[i >> 1]);
-                *reinterpret_cast<uint4*>(xh + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                if constexpr (NB == 2)
-                    *reinterpret_cast<uint4*>(xl + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                for (int u = 0; u < kU; ++u) {
+                    const int e = e0 + u * kThreads;
+                    const int r = e / per_row, c0 = (e - r * per_row) * 8;
+                    v[u][0] = v[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    // rows of T are 16-byte aligned (ld is a multiple of 4) and zero in [n, ld)
+                    if (e < total && r < s.n) {
+                        const float4* src = reinterpret_cast<const float4*>(t + static_cast<int64_t>(r) * s.ld + c0);
+                        if (c0 + 4 <= s.ld) v[u][0] = src[0];
+                        if (c0 + 8 <= s.ld) v[u][1] = src[1];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int e = e0 + u * kThreads;
+                    if (e >= total) break;
+                    const int r = e / per_row, c0 = (e - r * per_row) * 8;
+                    const float x[8] = {v[u][0].x * inv_b, v[u][0].y * inv_b, v[u][0].z * inv_b, v[u][0].w * inv_b,
+                                        v[u][1].x * inv_b, v[u][1].y * inv_b, v[u][1].z * inv_b, v[u][1].w * inv_b};
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int i = 0; i < 8; i += 2) split2<PREC, NB>(x[i], x[i + 1], hw[i >> 1], lw[i >> 1]);
+                    *reinterpret_cast<uint4*>(xh + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    if constexpr (NB == 2)
+                        *reinterpret_cast<uint4*>(xl + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
             }
             fence_proxy_async_global();
             if (tid == 0) { conv_s = 0; bad_s = 0; }
@@ -453,79 +452,88 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             if (it == 0) {
                 // A-posteriori scaling.  Z = X0^2; every eigenvalue of X0 satisfies
                 // |lambda|^2 <= s^2 with s^2 the bound on rho(Z) below, so
-                // X0' = (c/s) X0 has all |lambda| <= c = 1.2 < sqrt(3) and the
-                // iteration from X0' is guaranteed to converge.  The step is then
-                // X1 = X0' (3/2 I - 1/2 X0'^2) = 3/2 (c/s) X0 - 1/2 (c/s)^3 X0 Z.
+                // X0' = c X0 with c = 1.2/s has all |lambda| <= 1.2 < sqrt(3) and the
+                // iteration from X0' is guaranteed to converge.  The first step is
+                // X1 = X0' (3/2 I - 1/2 X0'^2) = -1/2 c^3 X0 (Z - 3/c^2 I): only the
+                // diagonal of Z changes before the second product.
                 //
                 // Bound on rho(Z) = rho(X0)^2 (Collatz-Wielandt): for any positive
                 // vector w, rho(Z) <= rho(|Z|) <= max_r (|Z| w)_r / w_r.  w = 1 gives
-                // the Gershgorin bound (the max row sum, from the product's
-                // epilogue); with the learned bound on, two power steps of |Z| from
-                // the row sums tighten it (on water-like submatrices from about
-                // 1.5 rho to 1.3 rho) so that good predictions pass the check.
-                // The power-step vectors live in the (still unused) buffer of X1.
+                // the Gershgorin bound (the max row sum r, from the product's
+                // epilogue); with the learned bound on, one power step (w = r)
+                // tightens it (on water-like submatrices from about 1.5 rho to
+                // 1.35 rho) so that good predictions pass the check.
+                // The row-sum vector lives in the (still unused) buffer of X1.
                 float* wv = reinterpret_cast<float*>(ws + static_cast<int64_t>(zn) * buf);
-                float* wn = wv + kpad;
                 for (int c = tid; c < kpad; c += kThreads) wv[c] = 0.0f;
                 __syncthreads();
                 gemm(kpad, s.n, 3, zx, zx, zy, 1.0f, wv);  // Z = X0^2, wv = row sums of |Z|
                 float rmax = 0.0f;
                 for (int r = tid; r < s.n; r += kThreads) rmax = fmaxf(rmax, wv[r]);
                 rmax = block_max2(rmax, 0.0f).x;
-                float best = rmax, wtop = rmax;
-                const uint16_t* zh = ws + static_cast<int64_t>(zy) * buf;
-                const uint16_t* zl = zh + buf;
-                for (int pass = 0; a.use_model && pass < 2 && best > 0.0f; ++pass) {
+                float best = rmax;
+                uint16_t* zh = ws + static_cast<int64_t>(zy) * buf;
+                uint16_t* zl = zh + buf;
+                if (a.use_model && rmax > 0.0f) {
                     // w > 0: rows that are zero in Z get a tiny positive weight
-                    for (int c = tid; c < s.n; c += kThreads) wv[c] = fmaxf(wv[c], 1e-12f * wtop);
+                    for (int c = tid; c < s.n; c += kThreads) wv[c] = fmaxf(wv[c], 1e-12f * rmax);
                     __syncthreads();
-                    float q = 0.0f, wm = 0.0f;
-                    // wn = |Z| wv, four rows per warp in flight, 8 columns per lane and load
-                    for (int r0 = warp * 4; r0 < s.n; r0 += 4 * (kThreads / 32)) {
-                        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    float q = 0.0f;
+                    // (|Z| w)_r for eight rows per warp at a time, 8 columns per lane and load
+                    constexpr int kR = 8;
+                    for (int r0 = warp * kR; r0 < s.n; r0 += kR * (kThreads / 32)) {
+                        float acc[kR];
+#pragma unroll
+                        for (int u = 0; u < kR; ++u) acc[u] = 0.0f;
                         for (int c = 8 * lane; c < kpad; c += 256) {
                             const float4 w0 = *reinterpret_cast<const float4*>(wv + c);
                             const float4 w1 = *reinterpret_cast<const float4*>(wv + c + 4);
                             const float wc[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                            float zr[kR][8];
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int r = r0 + u;
-                                if (r < s.n) {
-                                    float zr[8];
-                                    load8<PREC, NB>(zh + static_cast<int64_t>(r) * a.ld + c, zl + static_cast<int64_t>(r) * a.ld + c, zr);
-#pragma unroll
-                                    for (int i = 0; i < 8; ++i) acc[u] = fmaf(fabsf(zr[i]), wc[i], acc[u]);
-                                }
+                            for (int u = 0; u < kR; ++u) {
+                                const int r = min(r0 + u, s.n - 1);  // rows past n repeat the last (ignored below)
+                                load8<PREC, NB>(zh + static_cast<int64_t>(r) * a.ld + c, zl + static_cast<int64_t>(r) * a.ld + c, zr[u]);
                             }
+#pragma unroll
+                            for (int u = 0; u < kR; ++u)
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) acc[u] = fmaf(fabsf(zr[u][i]), wc[i], acc[u]);
                         }
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int r = r0 + u;
+                        for (int u = 0; u < kR; ++u) {
                             const float v = warp_sum_f(acc[u]);
-                            if (r < s.n) {
-                                if (lane == 0) wn[r] = v;
-                                q = fmaxf(q, v / wv[r]);
-                                wm = fmaxf(wm, v);
-                            }
+                            if (r0 + u < s.n) q = fmaxf(q, v / wv[r0 + u]);
                         }
                     }
-                    const float2 m2 = block_max2(q, wm);
-                    best = fminf(best, m2.x);
-                    if (!(m2.y > 0.0f)) break;
-                    const float inv = 1.0f / m2.y;
-                    for (int c = tid; c < s.n; c += kThreads) wv[c] = wn[c] * inv;
-                    wtop = 1.0f;
+                    best = fminf(best, block_max2(q, 0.0f).x);
                 }
                 const float smax = sqrtf(best * (1.0f + 1e-4f));  // margin for FP32 summation
                 // Without the learned bound X0 = A / G and X0 is always rescaled to
-                // c / s.  With it, the predicted scaling is kept when the guaranteed
-                // bound allows (s <= 1.6 < sqrt 3) and only enlarged, never shrunk;
-                // otherwise the prediction is discarded for the guaranteed c / s.
+                // c = 1.2 / s.  With it, the predicted scaling is kept when the
+                // guaranteed bound allows (s <= 1.7 < sqrt 3) and only enlarged, never
+                // shrunk; otherwise the prediction is discarded for c = 1.2 / s.
                 float scale = smax > 0.0f ? 1.2f / smax : 1.0f;
                 if (a.use_model && smax > 0.0f) {
-                    if (smax <= 1.6f) scale = fmaxf(1.0f, scale);
+                    if (smax <= 1.7f) scale = fmaxf(1.0f, scale);
                     else if (tid == 0) atomicAdd(a.fallbacks, 1);
                 }
+                // Z_rr -= 3 / c^2 (in place, the split re-done)
+                const float shift = 3.0f / (scale * scale);
+                for (int r = tid; r < s.n; r += kThreads) {
+                    const int64_t o = static_cast<int64_t>(r) * a.ld + r;
+                    float z = from16<PREC>(zh[o]);
+                    if constexpr (NB == 2) z += from16<PREC>(zl[o]);
+                    z -= shift;
+                    if constexpr (NB == 2) {
+                        const float hi = round16<PREC>(z);
+                        zh[o] = to16<PREC>(hi);
+                        zl[o] = to16<PREC>(z - hi);
+                    } else {
+                        zh[o] = to16<PREC>(z);
+                    }
+                }
+                fence_proxy_async_global();
                 if (tid == 0) {
                     // feature of the next snapshot: the Gershgorin bound of A^2, over G
                     const double s0 = sqrt(static_cast<double>(rmax) * (1.0 + 1e-5));
@@ -533,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     a.bound[j] = a.bound[j] / static_cast<double>(scale);  // effective scaling of X0'
                 }
                 __syncthreads();
-                gemm(kpad, s.n, 4, zx, zy, zn, scale, nullptr);  // X1 = 3/2 c X0 - 1/2 c^3 X0 Z
+                gemm(kpad, s.n, 2, zx, zy, zn, -0.5f * scale * scale * scale, nullptr);  // X1 = -c^3/2 X0 (Z - 3/c^2 I)
             } else {
                 gemm(kpad, s.n, 1, zx, zx, zy, 1.0f, nullptr);  // Y = 3/2 I - 1/2 X^2
                 if (tid == 0) {
