@@ -40,6 +40,10 @@ namespace {
 
 constexpr int kThreads = 384;
 constexpr int kEpiWarps = 8;
+// Submatrices with kpad <= kResKpad keep the iterate on chip: X in shared
+// memory (both factors of X X, the B factor of Y X) and Y in tensor memory
+// (the A factor of Y X); only X' goes through L2.
+constexpr int kResKpad = 192;
 constexpr uint32_t kABytes = 128 * 128;  // 128 rows x 64 K x 2 B
 
 template <int PREC>
@@ -140,6 +144,49 @@ __device__ __forceinline__ void load8(const uint16_t* hi, const uint16_t* lo, fl
     }
 }
 
+// 16 consecutive 32-bit TMEM columns of this thread's lane <- r
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// tcgen05.mma kind::f16 with the A operand (M = 128 rows in the 128 lanes, K
+// packed two 16-bit values per 32-bit column) in tensor memory
+__device__ __forceinline__ void tc_mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                              uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(
+            d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
+// MN-major 128-byte-swizzled B descriptor whose 64-column blocks are lbo bytes apart
+__device__ __forceinline__ uint64_t sdesc_mn_sw128_lbo(uint32_t saddr, uint32_t lbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>(lbo >> 4) << 16;
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;
+    d |= static_cast<uint64_t>(1) << 46;
+    d |= static_cast<uint64_t>(2) << 61;
+    return d;
+}
+
+// Orders this thread's generic shared-memory writes before later async-proxy
+// (tensor-core) reads issued after a barrier.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Byte offset of element (r, c) in a row-major matrix image held as 64 x 64
+// boxes in the 128-byte-swizzled layout (what a TMA box load writes), box
+// (row block rb, column block cb) at (cb * RB + rb) * 8 KB.
+__device__ __forceinline__ uint32_t img_offset(int r, int c, int RB) {
+    const int rb = r >> 6, rr = r & 63, cb = c >> 6, cc = c & 63;
+    return static_cast<uint32_t>((cb * RB + rb) * 8192 + rr * 128 + ((((cc >> 3) ^ (rr & 7))) << 4) + (cc & 7) * 2);
+}
+
 // two TMEM loads (32 columns each), one wait
 __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
@@ -173,6 +220,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s, job_s, conv_s, bad_s, p_issued_s, m_consumed_s;
     __shared__ float resid_s[kEpiWarps];
+    __shared__ uint64_t mma_bar, img_bar;
+    __shared__ float rpart_s[3][kResKpad];  // per-part partial row sums (summed in a fixed order)
+    __shared__ float rsum_s[kResKpad], rs2_s[kResKpad];
+    __shared__ int img_pending_s, img_parity_s;
+    __shared__ float resid_s2[kThreads / 32];
     __shared__ float red_s[2][kThreads / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -187,6 +239,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             mbar_init(&tempty[s], kEpiWarps);
         }
         mbar_init(&drain_bar, 1);
+        mbar_init(&mma_bar, 1);
+        mbar_init(&img_bar, 1);
+        img_pending_s = 0;
         abort_s = 0;
         p_issued_s = 0;
         m_consumed_s = 0;
@@ -230,12 +285,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     const int64_t buf = static_cast<int64_t>(a.ld) * a.ld;
     uint16_t* ws = static_cast<uint16_t*>(a.ws);
     const int slot_z = blockIdx.x * 6;
+    uint32_t mma_ph = 0, img_ph = 0;  // completed phases of mma_bar / img_bar (uniform over the CTA)
     const uint32_t idesc_b_mn = 1u << 16;  // B operand MN-major
 
     // C = A * B over K in [0, kpad), written to buffer zo (rows and columns < kpad).
     // mode 1: zo = 3/2 I - 1/2 A A, residual ||A A - I||_F^2 accumulated;
     // mode 2: zo = oscale * A B;
-    // mode 3: zo = A B and rsum[r] += sum_c |C_rc| (rsum zeroed by the caller).
+    // mode 3: zo = A B and rsum[(2 nt + half) kpad + r] = sum of |C_rc| over the columns of
+    //         N tile nt that epilogue half "half" drains (rows r < n).
     auto gemm = [&](int kpad, int n, int mode, int za, int zb, int zo, float oscale, float* rsum) {
         const int mtiles = (kpad + 127) / 128, ntiles = (kpad + NT - 1) / NT, kchunks = (kpad + 63) / 64;
         if (warp == 0) {
@@ -379,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                             }
                         }
                     }
-                    if (mode == 3 && row < n) atomicAdd(rsum + row, ra);
+                    if (mode == 3 && row < n) rsum[(2 * nt + half) * kpad + row] = ra;  // summed in order later
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&tempty[abuf]);
@@ -404,7 +461,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
 
         const int zx0 = slot_z + 0, zx1 = slot_z + 2, zy = slot_z + 4;
 
-        // prologue: X0 = (T_j - mu I) / b_j in FP32, zero-padded to kpad x kpad, split hi/lo
+        // on-chip form: the image of X (hi boxes, then lo boxes) at the start of the stage area
+        const bool resident = kpad <= kResKpad;
+        const int RB = (kpad + 63) >> 6;
+        const uint32_t img_lo_off = static_cast<uint32_t>(RB * RB) * 8192u;
+
+        // prologue: X0 = (T_j - mu I) / b_j in FP32, zero-padded to kpad x kpad, split hi/lo,
+        // into the shared-memory image (on-chip form) or the slot's X buffer
         {
             const float inv_b = static_cast<float>(1.0 / a.bound[j]);
             const float* t = a.T + s.t_off;
@@ -436,17 +499,320 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int i = 0; i < 8; i += 2) split2<PREC, NB>(x[i], x[i + 1], hw[i >> 1], lw[i >> 1]);
-                    *reinterpret_cast<uint4*>(xh + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    if constexpr (NB == 2)
-                        *reinterpret_cast<uint4*>(xl + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    if (resident) {
+                        const uint32_t off = img_offset(r, c0, RB);
+                        *reinterpret_cast<uint4*>(smem + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        if constexpr (NB == 2)
+                            *reinterpret_cast<uint4*>(smem + img_lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    } else {
+                        *reinterpret_cast<uint4*>(xh + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        if constexpr (NB == 2)
+                            *reinterpret_cast<uint4*>(xl + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
                 }
             }
-            fence_proxy_async_global();
+            if (resident) fence_proxy_async_smem();
+            else fence_proxy_async_global();
             if (tid == 0) { conv_s = 0; bad_s = 0; }
             __syncthreads();
         }
 
         int cur = 0, done = 0;
+        if (resident) {
+            // ---------------------------------------------------------------
+            // On-chip form.  Per iteration and 128-row tile t:
+            //   P <- X_t X            (A and B from the shared-memory image)
+            //   P <- A-operand form of Y_t = 3/2 I - 1/2 P (hi, lo packed 16-bit)
+            //   Q <- Y_t X            (A from tensor memory, B from the image)
+            //   X'_t <- Q             into the slot's next X buffer, overlapping the
+            //                         next tile's first product; the last tile goes
+            //                         straight into the image, the others are loaded
+            //                         back by TMA (the image is B until then).
+            // Y X = X Y (Y is a polynomial in X).  Iteration 0 first forms
+            // Z = X0^2 for every tile to bound rho(Z), then runs the same steps
+            // with A = Z - (3/c^2) I and X'_t = -(c^3/2) Q.  All 12 warps share the
+            // tensor-memory passes: warp w serves lanes 32 (w mod 4) and the
+            // 32-column chunks c0 = 32 (w / 4) + 96 k.
+            // ---------------------------------------------------------------
+            const uint32_t P = tmem_base, Q = tmem_base + 256;
+            const int mtiles = (kpad + 127) >> 7;
+            const int ksteps = kpad >> 4;
+            const uint32_t idesc = idesc_f16(128, kpad, C::kFmt) | idesc_b_mn;
+            const uint32_t img_hi = smem_u32(smem), img_lo = img_hi + img_lo_off;
+            const uint32_t lbo = static_cast<uint32_t>(RB) * 8192u;
+            const int q = warp & 3, part = warp >> 2;
+            const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
+            auto issue_xx = [&](int t, uint32_t d) {  // d <- X_t X
+                for (int kk = 0; kk < ksteps; ++kk) {
+                    const uint32_t aoff = static_cast<uint32_t>(((kk >> 2) * RB + 2 * t) * 8192 + (kk & 3) * 32);
+                    const uint32_t boff = static_cast<uint32_t>((kk >> 2) * 8192 + (kk & 3) * 2048);
+                    const uint64_t ah = sdesc_sw128(img_hi + aoff), bh = sdesc_mn_sw128_lbo(img_hi + boff, lbo);
+                    tc_mma_f16(d, ah, bh, idesc, kk ? 1u : 0u);
+                    if constexpr (NB == 2) {
+                        tc_mma_f16(d, ah, sdesc_mn_sw128_lbo(img_lo + boff, lbo), idesc, 1u);
+                        tc_mma_f16(d, sdesc_sw128(img_lo + aoff), bh, idesc, 1u);
+                    }
+                }
+            };
+            // A in tensor memory from column at: per 32 K values, 16 columns hi then 16 lo
+            auto issue_yx = [&](uint32_t at, uint32_t d) {  // d <- A X
+                for (int kk = 0; kk < ksteps; ++kk) {
+                    const uint32_t boff = static_cast<uint32_t>((kk >> 2) * 8192 + (kk & 3) * 2048);
+                    const uint32_t ah = at + 32 * (kk >> 1) + 8 * (kk & 1);
+                    const uint64_t bh = sdesc_mn_sw128_lbo(img_hi + boff, lbo);
+                    tc_mma_f16_ta(d, ah, bh, idesc, kk ? 1u : 0u);
+                    if constexpr (NB == 2) {
+                        tc_mma_f16_ta(d, ah, sdesc_mn_sw128_lbo(img_lo + boff, lbo), idesc, 1u);
+                        tc_mma_f16_ta(d, ah + 16, bh, idesc, 1u);
+                    }
+                }
+            };
+            auto mma_wait = [&]() {  // all threads
+                mbar_wait(&mma_bar, mma_ph & 1u, &abort_s, a.status);
+                ++mma_ph;
+                tc_fence_after();
+            };
+            // convert: accumulator at acc -> A operand in place (each 32-column chunk becomes
+            // 16 columns of packed hi pairs and 16 of lo pairs);
+            // cmode 0: Y = 3/2 I - 1/2 C with the residual ||C - I||_F^2; cmode 1: C - shift I
+            auto convert = [&](int t, uint32_t acc, int cmode, float shift, float& r2) {
+                const int row = 128 * t + 32 * q + lane;
+#pragma unroll 1
+                for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
+                    uint32_t raw[32];
+                    tmem_ld32_issue(acc + lane_off + c0, raw);
+                    tmem_wait_ld();
+                    float y[32];
+                    const int i0 = row - c0;  // the diagonal's position in this chunk, if 0 <= i0 < 32
+                    if (row < s.n && c0 + 32 <= s.n) {
+                        if (cmode == 0) {
+                            float sq = 0.0f, dv = 0.0f;
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                const float v = __uint_as_float(raw[i]);
+                                sq = fmaf(v, v, sq);
+                                y[i] = -0.5f * v;
+                                if (i == i0) { y[i] += 1.5f; dv = v; }
+                            }
+                            r2 += (i0 >= 0 && i0 < 32) ? sq - 2.0f * dv + 1.0f : sq;
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) y[i] = __uint_as_float(raw[i]) - (i == i0 ? shift : 0.0f);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const float v = __uint_as_float(raw[i]);
+                            const bool valid = row < s.n && c0 + i < s.n;
+                            const float dl = (i == i0) ? 1.0f : 0.0f;
+                            if (cmode == 0) {
+                                const float e = v - dl;
+                                y[i] = valid ? fmaf(-0.5f, v, 1.5f * dl) : 0.0f;
+                                r2 = valid ? fmaf(e, e, r2) : r2;
+                            } else {
+                                y[i] = valid ? fmaf(-shift, dl, v) : 0.0f;
+                            }
+                        }
+                    }
+                    uint32_t hw[16], lw[16];
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
+                    tmem_st16(acc + lane_off + c0, hw);
+                    if constexpr (NB == 2) tmem_st16(acc + lane_off + c0 + 16, lw);
+                }
+                tmem_wait_st();
+            };
+            // drain: X'_t = alpha C (zero outside n x n) -> rows of buffer zo, or into the image
+            auto drain = [&](int t, uint32_t acc, float alpha, int zo, bool to_image) {
+                const int row = 128 * t + 32 * q + lane;
+                uint16_t* out_hi = ws + static_cast<int64_t>(zo) * buf + static_cast<int64_t>(row) * a.ld;
+                uint16_t* out_lo = out_hi + buf;
+#pragma unroll 1
+                for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
+                    uint32_t raw[32];
+                    tmem_ld32_issue(acc + lane_off + c0, raw);
+                    tmem_wait_ld();
+                    if (row < kpad) {
+                        float y[32];
+                        if (row < s.n && c0 + 32 <= s.n) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) y[i] = alpha * __uint_as_float(raw[i]);
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                y[i] = (row < s.n && c0 + i < s.n) ? alpha * __uint_as_float(raw[i]) : 0.0f;
+                        }
+                        uint32_t hw[16], lw[16];
+#pragma unroll
+                        for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
+                        if (to_image) {
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const uint32_t off = img_offset(row, c0 + 8 * u, RB);
+                                *reinterpret_cast<uint4*>(smem + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                                if constexpr (NB == 2)
+                                    *reinterpret_cast<uint4*>(smem + img_lo_off + off) =
+                                        make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
+                            }
+                        } else {
+                            uint4* dh = reinterpret_cast<uint4*>(out_hi + c0);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) dh[u] = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                            if constexpr (NB == 2) {
+                                uint4* dlo = reinterpret_cast<uint4*>(out_lo + c0);
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) dlo[u] = make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
+                            }
+                        }
+                    }
+                }
+            };
+            // scan: rpart_s[part][row] = sum_c |C_rc| w_c over this thread's columns (w = 1 when null)
+            auto scan = [&](int t, uint32_t acc, const float* w) {
+                const int row = 128 * t + 32 * q + lane;
+                float sum = 0.0f;
+#pragma unroll 1
+                for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
+                    uint32_t raw[32];
+                    tmem_ld32_issue(acc + lane_off + c0, raw);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int c = c0 + i;
+                        if (row < s.n && c < s.n) sum = fmaf(fabsf(__uint_as_float(raw[i])), w ? w[c] : 1.0f, sum);
+                    }
+                }
+                if (row < s.n) rpart_s[part][row] = sum;
+            };
+            // out[r] = sum of the parts' partials, in part order (deterministic); after a barrier
+            auto gather_parts = [&](float* out) {
+                __syncthreads();
+                for (int r = tid; r < s.n; r += kThreads) out[r] = (rpart_s[0][r] + rpart_s[1][r]) + rpart_s[2][r];
+                __syncthreads();
+            };
+
+            for (int it = 0; it < a.max_iter; ++it) {
+                const int zn = cur ? zx0 : zx1;
+                float alpha = 1.0f, shift = 0.0f;
+                int cmode = 0;
+                if (it == 0) {
+                    // Z_t = X0_t X0 for every tile; the bound on rho(Z) as in the streamed form
+                    for (int r = tid; r < kpad; r += kThreads) rpart_s[0][r] = rpart_s[1][r] = rpart_s[2][r] = 0.0f;
+                    if (warp == 1 && lane == 0) {
+                        tc_fence_after();
+                        issue_xx(0, P);
+                        if (mtiles > 1) issue_xx(1, Q);
+                        tc_commit(&mma_bar);
+                    }
+                    mma_wait();
+                    __syncthreads();
+                    if (*abortp) break;
+                    scan(0, P, nullptr);
+                    if (mtiles > 1) scan(1, Q, nullptr);
+                    gather_parts(rsum_s);
+                    float rmax = 0.0f;
+                    for (int r = tid; r < s.n; r += kThreads) rmax = fmaxf(rmax, rsum_s[r]);
+                    rmax = block_max2(rmax, 0.0f).x;
+                    float best = rmax;
+                    if (a.use_model && rmax > 0.0f) {
+                        // one power step: w = the row sums (floored to stay positive)
+                        for (int r = tid; r < s.n; r += kThreads) rsum_s[r] = fmaxf(rsum_s[r], 1e-12f * rmax);
+                        __syncthreads();
+                        scan(0, P, rsum_s);
+                        if (mtiles > 1) scan(1, Q, rsum_s);
+                        gather_parts(rs2_s);
+                        float qm = 0.0f;
+                        for (int r = tid; r < s.n; r += kThreads) qm = fmaxf(qm, rs2_s[r] / rsum_s[r]);
+                        best = fminf(best, block_max2(qm, 0.0f).x);
+                    }
+                    const float smax = sqrtf(best * (1.0f + 1e-4f));  // margin for FP32 summation
+                    float scale = smax > 0.0f ? 1.2f / smax : 1.0f;
+                    if (a.use_model && smax > 0.0f) {
+                        if (smax <= 1.7f) scale = fmaxf(1.0f, scale);
+                        else if (tid == 0) atomicAdd(a.fallbacks, 1);
+                    }
+                    if (tid == 0) {
+                        const double s0 = sqrt(static_cast<double>(rmax) * (1.0 + 1e-5));
+                        a.sq_ratio[j] = static_cast<float>(s0 * a.bound[j] / a.gersh[j]);
+                        a.bound[j] = a.bound[j] / static_cast<double>(scale);
+                    }
+                    shift = 3.0f / (scale * scale);
+                    alpha = -0.5f * scale * scale * scale;
+                    cmode = 1;
+                    tc_fence_before();
+                    __syncthreads();
+                }
+                float r2 = 0.0f;
+                bool last = false;  // this iteration ends the submatrix (known after the last conversion)
+                for (int t = 0; t < mtiles; ++t) {
+                    const bool g1 = !(it == 0 && t == 0);  // Z_0 is already in P
+                    if (g1 && warp == 1 && lane == 0) {
+                        tc_fence_after();
+                        issue_xx(t, P);
+                        tc_commit(&mma_bar);
+                    }
+                    if (t > 0) drain(t - 1, Q, alpha, zn, false);  // overlaps the product
+                    if (g1) mma_wait();
+                    tc_fence_before();
+                    __syncthreads();
+                    if (*abortp) break;
+                    convert(t, P, cmode, shift, r2);
+                    if (t == mtiles - 1) {
+                        r2 = warp_sum_f(r2);
+                        if (lane == 0) resid_s2[warp] = r2;
+                    }
+                    tc_fence_before();
+                    __syncthreads();
+                    if (warp == 1 && lane == 0) {
+                        tc_fence_after();
+                        issue_yx(P, Q);
+                        tc_commit(&mma_bar);
+                    }
+                    if (t == mtiles - 1 && tid == 0) {  // convergence of this step, from ||X^2 - I||_F
+                        if (it > 0) {
+                            double rr = 0.0;
+                            for (int w = 0; w < kThreads / 32; ++w) rr += resid_s2[w];
+                            if (!isfinite(rr)) bad_s = 1;
+                            else if (sqrt(rr) <= a.tau) conv_s = 1;
+                        }
+                    }
+                    mma_wait();
+                    __syncthreads();
+                    if (*abortp) break;
+                }
+                if (*abortp) break;
+                last = conv_s || bad_s || it + 1 == a.max_iter;
+                // the last tile: into the image when the iteration continues, else to the X buffer
+                drain(mtiles - 1, Q, alpha, zn, !last);
+                if (last) fence_proxy_async_global();
+                else fence_proxy_async_smem();
+                if (!last && mtiles > 1) fence_proxy_async_global();
+                tc_fence_before();
+                __syncthreads();
+                cur ^= 1;
+                done = it + 1;
+                if (last) break;
+                if (mtiles > 1) {
+                    // the earlier tiles' rows of X' back into the image (row blocks < 2 (mtiles - 1))
+                    const int rbs = 2 * (mtiles - 1);
+                    if (tid == 0) {
+                        img_pending_s = 1;
+                        img_parity_s = static_cast<int>(img_ph & 1u);
+                        mbar_arrive_expect_tx(&img_bar, static_cast<uint32_t>(NB * RB * rbs) * 8192u);
+                        for (int b = 0; b < NB; ++b)
+                            for (int cb = 0; cb < RB; ++cb)
+                                for (int rb = 0; rb < rbs; ++rb)
+                                    tma_load_3d(smem + b * img_lo_off + (cb * RB + rb) * 8192, &tmap, 64 * cb, 64 * rb, zn + b,
+                                                &img_bar);
+                    }
+                    mbar_wait(&img_bar, img_ph & 1u, &abort_s, a.status);  // on failure the abort flag is raised
+                    ++img_ph;
+                    __syncthreads();
+                    if (*abortp) break;
+                    if (tid == 0) img_pending_s = 0;
+                }
+            }
+        } else {
         for (int it = 0; it < a.max_iter; ++it) {
             const int zx = cur ? zx1 : zx0, zn = cur ? zx0 : zx1;
             if (it == 0) {
@@ -465,9 +831,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 // 1.35 rho) so that good predictions pass the check.
                 // The row-sum vector lives in the (still unused) buffer of X1.
                 float* wv = reinterpret_cast<float*>(ws + static_cast<int64_t>(zn) * buf);
-                for (int c = tid; c < kpad; c += kThreads) wv[c] = 0.0f;
+                float* wparts = wv + kpad;  // 2 per N tile, kpad each
+                const int nparts = 2 * ((kpad + NT - 1) / NT);
+                for (int c = tid; c < nparts * kpad; c += kThreads) wparts[c] = 0.0f;
                 __syncthreads();
-                gemm(kpad, s.n, 3, zx, zx, zy, 1.0f, wv);  // Z = X0^2, wv = row sums of |Z|
+                gemm(kpad, s.n, 3, zx, zx, zy, 1.0f, wparts);  // Z = X0^2 and partial row sums of |Z|
+                for (int r = tid; r < kpad; r += kThreads) {  // wv = row sums of |Z|, parts added in order
+                    float sum = 0.0f;
+                    for (int p = 0; p < nparts; ++p) sum += wparts[p * kpad + r];
+                    wv[r] = sum;
+                }
+                __syncthreads();
                 float rmax = 0.0f;
                 for (int r = tid; r < s.n; r += kThreads) rmax = fmaxf(rmax, wv[r]);
                 rmax = block_max2(rmax, 0.0f).x;
@@ -556,6 +930,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             done = it + 1;
             if (conv_s || bad_s || *abortp) break;
         }
+        }  // streamed form
         if (*abortp) break;
         if (tid == 0) {
             a.iters[j] = done;
@@ -585,6 +960,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     if (*abortp && tid == 0) {
         for (int it = m_consumed_s; it < p_issued_s; ++it)
             mbar_wait_plain(&full_bar[it % S], (it / S) & 1, 1u << 20);
+        if (img_pending_s) mbar_wait_plain(&img_bar, static_cast<uint32_t>(img_parity_s), 1u << 20);
     }
     if (*abortp && warp == 1 && lane == 0) {
         tc_commit(&drain_bar);
