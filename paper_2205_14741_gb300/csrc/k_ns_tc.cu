@@ -144,15 +144,18 @@ __device__ __forceinline__ void load8(const uint16_t* hi, const uint16_t* lo, fl
     }
 }
 
-// 16 consecutive 32-bit TMEM columns of this thread's lane <- r
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// 32 consecutive 32-bit TMEM columns of this thread's lane <- r
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
         "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
         : "memory");
 }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // tcgen05.mma kind::f16 with the A operand (M = 128 rows in the 128 lanes, K
 // packed two 16-bit values per 32-bit column) in tensor memory
@@ -572,53 +575,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 ++mma_ph;
                 tc_fence_after();
             };
-            // convert: accumulator at acc -> A operand in place (each 32-column chunk becomes
-            // 16 columns of packed hi pairs and 16 of lo pairs);
-            // cmode 0: Y = 3/2 I - 1/2 C with the residual ||C - I||_F^2; cmode 1: C - shift I
-            auto convert = [&](int t, uint32_t acc, int cmode, float shift, float& r2) {
+            // Tensor-memory passes: thread (warp w, lane) owns row 128 t + 32 (w mod 4) + lane and
+            // the 32-column chunks c0 = 32 (w / 4) + 96 k of the tile.
+            //
+            // convert: accumulator at acc -> A = C - shift I in place, each 32-column chunk becoming
+            // 16 columns of packed hi pairs and 16 of lo pairs; with resid, r2 += ||C - I||_F^2 over
+            // the thread's entries (rows and columns < n; zero elsewhere)
+            auto convert = [&](int t, uint32_t acc, float shift, bool resid, float& r2) {
                 const int row = 128 * t + 32 * q + lane;
 #pragma unroll 1
                 for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + lane_off + c0, raw);
                     tmem_wait_ld();
+                    const int i0 = row - c0;
                     float y[32];
-                    const int i0 = row - c0;  // the diagonal's position in this chunk, if 0 <= i0 < 32
-                    if (row < s.n && c0 + 32 <= s.n) {
-                        if (cmode == 0) {
-                            float sq = 0.0f, dv = 0.0f;
+                    if (row < s.n && c0 + 32 <= s.n && !(i0 >= 0 && i0 < 32)) {
+                        float sq = 0.0f;
 #pragma unroll
-                            for (int i = 0; i < 32; ++i) {
-                                const float v = __uint_as_float(raw[i]);
-                                sq = fmaf(v, v, sq);
-                                y[i] = -0.5f * v;
-                                if (i == i0) { y[i] += 1.5f; dv = v; }
-                            }
-                            r2 += (i0 >= 0 && i0 < 32) ? sq - 2.0f * dv + 1.0f : sq;
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) y[i] = __uint_as_float(raw[i]) - (i == i0 ? shift : 0.0f);
+                        for (int i = 0; i < 32; ++i) {
+                            y[i] = __uint_as_float(raw[i]);
+                            sq = fmaf(y[i], y[i], sq);
                         }
+                        if (resid) r2 += sq;
                     } else {
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
                             const float v = __uint_as_float(raw[i]);
                             const bool valid = row < s.n && c0 + i < s.n;
                             const float dl = (i == i0) ? 1.0f : 0.0f;
-                            if (cmode == 0) {
-                                const float e = v - dl;
-                                y[i] = valid ? fmaf(-0.5f, v, 1.5f * dl) : 0.0f;
-                                r2 = valid ? fmaf(e, e, r2) : r2;
-                            } else {
-                                y[i] = valid ? fmaf(-shift, dl, v) : 0.0f;
-                            }
+                            const float e = v - dl;
+                            y[i] = valid ? fmaf(-shift, dl, v) : 0.0f;
+                            if (resid) r2 = valid ? fmaf(e, e, r2) : r2;
                         }
                     }
-                    uint32_t hw[16], lw[16];
+                    uint32_t w[32];
 #pragma unroll
-                    for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
-                    tmem_st16(acc + lane_off + c0, hw);
-                    if constexpr (NB == 2) tmem_st16(acc + lane_off + c0 + 16, lw);
+                    for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], w[i >> 1], w[16 + (i >> 1)]);
+                    tmem_st32(acc + lane_off + c0, w);
                 }
                 tmem_wait_st();
             };
@@ -632,37 +626,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + lane_off + c0, raw);
                     tmem_wait_ld();
-                    if (row < kpad) {
-                        float y[32];
-                        if (row < s.n && c0 + 32 <= s.n) {
+                    if (row >= kpad) continue;
+                    float y[32];
+                    if (row < s.n && c0 + 32 <= s.n) {
 #pragma unroll
-                            for (int i = 0; i < 32; ++i) y[i] = alpha * __uint_as_float(raw[i]);
-                        } else {
+                        for (int i = 0; i < 32; ++i) y[i] = alpha * __uint_as_float(raw[i]);
+                    } else {
 #pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                y[i] = (row < s.n && c0 + i < s.n) ? alpha * __uint_as_float(raw[i]) : 0.0f;
+                        for (int i = 0; i < 32; ++i)
+                            y[i] = (row < s.n && c0 + i < s.n) ? alpha * __uint_as_float(raw[i]) : 0.0f;
+                    }
+                    uint32_t hw[16], lw[16];
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
+                    if (to_image) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const uint32_t off = img_offset(row, c0 + 8 * u, RB);
+                            *reinterpret_cast<uint4*>(smem + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                            if constexpr (NB == 2)
+                                *reinterpret_cast<uint4*>(smem + img_lo_off + off) =
+                                    make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
                         }
-                        uint32_t hw[16], lw[16];
+                    } else {
+                        uint4* dh = reinterpret_cast<uint4*>(out_hi + c0);
 #pragma unroll
-                        for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
-                        if (to_image) {
+                        for (int u = 0; u < 4; ++u) dh[u] = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                        if constexpr (NB == 2) {
+                            uint4* dlo = reinterpret_cast<uint4*>(out_lo + c0);
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const uint32_t off = img_offset(row, c0 + 8 * u, RB);
-                                *reinterpret_cast<uint4*>(smem + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
-                                if constexpr (NB == 2)
-                                    *reinterpret_cast<uint4*>(smem + img_lo_off + off) =
-                                        make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
-                            }
-                        } else {
-                            uint4* dh = reinterpret_cast<uint4*>(out_hi + c0);
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) dh[u] = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
-                            if constexpr (NB == 2) {
-                                uint4* dlo = reinterpret_cast<uint4*>(out_lo + c0);
-#pragma unroll
-                                for (int u = 0; u < 4; ++u) dlo[u] = make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
-                            }
+                            for (int u = 0; u < 4; ++u) dlo[u] = make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
                         }
                     }
                 }
@@ -693,8 +686,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
 
             for (int it = 0; it < a.max_iter; ++it) {
                 const int zn = cur ? zx0 : zx1;
-                float alpha = 1.0f, shift = 0.0f;
-                int cmode = 0;
+                // A = Z - shift I and X' = alpha A X: shift = 3, alpha = -1/2 (Y = 3/2 I - 1/2 Z);
+                // at iteration 0 shift = 3/c^2, alpha = -c^3/2 (the a-posteriori scaling c)
+                float alpha = -0.5f, shift = 3.0f;
                 if (it == 0) {
                     // Z_t = X0_t X0 for every tile; the bound on rho(Z) as in the streamed form
                     for (int r = tid; r < kpad; r += kThreads) rpart_s[0][r] = rpart_s[1][r] = rpart_s[2][r] = 0.0f;
@@ -738,7 +732,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     }
                     shift = 3.0f / (scale * scale);
                     alpha = -0.5f * scale * scale * scale;
-                    cmode = 1;
                     tc_fence_before();
                     __syncthreads();
                 }
@@ -756,7 +749,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     tc_fence_before();
                     __syncthreads();
                     if (*abortp) break;
-                    convert(t, P, cmode, shift, r2);
+                    convert(t, P, shift, it > 0, r2);
                     if (t == mtiles - 1) {
                         r2 = warp_sum_f(r2);
                         if (lane == 0) resid_s2[warp] = r2;
