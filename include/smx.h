@@ -134,6 +134,13 @@ smx_status smx_set_values(smx_ctx* ctx, const double* values, int32_t on_device)
  * eps >= 0.  Errors: SMX_ERR_ARG. */
 smx_status smx_set_filter_threshold(smx_ctx* ctx, double eps);
 
+/* Upper bound (bytes, >= 1 MiB) on the device staging of the gathered
+ * submatrices T_j - mu I (counted as FP64).  Block columns are processed in
+ * consecutive chunks whose staging fits; one chunk when everything fits
+ * (default 24 GiB).  Results do not depend on the chunking.  Errors:
+ * SMX_ERR_ARG. */
+smx_status smx_set_staging_limit(smx_ctx* ctx, uint64_t bytes);
+
 /* Fixed chemical potential mu (Eq. 14) for smx_build_density.  Errors: SMX_ERR_ARG (non-finite). */
 smx_status smx_set_mu(smx_ctx* ctx, double mu);
 

@@ -97,6 +97,9 @@ class SubmatrixDensity:
     def set_filter_threshold(self, eps: float):
         check(self._lib.smx_set_filter_threshold(self._ctx, float(eps)), "smx_set_filter_threshold")
 
+    def set_staging_limit(self, nbytes: int):
+        check(self._lib.smx_set_staging_limit(self._ctx, C.c_uint64(int(nbytes))), "smx_set_staging_limit")
+
     def set_mu(self, mu: float):
         check(self._lib.smx_set_mu(self._ctx, float(mu)), "smx_set_mu")
 

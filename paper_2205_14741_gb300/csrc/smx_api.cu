@@ -98,6 +98,11 @@ struct smx_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ns_events;  // pool, one pair per pending launch
     size_t ns_pending = 0;
 
+    // staging of the submatrices T_j in chunks of consecutive block columns
+    size_t staging_limit = size_t(24) << 30;  // bytes (FP64 elements)
+    std::vector<int32_t> chunk_start;         // chunk c = block columns [chunk_start[c], chunk_start[c + 1])
+    int64_t t_chunk_max = 0;                  // elements of the largest chunk
+
     // learned spectral bound
     bool model_ready = false, model_on = false, sq_valid = false;
     int adam_t = 0;
@@ -247,6 +252,9 @@ static smx_status analyse(smx_ctx* c) {
     c->max_nblk = 0;
     c->max_n = 0;
     int64_t t_off = 0, x_off = 0;
+    const int64_t chunk_elems = std::max<int64_t>(1, static_cast<int64_t>(c->staging_limit / sizeof(double)));
+    c->chunk_start.assign(1, 0);
+    c->t_chunk_max = 0;
     for (int32_t j = 0; j < B; ++j) {
         SubDesc& s = c->subs[j];
         s.col = j;
@@ -264,19 +272,28 @@ static smx_status analyse(smx_ctx* c) {
         s.n = acc;
         s.ld = static_cast<int32_t>(round_up(acc, 4));  // 16-byte aligned FP32 rows
         s.bown = c->bs[j];
+        const int64_t t_size = round_up(static_cast<int64_t>(s.n) * s.ld, 32);
+        if (t_off > 0 && t_off + t_size > chunk_elems) {  // start a new chunk (staging offsets restart at 0)
+            c->chunk_start.push_back(j);
+            t_off = 0;
+        }
         s.t_off = t_off;
         s.x_off = x_off;
-        t_off += round_up(static_cast<int64_t>(s.n) * s.ld, 32);
+        t_off += t_size;
+        c->t_chunk_max = std::max(c->t_chunk_max, t_off);
         x_off += round_up(static_cast<int64_t>(s.n) * s.bown, 32);
         c->max_nblk = std::max(c->max_nblk, s.nblk);
         c->max_n = std::max(c->max_n, s.n);
     }
-    c->t_elems = t_off;
+    c->chunk_start.push_back(B);
+    c->t_elems = c->t_chunk_max;
     c->x_elems = x_off;
+    // processing order: largest first within each chunk
     c->order.resize(B);
     for (int32_t j = 0; j < B; ++j) c->order[j] = j;
-    std::stable_sort(c->order.begin(), c->order.end(),
-                     [&](int32_t x, int32_t y) { return c->subs[x].n > c->subs[y].n; });
+    for (size_t k = 0; k + 1 < c->chunk_start.size(); ++k)
+        std::stable_sort(c->order.begin() + c->chunk_start[k], c->order.begin() + c->chunk_start[k + 1],
+                         [&](int32_t x, int32_t y) { return c->subs[x].n > c->subs[y].n; });
 
     SMX_TRY(upload(c->d_fcol_ptr, c->fcol_ptr, st));
     SMX_TRY(upload(c->d_frow_idx, c->frow_idx, st));
@@ -355,90 +372,103 @@ static smx_status build_at(smx_ctx* c, double mu) {
     const int B = c->B;
     SMX_CUDA(cudaMemsetAsync(c->d_status.p, 0, sizeof(int), st));
     SMX_CUDA(cudaEventRecord(c->ev0, st));
-    const PatternView pv = pattern_view(c);
-    if (c->precision == SMX_FP64) {
-        SMX_CUDA(launch_gather_bound(dp<SubDesc>(c->d_subs), B, c->max_nblk, pv, dp<double>(c->d_H), mu,
-                                     dp<double>(c->d_T), dp<double>(c->d_bound), st));
-    } else {
-        SMX_CUDA(launch_gather_bound_f32(dp<SubDesc>(c->d_subs), B, c->max_nblk, pv, dp<float>(c->d_H32), mu,
-                                         dp<float>(c->d_T), dp<double>(c->d_bound), st));
-    }
-    SMX_CUDA(cudaMemcpyAsync(c->d_gersh.p, c->d_bound.p, sizeof(double) * B, cudaMemcpyDeviceToDevice, st));
     SMX_CUDA(cudaMemsetAsync(c->d_fallback.p, 0, sizeof(int), st));
-    if (c->model_on) {
-        // learned bound: features -> prediction -> b_j (checked inside the Newton-Schulz kernel)
-        SMX_CUDA(launch_features(dp<SubDesc>(c->d_subs), B, c->d_T.p, c->precision != SMX_FP64, dp<float>(c->d_prev_ratio),
-                                 dp<float>(c->d_feat), st));
-        SMX_CUDA(launch_mlp_predict(dp<float>(c->d_params), dp<float>(c->d_feat), B, dp<float>(c->d_pred), st));
-        SMX_CUDA(launch_model_bound(dp<float>(c->d_pred), dp<double>(c->d_gersh), dp<double>(c->d_bound), B, kModelMargin, st));
-        c->kernel_launches += 3;
-    }
-    cudaEvent_t ns0, ns1;
-    SMX_TRY(ns_event_pair(c, &ns0, &ns1));
+    const PatternView pv = pattern_view(c);
     if (c->precision == SMX_FP64) {
         SMX_TRY(ensure(c->d_W1, c->d_T.bytes));
         SMX_TRY(ensure(c->d_W2, c->d_T.bytes));
-        NsFp64Args a;
-        a.subs = dp<SubDesc>(c->d_subs);
-        a.n_subs = B;
-        a.T = dp<double>(c->d_T);
-        a.W1 = dp<double>(c->d_W1);
-        a.W2 = dp<double>(c->d_W2);
-        a.bound = dp<double>(c->d_bound);
-        a.tau = tau_for(SMX_FP64);
-        a.max_iter = 100;
-        a.iters = dp<int32_t>(c->d_iters);
-        a.work_n3 = dp<unsigned long long>(c->d_work_n3);
-        a.gersh = dp<double>(c->d_gersh);
-        a.sq_ratio = dp<float>(c->d_sq_ratio);
-        a.use_model = c->model_on ? 1 : 0;
-        a.fallbacks = dp<int>(c->d_fallback);
-        a.status = dp<int>(c->d_status);
-        a.pv = pv;
-        a.H = dp<double>(c->d_H);
-        a.D = dp<double>(c->d_D);
-        a.partial = dp<double2>(c->d_partial);
-        SMX_CUDA(cudaEventRecord(ns0, st));
-        SMX_CUDA(launch_ns_fp64(a, c->max_nblk, st));
-        SMX_CUDA(cudaEventRecord(ns1, st));
     } else {
         SMX_TRY(prepare_tc_workspace(c));
-        NsTcArgs a;
-        a.subs = dp<SubDesc>(c->d_subs);
-        a.order = dp<int32_t>(c->d_order);
-        a.n_subs = B;
-        a.work_counter = dp<int>(c->d_counter);
-        a.T = dp<float>(c->d_T);
-        a.bound = dp<double>(c->d_bound);
-        a.ws = c->d_ws.p;
-        a.ld = c->ws_ld;
-        a.n_slots = c->ws_slots;
-        a.tau = static_cast<float>(tau_for(c->precision));
-        a.max_iter = 100;
-        a.iters = dp<int32_t>(c->d_iters);
-        a.work_n3 = dp<unsigned long long>(c->d_work_n3);
-        a.gersh = dp<double>(c->d_gersh);
-        a.sq_ratio = dp<float>(c->d_sq_ratio);
-        a.use_model = c->model_on ? 1 : 0;
-        a.fallbacks = dp<int>(c->d_fallback);
-        a.status = dp<int>(c->d_status);
-        a.pv = pv;
-        a.H = dp<double>(c->d_H);
-        a.D = dp<double>(c->d_D);
-        a.partial = dp<double2>(c->d_partial);
         SMX_TRY(ensure(c->d_xown, static_cast<size_t>(c->x_elems) * sizeof(float)));
-        a.xown = dp<float>(c->d_xown);
-        SMX_CUDA(cudaEventRecord(ns0, st));
-        SMX_CUDA(launch_ns_tc(a, c->precision, c->tmap, c->max_nblk, st));
-        SMX_CUDA(cudaEventRecord(ns1, st));
-        SMX_CUDA(launch_scatter_owner(dp<SubDesc>(c->d_subs), B, c->max_nblk, pv, dp<float>(c->d_xown),
-                                      dp<double>(c->d_H), dp<double>(c->d_D), dp<double2>(c->d_partial), st));
+    }
+    SubDesc* subs = dp<SubDesc>(c->d_subs);
+    // one pass of a3-a7 per chunk of block columns (the staging of T_j is reused)
+    for (size_t k = 0; k + 1 < c->chunk_start.size(); ++k) {
+        const int j0 = c->chunk_start[k], m = c->chunk_start[k + 1] - j0;
+        if (c->precision == SMX_FP64) {
+            SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
+                                         dp<double>(c->d_bound) + j0, st));
+        } else {
+            SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
+                                             dp<double>(c->d_bound) + j0, st));
+        }
+        SMX_CUDA(cudaMemcpyAsync(dp<double>(c->d_gersh) + j0, dp<double>(c->d_bound) + j0, sizeof(double) * m,
+                                 cudaMemcpyDeviceToDevice, st));
         c->kernel_launches += 1;
+        if (c->model_on) {
+            // learned bound: features -> prediction -> b_j (checked inside the Newton-Schulz kernel)
+            SMX_CUDA(launch_features(subs + j0, m, c->d_T.p, c->precision != SMX_FP64, dp<float>(c->d_prev_ratio) + j0,
+                                     dp<float>(c->d_feat) + kModelFeatures * j0, st));
+            SMX_CUDA(launch_mlp_predict(dp<float>(c->d_params), dp<float>(c->d_feat) + kModelFeatures * j0, m,
+                                        dp<float>(c->d_pred) + 2 * j0, st));
+            SMX_CUDA(launch_model_bound(dp<float>(c->d_pred) + 2 * j0, dp<double>(c->d_gersh) + j0,
+                                        dp<double>(c->d_bound) + j0, m, kModelMargin, st));
+            c->kernel_launches += 3;
+        }
+        cudaEvent_t ns0, ns1;
+        SMX_TRY(ns_event_pair(c, &ns0, &ns1));
+        if (c->precision == SMX_FP64) {
+            NsFp64Args a;
+            a.subs = subs + j0;
+            a.n_subs = m;
+            a.T = dp<double>(c->d_T);
+            a.W1 = dp<double>(c->d_W1);
+            a.W2 = dp<double>(c->d_W2);
+            a.bound = dp<double>(c->d_bound) + j0;
+            a.tau = tau_for(SMX_FP64);
+            a.max_iter = 100;
+            a.iters = dp<int32_t>(c->d_iters);
+            a.work_n3 = dp<unsigned long long>(c->d_work_n3);
+            a.gersh = dp<double>(c->d_gersh) + j0;
+            a.sq_ratio = dp<float>(c->d_sq_ratio) + j0;
+            a.use_model = c->model_on ? 1 : 0;
+            a.fallbacks = dp<int>(c->d_fallback);
+            a.status = dp<int>(c->d_status);
+            a.pv = pv;
+            a.H = dp<double>(c->d_H);
+            a.D = dp<double>(c->d_D);
+            a.partial = dp<double2>(c->d_partial);
+            SMX_CUDA(cudaEventRecord(ns0, st));
+            SMX_CUDA(launch_ns_fp64(a, c->max_nblk, st));
+            SMX_CUDA(cudaEventRecord(ns1, st));
+        } else {
+            NsTcArgs a;
+            a.subs = subs;  // indexed by block column through the order slice
+            a.order = dp<int32_t>(c->d_order) + j0;
+            a.n_subs = m;
+            a.work_counter = dp<int>(c->d_counter);
+            a.T = dp<float>(c->d_T);
+            a.bound = dp<double>(c->d_bound);
+            a.ws = c->d_ws.p;
+            a.ld = c->ws_ld;
+            a.n_slots = std::min(c->ws_slots, m);
+            a.tau = static_cast<float>(tau_for(c->precision));
+            a.max_iter = 100;
+            a.iters = dp<int32_t>(c->d_iters);
+            a.work_n3 = dp<unsigned long long>(c->d_work_n3);
+            a.gersh = dp<double>(c->d_gersh);
+            a.sq_ratio = dp<float>(c->d_sq_ratio);
+            a.use_model = c->model_on ? 1 : 0;
+            a.fallbacks = dp<int>(c->d_fallback);
+            a.status = dp<int>(c->d_status);
+            a.pv = pv;
+            a.H = dp<double>(c->d_H);
+            a.D = dp<double>(c->d_D);
+            a.partial = dp<double2>(c->d_partial);
+            a.xown = dp<float>(c->d_xown);
+            SMX_CUDA(cudaEventRecord(ns0, st));
+            SMX_CUDA(launch_ns_tc(a, c->precision, c->tmap, c->max_nblk, st));
+            SMX_CUDA(cudaEventRecord(ns1, st));
+            SMX_CUDA(launch_scatter_owner(subs + j0, m, c->max_nblk, pv, dp<float>(c->d_xown), dp<double>(c->d_H),
+                                          dp<double>(c->d_D), dp<double2>(c->d_partial), st));
+            c->kernel_launches += 1;
+        }
+        c->kernel_launches += 1;
+        c->ns_launches += 1;
     }
     SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), nullptr, B, dp<double>(c->d_out), st));
     SMX_CUDA(cudaEventRecord(c->ev1, st));
-    c->kernel_launches += 3;
-    c->ns_launches += 1;
+    c->kernel_launches += 1;
     c->sq_valid = true;
     c->built = true;
     c->last_mu = mu;
@@ -574,6 +604,16 @@ smx_status smx_set_filter_threshold(smx_ctx* c, double eps) {
         c->eps = eps;
         c->dirty = true;
         c->analysed = false;  // force the keep flags to be read back
+    }
+    return SMX_OK;
+}
+
+smx_status smx_set_staging_limit(smx_ctx* c, uint64_t bytes) {
+    if (!c || bytes < (uint64_t(1) << 20)) return SMX_ERR_ARG;
+    if (bytes != c->staging_limit) {
+        c->staging_limit = static_cast<size_t>(bytes);
+        c->dirty = true;
+        c->analysed = false;  // re-chunk
     }
     return SMX_OK;
 }
@@ -769,20 +809,32 @@ static smx_status model_upload(smx_ctx* c, const std::vector<float>& p) {
     return SMX_OK;
 }
 
-// gather of T (staging for the context's precision) and the bound at the fixed mu
-static smx_status gather_current(smx_ctx* c) {
+// Per chunk of block columns: gather T (staging of the context's precision) and
+// the Gershgorin bound at the fixed mu, then the features (d_feat) and, when
+// lanczos_steps > 0, the Lanczos labels (d_labels) of every submatrix.
+static smx_status features_labels(smx_ctx* c, int32_t lanczos_steps) {
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
     const PatternView pv = pattern_view(c);
-    if (c->precision == SMX_FP64) {
-        SMX_TRY(ensure(c->d_T, static_cast<size_t>(c->t_elems) * sizeof(double)));
-        SMX_CUDA(launch_gather_bound(dp<SubDesc>(c->d_subs), c->B, c->max_nblk, pv, dp<double>(c->d_H), c->mu,
-                                     dp<double>(c->d_T), dp<double>(c->d_bound), c->stream));
-    } else {
-        SMX_TRY(ensure(c->d_T, static_cast<size_t>(c->t_elems) * sizeof(float)));
-        SMX_CUDA(launch_gather_bound_f32(dp<SubDesc>(c->d_subs), c->B, c->max_nblk, pv, dp<float>(c->d_H32), c->mu,
-                                         dp<float>(c->d_T), dp<double>(c->d_bound), c->stream));
+    const bool f32 = c->precision != SMX_FP64;
+    SubDesc* subs = dp<SubDesc>(c->d_subs);
+    for (size_t k = 0; k + 1 < c->chunk_start.size(); ++k) {
+        const int j0 = c->chunk_start[k], m = c->chunk_start[k + 1] - j0;
+        if (!f32) {
+            SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, pv, dp<double>(c->d_H), c->mu, dp<double>(c->d_T),
+                                         dp<double>(c->d_bound) + j0, c->stream));
+        } else {
+            SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, pv, dp<float>(c->d_H32), c->mu,
+                                             dp<float>(c->d_T), dp<double>(c->d_bound) + j0, c->stream));
+        }
+        SMX_CUDA(launch_features(subs + j0, m, c->d_T.p, f32, dp<float>(c->d_prev_ratio) + j0,
+                                 dp<float>(c->d_feat) + kModelFeatures * j0, c->stream));
+        c->kernel_launches += 2;
+        if (lanczos_steps > 0) {
+            SMX_CUDA(launch_lanczos(subs + j0, m, c->max_n, c->d_T.p, f32, lanczos_steps, dp<float>(c->d_labels) + 2 * j0,
+                                    c->stream));
+            c->kernel_launches += 1;
+        }
     }
-    c->kernel_launches += 1;
     return SMX_OK;
 }
 
@@ -824,14 +876,8 @@ smx_status smx_bound_model_get_params(smx_ctx* c, float* params, int32_t count) 
 smx_status smx_bound_model_collect(smx_ctx* c, int32_t lanczos_steps) {
     if (!c || lanczos_steps < 8 || lanczos_steps > kMaxLanczos) return SMX_ERR_ARG;
     DeviceGuard g(c->device);
-    SMX_TRY(gather_current(c));
+    SMX_TRY(features_labels(c, lanczos_steps));
     const int B = c->B;
-    const bool f32 = c->precision != SMX_FP64;
-    SMX_CUDA(launch_features(dp<SubDesc>(c->d_subs), B, c->d_T.p, f32, dp<float>(c->d_prev_ratio), dp<float>(c->d_feat),
-                             c->stream));
-    SMX_CUDA(launch_lanczos(dp<SubDesc>(c->d_subs), B, c->max_n, c->d_T.p, f32, lanczos_steps, dp<float>(c->d_labels),
-                            c->stream));
-    c->kernel_launches += 2;
     if (c->n_samples + B > c->cap_samples) {  // grow the sample store, keeping its contents
         const int64_t cap = std::max<int64_t>(2 * c->cap_samples, c->n_samples + B);
         DevBuf nx, nt;
@@ -922,23 +968,15 @@ smx_status smx_bound_model_predict(smx_ctx* c, float* features, float* pred, flo
     if (!c || (labels && (lanczos_steps < 8 || lanczos_steps > kMaxLanczos))) return SMX_ERR_ARG;
     if (pred && !c->model_ready) return SMX_ERR_STATE;
     DeviceGuard g(c->device);
-    SMX_TRY(gather_current(c));
+    SMX_TRY(features_labels(c, labels ? lanczos_steps : 0));
     const int B = c->B;
-    const bool f32 = c->precision != SMX_FP64;
-    SMX_CUDA(launch_features(dp<SubDesc>(c->d_subs), B, c->d_T.p, f32, dp<float>(c->d_prev_ratio), dp<float>(c->d_feat),
-                             c->stream));
-    c->kernel_launches += 1;
     if (pred) {
         SMX_CUDA(launch_mlp_predict(dp<float>(c->d_params), dp<float>(c->d_feat), B, dp<float>(c->d_pred), c->stream));
         SMX_CUDA(cudaMemcpyAsync(pred, c->d_pred.p, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost, c->stream));
         c->kernel_launches += 1;
     }
-    if (labels) {
-        SMX_CUDA(launch_lanczos(dp<SubDesc>(c->d_subs), B, c->max_n, c->d_T.p, f32, lanczos_steps, dp<float>(c->d_labels),
-                                c->stream));
+    if (labels)
         SMX_CUDA(cudaMemcpyAsync(labels, c->d_labels.p, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost, c->stream));
-        c->kernel_launches += 1;
-    }
     if (features)
         SMX_CUDA(cudaMemcpyAsync(features, c->d_feat.p, sizeof(float) * kModelFeatures * B, cudaMemcpyDeviceToHost, c->stream));
     SMX_CUDA(cudaStreamSynchronize(c->stream));
