@@ -141,6 +141,19 @@ smx_status smx_set_filter_threshold(smx_ctx* ctx, double eps);
  * SMX_ERR_ARG. */
 smx_status smx_set_staging_limit(smx_ctx* ctx, uint64_t bytes);
 
+/* Restricts the context to block columns [j0, j1) (one shard of a multi-GPU
+ * run; 0 <= j0 < j1 <= n_block_cols, the full range restores the default).
+ * Builds then compute D, trace(D) and trace(DH) over those columns only (D
+ * is zero elsewhere); the shards' traces add up to the full build's.  The
+ * bisection across shards is the caller's (smx_get_gershgorin_interval, a
+ * build per midpoint and a sum of the 16-byte traces over the shards);
+ * smx_solve_mu returns SMX_ERR_STATE on a shard.  Errors: SMX_ERR_ARG. */
+smx_status smx_set_column_range(smx_ctx* ctx, int32_t j0, int32_t j1);
+
+/* Gershgorin interval [lo, hi] of the whole filtered H (Eq. 14's mu lies in
+ * it): the bisection bracket.  Synchronises.  Errors: SMX_ERR_ARG, SMX_ERR_CUDA. */
+smx_status smx_get_gershgorin_interval(smx_ctx* ctx, double* lo, double* hi);
+
 /* Fixed chemical potential mu (Eq. 14) for smx_build_density.  Errors: SMX_ERR_ARG (non-finite). */
 smx_status smx_set_mu(smx_ctx* ctx, double mu);
 

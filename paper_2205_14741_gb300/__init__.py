@@ -100,6 +100,14 @@ class SubmatrixDensity:
     def set_staging_limit(self, nbytes: int):
         check(self._lib.smx_set_staging_limit(self._ctx, C.c_uint64(int(nbytes))), "smx_set_staging_limit")
 
+    def set_column_range(self, j0: int, j1: int):
+        check(self._lib.smx_set_column_range(self._ctx, int(j0), int(j1)), "smx_set_column_range")
+
+    def get_gershgorin_interval(self):
+        lo, hi = C.c_double(0.0), C.c_double(0.0)
+        check(self._lib.smx_get_gershgorin_interval(self._ctx, C.byref(lo), C.byref(hi)), "smx_get_gershgorin_interval")
+        return lo.value, hi.value
+
     def set_mu(self, mu: float):
         check(self._lib.smx_set_mu(self._ctx, float(mu)), "smx_set_mu")
 

@@ -61,6 +61,8 @@ SIGNATURES = {
     "smx_set_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "smx_set_filter_threshold": (C.c_int, [C.c_void_p, C.c_double]),
     "smx_set_staging_limit": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "smx_set_column_range": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "smx_get_gershgorin_interval": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "smx_set_mu": (C.c_int, [C.c_void_p, C.c_double]),
     "smx_set_electron_count": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_double]),
     "smx_set_precision": (C.c_int, [C.c_void_p, C.c_int, C.c_int32]),

@@ -101,6 +101,7 @@ struct smx_ctx {
     // staging of the submatrices T_j in chunks of consecutive block columns
     size_t staging_limit = size_t(24) << 30;  // bytes (FP64 elements)
     std::vector<int32_t> chunk_start;         // chunk c = block columns [chunk_start[c], chunk_start[c + 1])
+    int32_t col_lo = 0, col_hi = -1;          // block columns this context builds (a shard); col_hi < 0: all
     int64_t t_chunk_max = 0;                  // elements of the largest chunk
 
     // learned spectral bound
@@ -253,7 +254,8 @@ static smx_status analyse(smx_ctx* c) {
     c->max_n = 0;
     int64_t t_off = 0, x_off = 0;
     const int64_t chunk_elems = std::max<int64_t>(1, static_cast<int64_t>(c->staging_limit / sizeof(double)));
-    c->chunk_start.assign(1, 0);
+    const int32_t lo = c->col_lo, hi = c->col_hi < 0 ? B : c->col_hi;
+    c->chunk_start.assign(1, lo);
     c->t_chunk_max = 0;
     for (int32_t j = 0; j < B; ++j) {
         SubDesc& s = c->subs[j];
@@ -273,19 +275,22 @@ static smx_status analyse(smx_ctx* c) {
         s.ld = static_cast<int32_t>(round_up(acc, 4));  // 16-byte aligned FP32 rows
         s.bown = c->bs[j];
         const int64_t t_size = round_up(static_cast<int64_t>(s.n) * s.ld, 32);
-        if (t_off > 0 && t_off + t_size > chunk_elems) {  // start a new chunk (staging offsets restart at 0)
-            c->chunk_start.push_back(j);
-            t_off = 0;
-        }
-        s.t_off = t_off;
         s.x_off = x_off;
-        t_off += t_size;
-        c->t_chunk_max = std::max(c->t_chunk_max, t_off);
+        s.t_off = 0;
+        if (j >= lo && j < hi) {
+            if (t_off > 0 && t_off + t_size > chunk_elems) {  // start a new chunk (staging offsets restart at 0)
+                c->chunk_start.push_back(j);
+                t_off = 0;
+            }
+            s.t_off = t_off;
+            t_off += t_size;
+            c->t_chunk_max = std::max(c->t_chunk_max, t_off);
+        }
         x_off += round_up(static_cast<int64_t>(s.n) * s.bown, 32);
         c->max_nblk = std::max(c->max_nblk, s.nblk);
         c->max_n = std::max(c->max_n, s.n);
     }
-    c->chunk_start.push_back(B);
+    c->chunk_start.push_back(hi);
     c->t_elems = c->t_chunk_max;
     c->x_elems = x_off;
     // processing order: largest first within each chunk
@@ -303,6 +308,8 @@ static smx_status analyse(smx_ctx* c) {
     SMX_TRY(upload(c->d_order, c->order, st));
     SMX_TRY(ensure(c->d_T, static_cast<size_t>(c->t_elems) * sizeof(double)));
     SMX_CUDA(cudaMemsetAsync(c->d_D.p, 0, c->n_values * sizeof(double), st));
+    SMX_CUDA(cudaMemsetAsync(c->d_partial.p, 0, sizeof(double2) * B, st));  // columns outside the shard add zero
+    SMX_CUDA(cudaMemsetAsync(c->d_iters.p, 0, sizeof(int32_t) * B, st));
     c->analysed = true;
     c->dirty = false;
     c->ws_prec = -1;  // tensor-core workspace must be re-checked
@@ -618,6 +625,35 @@ smx_status smx_set_staging_limit(smx_ctx* c, uint64_t bytes) {
     return SMX_OK;
 }
 
+smx_status smx_set_column_range(smx_ctx* c, int32_t j0, int32_t j1) {
+    if (!c || j0 < 0 || j1 > c->B || j0 >= j1) return SMX_ERR_ARG;
+    const int32_t hi = (j0 == 0 && j1 == c->B) ? -1 : j1;
+    if (j0 != c->col_lo || hi != c->col_hi) {
+        c->col_lo = j0;
+        c->col_hi = hi;
+        c->dirty = true;
+        c->analysed = false;
+        c->built = false;
+    }
+    return SMX_OK;
+}
+
+smx_status smx_get_gershgorin_interval(smx_ctx* c, double* lo, double* hi) {
+    if (!c || !lo || !hi) return SMX_ERR_ARG;
+    DeviceGuard g(c->device);
+    if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
+    SMX_CUDA(launch_column_gershgorin(pattern_view(c), dp<double>(c->d_H), nullptr, c->B, dp<double>(c->d_lohi),
+                                      c->stream));
+    SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), dp<double>(c->d_lohi), c->B, dp<double>(c->d_out_br), c->stream));
+    c->kernel_launches += 2;
+    double br[4];
+    SMX_CUDA(cudaMemcpyAsync(br, c->d_out_br.p, sizeof(br), cudaMemcpyDeviceToHost, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    *lo = br[2];
+    *hi = br[3];
+    return SMX_OK;
+}
+
 smx_status smx_set_mu(smx_ctx* c, double mu) {
     if (!c || !std::isfinite(mu)) return SMX_ERR_ARG;
     c->mu = mu;
@@ -652,7 +688,7 @@ smx_status smx_build_density(smx_ctx* c) {
 
 smx_status smx_solve_mu(smx_ctx* c) {
     if (!c) return SMX_ERR_ARG;
-    if (!c->have_ne) return SMX_ERR_STATE;
+    if (!c->have_ne || c->col_hi >= 0) return SMX_ERR_STATE;  // a shard's trace is partial
     DeviceGuard g(c->device);
     if (c->n_e < 0.0 || c->n_e > static_cast<double>(c->N)) return SMX_ERR_NOBRACKET;
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
@@ -737,6 +773,7 @@ smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
     accumulate_timers(c);
     std::memset(out, 0, sizeof(*out));
     out->n_block_cols = c->B;
+    const int32_t lo = c->col_lo, hi = c->col_hi < 0 ? c->B : c->col_hi;
     out->n = c->N;
     out->nnzb_input = c->nnzb;
     out->nnzb_filtered = static_cast<int64_t>(c->frow_idx.size());
@@ -744,7 +781,7 @@ smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
     out->iters_min = 1 << 30;
     double dsum = 0.0, isum = 0.0, flops = 0.0;
     int noconv = 0;
-    for (int32_t j = 0; j < c->B; ++j) {
+    for (int32_t j = lo; j < hi; ++j) {  // the context's block columns
         const int n = c->subs[j].n;
         out->dim_min = std::min(out->dim_min, n);
         out->dim_max = std::max(out->dim_max, n);
@@ -755,8 +792,8 @@ smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
         flops += 4.0 * n * static_cast<double>(n) * n * it[j];
         if (it[j] >= 100) ++noconv;
     }
-    out->dim_mean = dsum / c->B;
-    out->iters_mean = isum / c->B;
+    out->dim_mean = dsum / (hi - lo);
+    out->iters_mean = isum / (hi - lo);
     out->n_noconv = noconv;
     out->n_bound_fallback = fallbacks;
     out->bisection_steps = c->bisection_steps;

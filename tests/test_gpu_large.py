@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 from synth import WORKLOADS, make_workload
-from tests.helpers import max_abs_on_columns, oracle_in_input_layout, sample_columns
+from tests.helpers import column_slices, max_abs_on_columns, oracle_in_input_layout, sample_columns
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -111,3 +111,72 @@ def test_slab_wide_chunked_sampled_columns():
     cols = sorted({int(order[0]), int(order[len(order) // 2]), int(order[-1])})
     d_or, _, _ = oracle_in_input_layout(s, w["eps"], 0.0, columns=cols)
     assert max_abs_on_columns(d, d_or, s, cols) <= TOL_D["fp16x3"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x3"])
+def test_column_shards_add_up_to_the_full_build(prec):
+    from paper_2205_14741_gb300.shard import partition_columns
+
+    s = make_workload("water1024")
+    with _ctx(s, prec, 1e-5) as c:
+        c.set_mu(0.012)
+        c.build_density()
+        d_full = c.get_density().copy()
+        tr_full, en_full, _ = c.get_trace()
+        dims, _, _ = c.get_submatrix_info()
+        lo, hi = c.get_gershgorin_interval()
+    parts = partition_columns(dims, 3)
+    d_sum = np.zeros_like(d_full)
+    tr_sum = en_sum = 0.0
+    for j0, j1 in parts:
+        with _ctx(s, prec, 1e-5) as c:
+            c.set_column_range(j0, j1)
+            assert c.get_gershgorin_interval() == (lo, hi)  # the bracket is the whole H's
+            c.set_mu(0.012)
+            c.build_density()
+            d = c.get_density()
+            tr, en, _ = c.get_trace()
+            st = c.get_stats()
+        outside = [j for j in range(len(dims)) if not j0 <= j < j1]
+        assert all(np.count_nonzero(d[sl]) == 0 for sl in column_slices(s, outside))  # D is zero off the shard
+        assert st["dim_min"] == dims[j0:j1].min()
+        d_sum += d
+        tr_sum += tr
+        en_sum += en
+    assert np.array_equal(d_sum, d_full)
+    assert abs(tr_sum - tr_full) <= 1e-10 * abs(tr_full) and abs(en_sum - en_full) <= 1e-10 * abs(en_full)
+
+
+def test_sharded_bisection_matches_solve_mu():
+    # three shards in lockstep on one GPU: the decisions and the final mu equal smx_solve_mu's
+    from paper_2205_14741_gb300 import SmxError
+    from paper_2205_14741_gb300.shard import partition_columns
+
+    s = make_workload("water1024")
+    with _ctx(s, "fp16x3", 1e-5) as c:
+        c.set_electron_count(3072.0, max_steps=30, tol=1e-2)
+        c.solve_mu()
+        tr_ref, en_ref, mu_ref = c.get_trace()
+        dims, _, _ = c.get_submatrix_info()
+    ctxs = []
+    for j0, j1 in partition_columns(dims, 3):
+        c = _ctx(s, "fp16x3", 1e-5)
+        c.set_column_range(j0, j1)
+        c.set_electron_count(3072.0, max_steps=30, tol=1e-2)
+        with pytest.raises(SmxError):
+            c.solve_mu()  # a shard's trace is partial
+        ctxs.append(c)
+    lo, hi = ctxs[0].get_gershgorin_interval()
+    for _ in range(30):
+        mid = 0.5 * (lo + hi)
+        tr = 0.0
+        for c in ctxs:
+            c.set_mu(mid)
+            c.build_density()
+            tr += c.get_trace()[0]
+        if abs(tr - 3072.0) <= 1e-2:
+            break
+        lo, hi = (mid, hi) if tr < 3072.0 else (lo, mid)
+    for c in ctxs:
+        c.close()
+    assert mid == mu_ref and abs(tr - tr_ref) <= 1e-9 * tr_ref
