@@ -4,6 +4,8 @@
 //  a3  gather T_j = H[R_j, R_j] - mu I (Fig. 2 step (i), shift of Eq. 14)
 //  a4  Gershgorin bound b_j >= spectral radius of T_j - mu I
 //  a8  deterministic FP64 sums of trace(D) and trace(D H)
+#include <algorithm>
+
 #include "smx_finish.cuh"
 #include "smx_kernels.h"
 
@@ -87,35 +89,47 @@ cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, con
     return cudaGetLastError();
 }
 
-// One CTA per submatrix.  T_j is stored row-major with leading dimension
-// s.ld; it is symmetric, so block (R_j[a], R_j[c]) of H (column-major in the
-// input) is written transposed at rows of c / columns of a, which makes each
-// column of the source block a contiguous run in T_j.
+// One CTA per submatrix; T_j is row-major with leading dimension s.ld (zero
+// in columns [n, ld)).  Warp w assembles the rows of block rows c = w, w + 8,
+// ...: the blocks of H's column R_j[c] whose rows lie in R_j are listed once
+// per block row (position a in R_j, value offset); row x = start(c) + q of T_j
+// then takes, from each listed block (R_j[a], R_j[c]) (column-major), its
+// column q -- T_j is symmetric, so that column is row x restricted to block a.
+// The row is put together in shared memory and written once, coalesced, with
+// its absolute sum for the Gershgorin bound b_j = max_x sum_y |T[x][y]|.
 template <class R>
 __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict__ subs, PatternView pv,
                                                       const R* __restrict__ H, double mu_d, R* __restrict__ T,
-                                                      double* __restrict__ bound) {
-    extern __shared__ int sm_int[];
-    __shared__ R warp_max_s[8];
+                                                      double* __restrict__ bound, int ld_max, int nblk_max, int nw) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    __shared__ double warp_max_s[8];
     const R mu = static_cast<R>(mu_d);
     const SubDesc s = subs[blockIdx.x];
-    int* rows = sm_int;               // R_j
-    int* ls = sm_int + s.nblk;        // local starts, nblk + 1 entries
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int* rows = reinterpret_cast<int*>(gsm);  // R_j
+    int* ls = rows + nblk_max;                // local starts, nblk + 1 entries
+    const size_t head = (static_cast<size_t>(2 * nblk_max + 1) * sizeof(int) + 15) & ~size_t(15);
+    const size_t lists = (static_cast<size_t>(nblk_max) * (sizeof(int64_t) + sizeof(int)) + 15) & ~size_t(15);
+    const size_t per_warp = lists + ((static_cast<size_t>(ld_max) * sizeof(R) + 15) & ~size_t(15));
+    unsigned char* wbase = gsm + head + warp * per_warp;
+    int64_t* vo_list = reinterpret_cast<int64_t*>(wbase);
+    int* a_list = reinterpret_cast<int*>(wbase + static_cast<size_t>(nblk_max) * sizeof(int64_t));
+    R* rowbuf = reinterpret_cast<R*>(wbase + lists);
     for (int a = tid; a < s.nblk; a += blockDim.x) {
         rows[a] = pv.frow_idx[s.fptr + a];
         ls[a] = pv.lstart[s.fptr + a];
     }
     if (tid == 0) ls[s.nblk] = s.n;
-    R* t = T + s.t_off;
-    const int64_t area = static_cast<int64_t>(s.n) * s.ld;
-    for (int64_t e = tid; e < area; e += blockDim.x) t[e] = R(0);
     __syncthreads();
 
-    for (int c = warp; c < s.nblk; c += 8) {
+    R* t = T + s.t_off;
+    double m = 0.0;
+    for (int c = warp; c < s.nblk && warp < nw; c += nw) {  // nw warps own a row buffer each
         const int col = rows[c];
         const int bc = ls[c + 1] - ls[c];
         const int64_t k0 = pv.fcol_ptr[col], k1 = pv.fcol_ptr[col + 1];
+        // the blocks of column col inside R_j
+        int cnt = 0;
         for (int64_t kb = k0; kb < k1; kb += 32) {
             const int64_t k = kb + lane;
             int a = -1;
@@ -128,59 +142,77 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
                 }
                 if (rows[lo] == r) a = lo;
             }
-            unsigned found = __ballot_sync(0xffffffffu, a >= 0);
-            while (found) {
-                const int src = __ffs(found) - 1;
-                found &= found - 1;
-                const int aa = __shfl_sync(0xffffffffu, a, src);
-                const int64_t kk = kb + src;
-                const int br = ls[aa + 1] - ls[aa];
-                const R* blk = H + pv.fvoff[kk];
-                const int sz = br * bc;
-                for (int e = lane; e < sz; e += 32) {
-                    const int q = e / br, p = e - q * br;
-                    R v = blk[e];
-                    if (aa == c && p == q) v -= mu;
-                    t[static_cast<int64_t>(ls[c] + q) * s.ld + ls[aa] + p] = v;
+            const unsigned found = __ballot_sync(0xffffffffu, a >= 0);
+            if (a >= 0) {
+                const int pos = cnt + __popc(found & ((1u << lane) - 1u));
+                a_list[pos] = a;
+                vo_list[pos] = pv.fvoff[k];
+            }
+            cnt += __popc(found);
+        }
+        __syncwarp();
+        for (int q = 0; q < bc; ++q) {
+            for (int y = lane; y < s.ld; y += 32) rowbuf[y] = R(0);
+            __syncwarp();
+            for (int e = lane; e < cnt; e += 32) {  // a lane per listed block: column q of block (R_j[a], col)
+                const int a = a_list[e];
+                const int br = ls[a + 1] - ls[a];
+                const R* src = H + vo_list[e] + static_cast<int64_t>(q) * br;
+                R* dst = rowbuf + ls[a];
+                for (int p = 0; p < br; ++p) {
+                    R v = src[p];
+                    if (a == c && p == q) v -= mu;
+                    dst[p] = v;
                 }
             }
-        }
-    }
-    __syncthreads();
-
-    // b_j = max_x sum_y |T[x][y]|  (T already holds the shift).  In FP32 the
-    // sum carries a relative error below n * 2^-24, covered by the 1e-5 margin.
-    R m = R(0);
-    for (int x = warp; x < s.n; x += 8) {
-        const R* row = t + static_cast<int64_t>(x) * s.ld;
-        R acc = R(0);
-        for (int y = lane; y < s.n; y += 32) acc += fabs(row[y]);
+            __syncwarp();
+            R* trow = t + static_cast<int64_t>(ls[c] + q) * s.ld;
+            R acc = R(0);
+            for (int y = lane; y < s.ld; y += 32) {
+                const R v = rowbuf[y];
+                trow[y] = v;
+                acc += fabs(v);
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        m = m > acc ? m : acc;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            m = fmax(m, static_cast<double>(acc));
+            __syncwarp();
+        }
     }
     if (lane == 0) warp_max_s[warp] = m;
     __syncthreads();
     if (tid == 0) {
+        // in FP32 the row sums carry a relative error below n 2^-24, covered by the 1e-5 margin
         double g = 0.0;
-        for (int w = 0; w < 8; ++w) g = fmax(g, static_cast<double>(warp_max_s[w]));
+        for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
         if (sizeof(R) == 4) g *= 1.0 + 1e-5;
         bound[blockIdx.x] = g > 0.0 ? g : 1.0;
     }
 }
 
-cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv, const double* H,
-                                double mu, double* T, double* bound, cudaStream_t st) {
-    const size_t smem = sizeof(int) * (2 * static_cast<size_t>(max_nblk) + 1);
-    k_gather_bound<double><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound);
+template <class R>
+static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
+                                 const R* H, double mu, R* T, double* bound, cudaStream_t st) {
+    const size_t head = (static_cast<size_t>(2 * max_nblk + 1) * sizeof(int) + 15) & ~size_t(15);
+    const size_t lists = (static_cast<size_t>(max_nblk) * (sizeof(int64_t) + sizeof(int)) + 15) & ~size_t(15);
+    const size_t per_warp = lists + ((static_cast<size_t>(max_ld) * sizeof(R) + 15) & ~size_t(15));
+    // as many row-buffer warps (up to 8) as fit in 200 KB of shared memory
+    const int nw = static_cast<int>(std::max<size_t>(1, std::min<size_t>(8, (200u << 10) / per_warp)));
+    const size_t smem = head + nw * per_warp;
+    cudaError_t e = cudaFuncSetAttribute(k_gather_bound<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_gather_bound<R><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound, max_ld, max_nblk, nw);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
+                                const double* H, double mu, double* T, double* bound, cudaStream_t st) {
+    return launch_gather<double>(subs, n_subs, max_nblk, max_ld, pv, H, mu, T, bound, st);
+}
+
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
                                     const float* H32, double mu, float* T32, double* bound, cudaStream_t st) {
-    const size_t smem = sizeof(int) * (2 * static_cast<size_t>(max_nblk) + 1);
-    k_gather_bound<float><<<n_subs, 256, smem, st>>>(subs, pv, H32, mu, T32, bound);
-    return cudaGetLastError();
+    return launch_gather<float>(subs, n_subs, max_nblk, max_ld, pv, H32, mu, T32, bound, st);
 }
 
 // One CTA per submatrix: scatter of the saved owner columns (Fig. 2 step (iii)).

@@ -393,10 +393,10 @@ static smx_status build_at(smx_ctx* c, double mu) {
     for (size_t k = 0; k + 1 < c->chunk_start.size(); ++k) {
         const int j0 = c->chunk_start[k], m = c->chunk_start[k + 1] - j0;
         if (c->precision == SMX_FP64) {
-            SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
+            SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, static_cast<int>(round_up(c->max_n, 4)), pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
                                          dp<double>(c->d_bound) + j0, st));
         } else {
-            SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
+            SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, static_cast<int>(round_up(c->max_n, 4)), pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
                                              dp<double>(c->d_bound) + j0, st));
         }
         SMX_CUDA(cudaMemcpyAsync(dp<double>(c->d_gersh) + j0, dp<double>(c->d_bound) + j0, sizeof(double) * m,
@@ -857,10 +857,10 @@ static smx_status features_labels(smx_ctx* c, int32_t lanczos_steps) {
     for (size_t k = 0; k + 1 < c->chunk_start.size(); ++k) {
         const int j0 = c->chunk_start[k], m = c->chunk_start[k + 1] - j0;
         if (!f32) {
-            SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, pv, dp<double>(c->d_H), c->mu, dp<double>(c->d_T),
+            SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, static_cast<int>(round_up(c->max_n, 4)), pv, dp<double>(c->d_H), c->mu, dp<double>(c->d_T),
                                          dp<double>(c->d_bound) + j0, c->stream));
         } else {
-            SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, pv, dp<float>(c->d_H32), c->mu,
+            SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, static_cast<int>(round_up(c->max_n, 4)), pv, dp<float>(c->d_H32), c->mu,
                                              dp<float>(c->d_T), dp<double>(c->d_bound) + j0, c->stream));
         }
         SMX_CUDA(launch_features(subs + j0, m, c->d_T.p, f32, dp<float>(c->d_prev_ratio) + j0,

@@ -22,11 +22,11 @@ cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, con
 
 // a3 + a4: T_j = H[R_j, R_j] - mu I into the FP64 staging buffer, then the
 // Gershgorin bound b_j = max row abs-sum of T_j (>= spectral radius).
-cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
                                 const double* H, double mu, double* T, double* bound, cudaStream_t st);
 // The same in FP32 (tensor-core path): T32 from the FP32 copy of H; the bound
 // is enlarged by 1e-5 relative to cover FP32 summation.
-cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
                                     const float* H32, double mu, float* T32, double* bound, cudaStream_t st);
 
 // a8: deterministic sums of the per-column partials -> out[0] = trace(D),
