@@ -537,7 +537,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             // tensor-memory passes: warp w serves lanes 32 (w mod 4) and the
             // 32-column chunks c0 = 32 (w / 4) + 96 k.
             // ---------------------------------------------------------------
-            const uint32_t P = tmem_base, Q = tmem_base + 256;
+            // Tensor memory: P holds Y_t (then its A operand), Q the second product.  When
+            // kpad <= 160 every tile's X' keeps its own region (Q, R) until the last tile's
+            // second product is done and then goes straight into the image: no L2 traffic.
+            const bool onchip = kpad <= 160;
+            const uint32_t P = tmem_base, Q = tmem_base + (onchip ? 160 : 256), R = tmem_base + 320;
             const int mtiles = (kpad + 127) >> 7;
             const int ksteps = kpad >> 4;
             const uint32_t idesc = idesc_f16(128, kpad, C::kFmt) | idesc_b_mn;
@@ -744,7 +748,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                         issue_xx(t, P);
                         tc_commit(&mma_bar);
                     }
-                    if (t > 0) drain(t - 1, Q, alpha, zn, false);  // overlaps the product
+                    if (t > 0 && !onchip) drain(t - 1, Q, alpha, zn, false);  // overlaps the product
                     if (g1) mma_wait();
                     tc_fence_before();
                     __syncthreads();
@@ -758,7 +762,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     __syncthreads();
                     if (warp == 1 && lane == 0) {
                         tc_fence_after();
-                        issue_yx(P, Q);
+                        issue_yx(P, (onchip && t == 1) ? R : Q);
                         tc_commit(&mma_bar);
                     }
                     if (t == mtiles - 1 && tid == 0) {  // convergence of this step, from ||X^2 - I||_F
@@ -775,17 +779,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
                 if (*abortp) break;
                 last = conv_s || bad_s || it + 1 == a.max_iter;
-                // the last tile: into the image when the iteration continues, else to the X buffer
-                drain(mtiles - 1, Q, alpha, zn, !last);
-                if (last) fence_proxy_async_global();
-                else fence_proxy_async_smem();
-                if (!last && mtiles > 1) fence_proxy_async_global();
+                if (onchip) {
+                    // every tile: into the image when the iteration continues, else to the X buffer
+                    drain(0, Q, alpha, zn, !last);
+                    if (mtiles > 1) drain(1, R, alpha, zn, !last);
+                    if (last) fence_proxy_async_global();
+                    else fence_proxy_async_smem();
+                } else {
+                    // the last tile: into the image when the iteration continues, else to the X buffer
+                    drain(mtiles - 1, Q, alpha, zn, !last);
+                    if (last) fence_proxy_async_global();
+                    else fence_proxy_async_smem();
+                    if (!last && mtiles > 1) fence_proxy_async_global();
+                }
                 tc_fence_before();
                 __syncthreads();
                 cur ^= 1;
                 done = it + 1;
                 if (last) break;
-                if (mtiles > 1) {
+                if (mtiles > 1 && !onchip) {
                     // the earlier tiles' rows of X' back into the image (row blocks < 2 (mtiles - 1))
                     const int rbs = 2 * (mtiles - 1);
                     if (tid == 0) {
