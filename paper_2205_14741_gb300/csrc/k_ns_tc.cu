@@ -54,7 +54,11 @@ struct TcCfg {
     static constexpr int kStages = (PREC == 1) ? 2 : 4;    // smem ring depth
     static constexpr uint32_t kStage = kNb * (kABytes + kBBytes);
     static constexpr int kFmt = (PREC == 3) ? 1 : 0;       // 0 = FP16, 1 = BF16
-    static constexpr size_t kDynSmem = 1024 + static_cast<size_t>(kStages) * kStage;
+    // the streamed form's stages, or the on-chip form's images: for kpad = 192 two hi images
+    // and a lo image of 72 KB each plus 8 KB read past the end by the last row tile's MMAs
+    static constexpr size_t kResSmem = static_cast<size_t>(kNb + 1) * 9 * 8192 + 8192;
+    static constexpr size_t kDynSmem = 1024 + (static_cast<size_t>(kStages) * kStage > kResSmem
+                                                   ? static_cast<size_t>(kStages) * kStage : kResSmem);
 };
 
 // Shared-memory descriptor of a B tile in the MN-major 128-byte-swizzled
@@ -145,6 +149,22 @@ __device__ __forceinline__ void load8(const uint16_t* hi, const uint16_t* lo, fl
 }
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// 16 consecutive 32-bit TMEM columns of this thread's lane <- r / -> r
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 // 32 consecutive 32-bit TMEM columns of this thread's lane <- r
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
     asm volatile(
@@ -217,16 +237,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     constexpr int NB = C::kNb, S = C::kStages, NT = C::kNmax;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    int* ls_smem = reinterpret_cast<int*>(smem + static_cast<size_t>(S) * C::kStage);
 
     __shared__ uint64_t full_bar[S], empty_bar[S], tfull[2], tempty[2], drain_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s, job_s, conv_s, bad_s, p_issued_s, m_consumed_s;
     __shared__ float resid_s[kEpiWarps];
-    __shared__ uint64_t mma_bar, img_bar;
-    __shared__ float rpart_s[3][kResKpad];  // per-part partial row sums (summed in a fixed order)
-    __shared__ float rsum_s[kResKpad], rs2_s[kResKpad];
-    __shared__ int img_pending_s, img_parity_s;
+    __shared__ uint64_t mma_bar;
     __shared__ float resid_s2[kThreads / 32];
     __shared__ float red_s[2][kThreads / 32];
 
@@ -243,8 +259,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         }
         mbar_init(&drain_bar, 1);
         mbar_init(&mma_bar, 1);
-        mbar_init(&img_bar, 1);
-        img_pending_s = 0;
         abort_s = 0;
         p_issued_s = 0;
         m_consumed_s = 0;
@@ -288,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     const int64_t buf = static_cast<int64_t>(a.ld) * a.ld;
     uint16_t* ws = static_cast<uint16_t*>(a.ws);
     const int slot_z = blockIdx.x * 6;
-    uint32_t mma_ph = 0, img_ph = 0;  // completed phases of mma_bar / img_bar (uniform over the CTA)
+    uint32_t mma_ph = 0;  // completed phases of mma_bar (uniform over the CTA)
     const uint32_t idesc_b_mn = 1u << 16;  // B operand MN-major
 
     // C = A * B over K in [0, kpad), written to buffer zo (rows and columns < kpad).
@@ -467,7 +481,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         // on-chip form: the image of X (hi boxes, then lo boxes) at the start of the stage area
         const bool resident = kpad <= kResKpad;
         const int RB = (kpad + 63) >> 6;
-        const uint32_t img_lo_off = static_cast<uint32_t>(RB * RB) * 8192u;
+        const uint32_t img_bytes = static_cast<uint32_t>(RB * RB) * 8192u;
+        // kpad in (160, 192]: the hi image is double-buffered (X' is written while X is read)
+        const bool dbl = resident && kpad > 160;
+        uint32_t hi_off = dbl ? (NB == 2 ? img_bytes : 0u) : 0u;  // current hi image
+        const uint32_t lo_off = dbl ? 0u : img_bytes;            // lo image (split form)
 
         // prologue: X0 = (T_j - mu I) / b_j in FP32, zero-padded to kpad x kpad, split hi/lo,
         // into the shared-memory image (on-chip form) or the slot's X buffer
@@ -504,9 +522,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     for (int i = 0; i < 8; i += 2) split2<PREC, NB>(x[i], x[i + 1], hw[i >> 1], lw[i >> 1]);
                     if (resident) {
                         const uint32_t off = img_offset(r, c0, RB);
-                        *reinterpret_cast<uint4*>(smem + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(smem + hi_off + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                         if constexpr (NB == 2)
-                            *reinterpret_cast<uint4*>(smem + img_lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                            *reinterpret_cast<uint4*>(smem + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     } else {
                         *reinterpret_cast<uint4*>(xh + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                         if constexpr (NB == 2)
@@ -541,11 +559,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             // kpad <= 160 every tile's X' keeps its own region (Q, R) until the last tile's
             // second product is done and then goes straight into the image: no L2 traffic.
             const bool onchip = kpad <= 160;
-            const uint32_t P = tmem_base, Q = tmem_base + (onchip ? 160 : 256), R = tmem_base + 320;
+            const uint32_t P = tmem_base, Q = tmem_base + (onchip ? 160 : 192), R = tmem_base + 320;
             const int mtiles = (kpad + 127) >> 7;
             const int ksteps = kpad >> 4;
             const uint32_t idesc = idesc_f16(128, kpad, C::kFmt) | idesc_b_mn;
-            const uint32_t img_hi = smem_u32(smem), img_lo = img_hi + img_lo_off;
+            const uint32_t smem_base = smem_u32(smem), img_lo = smem_base + lo_off;
+            uint32_t img_hi = smem_base + hi_off;  // moves with hi_off (double-buffered form)
+            const uint32_t L = tmem_base + 384;    // double-buffered form: lo of tile 0's X' (96 columns)
+            float* rpart_s = reinterpret_cast<float*>(smem + 160 * 1024);  // [3][kResKpad], iteration 0 only
+            float* rsum_s = rpart_s + 3 * kResKpad;
+            float* rs2_s = rsum_s + kResKpad;
             const uint32_t lbo = static_cast<uint32_t>(RB) * 8192u;
             const int q = warp & 3, part = warp >> 2;
             const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
@@ -621,7 +644,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 tmem_wait_st();
             };
             // drain: X'_t = alpha C (zero outside n x n) -> rows of buffer zo, or into the image
-            auto drain = [&](int t, uint32_t acc, float alpha, int zo, bool to_image) {
+            auto drain = [&](int t, uint32_t acc, float alpha, int zo, bool to_image, uint32_t hi_dst) {
                 const int row = 128 * t + 32 * q + lane;
                 uint16_t* out_hi = ws + static_cast<int64_t>(zo) * buf + static_cast<int64_t>(row) * a.ld;
                 uint16_t* out_lo = out_hi + buf;
@@ -647,9 +670,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const uint32_t off = img_offset(row, c0 + 8 * u, RB);
-                            *reinterpret_cast<uint4*>(smem + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                            *reinterpret_cast<uint4*>(smem + hi_dst + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
                             if constexpr (NB == 2)
-                                *reinterpret_cast<uint4*>(smem + img_lo_off + off) =
+                                *reinterpret_cast<uint4*>(smem + lo_off + off) =
                                     make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
                         }
                     } else {
@@ -664,7 +687,63 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     }
                 }
             };
-            // scan: rpart_s[part][row] = sum_c |C_rc| w_c over this thread's columns (w = 1 when null)
+            // Double-buffered form, tile 0 of X' while the image is still read: hi into the next
+            // hi image, lo (packed pairs, 16 columns per 32-column chunk) into tensor memory at L.
+            auto drain_split0 = [&](uint32_t acc, float alpha, uint32_t hi_dst) {
+                const int row = 32 * q + lane;
+#pragma unroll 1
+                for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
+                    uint32_t raw[32];
+                    tmem_ld32_issue(acc + lane_off + c0, raw);
+                    tmem_wait_ld();
+                    float y[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) y[i] = (row < s.n && c0 + i < s.n) ? alpha * __uint_as_float(raw[i]) : 0.0f;
+                    uint32_t hw[16], lw[16];
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        *reinterpret_cast<uint4*>(smem + hi_dst + img_offset(row, c0 + 8 * u, RB)) =
+                            make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                    if constexpr (NB == 2) tmem_st16(L + lane_off + c0 / 2, lw);
+                }
+                tmem_wait_st();
+            };
+            // ... then, once the image is free: the lo half from tensor memory into the lo image
+            auto fill_lo0 = [&]() {
+                if constexpr (NB == 2) {
+                    const int row = 32 * q + lane;
+#pragma unroll 1
+                    for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
+                        uint32_t lw[16];
+                        tmem_ld16(L + lane_off + c0 / 2, lw);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            *reinterpret_cast<uint4*>(smem + lo_off + img_offset(row, c0 + 8 * u, RB)) =
+                                make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
+                    }
+                }
+            };
+            // ... or, after the last iteration, tile 0 of X' into the slot's X buffer zo
+            auto spill0 = [&](int zo, uint32_t hi_src) {
+                const int row = 32 * q + lane;
+                uint16_t* out_hi = ws + static_cast<int64_t>(zo) * buf + static_cast<int64_t>(row) * a.ld;
+                uint16_t* out_lo = out_hi + buf;
+#pragma unroll 1
+                for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
+                    uint32_t lw[16];
+                    if constexpr (NB == 2) tmem_ld16(L + lane_off + c0 / 2, lw);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        reinterpret_cast<uint4*>(out_hi + c0)[u] =
+                            *reinterpret_cast<const uint4*>(smem + hi_src + img_offset(row, c0 + 8 * u, RB));
+                        if constexpr (NB == 2)
+                            reinterpret_cast<uint4*>(out_lo + c0)[u] = make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
+                    }
+                }
+            };
+            // scan: rpart_s[part, row] = sum_c |C_rc| w_c over this thread's columns (w = 1 when null)
             auto scan = [&](int t, uint32_t acc, const float* w) {
                 const int row = 128 * t + 32 * q + lane;
                 float sum = 0.0f;
@@ -679,12 +758,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                         if (row < s.n && c < s.n) sum = fmaf(fabsf(__uint_as_float(raw[i])), w ? w[c] : 1.0f, sum);
                     }
                 }
-                if (row < s.n) rpart_s[part][row] = sum;
+                if (row < s.n) rpart_s[part * kResKpad + row] = sum;
             };
             // out[r] = sum of the parts' partials, in part order (deterministic); after a barrier
             auto gather_parts = [&](float* out) {
                 __syncthreads();
-                for (int r = tid; r < s.n; r += kThreads) out[r] = (rpart_s[0][r] + rpart_s[1][r]) + rpart_s[2][r];
+                for (int r = tid; r < s.n; r += kThreads) out[r] = (rpart_s[r] + rpart_s[kResKpad + r]) + rpart_s[2 * kResKpad + r];
                 __syncthreads();
             };
 
@@ -695,7 +774,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 float alpha = -0.5f, shift = 3.0f;
                 if (it == 0) {
                     // Z_t = X0_t X0 for every tile; the bound on rho(Z) as in the streamed form
-                    for (int r = tid; r < kpad; r += kThreads) rpart_s[0][r] = rpart_s[1][r] = rpart_s[2][r] = 0.0f;
+                    for (int r = tid; r < 3 * kResKpad; r += kThreads) rpart_s[r] = 0.0f;
                     if (warp == 1 && lane == 0) {
                         tc_fence_after();
                         issue_xx(0, P);
@@ -748,7 +827,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                         issue_xx(t, P);
                         tc_commit(&mma_bar);
                     }
-                    if (t > 0 && !onchip) drain(t - 1, Q, alpha, zn, false);  // overlaps the product
+                    const uint32_t hi_next = hi_off == img_bytes ? 2 * img_bytes : img_bytes;  // NB == 2
+                    const uint32_t hi_next1 = hi_off == 0 ? img_bytes : 0;                    // NB == 1
+                    if (t == 1 && !onchip) drain_split0(Q, alpha, NB == 2 ? hi_next : hi_next1);  // overlaps the product
                     if (g1) mma_wait();
                     tc_fence_before();
                     __syncthreads();
@@ -781,41 +862,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 last = conv_s || bad_s || it + 1 == a.max_iter;
                 if (onchip) {
                     // every tile: into the image when the iteration continues, else to the X buffer
-                    drain(0, Q, alpha, zn, !last);
-                    if (mtiles > 1) drain(1, R, alpha, zn, !last);
+                    drain(0, Q, alpha, zn, !last, hi_off);
+                    if (mtiles > 1) drain(1, R, alpha, zn, !last, hi_off);
                     if (last) fence_proxy_async_global();
                     else fence_proxy_async_smem();
                 } else {
-                    // the last tile: into the image when the iteration continues, else to the X buffer
-                    drain(mtiles - 1, Q, alpha, zn, !last);
-                    if (last) fence_proxy_async_global();
-                    else fence_proxy_async_smem();
-                    if (!last && mtiles > 1) fence_proxy_async_global();
+                    // double-buffered: tile 0 is in the next hi image and (lo) in tensor memory
+                    const uint32_t hi_next = NB == 2 ? (hi_off == img_bytes ? 2 * img_bytes : img_bytes)
+                                                     : (hi_off == 0 ? img_bytes : 0);
+                    if (last) {
+                        spill0(zn, hi_next);
+                        drain(1, Q, alpha, zn, false, hi_next);
+                        fence_proxy_async_global();
+                    } else {
+                        drain(1, Q, alpha, zn, true, hi_next);
+                        fill_lo0();
+                        fence_proxy_async_smem();
+                        hi_off = hi_next;
+                        img_hi = smem_base + hi_off;
+                    }
                 }
                 tc_fence_before();
                 __syncthreads();
                 cur ^= 1;
                 done = it + 1;
                 if (last) break;
-                if (mtiles > 1 && !onchip) {
-                    // the earlier tiles' rows of X' back into the image (row blocks < 2 (mtiles - 1))
-                    const int rbs = 2 * (mtiles - 1);
-                    if (tid == 0) {
-                        img_pending_s = 1;
-                        img_parity_s = static_cast<int>(img_ph & 1u);
-                        mbar_arrive_expect_tx(&img_bar, static_cast<uint32_t>(NB * RB * rbs) * 8192u);
-                        for (int b = 0; b < NB; ++b)
-                            for (int cb = 0; cb < RB; ++cb)
-                                for (int rb = 0; rb < rbs; ++rb)
-                                    tma_load_3d(smem + b * img_lo_off + (cb * RB + rb) * 8192, &tmap, 64 * cb, 64 * rb, zn + b,
-                                                &img_bar);
-                    }
-                    mbar_wait(&img_bar, img_ph & 1u, &abort_s, a.status);  // on failure the abort flag is raised
-                    ++img_ph;
-                    __syncthreads();
-                    if (*abortp) break;
-                    if (tid == 0) img_pending_s = 0;
-                }
             }
         } else {
         for (int it = 0; it < a.max_iter; ++it) {
@@ -965,7 +1036,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     if (*abortp && tid == 0) {
         for (int it = m_consumed_s; it < p_issued_s; ++it)
             mbar_wait_plain(&full_bar[it % S], (it / S) & 1, 1u << 20);
-        if (img_pending_s) mbar_wait_plain(&img_bar, static_cast<uint32_t>(img_parity_s), 1u << 20);
     }
     if (*abortp && warp == 1 && lane == 0) {
         tc_commit(&drain_bar);
@@ -989,7 +1059,8 @@ size_t ns_tc_smem_bytes(int precision) {
 
 template <int PREC>
 static cudaError_t launch_prec(const NsTcArgs& a, const CUtensorMap& tmap, int max_nblk, cudaStream_t st) {
-    const size_t smem = TcCfg<PREC>::kDynSmem + sizeof(int) * (static_cast<size_t>(max_nblk) + 1);
+    (void)max_nblk;
+    const size_t smem = TcCfg<PREC>::kDynSmem;
     cudaError_t e = cudaFuncSetAttribute(k_ns_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.work_counter, 0, sizeof(int), st);
