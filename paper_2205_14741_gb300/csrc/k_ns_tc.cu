@@ -101,24 +101,15 @@ __device__ __forceinline__ float from16(uint16_t h) {
     else return __half2float(__ushort_as_half(h));
 }
 
-// x rounded to the significand width of the 16-bit format (11 bits for FP16,
-// 8 for BF16), half away from zero, as an FP32 number: exactly representable
-// in the 16-bit format except in the FP16 subnormal range (|x| < 2^-14), where
-// the conversion below rounds it once more (absolute error < 2^-25).
-template <int PREC>
-__device__ __forceinline__ float round16(float x) {
-    constexpr uint32_t half_ulp = (PREC == 3) ? 0x8000u : 0x1000u;
-    constexpr uint32_t mask = (PREC == 3) ? 0xFFFF0000u : 0xFFFFE000u;
-    return __uint_as_float((__float_as_uint(x) + half_ulp) & mask);
-}
 
 // (a, b) -> hi pair and lo pair with a ~ hi.x + lo.x, b ~ hi.y + lo.y
 template <int PREC, int NB>
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hw, uint32_t& lw) {
     if constexpr (NB == 2) {
-        const float ha = round16<PREC>(a), hb = round16<PREC>(b);
-        hw = pack2<PREC>(ha, hb);
-        lw = pack2<PREC>(a - ha, b - hb);
+        // hi = (a, b) rounded to the 16-bit format; lo = the FP32 remainder, rounded
+        hw = pack2<PREC>(a, b);
+        const float2 h = unpack2<PREC>(hw);
+        lw = pack2<PREC>(a - h.x, b - h.y);
     } else {
         hw = pack2<PREC>(a, b);
         lw = 0;
@@ -976,9 +967,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     if constexpr (NB == 2) z += from16<PREC>(zl[o]);
                     z -= shift;
                     if constexpr (NB == 2) {
-                        const float hi = round16<PREC>(z);
-                        zh[o] = to16<PREC>(hi);
-                        zl[o] = to16<PREC>(z - hi);
+                        const uint16_t hi = to16<PREC>(z);
+                        zh[o] = hi;
+                        zl[o] = to16<PREC>(z - from16<PREC>(hi));
                     } else {
                         zh[o] = to16<PREC>(z);
                     }
