@@ -189,6 +189,11 @@ __device__ __forceinline__ uint64_t sdesc_mn_sw128_lbo(uint32_t saddr, uint32_t 
     return d;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (bytes a multiple of 16, p 16-byte aligned).
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Orders this thread's generic shared-memory writes before later async-proxy
 // (tensor-core) reads issued after a barrier.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -458,8 +463,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         __syncthreads();
     };
 
+    // Jobs are claimed one ahead: while a submatrix iterates, its successor's staged
+    // T_j is prefetched into L2 (the prologue then reads it from there).
+    __shared__ int next_s;
+    if (tid == 0) next_s = atomicAdd(a.work_counter, 1);
     for (;;) {
-        if (tid == 0) job_s = atomicAdd(a.work_counter, 1);
+        if (tid == 0) {
+            job_s = next_s;
+            next_s = atomicAdd(a.work_counter, 1);
+            if (next_s < a.n_subs) {
+                const SubDesc sn = a.subs[a.order[next_s]];
+                const uint64_t bytes = static_cast<uint64_t>(sn.n) * sn.ld * sizeof(float);
+                const uint32_t len = static_cast<uint32_t>(bytes < (4u << 20) ? bytes : (4u << 20)) & ~15u;
+                if (len) prefetch_l2_bulk(a.T + sn.t_off, len);
+            }
+        }
         __syncthreads();
         const int job = job_s;
         if (job >= a.n_subs || *abortp) break;
