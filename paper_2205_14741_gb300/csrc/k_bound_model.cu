@@ -1,4 +1,5 @@
-// Learned spectral bound: features, Lanczos labels, MLP inference and training.
+// Learned spectral bound: Lanczos labels and MLP training (the features and the
+// inference run inside the gather kernel, k_pattern.cu).
 //
 // The network predicts, per submatrix A = T_j - mu I, the ratios rho/G and
 // delta/G (spectral radius and smallest |eigenvalue| over the Gershgorin
@@ -20,10 +21,7 @@ namespace smx {
 
 namespace {
 
-constexpr int kF = kModelFeatures, kH = 64, kO = 2;
-constexpr int kOffB1 = kH * kF, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kH * kH, kOffW3 = kOffB2 + kH,
-              kOffB3 = kOffW3 + kO * kH;
-static_assert(kOffB3 + kO == kModelParams, "parameter layout");
+constexpr int kF = kModelFeatures, kH = kModelHidden, kO = 2;
 
 constexpr int kChunk = 64;  // samples per gradient block
 
@@ -34,63 +32,6 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 }
 
 }  // namespace
-
-// ---------------------------------------------------------------------------
-// features (one CTA of 256 threads per submatrix, a warp per row)
-// ---------------------------------------------------------------------------
-template <class R>
-__global__ void __launch_bounds__(256) k_features(const SubDesc* __restrict__ subs, const R* __restrict__ T,
-                                                  const float* __restrict__ prev_ratio, float* __restrict__ feat) {
-    __shared__ float part[8][9];
-    const SubDesc s = subs[blockIdx.x];
-    const R* t = T + s.t_off;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float g = 0.f, fro = 0.f, dmax = 0.f, dabs = 0.f, dsum = 0.f, dsq = 0.f, rmax = 0.f, rsum = 0.f;
-    for (int r = warp; r < s.n; r += 8) {
-        float sa = 0.f, sq = 0.f;
-        for (int c = lane; c < s.n; c += 32) {
-            const float v = static_cast<float>(t[static_cast<int64_t>(r) * s.ld + c]);
-            sa += fabsf(v);
-            sq = fmaf(v, v, sq);
-        }
-        sa = warp_sum_f(sa);
-        sq = warp_sum_f(sq);
-        const float d = static_cast<float>(t[static_cast<int64_t>(r) * s.ld + r]);
-        g = fmaxf(g, sa);
-        fro += sq;
-        dmax = fmaxf(dmax, fabsf(d));
-        dabs += fabsf(d);
-        dsum += d;
-        dsq = fmaf(d, d, dsq);
-        rmax = fmaxf(rmax, sa - fabsf(d));
-        rsum += sa - fabsf(d);
-    }
-    if (lane == 0) {
-        part[warp][0] = g; part[warp][1] = fro; part[warp][2] = dmax; part[warp][3] = dabs;
-        part[warp][4] = dsum; part[warp][5] = dsq; part[warp][6] = rmax; part[warp][7] = rsum;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float G = 0.f, F2 = 0.f, Dm = 0.f, Da = 0.f, Ds = 0.f, Dq = 0.f, Rm = 0.f, Rs = 0.f;
-        for (int w = 0; w < 8; ++w) {
-            G = fmaxf(G, part[w][0]); F2 += part[w][1]; Dm = fmaxf(Dm, part[w][2]); Da += part[w][3];
-            Ds += part[w][4]; Dq += part[w][5]; Rm = fmaxf(Rm, part[w][6]); Rs += part[w][7];
-        }
-        const float n = static_cast<float>(s.n);
-        const float ig = G > 0.f ? 1.f / G : 0.f;
-        const float mean = Ds / n;
-        float* f = feat + static_cast<int64_t>(blockIdx.x) * kF;
-        f[0] = sqrtf(F2 / n) * ig;
-        f[1] = Dm * ig;
-        f[2] = Da / n * ig;
-        f[3] = sqrtf(fmaxf(Dq / n - mean * mean, 0.f)) * ig;
-        f[4] = Rm * ig;
-        f[5] = Rs / n * ig;
-        f[6] = n / 256.f;
-        f[7] = mean * ig;
-        f[8] = prev_ratio ? prev_ratio[blockIdx.x] : 0.f;
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Lanczos labels (one CTA per submatrix): rho from A, delta from A^2
@@ -239,36 +180,6 @@ __global__ void __launch_bounds__(256) k_lanczos(const SubDesc* __restrict__ sub
 // MLP
 // ---------------------------------------------------------------------------
 
-// Inference with FP16-rounded weights, one thread per sample.
-__global__ void __launch_bounds__(128) k_mlp_predict(const float* __restrict__ params, const float* __restrict__ feat,
-                                                     int m, float* __restrict__ out) {
-    __shared__ float p[kModelParams];
-    for (int i = threadIdx.x; i < kModelParams; i += blockDim.x) p[i] = __half2float(__float2half_rn(params[i]));
-    __syncthreads();
-    const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (sidx >= m) return;
-    float x[kF];
-#pragma unroll
-    for (int k = 0; k < kF; ++k) x[k] = feat[static_cast<int64_t>(sidx) * kF + k];
-    float h1[kH];
-    for (int i = 0; i < kH; ++i) {
-        float a = p[kOffB1 + i];
-#pragma unroll
-        for (int k = 0; k < kF; ++k) a = fmaf(p[i * kF + k], x[k], a);
-        h1[i] = tanhf(a);
-    }
-    float y0 = p[kOffB3], y1 = p[kOffB3 + 1];
-    for (int i = 0; i < kH; ++i) {
-        float a = p[kOffB2 + i];
-        for (int k = 0; k < kH; ++k) a = fmaf(p[kOffW2 + i * kH + k], h1[k], a);
-        const float h2 = tanhf(a);
-        y0 = fmaf(p[kOffW3 + i], h2, y0);
-        y1 = fmaf(p[kOffW3 + kH + i], h2, y1);
-    }
-    out[2 * static_cast<int64_t>(sidx)] = y0;
-    out[2 * static_cast<int64_t>(sidx) + 1] = y1;
-}
-
 // Forward + backward for samples [blockIdx.x * 64, +64): per-block gradient sums
 // (sum over the block's samples, in sample order) and half the squared residual.
 __global__ void __launch_bounds__(256) k_mlp_grad(const float* __restrict__ params, const float* __restrict__ X,
@@ -395,26 +306,9 @@ __global__ void k_mlp_reduce_adam(const float* __restrict__ partial, const float
     }
 }
 
-// b_j = G_j * clamp(rho_hat / G) * (1 + margin) / 1.2: the largest eigenvalue of
-// X0 = A / b_j lands near 1.2 / (1 + margin) when the prediction is right.
-__global__ void k_model_bound(const float* __restrict__ pred, const double* __restrict__ gersh, double* __restrict__ bound,
-                              int n, float margin) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const double r = fmin(fmax(static_cast<double>(pred[2 * j]), 0.02), 1.0);
-    bound[j] = gersh[j] * r * (1.0 + margin) / 1.2;
-}
-
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_features(const SubDesc* subs, int n_subs, const void* T, bool fp32, const float* prev_ratio,
-                            float* feat, cudaStream_t st) {
-    if (fp32) k_features<float><<<n_subs, 256, 0, st>>>(subs, static_cast<const float*>(T), prev_ratio, feat);
-    else k_features<double><<<n_subs, 256, 0, st>>>(subs, static_cast<const double*>(T), prev_ratio, feat);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_lanczos(const SubDesc* subs, int n_subs, int max_n, const void* T, bool fp32, int ksteps,
                            float* labels, cudaStream_t st) {
     const size_t smem = sizeof(float) * 4 * static_cast<size_t>(max_n);
@@ -427,12 +321,6 @@ cudaError_t launch_lanczos(const SubDesc* subs, int n_subs, int max_n, const voi
         if (e != cudaSuccess) return e;
         k_lanczos<double><<<n_subs, 256, smem, st>>>(subs, static_cast<const double*>(T), ksteps, labels);
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mlp_predict(const float* params, const float* feat, int m, float* out, cudaStream_t st) {
-    if (m <= 0) return cudaSuccess;
-    k_mlp_predict<<<(m + 127) / 128, 128, 0, st>>>(params, feat, m, out);
     return cudaGetLastError();
 }
 
@@ -452,12 +340,6 @@ cudaError_t launch_mlp_step(const float* params_in, const float* X, const float*
     if (e != cudaSuccess) return e;
     k_mlp_reduce_adam<<<(kModelParams + 255) / 256, 256, 0, st>>>(partial, partial_loss, nb, m, params, mst, vst, t, lr,
                                                                   grad_out, loss_out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_model_bound(const float* pred, const double* gersh, double* bound, int n, float margin,
-                               cudaStream_t st) {
-    k_model_bound<<<(n + 255) / 256, 256, 0, st>>>(pred, gersh, bound, n, margin);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,8 @@
 //  a8  deterministic FP64 sums of trace(D) and trace(D H)
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "smx_finish.cuh"
 #include "smx_kernels.h"
 
@@ -96,13 +98,23 @@ cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, con
 // then takes, from each listed block (R_j[a], R_j[c]) (column-major), its
 // column q -- T_j is symmetric, so that column is row x restricted to block a.
 // The row is put together in shared memory and written once, coalesced, with
-// its absolute sum for the Gershgorin bound b_j = max_x sum_y |T[x][y]|.
+// its absolute sum for the Gershgorin bound b_j = max_x sum_y |T[x][y]|, and
+// the row statistics of the learned bound's features.
+//
+// Learned bound (optional): features of A = T_j - mu I (all over G except f6,
+// f8): f0 ||A||_F/sqrt(n), f1 max|A_rr|, f2 mean|A_rr|, f3 std(A_rr), f4 max_r
+// R_r, f5 mean_r R_r (R_r = sum_{c != r} |A_rc|), f6 n/256, f7 mean A_rr, f8
+// the previous step's ratio; then the 9 -> 64 -> 64 -> 2 tanh network with the
+// parameters rounded to FP16, and b_j = G clamp(rho_hat/G, 0.02, 1) (1 + margin)/1.2.
 template <class R>
 __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict__ subs, PatternView pv,
                                                       const R* __restrict__ H, double mu_d, R* __restrict__ T,
-                                                      double* __restrict__ bound, int ld_max, int nblk_max, int nw) {
+                                                      double* __restrict__ bound, int ld_max, int nblk_max, int nw,
+                                                      GatherExtras ex) {
     extern __shared__ __align__(16) unsigned char gsm[];
     __shared__ double warp_max_s[8];
+    __shared__ float stat_s[8][7];  // per warp: F2, Da, Ds, Dq, Rs (sums), Dm, Rm (maxima)
+    __shared__ float x_s[kModelFeatures], h1_s[kModelHidden], y_s[2][2];
     const R mu = static_cast<R>(mu_d);
     const SubDesc s = subs[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -124,6 +136,7 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
 
     R* t = T + s.t_off;
     double m = 0.0;
+    float f2 = 0.f, da = 0.f, ds = 0.f, dq = 0.f, rs = 0.f, dm = 0.f, rm = 0.f;  // feature statistics
     for (int c = warp; c < s.nblk && warp < nw; c += nw) {  // nw warps own a row buffer each
         const int col = rows[c];
         const int bc = ls[c + 1] - ls[c];
@@ -168,31 +181,119 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
             __syncwarp();
             R* trow = t + static_cast<int64_t>(ls[c] + q) * s.ld;
             R acc = R(0);
+            float sq = 0.f;
             for (int y = lane; y < s.ld; y += 32) {
                 const R v = rowbuf[y];
                 trow[y] = v;
                 acc += fabs(v);
+                sq = fmaf(static_cast<float>(v), static_cast<float>(v), sq);
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            }
             m = fmax(m, static_cast<double>(acc));
+            const float d = static_cast<float>(rowbuf[ls[c] + q]), ad = fabsf(d), rr = static_cast<float>(acc) - ad;
+            f2 += sq;
+            da += ad;
+            ds += d;
+            dq = fmaf(d, d, dq);
+            rs += rr;
+            dm = fmaxf(dm, ad);
+            rm = fmaxf(rm, rr);
             __syncwarp();
         }
     }
-    if (lane == 0) warp_max_s[warp] = m;
+    if (lane == 0) {
+        warp_max_s[warp] = m;
+        stat_s[warp][0] = f2;
+        stat_s[warp][1] = da;
+        stat_s[warp][2] = ds;
+        stat_s[warp][3] = dq;
+        stat_s[warp][4] = rs;
+        stat_s[warp][5] = dm;
+        stat_s[warp][6] = rm;
+    }
     __syncthreads();
+    double g = 0.0;
+    for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
+    const double graw = g;
+    // in FP32 the row sums carry a relative error below n 2^-24, covered by the 1e-5 margin
+    if (sizeof(R) == 4) g *= 1.0 + 1e-5;
+    if (!(g > 0.0)) g = 1.0;
+    if (ex.feat || ex.params) {
+        if (tid == 0) {
+            float F2 = 0.f, Da = 0.f, Ds = 0.f, Dq = 0.f, Rs = 0.f, Dm = 0.f, Rm = 0.f;
+            for (int w = 0; w < 8; ++w) {
+                F2 += stat_s[w][0];
+                Da += stat_s[w][1];
+                Ds += stat_s[w][2];
+                Dq += stat_s[w][3];
+                Rs += stat_s[w][4];
+                Dm = fmaxf(Dm, stat_s[w][5]);
+                Rm = fmaxf(Rm, stat_s[w][6]);
+            }
+            const float n = static_cast<float>(s.n), G = static_cast<float>(graw);
+            const float ig = G > 0.f ? 1.f / G : 0.f, mean = Ds / n;
+            x_s[0] = sqrtf(F2 / n) * ig;
+            x_s[1] = Dm * ig;
+            x_s[2] = Da / n * ig;
+            x_s[3] = sqrtf(fmaxf(Dq / n - mean * mean, 0.f)) * ig;
+            x_s[4] = Rm * ig;
+            x_s[5] = Rs / n * ig;
+            x_s[6] = n / 256.f;
+            x_s[7] = mean * ig;
+            x_s[8] = ex.prev_ratio ? ex.prev_ratio[blockIdx.x] : 0.f;
+            if (ex.feat)
+                for (int k = 0; k < kModelFeatures; ++k) ex.feat[static_cast<int64_t>(blockIdx.x) * kModelFeatures + k] = x_s[k];
+        }
+        __syncthreads();
+    }
+    double b = g;
+    if (ex.params) {
+        // the network, weights rounded to FP16 (threads 0..63: one hidden unit each)
+        const float* p = ex.params;
+        auto w16 = [](float v) { return __half2float(__float2half_rn(v)); };
+        if (tid < kModelHidden) {
+            float acc = w16(p[kOffB1 + tid]);
+            for (int k = 0; k < kModelFeatures; ++k) acc = fmaf(w16(p[tid * kModelFeatures + k]), x_s[k], acc);
+            h1_s[tid] = tanhf(acc);
+        }
+        __syncthreads();
+        if (tid < kModelHidden) {
+            float acc = w16(p[kOffB2 + tid]);
+            for (int k = 0; k < kModelHidden; ++k) acc = fmaf(w16(p[kOffW2 + tid * kModelHidden + k]), h1_s[k], acc);
+            const float h2 = tanhf(acc);
+            float y0 = w16(p[kOffW3 + tid]) * h2, y1 = w16(p[kOffW3 + kModelHidden + tid]) * h2;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+                y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+            }
+            if (lane == 0) {
+                y_s[warp][0] = y0;
+                y_s[warp][1] = y1;
+            }
+        }
+        __syncthreads();
+        const float y0 = (y_s[0][0] + y_s[1][0]) + w16(p[kOffB3]);
+        const float y1 = (y_s[0][1] + y_s[1][1]) + w16(p[kOffB3 + 1]);
+        if (tid == 0 && ex.pred) {
+            ex.pred[2 * static_cast<int64_t>(blockIdx.x)] = y0;
+            ex.pred[2 * static_cast<int64_t>(blockIdx.x) + 1] = y1;
+        }
+        b = g * fmin(fmax(static_cast<double>(y0), 0.02), 1.0) * (1.0 + ex.margin) / 1.2;
+    }
     if (tid == 0) {
-        // in FP32 the row sums carry a relative error below n 2^-24, covered by the 1e-5 margin
-        double g = 0.0;
-        for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
-        if (sizeof(R) == 4) g *= 1.0 + 1e-5;
-        bound[blockIdx.x] = g > 0.0 ? g : 1.0;
+        bound[blockIdx.x] = b;
+        if (ex.gersh) ex.gersh[blockIdx.x] = g;
     }
 }
 
 template <class R>
 static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
-                                 const R* H, double mu, R* T, double* bound, cudaStream_t st) {
+                                 const R* H, double mu, R* T, double* bound, const GatherExtras& ex, cudaStream_t st) {
     const size_t head = (static_cast<size_t>(2 * max_nblk + 1) * sizeof(int) + 15) & ~size_t(15);
     const size_t lists = (static_cast<size_t>(max_nblk) * (sizeof(int64_t) + sizeof(int)) + 15) & ~size_t(15);
     const size_t per_warp = lists + ((static_cast<size_t>(max_ld) * sizeof(R) + 15) & ~size_t(15));
@@ -201,18 +302,20 @@ static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, 
     const size_t smem = head + nw * per_warp;
     cudaError_t e = cudaFuncSetAttribute(k_gather_bound<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    k_gather_bound<R><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound, max_ld, max_nblk, nw);
+    k_gather_bound<R><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound, max_ld, max_nblk, nw, ex);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
-                                const double* H, double mu, double* T, double* bound, cudaStream_t st) {
-    return launch_gather<double>(subs, n_subs, max_nblk, max_ld, pv, H, mu, T, bound, st);
+                                const double* H, double mu, double* T, double* bound, const GatherExtras& ex,
+                                cudaStream_t st) {
+    return launch_gather<double>(subs, n_subs, max_nblk, max_ld, pv, H, mu, T, bound, ex, st);
 }
 
 cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
-                                    const float* H32, double mu, float* T32, double* bound, cudaStream_t st) {
-    return launch_gather<float>(subs, n_subs, max_nblk, max_ld, pv, H32, mu, T32, bound, st);
+                                    const float* H32, double mu, float* T32, double* bound, const GatherExtras& ex,
+                                    cudaStream_t st) {
+    return launch_gather<float>(subs, n_subs, max_nblk, max_ld, pv, H32, mu, T32, bound, ex, st);
 }
 
 // One CTA per submatrix: scatter of the saved owner columns (Fig. 2 step (iii)).

@@ -373,6 +373,22 @@ static smx_status ns_event_pair(smx_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
 }
 
 // One build at chemical potential mu (a3 - a8).
+// a3 + a4 for block columns [j0, j0 + m) into the staging buffer.
+static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const GatherExtras& ex) {
+    const PatternView pv = pattern_view(c);
+    const int max_ld = static_cast<int>(round_up(c->max_n, 4));
+    SubDesc* subs = dp<SubDesc>(c->d_subs);
+    if (c->precision == SMX_FP64) {
+        SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, max_ld, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
+                                     dp<double>(c->d_bound) + j0, ex, c->stream));
+    } else {
+        SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, max_ld, pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
+                                         dp<double>(c->d_bound) + j0, ex, c->stream));
+    }
+    c->kernel_launches += 1;
+    return SMX_OK;
+}
+
 static smx_status build_at(smx_ctx* c, double mu) {
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
     cudaStream_t st = c->stream;
@@ -392,26 +408,14 @@ static smx_status build_at(smx_ctx* c, double mu) {
     // one pass of a3-a7 per chunk of block columns (the staging of T_j is reused)
     for (size_t k = 0; k + 1 < c->chunk_start.size(); ++k) {
         const int j0 = c->chunk_start[k], m = c->chunk_start[k + 1] - j0;
-        if (c->precision == SMX_FP64) {
-            SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, static_cast<int>(round_up(c->max_n, 4)), pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
-                                         dp<double>(c->d_bound) + j0, st));
-        } else {
-            SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, static_cast<int>(round_up(c->max_n, 4)), pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
-                                             dp<double>(c->d_bound) + j0, st));
+        GatherExtras ex;
+        ex.gersh = dp<double>(c->d_gersh) + j0;
+        if (c->model_on) {  // learned bound: features and prediction inside the gather (checked in the NS kernel)
+            ex.prev_ratio = dp<float>(c->d_prev_ratio) + j0;
+            ex.params = dp<float>(c->d_params);
+            ex.margin = kModelMargin;
         }
-        SMX_CUDA(cudaMemcpyAsync(dp<double>(c->d_gersh) + j0, dp<double>(c->d_bound) + j0, sizeof(double) * m,
-                                 cudaMemcpyDeviceToDevice, st));
-        c->kernel_launches += 1;
-        if (c->model_on) {
-            // learned bound: features -> prediction -> b_j (checked inside the Newton-Schulz kernel)
-            SMX_CUDA(launch_features(subs + j0, m, c->d_T.p, c->precision != SMX_FP64, dp<float>(c->d_prev_ratio) + j0,
-                                     dp<float>(c->d_feat) + kModelFeatures * j0, st));
-            SMX_CUDA(launch_mlp_predict(dp<float>(c->d_params), dp<float>(c->d_feat) + kModelFeatures * j0, m,
-                                        dp<float>(c->d_pred) + 2 * j0, st));
-            SMX_CUDA(launch_model_bound(dp<float>(c->d_pred) + 2 * j0, dp<double>(c->d_gersh) + j0,
-                                        dp<double>(c->d_bound) + j0, m, kModelMargin, st));
-            c->kernel_launches += 3;
-        }
+        SMX_TRY(gather_chunk(c, j0, m, mu, ex));
         cudaEvent_t ns0, ns1;
         SMX_TRY(ns_event_pair(c, &ns0, &ns1));
         if (c->precision == SMX_FP64) {
@@ -846,26 +850,26 @@ static smx_status model_upload(smx_ctx* c, const std::vector<float>& p) {
     return SMX_OK;
 }
 
-// Per chunk of block columns: gather T (staging of the context's precision) and
-// the Gershgorin bound at the fixed mu, then the features (d_feat) and, when
-// lanczos_steps > 0, the Lanczos labels (d_labels) of every submatrix.
-static smx_status features_labels(smx_ctx* c, int32_t lanczos_steps) {
+// Per chunk of block columns: gather T (staging of the context's precision),
+// the Gershgorin bound and the features (d_feat) at the fixed mu, the model's
+// predictions (d_pred) when asked, and, when lanczos_steps > 0, the Lanczos
+// labels (d_labels) of every submatrix.
+static smx_status features_labels(smx_ctx* c, int32_t lanczos_steps, bool predict) {
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
-    const PatternView pv = pattern_view(c);
     const bool f32 = c->precision != SMX_FP64;
     SubDesc* subs = dp<SubDesc>(c->d_subs);
     for (size_t k = 0; k + 1 < c->chunk_start.size(); ++k) {
         const int j0 = c->chunk_start[k], m = c->chunk_start[k + 1] - j0;
-        if (!f32) {
-            SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, static_cast<int>(round_up(c->max_n, 4)), pv, dp<double>(c->d_H), c->mu, dp<double>(c->d_T),
-                                         dp<double>(c->d_bound) + j0, c->stream));
-        } else {
-            SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, static_cast<int>(round_up(c->max_n, 4)), pv, dp<float>(c->d_H32), c->mu,
-                                             dp<float>(c->d_T), dp<double>(c->d_bound) + j0, c->stream));
+        GatherExtras ex;
+        ex.gersh = dp<double>(c->d_gersh) + j0;
+        ex.prev_ratio = dp<float>(c->d_prev_ratio) + j0;
+        ex.feat = dp<float>(c->d_feat) + kModelFeatures * j0;
+        if (predict) {
+            ex.params = dp<float>(c->d_params);
+            ex.pred = dp<float>(c->d_pred) + 2 * j0;
+            ex.margin = kModelMargin;
         }
-        SMX_CUDA(launch_features(subs + j0, m, c->d_T.p, f32, dp<float>(c->d_prev_ratio) + j0,
-                                 dp<float>(c->d_feat) + kModelFeatures * j0, c->stream));
-        c->kernel_launches += 2;
+        SMX_TRY(gather_chunk(c, j0, m, c->mu, ex));
         if (lanczos_steps > 0) {
             SMX_CUDA(launch_lanczos(subs + j0, m, c->max_n, c->d_T.p, f32, lanczos_steps, dp<float>(c->d_labels) + 2 * j0,
                                     c->stream));
@@ -913,7 +917,7 @@ smx_status smx_bound_model_get_params(smx_ctx* c, float* params, int32_t count) 
 smx_status smx_bound_model_collect(smx_ctx* c, int32_t lanczos_steps) {
     if (!c || lanczos_steps < 8 || lanczos_steps > kMaxLanczos) return SMX_ERR_ARG;
     DeviceGuard g(c->device);
-    SMX_TRY(features_labels(c, lanczos_steps));
+    SMX_TRY(features_labels(c, lanczos_steps, false));
     const int B = c->B;
     if (c->n_samples + B > c->cap_samples) {  // grow the sample store, keeping its contents
         const int64_t cap = std::max<int64_t>(2 * c->cap_samples, c->n_samples + B);
@@ -1005,13 +1009,9 @@ smx_status smx_bound_model_predict(smx_ctx* c, float* features, float* pred, flo
     if (!c || (labels && (lanczos_steps < 8 || lanczos_steps > kMaxLanczos))) return SMX_ERR_ARG;
     if (pred && !c->model_ready) return SMX_ERR_STATE;
     DeviceGuard g(c->device);
-    SMX_TRY(features_labels(c, labels ? lanczos_steps : 0));
+    SMX_TRY(features_labels(c, labels ? lanczos_steps : 0, pred != nullptr));
     const int B = c->B;
-    if (pred) {
-        SMX_CUDA(launch_mlp_predict(dp<float>(c->d_params), dp<float>(c->d_feat), B, dp<float>(c->d_pred), c->stream));
-        SMX_CUDA(cudaMemcpyAsync(pred, c->d_pred.p, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost, c->stream));
-        c->kernel_launches += 1;
-    }
+    if (pred) SMX_CUDA(cudaMemcpyAsync(pred, c->d_pred.p, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost, c->stream));
     if (labels)
         SMX_CUDA(cudaMemcpyAsync(labels, c->d_labels.p, sizeof(float) * 2 * B, cudaMemcpyDeviceToHost, c->stream));
     if (features)

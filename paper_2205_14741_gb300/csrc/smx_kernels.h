@@ -20,14 +20,27 @@ cudaError_t launch_block_filter(const double* H, const int64_t* voff, const int3
 cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, const int64_t* row_start, int n_cols,
                                      double* lohi, cudaStream_t st);
 
+// Optional outputs of the gather, per submatrix (pointers offset like subs; null = not wanted).
+struct GatherExtras {
+    double* gersh = nullptr;             // the Gershgorin bound G_j
+    const float* prev_ratio = nullptr;   // learned bound: previous-step feature (null = 0)
+    float* feat = nullptr;               // learned bound: the 9 features of T_j - mu I
+    const float* params = nullptr;       // learned bound: parameters; when set, b_j is the model's
+    float* pred = nullptr;               // ... and its two predictions
+    float margin = 0.0f;                 // ... b_j = G_j clamp(pred_0, 0.02, 1) (1 + margin) / 1.2
+};
+
 // a3 + a4: T_j = H[R_j, R_j] - mu I into the FP64 staging buffer, then the
-// Gershgorin bound b_j = max row abs-sum of T_j (>= spectral radius).
+// Gershgorin bound b_j = max row abs-sum of T_j (>= spectral radius), or the
+// learned bound (extras.params).
 cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
-                                const double* H, double mu, double* T, double* bound, cudaStream_t st);
+                                const double* H, double mu, double* T, double* bound, const GatherExtras& ex,
+                                cudaStream_t st);
 // The same in FP32 (tensor-core path): T32 from the FP32 copy of H; the bound
 // is enlarged by 1e-5 relative to cover FP32 summation.
 cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
-                                    const float* H32, double mu, float* T32, double* bound, cudaStream_t st);
+                                    const float* H32, double mu, float* T32, double* bound, const GatherExtras& ex,
+                                    cudaStream_t st);
 
 // a8: deterministic sums of the per-column partials -> out[0] = trace(D),
 // out[1] = trace(D H); also min/max of the column Gershgorin bounds into
@@ -96,28 +109,27 @@ cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, 
 // learned spectral bound (k_bound_model.cu)
 // ---------------------------------------------------------------------------
 constexpr int kModelFeatures = 9;
+constexpr int kModelHidden = 64;
 constexpr int kModelParams = 64 * kModelFeatures + 64 + 64 * 64 + 64 + 2 * 64 + 2;  // 4930
+// flat parameter layout: W1 (64 x 9, row-major), b1, W2 (64 x 64), b2, W3 (2 x 64), b3
+constexpr int kOffB1 = kModelHidden * kModelFeatures, kOffW2 = kOffB1 + kModelHidden,
+              kOffB2 = kOffW2 + kModelHidden * kModelHidden, kOffW3 = kOffB2 + kModelHidden,
+              kOffB3 = kOffW3 + 2 * kModelHidden;
+static_assert(kOffB3 + 2 == kModelParams, "parameter layout");
 constexpr int kMaxLanczos = 64;
 // b_j = rho_hat (1 + margin) / 1.2: the margin covers the model's typical
 // under-prediction (a few percent) so that the first-product check passes
 constexpr float kModelMargin = 0.05f;
 
-// features[j*9 + k] of A_j = T_j - mu I from the staging buffer (FP32 or FP64)
-cudaError_t launch_features(const SubDesc* subs, int n_subs, const void* T, bool fp32, const float* prev_ratio,
-                            float* feat, cudaStream_t st);
 // labels[2j] = rho/G, labels[2j+1] = delta/G by Lanczos on A and A^2
 cudaError_t launch_lanczos(const SubDesc* subs, int n_subs, int max_n, const void* T, bool fp32, int ksteps,
                            float* labels, cudaStream_t st);
-cudaError_t launch_mlp_predict(const float* params, const float* feat, int m, float* out, cudaStream_t st);
 // floats of scratch one gradient/Adam step on m samples needs
 size_t mlp_partial_floats(int m);
 // gradient at params_in on (X, Tg); grad_out/loss_out optional; Adam update of params when lr > 0
 cudaError_t launch_mlp_step(const float* params_in, const float* X, const float* Tg, int m, float* partial,
                             float* params, float* mst, float* vst, int t, float lr, float* grad_out, float* loss_out,
                             cudaStream_t st);
-// bound[j] = gersh[j] * clamp(pred[2j]) * (1 + margin) / 1.2
-cudaError_t launch_model_bound(const float* pred, const double* gersh, double* bound, int n, float margin,
-                               cudaStream_t st);
 
 // Dynamic shared memory the tcgen05 kernel needs for a precision.
 size_t ns_tc_smem_bytes(int precision);
