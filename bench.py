@@ -330,6 +330,29 @@ def run_ours(args):
             ms = float(t.item())
         return ms, stats, clk
 
+    # -- the same form without the learned bound ----------------------------
+    plain_scaling = None
+    model_setup = None
+    if args.bound_model:
+        ms0, st0, _ = timed(args.steps, args.precision)
+        plain_scaling = {"value": args.steps * world / (ms0 / 1e3), "ms_per_step": ms0 / args.steps,
+                         "ns_ms_per_step": st0["ns_ms_total"] / args.steps, "iters_mean": st0["iters_mean"]}
+        # learned bound: trained on this system's own submatrices before timing (features and
+        # 48-step Lanczos labels at the solved mu, without and with the previous-step feature)
+        t0 = time.perf_counter()
+        ctx.set_precision(args.precision)
+        ctx.bound_model_init(w.get("seed", 0))
+        for _ in range(2):
+            ctx.set_values(h_dev, on_device=True)
+            ctx.solve_mu()
+            ctx.set_mu(ctx.get_trace()[2])
+            ctx.bound_model_collect(48)
+        loss = ctx.bound_model_train(epochs=args.model_epochs, batch=256, lr=2e-3)
+        ctx.set_bound_model(True)
+        torch.cuda.synchronize()
+        model_setup = {"seconds": time.perf_counter() - t0, "samples": 2 * sysm.n_blocks, "epochs": args.model_epochs,
+                       "train_loss": loss}
+
     # -- mixed-precision form (the headline) --------------------------------
     ms, st, clk = timed(args.steps, args.precision)
     tr, en, mu = ctx.get_trace()
@@ -383,6 +406,7 @@ def run_ours(args):
     # -- the plain FP64 form on the same workload ------------------------------
     fp64 = None
     if not args.no_fp64:
+        ctx.set_bound_model(False)  # the plain form: Gershgorin start
         ms64, st64, _ = timed(args.fp64_steps, "fp64")
         d64 = ctx.get_density()
         fp64 = {"value": args.fp64_steps * world / (ms64 / 1e3), "unit": "density matrices/s",
@@ -426,6 +450,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT.get(args.workload, args.workload),
                        "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
+                       "spectral_bound": ("learned (trained on this system's submatrices before timing)"
+                                          if args.bound_model else "a-posteriori Gershgorin"),
                        "bisection_builds_per_step": float(np.mean(bis_steps)) if bis_steps else None,
                        "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
             "submatrix_tflops": submatrix_tflops,
@@ -440,6 +466,9 @@ def run_ours(args):
             "iters": {"min": st["iters_min"], "max": st["iters_max"], "mean": st["iters_mean"]},
             "dims": {"min": st["dim_min"], "max": st["dim_max"], "mean": st["dim_mean"]},
             "learned_scaling": learned,
+            "bound_model": ({"headline_uses_learned_bound": True, "setup": model_setup,
+                             "fallback_rate": st["n_bound_fallback"] / sysm.n_blocks,
+                             "without_learned_bound": plain_scaling} if args.bound_model else None),
         }
         print(json.dumps(out))
     ctx.close()
@@ -463,6 +492,9 @@ def main():
     ap.add_argument("--learned-snapshots", type=int, default=200,
                     help="trajectory length of the learned-bound report (0 skips it)")
     ap.add_argument("--learned-epochs", type=int, default=40)
+    ap.add_argument("--no-bound-model", dest="bound_model", action="store_false",
+                    help="time the headline without the learned spectral bound")
+    ap.add_argument("--model-epochs", type=int, default=100)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
