@@ -1,6 +1,7 @@
 // Filter, gather + spectral bound, Gershgorin bracket and reductions.
 //
-//  a1  block filter (Frobenius norm per block; diagonal blocks kept)
+//  a1  block filter (Frobenius norm per block; diagonal blocks kept) and the
+//      Gershgorin bracket of the filtered H (mu bisection)
 //  a3  gather T_j = H[R_j, R_j] - mu I (Fig. 2 step (i), shift of Eq. 14)
 //  a4  Gershgorin bound b_j >= spectral radius of T_j - mu I
 //  a8  deterministic FP64 sums of trace(D) and trace(D H)
@@ -13,66 +14,71 @@
 
 namespace smx {
 
-// One warp per stored block.
-__global__ void k_block_filter(const double* __restrict__ H, const int64_t* __restrict__ voff,
-                               const int32_t* __restrict__ row_idx, const int32_t* __restrict__ bcol,
-                               const int32_t* __restrict__ bsize, int64_t nnzb, double eps, uint8_t* __restrict__ keep,
-                               int* status, float* __restrict__ H32) {
-    const int64_t k = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (k >= nnzb) return;
-    const int r = row_idx[k], c = bcol[k];
-    const int sz = bsize[r] * bsize[c];
-    const double* blk = H + voff[k];
-    float* blk32 = H32 + voff[k];
-    double s = 0.0;
-    bool finite = true;
-    for (int e = lane; e < sz; e += 32) {
-        const double v = blk[e];
-        s = fma(v, v, s);
-        finite = finite && isfinite(v);
-        blk32[e] = __double2float_rn(v);
-    }
-    s = warp_sum(s);
-    finite = __all_sync(0xffffffffu, finite);
-    if (lane == 0) {
-        keep[k] = (r == c || !(sqrt(s) < eps)) ? 1 : 0;
-        if (!finite) atomicCAS(status, kOk, kErrNonfinite);
-    }
-}
-
-cudaError_t launch_block_filter(const double* H, const int64_t* voff, const int32_t* row_idx, const int32_t* bcol,
-                                const int32_t* bsize, int64_t nnzb, double eps, uint8_t* keep, int* status,
-                                float* H32, cudaStream_t st) {
-    if (nnzb == 0) return cudaSuccess;
-    const int64_t threads = nnzb * 32;
-    const int grid = static_cast<int>((threads + 255) / 256);
-    k_block_filter<<<grid, 256, 0, st>>>(H, voff, row_idx, bcol, bsize, nnzb, eps, keep, status, H32);
-    return cudaGetLastError();
-}
-
-// One warp per block column j: column abs-sums over the filtered blocks of
-// column j (equal to row sums, H being symmetric) give the Gershgorin
-// interval of the rows of block j.
-__global__ void k_column_gershgorin(PatternView pv, const double* __restrict__ H, int n_cols, double* lohi) {
+// a1 + the Gershgorin bracket of a9, one warp per block column j of the input
+// pattern, a lane per block: each block's Frobenius norm decides whether it is
+// kept (diagonal blocks always), its values are checked for finiteness and
+// copied to FP32; then, per column q of the block column, the absolute sums of
+// the kept blocks' columns are reduced over the lanes (H is symmetric: these
+// are the row sums), giving the column's Gershgorin interval
+// [min_q (d_q - r_q), max_q (d_q + r_q)] (d_q the diagonal entry, r_q the sum
+// without it).  Deterministic: every sum has a fixed order.
+__global__ void __launch_bounds__(256) k_filter_gershgorin(const double* __restrict__ H, const int64_t* __restrict__ col_ptr,
+                                                           const int32_t* __restrict__ row_idx,
+                                                           const int64_t* __restrict__ voff,
+                                                           const int32_t* __restrict__ bsize, int n_cols, double eps,
+                                                           uint8_t* __restrict__ keep, int* status, float* __restrict__ H32,
+                                                           double* __restrict__ lohi, int bmax) {
+    extern __shared__ double fg_smem[];  // per warp: column sums and diagonal entries, bmax each
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (j >= n_cols) return;
-    const int bj = pv.bsize[j];
-    double lo = INFINITY, hi = -INFINITY;
-    for (int q = lane; q < bj; q += 32) {
-        double s = 0.0, d = 0.0;
-        for (int64_t k = pv.fcol_ptr[j]; k < pv.fcol_ptr[j + 1]; ++k) {
-            const int r = pv.frow_idx[k];
-            const int br = pv.bsize[r];
-            const double* col = H + pv.fvoff[k] + static_cast<int64_t>(q) * br;
-            for (int p = 0; p < br; ++p) s += fabs(col[p]);
-            if (r == j) d = col[q];
+    double* colsum = fg_smem + static_cast<size_t>(warp) * 2 * bmax;
+    double* diag = colsum + bmax;
+    const int bc = bsize[j];
+    for (int q = lane; q < bc; q += 32) colsum[q] = diag[q] = 0.0;
+    __syncwarp();
+    const int64_t k0 = col_ptr[j], k1 = col_ptr[j + 1];
+    bool finite = true;
+    for (int64_t kb = k0; kb < k1; kb += 32) {
+        const int64_t k = kb + lane;
+        int r = -1, br = 0;
+        bool kept = false;
+        const double* blk = nullptr;
+        if (k < k1) {
+            r = row_idx[k];
+            br = bsize[r];
+            blk = H + voff[k];
+            float* blk32 = H32 + voff[k];
+            const int sz = br * bc;
+            double ss = 0.0;
+            for (int e = 0; e < sz; ++e) {
+                const double v = blk[e];
+                ss = fma(v, v, ss);
+                finite = finite && isfinite(v);
+                blk32[e] = __double2float_rn(v);
+            }
+            kept = r == j || !(sqrt(ss) < eps);
+            keep[k] = kept ? 1 : 0;
         }
-        const double rad = s - fabs(d);
+        for (int q = 0; q < bc; ++q) {
+            double cs = 0.0;
+            if (kept) {
+                const double* col = blk + static_cast<int64_t>(q) * br;
+                for (int p = 0; p < br; ++p) cs += fabs(col[p]);
+                if (r == j) diag[q] = col[q];
+            }
+            cs = warp_sum(cs);
+            if (lane == 0) colsum[q] += cs;
+        }
+    }
+    __syncwarp();
+    double lo = INFINITY, hi = -INFINITY;
+    for (int q = lane; q < bc; q += 32) {
+        const double d = diag[q], rad = colsum[q] - fabs(d);
         lo = fmin(lo, d - rad);
         hi = fmax(hi, d + rad);
     }
+    finite = __all_sync(0xffffffffu, finite);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
@@ -81,13 +87,21 @@ __global__ void k_column_gershgorin(PatternView pv, const double* __restrict__ H
     if (lane == 0) {
         lohi[2 * j] = lo;
         lohi[2 * j + 1] = hi;
+        if (!finite) atomicCAS(status, kOk, kErrNonfinite);
     }
 }
 
-cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, const int64_t* /*row_start*/,
-                                     int n_cols, double* lohi, cudaStream_t st) {
-    const int grid = (n_cols * 32 + 255) / 256;
-    k_column_gershgorin<<<grid, 256, 0, st>>>(pv, H, n_cols, lohi);
+cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
+                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep, int* status,
+                                     float* H32, double* lohi, cudaStream_t st) {
+    if (n_cols <= 0) return cudaSuccess;
+    const int grid = static_cast<int>((static_cast<int64_t>(n_cols) * 32 + 255) / 256);
+    const size_t smem = sizeof(double) * 2 * static_cast<size_t>(bmax) * 8;
+    if (smem > (48u << 10)) {
+        cudaError_t e = cudaFuncSetAttribute(k_filter_gershgorin, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    k_filter_gershgorin<<<grid, 256, smem, st>>>(H, col_ptr, row_idx, voff, bsize, n_cols, eps, keep, status, H32, lohi, bmax);
     return cudaGetLastError();
 }
 

@@ -53,6 +53,7 @@ struct smx_ctx {
 
     // input pattern
     int32_t B = 0;
+    int32_t bmax = 0;  // largest block size
     int64_t N = 0, nnzb = 0, n_values = 0;
     std::vector<int32_t> bs, row_idx, bcol;
     std::vector<int64_t> col_ptr, voff, row_start;
@@ -75,7 +76,7 @@ struct smx_ctx {
     int64_t t_elems = 0, x_elems = 0;
 
     // device buffers
-    DevBuf d_H, d_H32, d_voff, d_row_idx, d_bcol, d_bs, d_keep;
+    DevBuf d_H, d_H32, d_voff, d_row_idx, d_col_ptr, d_bs, d_keep;
     DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order;
     DevBuf d_T, d_W1, d_W2, d_ws, d_D, d_xown;
     DevBuf d_bound, d_iters, d_partial, d_lohi, d_out, d_out_br, d_status, d_counter, d_work_n3;
@@ -209,13 +210,14 @@ static smx_status get_encoder(smx_ctx* c) {
     return SMX_OK;
 }
 
-// Filter (a1) and symbolic analysis (a2).
+// Filter (a1), the Gershgorin bracket of the filtered H, and symbolic analysis (a2).
 static smx_status analyse(smx_ctx* c) {
     cudaStream_t st = c->stream;
     SMX_CUDA(cudaMemsetAsync(c->d_status.p, 0, sizeof(int), st));
-    SMX_CUDA(launch_block_filter(dp<double>(c->d_H), dp<int64_t>(c->d_voff), dp<int32_t>(c->d_row_idx),
-                                 dp<int32_t>(c->d_bcol), dp<int32_t>(c->d_bs), c->nnzb, c->eps, dp<uint8_t>(c->d_keep),
-                                 dp<int>(c->d_status), dp<float>(c->d_H32), st));
+    SMX_CUDA(launch_filter_gershgorin(dp<double>(c->d_H), dp<int64_t>(c->d_col_ptr), dp<int32_t>(c->d_row_idx),
+                                      dp<int64_t>(c->d_voff), dp<int32_t>(c->d_bs), c->B, c->bmax, c->eps,
+                                      dp<uint8_t>(c->d_keep),
+                                      dp<int>(c->d_status), dp<float>(c->d_H32), dp<double>(c->d_lohi), st));
     c->kernel_launches += 1;
     int status = 0;
     const bool need_flags = c->eps > 0.0 || !c->analysed;
@@ -530,6 +532,7 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->B = n_block_cols;
     c->bs.assign(block_size, block_size + n_block_cols);
+    c->bmax = *std::max_element(c->bs.begin(), c->bs.end());
     c->col_ptr.assign(col_ptr, col_ptr + n_block_cols + 1);
     c->nnzb = col_ptr[n_block_cols];
     c->row_idx.assign(row_idx, row_idx + c->nnzb);
@@ -552,7 +555,7 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return fail(SMX_ERR_CUDA);
     if ((s = upload(c->d_voff, c->voff, c->stream)) != SMX_OK) return fail(s);
     if ((s = upload(c->d_row_idx, c->row_idx, c->stream)) != SMX_OK) return fail(s);
-    if ((s = upload(c->d_bcol, c->bcol, c->stream)) != SMX_OK) return fail(s);
+    if ((s = upload(c->d_col_ptr, c->col_ptr, c->stream)) != SMX_OK) return fail(s);
     if ((s = upload(c->d_bs, c->bs, c->stream)) != SMX_OK) return fail(s);
     const size_t vb = static_cast<size_t>(c->n_values) * sizeof(double);
     if ((s = ensure(c->d_H, vb)) != SMX_OK) return fail(s);
@@ -646,10 +649,9 @@ smx_status smx_get_gershgorin_interval(smx_ctx* c, double* lo, double* hi) {
     if (!c || !lo || !hi) return SMX_ERR_ARG;
     DeviceGuard g(c->device);
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
-    SMX_CUDA(launch_column_gershgorin(pattern_view(c), dp<double>(c->d_H), nullptr, c->B, dp<double>(c->d_lohi),
-                                      c->stream));
+    // the per-column intervals come with the filter (analyse)
     SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), dp<double>(c->d_lohi), c->B, dp<double>(c->d_out_br), c->stream));
-    c->kernel_launches += 2;
+    c->kernel_launches += 1;
     double br[4];
     SMX_CUDA(cudaMemcpyAsync(br, c->d_out_br.p, sizeof(br), cudaMemcpyDeviceToHost, c->stream));
     SMX_CUDA(cudaStreamSynchronize(c->stream));
@@ -696,10 +698,9 @@ smx_status smx_solve_mu(smx_ctx* c) {
     DeviceGuard g(c->device);
     if (c->n_e < 0.0 || c->n_e > static_cast<double>(c->N)) return SMX_ERR_NOBRACKET;
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
-    SMX_CUDA(launch_column_gershgorin(pattern_view(c), dp<double>(c->d_H), nullptr, c->B, dp<double>(c->d_lohi),
-                                      c->stream));
+    // the per-column intervals come with the filter (analyse)
     SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), dp<double>(c->d_lohi), c->B, dp<double>(c->d_out_br), c->stream));
-    c->kernel_launches += 2;
+    c->kernel_launches += 1;
     double br[4];
     SMX_CUDA(cudaMemcpyAsync(br, c->d_out_br.p, sizeof(br), cudaMemcpyDeviceToHost, c->stream));
     SMX_CUDA(cudaStreamSynchronize(c->stream));
@@ -1076,7 +1077,7 @@ void smx_destroy(smx_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_bcol, &c->d_bs, &c->d_keep, &c->d_fcol_ptr,
+    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep, &c->d_fcol_ptr,
                       &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
                       &c->d_W2, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
                       &c->d_out, &c->d_out_br, &c->d_status, &c->d_counter, &c->d_work_n3,

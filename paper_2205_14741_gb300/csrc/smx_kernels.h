@@ -9,16 +9,12 @@
 
 namespace smx {
 
-// a1: per-block Frobenius norms -> keep flags (diagonal always kept), a
-// non-finite check of the values, and an FP32 copy of H (same layout) for the
-// tensor-core path.  keep[k] = 1 if block k survives.
-cudaError_t launch_block_filter(const double* H, const int64_t* voff, const int32_t* row_idx, const int32_t* bcol,
-                                const int32_t* bsize, int64_t nnzb, double eps, uint8_t* keep, int* status,
-                                float* H32, cudaStream_t st);
-
-// Gershgorin interval of the filtered H, per block column (lohi[2j], lohi[2j+1]).
-cudaError_t launch_column_gershgorin(const PatternView& pv, const double* H, const int64_t* row_start, int n_cols,
-                                     double* lohi, cudaStream_t st);
+// a1 + bracket: per block column j, keep flags of its blocks (Frobenius norm
+// >= eps, diagonal always), non-finite check, FP32 copy of H, and the
+// Gershgorin interval of the filtered column (lohi[2j], lohi[2j + 1]).
+cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
+                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep, int* status,
+                                     float* H32, double* lohi, cudaStream_t st);
 
 // Optional outputs of the gather, per submatrix (pointers offset like subs; null = not wanted).
 struct GatherExtras {
