@@ -124,7 +124,7 @@ template <class R>
 __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict__ subs, PatternView pv,
                                                       const R* __restrict__ H, double mu_d, R* __restrict__ T,
                                                       double* __restrict__ bound, int ld_max, int nblk_max, int nw,
-                                                      GatherExtras ex) {
+                                                      int rg, GatherExtras ex) {
     extern __shared__ __align__(16) unsigned char gsm[];
     __shared__ double warp_max_s[8];
     __shared__ float stat_s[8][7];  // per warp: F2, Da, Ds, Dq, Rs (sums), Dm, Rm (maxima)
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
     int* ls = rows + nblk_max;                // local starts, nblk + 1 entries
     const size_t head = (static_cast<size_t>(2 * nblk_max + 1) * sizeof(int) + 15) & ~size_t(15);
     const size_t lists = (static_cast<size_t>(nblk_max) * (sizeof(int64_t) + sizeof(int)) + 15) & ~size_t(15);
-    const size_t per_warp = lists + ((static_cast<size_t>(ld_max) * sizeof(R) + 15) & ~size_t(15));
+    const size_t per_warp = lists + rg * ((static_cast<size_t>(ld_max) * sizeof(R) + 15) & ~size_t(15));
     unsigned char* wbase = gsm + head + warp * per_warp;
     int64_t* vo_list = reinterpret_cast<int64_t*>(wbase);
     int* a_list = reinterpret_cast<int*>(wbase + static_cast<size_t>(nblk_max) * sizeof(int64_t));
@@ -178,26 +178,33 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
             cnt += __popc(found);
         }
         __syncwarp();
-        for (int q = 0; q < bc; ++q) {
-            for (int y = lane; y < s.ld; y += 32) rowbuf[y] = R(0);
-            __syncwarp();
-            for (int e = lane; e < cnt; e += 32) {  // a lane per listed block: column q of block (R_j[a], col)
-                const int a = a_list[e];
-                const int br = ls[a + 1] - ls[a];
-                const R* src = H + vo_list[e] + static_cast<int64_t>(q) * br;
-                R* dst = rowbuf + ls[a];
-                for (int p = 0; p < br; ++p) {
-                    R v = src[p];
-                    if (a == c && p == q) v -= mu;
-                    dst[p] = v;
-                }
-            }
-            __syncwarp();
+        // rows q0 .. q0 + rg - 1 of the block row together: the listed blocks' columns are
+        // loaded in one pass (a lane per block) into rg row buffers
+        for (int q0 = 0; q0 < bc; q0 += rg) {
+          const int nq = min(rg, bc - q0);
+          for (int y = lane; y < nq * s.ld; y += 32) rowbuf[y] = R(0);
+          __syncwarp();
+          for (int e = lane; e < cnt; e += 32) {  // a lane per listed block: columns q0.. of block (R_j[a], col)
+              const int a = a_list[e];
+              const int br = ls[a + 1] - ls[a];
+              const R* src = H + vo_list[e] + static_cast<int64_t>(q0) * br;
+              R* dst = rowbuf + ls[a];
+              for (int qq = 0; qq < nq; ++qq)
+                  for (int p = 0; p < br; ++p) {
+                      R v = src[qq * br + p];
+                      if (a == c && p == q0 + qq) v -= mu;
+                      dst[qq * s.ld + p] = v;
+                  }
+          }
+          __syncwarp();
+          for (int qq = 0; qq < nq; ++qq) {
+            const int q = q0 + qq;
+            const R* rowq = rowbuf + qq * s.ld;
             R* trow = t + static_cast<int64_t>(ls[c] + q) * s.ld;
             R acc = R(0);
             float sq = 0.f;
             for (int y = lane; y < s.ld; y += 32) {
-                const R v = rowbuf[y];
+                const R v = rowq[y];
                 trow[y] = v;
                 acc += fabs(v);
                 sq = fmaf(static_cast<float>(v), static_cast<float>(v), sq);
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
                 sq += __shfl_xor_sync(0xffffffffu, sq, o);
             }
             m = fmax(m, static_cast<double>(acc));
-            const float d = static_cast<float>(rowbuf[ls[c] + q]), ad = fabsf(d), rr = static_cast<float>(acc) - ad;
+            const float d = static_cast<float>(rowq[ls[c] + q]), ad = fabsf(d), rr = static_cast<float>(acc) - ad;
             f2 += sq;
             da += ad;
             ds += d;
@@ -216,7 +223,8 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
             rs += rr;
             dm = fmaxf(dm, ad);
             rm = fmaxf(rm, rr);
-            __syncwarp();
+          }
+          __syncwarp();
         }
     }
     if (lane == 0) {
@@ -306,30 +314,34 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
 }
 
 template <class R>
-static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
+static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, int max_bs, const PatternView& pv,
                                  const R* H, double mu, R* T, double* bound, const GatherExtras& ex, cudaStream_t st) {
     const size_t head = (static_cast<size_t>(2 * max_nblk + 1) * sizeof(int) + 15) & ~size_t(15);
     const size_t lists = (static_cast<size_t>(max_nblk) * (sizeof(int64_t) + sizeof(int)) + 15) & ~size_t(15);
-    const size_t per_warp = lists + ((static_cast<size_t>(max_ld) * sizeof(R) + 15) & ~size_t(15));
-    // as many row-buffer warps (up to 8) as fit in 200 KB of shared memory
+    // rows per warp buffer: up to the largest block size, 8 warps within 200 KB of shared memory
+    const size_t row_bytes = (static_cast<size_t>(max_ld) * sizeof(R) + 15) & ~size_t(15);
+    const size_t budget = (200u << 10) / 8;
+    const int rg = static_cast<int>(std::max<size_t>(1, std::min<size_t>(static_cast<size_t>(max_bs),
+                                                                          budget > lists ? (budget - lists) / row_bytes : 1)));
+    const size_t per_warp = lists + rg * row_bytes;
     const int nw = static_cast<int>(std::max<size_t>(1, std::min<size_t>(8, (200u << 10) / per_warp)));
     const size_t smem = head + nw * per_warp;
     cudaError_t e = cudaFuncSetAttribute(k_gather_bound<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    k_gather_bound<R><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound, max_ld, max_nblk, nw, ex);
+    k_gather_bound<R><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound, max_ld, max_nblk, nw, rg, ex);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, int max_bs, const PatternView& pv,
                                 const double* H, double mu, double* T, double* bound, const GatherExtras& ex,
                                 cudaStream_t st) {
-    return launch_gather<double>(subs, n_subs, max_nblk, max_ld, pv, H, mu, T, bound, ex, st);
+    return launch_gather<double>(subs, n_subs, max_nblk, max_ld, max_bs, pv, H, mu, T, bound, ex, st);
 }
 
-cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, const PatternView& pv,
-                                    const float* H32, double mu, float* T32, double* bound, const GatherExtras& ex,
-                                    cudaStream_t st) {
-    return launch_gather<float>(subs, n_subs, max_nblk, max_ld, pv, H32, mu, T32, bound, ex, st);
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, int max_bs,
+                                    const PatternView& pv, const float* H32, double mu, float* T32, double* bound,
+                                    const GatherExtras& ex, cudaStream_t st) {
+    return launch_gather<float>(subs, n_subs, max_nblk, max_ld, max_bs, pv, H32, mu, T32, bound, ex, st);
 }
 
 // One CTA per submatrix: scatter of the saved owner columns (Fig. 2 step (iii)).
