@@ -91,6 +91,23 @@ __global__ void __launch_bounds__(256) k_filter_gershgorin(const double* __restr
     }
 }
 
+// *changed |= 1 when the keep flags differ from those of the current filtered pattern.
+__global__ void k_keep_changed(const uint8_t* __restrict__ keep, const uint8_t* __restrict__ prev, int64_t n, int* changed) {
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n;
+         k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        if (keep[k] != prev[k]) {
+            atomicOr(changed, 1);
+            return;
+        }
+}
+
+cudaError_t launch_keep_changed(const uint8_t* keep, const uint8_t* prev, int64_t n, int* changed, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 1024));
+    k_keep_changed<<<grid, 256, 0, st>>>(keep, prev, n, changed);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
                                      const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep, int* status,
                                      float* H32, double* lohi, cudaStream_t st) {

@@ -76,7 +76,9 @@ struct smx_ctx {
     int64_t t_elems = 0, x_elems = 0;
 
     // device buffers
-    DevBuf d_H, d_H32, d_voff, d_row_idx, d_col_ptr, d_bs, d_keep;
+    DevBuf d_H, d_H32, d_voff, d_row_idx, d_col_ptr, d_bs, d_keep, d_keep_prev, d_changed;
+    double br_lo = 0.0, br_hi = 0.0;  // Gershgorin bracket of the filtered H (from the last analyse)
+    int32_t* h_small = nullptr;       // pinned: status, changed flag, then the bracket (4 doubles)
     DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order;
     DevBuf d_T, d_W1, d_W2, d_ws, d_D, d_xown;
     DevBuf d_bound, d_iters, d_partial, d_lohi, d_out, d_out_br, d_status, d_counter, d_work_n3;
@@ -214,27 +216,37 @@ static smx_status get_encoder(smx_ctx* c) {
 static smx_status analyse(smx_ctx* c) {
     cudaStream_t st = c->stream;
     SMX_CUDA(cudaMemsetAsync(c->d_status.p, 0, sizeof(int), st));
+    SMX_CUDA(cudaMemsetAsync(c->d_changed.p, 0, sizeof(int), st));
     SMX_CUDA(launch_filter_gershgorin(dp<double>(c->d_H), dp<int64_t>(c->d_col_ptr), dp<int32_t>(c->d_row_idx),
                                       dp<int64_t>(c->d_voff), dp<int32_t>(c->d_bs), c->B, c->bmax, c->eps,
                                       dp<uint8_t>(c->d_keep),
                                       dp<int>(c->d_status), dp<float>(c->d_H32), dp<double>(c->d_lohi), st));
-    c->kernel_launches += 1;
-    int status = 0;
-    const bool need_flags = c->eps > 0.0 || !c->analysed;
-    if (need_flags) {
-        SMX_CUDA(cudaMemcpyAsync(c->h_keep_pinned, c->d_keep.p, c->nnzb, cudaMemcpyDeviceToHost, st));
+    SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), dp<double>(c->d_lohi), c->B, dp<double>(c->d_out_br), st));
+    c->kernel_launches += 2;
+    // with a threshold the filtered pattern may change: compared on the device, the flags
+    // are read back only when it did (or the first time)
+    const bool compare = c->analysed && c->eps > 0.0;
+    if (compare) {
+        SMX_CUDA(launch_keep_changed(dp<uint8_t>(c->d_keep), dp<uint8_t>(c->d_keep_prev), c->nnzb, dp<int>(c->d_changed), st));
+        c->kernel_launches += 1;
     }
-    SMX_CUDA(cudaMemcpyAsync(&status, c->d_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SMX_CUDA(cudaMemcpyAsync(c->h_small, c->d_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SMX_CUDA(cudaMemcpyAsync(c->h_small + 1, c->d_changed.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SMX_CUDA(cudaMemcpyAsync(c->h_small + 2, c->d_out_br.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SMX_CUDA(cudaStreamSynchronize(st));
-    if (status == kErrNonfinite) return SMX_ERR_NONFINITE;
-    if (!need_flags) {
-        c->dirty = false;
-        return SMX_OK;
+    if (c->h_small[0] == kErrNonfinite) return SMX_ERR_NONFINITE;
+    {
+        double br[4];
+        std::memcpy(br, c->h_small + 2, sizeof(br));
+        c->br_lo = br[2];
+        c->br_hi = br[3];
     }
-    if (c->analysed && std::equal(c->keep.begin(), c->keep.end(), c->h_keep_pinned)) {
+    if (c->analysed && (!compare || c->h_small[1] == 0)) {
         c->dirty = false;
         return SMX_OK;  // same filtered pattern
     }
+    SMX_CUDA(cudaMemcpyAsync(c->h_keep_pinned, c->d_keep.p, c->nnzb, cudaMemcpyDeviceToHost, st));
+    SMX_CUDA(cudaStreamSynchronize(st));
     c->keep.assign(c->h_keep_pinned, c->h_keep_pinned + c->nnzb);
 
     const int32_t B = c->B;
@@ -312,6 +324,7 @@ static smx_status analyse(smx_ctx* c) {
     SMX_CUDA(cudaMemsetAsync(c->d_D.p, 0, c->n_values * sizeof(double), st));
     SMX_CUDA(cudaMemsetAsync(c->d_partial.p, 0, sizeof(double2) * B, st));  // columns outside the shard add zero
     SMX_CUDA(cudaMemsetAsync(c->d_iters.p, 0, sizeof(int32_t) * B, st));
+    SMX_CUDA(cudaMemcpyAsync(c->d_keep_prev.p, c->d_keep.p, c->nnzb, cudaMemcpyDeviceToDevice, st));
     c->analysed = true;
     c->dirty = false;
     c->ws_prec = -1;  // tensor-core workspace must be re-checked
@@ -562,6 +575,9 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if ((s = ensure(c->d_H32, vb / 2)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_D, vb)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_keep, c->nnzb)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_keep_prev, c->nnzb)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_changed, sizeof(int))) != SMX_OK) return fail(s);
+    if (cudaMallocHost(&c->h_small, 64) != cudaSuccess) return fail(SMX_ERR_OOM);
     if ((s = ensure(c->d_bound, sizeof(double) * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_iters, sizeof(int32_t) * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_partial, sizeof(double2) * n_block_cols)) != SMX_OK) return fail(s);
@@ -648,15 +664,9 @@ smx_status smx_set_column_range(smx_ctx* c, int32_t j0, int32_t j1) {
 smx_status smx_get_gershgorin_interval(smx_ctx* c, double* lo, double* hi) {
     if (!c || !lo || !hi) return SMX_ERR_ARG;
     DeviceGuard g(c->device);
-    if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
-    // the per-column intervals come with the filter (analyse)
-    SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), dp<double>(c->d_lohi), c->B, dp<double>(c->d_out_br), c->stream));
-    c->kernel_launches += 1;
-    double br[4];
-    SMX_CUDA(cudaMemcpyAsync(br, c->d_out_br.p, sizeof(br), cudaMemcpyDeviceToHost, c->stream));
-    SMX_CUDA(cudaStreamSynchronize(c->stream));
-    *lo = br[2];
-    *hi = br[3];
+    if (c->dirty || !c->analysed) SMX_TRY(analyse(c));  // the bracket comes with the filter
+    *lo = c->br_lo;
+    *hi = c->br_hi;
     return SMX_OK;
 }
 
@@ -697,14 +707,8 @@ smx_status smx_solve_mu(smx_ctx* c) {
     if (!c->have_ne || c->col_hi >= 0) return SMX_ERR_STATE;  // a shard's trace is partial
     DeviceGuard g(c->device);
     if (c->n_e < 0.0 || c->n_e > static_cast<double>(c->N)) return SMX_ERR_NOBRACKET;
-    if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
-    // the per-column intervals come with the filter (analyse)
-    SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), dp<double>(c->d_lohi), c->B, dp<double>(c->d_out_br), c->stream));
-    c->kernel_launches += 1;
-    double br[4];
-    SMX_CUDA(cudaMemcpyAsync(br, c->d_out_br.p, sizeof(br), cudaMemcpyDeviceToHost, c->stream));
-    SMX_CUDA(cudaStreamSynchronize(c->stream));
-    double lo = br[2], hi = br[3];
+    if (c->dirty || !c->analysed) SMX_TRY(analyse(c));  // the bracket comes with the filter
+    double lo = c->br_lo, hi = c->br_hi;
     c->bisection_steps = 0;
     for (int step = 0; step < c->max_steps; ++step) {
         const double mid = 0.5 * (lo + hi);
@@ -1077,7 +1081,7 @@ void smx_destroy(smx_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep, &c->d_fcol_ptr,
+    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep_prev, &c->d_changed, &c->d_keep, &c->d_fcol_ptr,
                       &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
                       &c->d_W2, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
                       &c->d_out, &c->d_out_br, &c->d_status, &c->d_counter, &c->d_work_n3,
@@ -1090,6 +1094,7 @@ void smx_destroy(smx_ctx* c) {
         cudaEventDestroy(pr.second);
     }
     if (c->h_keep_pinned) cudaFreeHost(c->h_keep_pinned);
+    if (c->h_small) cudaFreeHost(c->h_small);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;

@@ -16,6 +16,9 @@ cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, co
                                      const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep, int* status,
                                      float* H32, double* lohi, cudaStream_t st);
 
+// *changed |= 1 when keep differs from prev (the flags of the current filtered pattern).
+cudaError_t launch_keep_changed(const uint8_t* keep, const uint8_t* prev, int64_t n, int* changed, cudaStream_t st);
+
 // Optional outputs of the gather, per submatrix (pointers offset like subs; null = not wanted).
 struct GatherExtras {
     double* gersh = nullptr;             // the Gershgorin bound G_j
