@@ -1,10 +1,10 @@
 """Learned spectral-bound model: features, labels and the MLP, FP64 numpy.
 
 TEST INFRASTRUCTURE ONLY: the reference the GPU model kernels are checked
-against (the paper's Section 4 names learning on the fly as a direction; the
-model here follows the spec reading: a small network predicts each
-submatrix's spectral bounds from cheap features, to scale the Newton-Schulz
-start tighter than the Gershgorin bound).
+against (the paper's Section 4 names learning on the fly as a direction; here
+a small network predicts each submatrix's spectral bounds from cheap
+features, to scale the Newton-Schulz start tighter than the Gershgorin
+bound).
 
 Definitions shared with the GPU path (both sides implement them separately):
 
