@@ -20,7 +20,7 @@
 // transposed B, the antisymmetric rounding residue of an iterate would double
 // at every step.
 //
-// CTA layout (384 threads):
+// CTA layout (384 threads).  Streamed form (submatrices larger than 192):
 //   warp 0       TMA producer (one lane): 64-wide K chunks of A (128 rows)
 //                and B (all columns of the tile, N <= 256) into a ring of
 //                shared-memory stages (128-byte swizzle); a row tile spans
@@ -31,6 +31,8 @@
 //   warps 4..11  epilogue: tcgen05.ld, Y = 3/2 I - 1/2 acc (or X' = acc),
 //                residual ||X^2 - I||_F^2 in FP32, split to hi/lo, 16-byte
 //                stores to the slot (L2-resident)
+// On-chip form (up to 192): all 12 warps share the tensor-memory passes; one
+// lane of warp 1 issues the MMAs.
 #include "smx_finish.cuh"
 #include "smx_kernels.h"
 
@@ -218,6 +220,18 @@ __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// the same wait, tied to the registers of one load in flight so that no use of them is
+// scheduled before it
+__device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+                   "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]),
+                   "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                   "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
 
 __device__ __forceinline__ bool mbar_wait_plain(uint64_t* bar, uint32_t parity, uint32_t limit) {
     for (uint32_t i = 0; i < limit; ++i)
@@ -238,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s, job_s, conv_s, bad_s, p_issued_s, m_consumed_s;
     __shared__ float resid_s[kEpiWarps];
-    __shared__ uint64_t mma_bar;
+    __shared__ uint64_t mma_bar, mma_bar2;
     __shared__ float resid_s2[kThreads / 32];
     __shared__ float red_s[2][kThreads / 32];
 
@@ -255,6 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         }
         mbar_init(&drain_bar, 1);
         mbar_init(&mma_bar, 1);
+        mbar_init(&mma_bar2, 1);
         abort_s = 0;
         p_issued_s = 0;
         m_consumed_s = 0;
@@ -298,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     const int64_t buf = static_cast<int64_t>(a.ld) * a.ld;
     uint16_t* ws = static_cast<uint16_t*>(a.ws);
     const int slot_z = blockIdx.x * 6;
-    uint32_t mma_ph = 0;  // completed phases of mma_bar (uniform over the CTA)
+    uint32_t mma_ph = 0, mma_ph2 = 0;  // completed phases of mma_bar, mma_bar2 (uniform over the CTA)
     const uint32_t idesc_b_mn = 1u << 16;  // B operand MN-major
 
     // C = A * B over K in [0, kpad), written to buffer zo (rows and columns < kpad).
@@ -551,24 +566,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         if (resident) {
             // ---------------------------------------------------------------
             // On-chip form.  Per iteration and 128-row tile t:
-            //   P <- X_t X            (A and B from the shared-memory image)
-            //   P <- A-operand form of Y_t = 3/2 I - 1/2 P (hi, lo packed 16-bit)
-            //   Q <- Y_t X            (A from tensor memory, B from the image)
-            //   X'_t <- Q             into the slot's next X buffer, overlapping the
-            //                         next tile's first product; the last tile goes
-            //                         straight into the image, the others are loaded
-            //                         back by TMA (the image is B until then).
-            // Y X = X Y (Y is a polynomial in X).  Iteration 0 first forms
-            // Z = X0^2 for every tile to bound rho(Z), then runs the same steps
-            // with A = Z - (3/c^2) I and X'_t = -(c^3/2) Q.  All 12 warps share the
-            // tensor-memory passes: warp w serves lanes 32 (w mod 4) and the
-            // 32-column chunks c0 = 32 (w / 4) + 96 k.
+            //   Z_t <- X_t X          (A and B from the shared-memory image)
+            //   Z_t <- A-operand form of Z_t - shift I (hi, lo packed 16-bit, in place)
+            //   Q_t <- (Z_t - shift I) X   (A from tensor memory, B from the image)
+            //   X'_t = alpha Q_t      into the image once every product of the
+            //                         iteration has read it
+            // Y X = X Y (Y is a polynomial in X).  Iteration 0 forms Z = X0^2 for
+            // every tile, bounds rho(Z), and continues with shift = 3/c^2 and
+            // alpha = -c^3/2; later iterations use shift = 3, alpha = -1/2.  All 12
+            // warps share the tensor-memory passes: warp w serves lanes 32 (w mod 4)
+            // and the 32-column chunks c0 = 32 (w / 4) + 96 k; each pass loads its
+            // next chunk while the current one is converted.
             // ---------------------------------------------------------------
-            // Tensor memory: P holds Y_t (then its A operand), Q the second product.  When
-            // kpad <= 160 every tile's X' keeps its own region (Q, R) until the last tile's
-            // second product is done and then goes straight into the image: no L2 traffic.
             const bool onchip = kpad <= 160;
-            const uint32_t P = tmem_base, Q = tmem_base + (onchip ? 160 : 192), R = tmem_base + 320;
             const int mtiles = (kpad + 127) >> 7;
             const int ksteps = kpad >> 4;
             const uint32_t idesc = idesc_f16(128, kpad, C::kFmt) | idesc_b_mn;
@@ -611,40 +621,52 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 ++mma_ph;
                 tc_fence_after();
             };
+            auto mma_wait2 = [&]() {  // all threads; the second barrier of the pipelined form
+                mbar_wait(&mma_bar2, mma_ph2 & 1u, &abort_s, a.status);
+                ++mma_ph2;
+                tc_fence_after();
+            };
             // Tensor-memory passes: thread (warp w, lane) owns row 128 t + 32 (w mod 4) + lane and
             // the 32-column chunks c0 = 32 (w / 4) + 96 k of the tile.
             //
             // convert: accumulator at acc -> A = C - shift I in place, each 32-column chunk becoming
             // 16 columns of packed hi pairs and 16 of lo pairs; with resid, r2 += ||C - I||_F^2 over
             // the thread's entries (rows and columns < n; zero elsewhere)
+            // Padding is exact: rows and columns of X in [n, kpad) are zero, so are those of
+            // Z = X X, of the A operand and of the second product.  Only the diagonal needs a
+            // rule of its own, and rows past kpad (tile 1 of a submatrix with kpad <= 192) are
+            // never read back, so their warps skip the passes.
+            //
+            // convert: accumulator at acc -> A = C - shift I in place, each 32-column chunk becoming
+            // 16 columns of packed hi pairs and 16 of lo pairs; with resid, r2 += ||C - I||_F^2 over
+            // the thread's entries (the n x n block; the padding contributes nothing)
             auto convert = [&](int t, uint32_t acc, float shift, bool resid, float& r2) {
-                const int row = 128 * t + 32 * q + lane;
+                const int row0 = 128 * t + 32 * q;  // the warp's first row
+                if (row0 >= kpad) return;
+                const bool live = row0 + lane < s.n;
 #pragma unroll 1
                 for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + lane_off + c0, raw);
-                    tmem_wait_ld();
-                    const int i0 = row - c0;
-                    float y[32];
-                    if (row < s.n && c0 + 32 <= s.n && !(i0 >= 0 && i0 < 32)) {
-                        float sq = 0.0f;
+                    tmem_wait_ld_regs(raw);
+                    float y[32], sq = 0.0f;
+                    if (c0 != row0) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
                             y[i] = __uint_as_float(raw[i]);
                             sq = fmaf(y[i], y[i], sq);
                         }
-                        if (resid) r2 += sq;
-                    } else {
+                    } else {  // the chunk of the warp's diagonal: element `lane` of each row
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
                             const float v = __uint_as_float(raw[i]);
-                            const bool valid = row < s.n && c0 + i < s.n;
-                            const float dl = (i == i0) ? 1.0f : 0.0f;
-                            const float e = v - dl;
-                            y[i] = valid ? fmaf(-shift, dl, v) : 0.0f;
-                            if (resid) r2 = valid ? fmaf(e, e, r2) : r2;
+                            const bool d = (i == lane) && live;
+                            const float e = d ? v - 1.0f : v;
+                            y[i] = d ? v - shift : v;
+                            sq = fmaf(e, e, sq);
                         }
                     }
+                    if (resid) r2 += sq;
                     uint32_t w[32];
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], w[i >> 1], w[16 + (i >> 1)]);
@@ -652,26 +674,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
                 tmem_wait_st();
             };
-            // drain: X'_t = alpha C (zero outside n x n) -> rows of buffer zo, or into the image
+            // drain: X'_t = alpha C (its padding is zero already) -> rows of buffer zo, or into the image
             auto drain = [&](int t, uint32_t acc, float alpha, int zo, bool to_image, uint32_t hi_dst) {
                 const int row = 128 * t + 32 * q + lane;
+                if (row - lane >= kpad) return;
                 uint16_t* out_hi = ws + static_cast<int64_t>(zo) * buf + static_cast<int64_t>(row) * a.ld;
                 uint16_t* out_lo = out_hi + buf;
 #pragma unroll 1
                 for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + lane_off + c0, raw);
-                    tmem_wait_ld();
-                    if (row >= kpad) continue;
+                    tmem_wait_ld_regs(raw);
                     float y[32];
-                    if (row < s.n && c0 + 32 <= s.n) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) y[i] = alpha * __uint_as_float(raw[i]);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            y[i] = (row < s.n && c0 + i < s.n) ? alpha * __uint_as_float(raw[i]) : 0.0f;
-                    }
+                    for (int i = 0; i < 32; ++i) y[i] = alpha * __uint_as_float(raw[i]);
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
@@ -704,10 +720,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + lane_off + c0, raw);
-                    tmem_wait_ld();
+                    tmem_wait_ld_regs(raw);
                     float y[32];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) y[i] = (row < s.n && c0 + i < s.n) ? alpha * __uint_as_float(raw[i]) : 0.0f;
+                    for (int i = 0; i < 32; ++i) y[i] = alpha * __uint_as_float(raw[i]);
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
@@ -776,75 +792,86 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 __syncthreads();
             };
 
-            for (int it = 0; it < a.max_iter; ++it) {
-                const int zn = cur ? zx0 : zx1;
-                // A = Z - shift I and X' = alpha A X: shift = 3, alpha = -1/2 (Y = 3/2 I - 1/2 Z);
-                // at iteration 0 shift = 3/c^2, alpha = -c^3/2 (the a-posteriori scaling c)
-                float alpha = -0.5f, shift = 3.0f;
-                if (it == 0) {
-                    // Z_t = X0_t X0 for every tile; the bound on rho(Z) as in the streamed form
-                    for (int r = tid; r < 3 * kResKpad; r += kThreads) rpart_s[r] = 0.0f;
+            // it = 0: the bound on rho(Z) from the first products' row sums (tile 0 in z0, tile 1
+            // in z1; after a barrier) and the a-posteriori scaling c = 1.2/s (every thread gets c)
+            auto start_scale = [&](uint32_t z0, uint32_t z1) -> float {
+                scan(0, z0, nullptr);
+                if (mtiles > 1) scan(1, z1, nullptr);
+                gather_parts(rsum_s);
+                float rmax = 0.0f;
+                for (int r = tid; r < s.n; r += kThreads) rmax = fmaxf(rmax, rsum_s[r]);
+                rmax = block_max2(rmax, 0.0f).x;
+                float best = rmax;
+                if (a.use_model && rmax > 0.0f) {
+                    // one power step: w = the row sums (floored to stay positive)
+                    for (int r = tid; r < s.n; r += kThreads) rsum_s[r] = fmaxf(rsum_s[r], 1e-12f * rmax);
+                    __syncthreads();
+                    scan(0, z0, rsum_s);
+                    if (mtiles > 1) scan(1, z1, rsum_s);
+                    gather_parts(rs2_s);
+                    float qm = 0.0f;
+                    for (int r = tid; r < s.n; r += kThreads) qm = fmaxf(qm, rs2_s[r] / rsum_s[r]);
+                    best = fminf(best, block_max2(qm, 0.0f).x);
+                }
+                const float smax = sqrtf(best * (1.0f + 1e-4f));  // margin for FP32 summation
+                float scale = smax > 0.0f ? 1.2f / smax : 1.0f;
+                if (a.use_model && smax > 0.0f) {
+                    if (smax <= 1.7f) scale = fmaxf(1.0f, scale);
+                    else if (tid == 0) atomicAdd(a.fallbacks, 1);
+                }
+                if (tid == 0) {
+                    const double s0 = sqrt(static_cast<double>(rmax) * (1.0 + 1e-5));
+                    a.sq_ratio[j] = static_cast<float>(s0 * a.bound[j] / a.gersh[j]);
+                    a.bound[j] = a.bound[j] / static_cast<double>(scale);
+                }
+                return scale;
+            };
+            // convergence of this step from ||X^2 - I||_F (the residual partials of every warp)
+            auto decide = [&]() {
+                double rr = 0.0;
+                for (int w = 0; w < kThreads / 32; ++w) rr += resid_s2[w];
+                if (!isfinite(rr)) bad_s = 1;
+                else if (sqrt(rr) <= a.tau) conv_s = 1;
+            };
+
+            if (onchip) {
+                // kpad <= 160: three tensor-memory regions TA, TB, TC.  Per iteration
+                //   Z_0 -> TA and Z_1 -> TB back to back, each on its own barrier;
+                //   TA -> A operand of tile 0 while Z_1 is multiplied; Q_0 = A_0 X -> TC;
+                //   TB -> A operand of tile 1 while Q_0 is multiplied; Q_1 = A_1 X -> TA
+                //   (free once Q_0 is done); X' = alpha Q of both tiles into the image.
+                // With a single tile: Z_0 -> TA, Q_0 -> TB.
+                const uint32_t TA = tmem_base, TB = tmem_base + 160, TC = tmem_base + 320;
+                const uint32_t q0_reg = mtiles > 1 ? TC : TB;
+                for (int it = 0; it < a.max_iter; ++it) {
+                    const int zn = cur ? zx0 : zx1;
+                    // A = Z - shift I and X' = alpha A X: shift = 3, alpha = -1/2 (Y = 3/2 I - 1/2 Z);
+                    // at iteration 0 shift = 3/c^2, alpha = -c^3/2 (the a-posteriori scaling c)
+                    float alpha = -0.5f, shift = 3.0f;
                     if (warp == 1 && lane == 0) {
                         tc_fence_after();
-                        issue_xx(0, P);
-                        if (mtiles > 1) issue_xx(1, Q);
+                        issue_xx(0, TA);
                         tc_commit(&mma_bar);
+                        if (mtiles > 1) {
+                            issue_xx(1, TB);
+                            tc_commit(&mma_bar2);
+                        }
                     }
-                    mma_wait();
-                    __syncthreads();
-                    if (*abortp) break;
-                    scan(0, P, nullptr);
-                    if (mtiles > 1) scan(1, Q, nullptr);
-                    gather_parts(rsum_s);
-                    float rmax = 0.0f;
-                    for (int r = tid; r < s.n; r += kThreads) rmax = fmaxf(rmax, rsum_s[r]);
-                    rmax = block_max2(rmax, 0.0f).x;
-                    float best = rmax;
-                    if (a.use_model && rmax > 0.0f) {
-                        // one power step: w = the row sums (floored to stay positive)
-                        for (int r = tid; r < s.n; r += kThreads) rsum_s[r] = fmaxf(rsum_s[r], 1e-12f * rmax);
+                    mma_wait();  // Z_0
+                    if (it == 0) {
+                        if (mtiles > 1) mma_wait2();  // Z_1
                         __syncthreads();
-                        scan(0, P, rsum_s);
-                        if (mtiles > 1) scan(1, Q, rsum_s);
-                        gather_parts(rs2_s);
-                        float qm = 0.0f;
-                        for (int r = tid; r < s.n; r += kThreads) qm = fmaxf(qm, rs2_s[r] / rsum_s[r]);
-                        best = fminf(best, block_max2(qm, 0.0f).x);
+                        if (*abortp) break;
+                        const float c = start_scale(TA, TB);
+                        shift = 3.0f / (c * c);
+                        alpha = -0.5f * c * c * c;
                     }
-                    const float smax = sqrtf(best * (1.0f + 1e-4f));  // margin for FP32 summation
-                    float scale = smax > 0.0f ? 1.2f / smax : 1.0f;
-                    if (a.use_model && smax > 0.0f) {
-                        if (smax <= 1.7f) scale = fmaxf(1.0f, scale);
-                        else if (tid == 0) atomicAdd(a.fallbacks, 1);
-                    }
-                    if (tid == 0) {
-                        const double s0 = sqrt(static_cast<double>(rmax) * (1.0 + 1e-5));
-                        a.sq_ratio[j] = static_cast<float>(s0 * a.bound[j] / a.gersh[j]);
-                        a.bound[j] = a.bound[j] / static_cast<double>(scale);
-                    }
-                    shift = 3.0f / (scale * scale);
-                    alpha = -0.5f * scale * scale * scale;
-                    tc_fence_before();
-                    __syncthreads();
-                }
-                float r2 = 0.0f;
-                bool last = false;  // this iteration ends the submatrix (known after the last conversion)
-                for (int t = 0; t < mtiles; ++t) {
-                    const bool g1 = !(it == 0 && t == 0);  // Z_0 is already in P
-                    if (g1 && warp == 1 && lane == 0) {
-                        tc_fence_after();
-                        issue_xx(t, P);
-                        tc_commit(&mma_bar);
-                    }
-                    const uint32_t hi_next = hi_off == img_bytes ? 2 * img_bytes : img_bytes;  // NB == 2
-                    const uint32_t hi_next1 = hi_off == 0 ? img_bytes : 0;                    // NB == 1
-                    if (t == 1 && !onchip) drain_split0(Q, alpha, NB == 2 ? hi_next : hi_next1);  // overlaps the product
-                    if (g1) mma_wait();
                     tc_fence_before();
                     __syncthreads();
                     if (*abortp) break;
-                    convert(t, P, shift, it > 0, r2);
-                    if (t == mtiles - 1) {
+                    float r2 = 0.0f;
+                    convert(0, TA, shift, it > 0, r2);
+                    if (mtiles == 1) {
                         r2 = warp_sum_f(r2);
                         if (lane == 0) resid_s2[warp] = r2;
                     }
@@ -852,31 +879,100 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     __syncthreads();
                     if (warp == 1 && lane == 0) {
                         tc_fence_after();
-                        issue_yx(P, (onchip && t == 1) ? R : Q);
+                        issue_yx(TA, q0_reg);
                         tc_commit(&mma_bar);
                     }
-                    if (t == mtiles - 1 && tid == 0) {  // convergence of this step, from ||X^2 - I||_F
-                        if (it > 0) {
-                            double rr = 0.0;
-                            for (int w = 0; w < kThreads / 32; ++w) rr += resid_s2[w];
-                            if (!isfinite(rr)) bad_s = 1;
-                            else if (sqrt(rr) <= a.tau) conv_s = 1;
+                    if (mtiles > 1) {
+                        if (it > 0) mma_wait2();  // Z_1, multiplied while tile 0 was converted
+                        convert(1, TB, shift, it > 0, r2);
+                        r2 = warp_sum_f(r2);
+                        if (lane == 0) resid_s2[warp] = r2;
+                        tc_fence_before();
+                        mma_wait();  // Q_0: TA is free
+                        __syncthreads();
+                        if (*abortp) break;
+                        if (warp == 1 && lane == 0) {
+                            tc_fence_after();
+                            issue_yx(TB, TA);
+                            tc_commit(&mma_bar2);
                         }
                     }
-                    mma_wait();
+                    if (tid == 0 && it > 0) decide();
+                    if (mtiles > 1) mma_wait2();  // the last second product
+                    else mma_wait();
                     __syncthreads();
                     if (*abortp) break;
-                }
-                if (*abortp) break;
-                last = conv_s || bad_s || it + 1 == a.max_iter;
-                if (onchip) {
-                    // every tile: into the image when the iteration continues, else to the X buffer
-                    drain(0, Q, alpha, zn, !last, hi_off);
-                    if (mtiles > 1) drain(1, R, alpha, zn, !last, hi_off);
+                    // into the image when the iteration continues, else to the slot's X buffer
+                    const bool last = conv_s || bad_s || it + 1 == a.max_iter;
+                    drain(0, q0_reg, alpha, zn, !last, hi_off);
+                    if (mtiles > 1) drain(1, TA, alpha, zn, !last, hi_off);
                     if (last) fence_proxy_async_global();
                     else fence_proxy_async_smem();
-                } else {
-                    // double-buffered: tile 0 is in the next hi image and (lo) in tensor memory
+                    tc_fence_before();
+                    __syncthreads();
+                    cur ^= 1;
+                    done = it + 1;
+                    if (last) break;
+                }
+            } else {
+                // kpad in (160, 192]: P = Y_t (then its A operand), Q = the second product; the hi
+                // image is double-buffered and tile 0's X' lo half waits in tensor memory (L)
+                const uint32_t P = tmem_base, Q = tmem_base + 192;
+                for (int it = 0; it < a.max_iter; ++it) {
+                    const int zn = cur ? zx0 : zx1;
+                    float alpha = -0.5f, shift = 3.0f;
+                    if (it == 0) {
+                        // Z_t = X0_t X0 for both tiles, the bound, then tile 1 is multiplied again
+                        if (warp == 1 && lane == 0) {
+                            tc_fence_after();
+                            issue_xx(0, P);
+                            issue_xx(1, Q);
+                            tc_commit(&mma_bar);
+                        }
+                        mma_wait();
+                        __syncthreads();
+                        if (*abortp) break;
+                        const float c = start_scale(P, Q);
+                        shift = 3.0f / (c * c);
+                        alpha = -0.5f * c * c * c;
+                        tc_fence_before();
+                        __syncthreads();
+                    }
+                    float r2 = 0.0f;
+                    for (int t = 0; t < mtiles; ++t) {
+                        const bool g1 = !(it == 0 && t == 0);  // Z_0 is already in P
+                        if (g1 && warp == 1 && lane == 0) {
+                            tc_fence_after();
+                            issue_xx(t, P);
+                            tc_commit(&mma_bar);
+                        }
+                        const uint32_t hi_next = NB == 2 ? (hi_off == img_bytes ? 2 * img_bytes : img_bytes)
+                                                         : (hi_off == 0 ? img_bytes : 0);
+                        if (t == 1) drain_split0(Q, alpha, hi_next);  // overlaps the product
+                        if (g1) mma_wait();
+                        tc_fence_before();
+                        __syncthreads();
+                        if (*abortp) break;
+                        convert(t, P, shift, it > 0, r2);
+                        if (t == mtiles - 1) {
+                            r2 = warp_sum_f(r2);
+                            if (lane == 0) resid_s2[warp] = r2;
+                        }
+                        tc_fence_before();
+                        __syncthreads();
+                        if (warp == 1 && lane == 0) {
+                            tc_fence_after();
+                            issue_yx(P, Q);
+                            tc_commit(&mma_bar);
+                        }
+                        if (t == mtiles - 1 && tid == 0 && it > 0) decide();
+                        mma_wait();
+                        __syncthreads();
+                        if (*abortp) break;
+                    }
+                    if (*abortp) break;
+                    const bool last = conv_s || bad_s || it + 1 == a.max_iter;
+                    // tile 0 is in the next hi image and (lo) in tensor memory
                     const uint32_t hi_next = NB == 2 ? (hi_off == img_bytes ? 2 * img_bytes : img_bytes)
                                                      : (hi_off == 0 ? img_bytes : 0);
                     if (last) {
@@ -890,12 +986,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                         hi_off = hi_next;
                         img_hi = smem_base + hi_off;
                     }
+                    tc_fence_before();
+                    __syncthreads();
+                    cur ^= 1;
+                    done = it + 1;
+                    if (last) break;
                 }
-                tc_fence_before();
-                __syncthreads();
-                cur ^= 1;
-                done = it + 1;
-                if (last) break;
             }
         } else {
         for (int it = 0; it < a.max_iter; ++it) {
