@@ -92,7 +92,7 @@ typedef struct {
     double iters_mean;
     int32_t n_noconv;           /* submatrices that hit the iteration cap */
     int32_t n_bound_fallback;   /* submatrices whose learned bound failed the safe check */
-    int32_t bisection_steps;    /* builds done by the last smx_solve_mu */
+    int32_t bisection_steps;    /* builds done by the last smx_solve_mu (a first step taken again counts twice) */
     double flops_ns;            /* algorithmic flops of the last build: sum_j 4 n_j^3 iters_j */
     double ms_last_build;       /* device time of the last build (CUDA events), ms */
     double mu;                  /* mu of the last build */
@@ -176,7 +176,11 @@ smx_status smx_set_precision(smx_ctx* ctx, smx_precision bulk, int32_t fp64_fina
 smx_status smx_build_density(smx_ctx* ctx);
 
 /* Finds mu by bisection (see smx_set_electron_count) and leaves the last
- * build's D in the context.  Synchronises once per bisection step.
+ * build's D in the context.  Synchronises once per bisection step.  With new
+ * values on an analysed context the filter and the first step (at the
+ * bracket's midpoint, computed on the device) are issued together and read
+ * back once; if the filter changed the filtered pattern, that step is taken
+ * again on the new pattern (and counted in bisection_steps).
  * Errors: as smx_build_density, plus SMX_ERR_STATE (no electron count set),
  * SMX_ERR_NOBRACKET, and latched device errors. */
 smx_status smx_solve_mu(smx_ctx* ctx);

@@ -1168,8 +1168,6 @@ static cudaError_t launch_prec(const NsTcArgs& a, const CUtensorMap& tmap, int m
     const size_t smem = TcCfg<PREC>::kDynSmem;
     cudaError_t e = cudaFuncSetAttribute(k_ns_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(a.work_counter, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
     k_ns_tc<PREC><<<a.n_slots, kThreads, smem, st>>>(a, tmap);
     return cudaGetLastError();
 }

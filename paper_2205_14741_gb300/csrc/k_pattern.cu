@@ -21,96 +21,124 @@ namespace smx {
 // the kept blocks' columns are reduced over the lanes (H is symmetric: these
 // are the row sums), giving the column's Gershgorin interval
 // [min_q (d_q - r_q), max_q (d_q + r_q)] (d_q the diagonal entry, r_q the sum
-// without it).  Deterministic: every sum has a fixed order.
+// without it).  With keep_prev the new flags are compared with the current
+// filtered pattern's.  The last block to finish takes the minimum and maximum
+// over the columns: the bracket of the whole filtered H and its midpoint.
+// Deterministic: every sum has a fixed order, minima and maxima are exact.
 __global__ void __launch_bounds__(256) k_filter_gershgorin(const double* __restrict__ H, const int64_t* __restrict__ col_ptr,
                                                            const int32_t* __restrict__ row_idx,
                                                            const int64_t* __restrict__ voff,
                                                            const int32_t* __restrict__ bsize, int n_cols, double eps,
-                                                           uint8_t* __restrict__ keep, int* status, float* __restrict__ H32,
-                                                           double* __restrict__ lohi, int bmax) {
+                                                           uint8_t* __restrict__ keep, const uint8_t* __restrict__ keep_prev,
+                                                           float* __restrict__ H32, double* __restrict__ lohi, int bmax,
+                                                           DevScalars* sc) {
     extern __shared__ double fg_smem[];  // per warp: column sums and diagonal entries, bmax each
+    __shared__ double mm_s[2][8];
+    __shared__ bool last_s;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (j >= n_cols) return;
-    double* colsum = fg_smem + static_cast<size_t>(warp) * 2 * bmax;
-    double* diag = colsum + bmax;
-    const int bc = bsize[j];
-    for (int q = lane; q < bc; q += 32) colsum[q] = diag[q] = 0.0;
-    __syncwarp();
-    const int64_t k0 = col_ptr[j], k1 = col_ptr[j + 1];
-    bool finite = true;
-    for (int64_t kb = k0; kb < k1; kb += 32) {
-        const int64_t k = kb + lane;
-        int r = -1, br = 0;
-        bool kept = false;
-        const double* blk = nullptr;
-        if (k < k1) {
-            r = row_idx[k];
-            br = bsize[r];
-            blk = H + voff[k];
-            float* blk32 = H32 + voff[k];
-            const int sz = br * bc;
-            double ss = 0.0;
-            for (int e = 0; e < sz; ++e) {
-                const double v = blk[e];
-                ss = fma(v, v, ss);
-                finite = finite && isfinite(v);
-                blk32[e] = __double2float_rn(v);
+    if (j < n_cols) {
+        double* colsum = fg_smem + static_cast<size_t>(warp) * 2 * bmax;
+        double* diag = colsum + bmax;
+        const int bc = bsize[j];
+        for (int q = lane; q < bc; q += 32) colsum[q] = diag[q] = 0.0;
+        __syncwarp();
+        const int64_t k0 = col_ptr[j], k1 = col_ptr[j + 1];
+        bool finite = true, differs = false;
+        for (int64_t kb = k0; kb < k1; kb += 32) {
+            const int64_t k = kb + lane;
+            int r = -1, br = 0;
+            bool kept = false;
+            const double* blk = nullptr;
+            if (k < k1) {
+                r = row_idx[k];
+                br = bsize[r];
+                blk = H + voff[k];
+                float* blk32 = H32 + voff[k];
+                const int sz = br * bc;
+                double ss = 0.0;
+                for (int e = 0; e < sz; ++e) {
+                    const double v = blk[e];
+                    ss = fma(v, v, ss);
+                    finite = finite && isfinite(v);
+                    blk32[e] = __double2float_rn(v);
+                }
+                kept = r == j || !(sqrt(ss) < eps);
+                keep[k] = kept ? 1 : 0;
+                if (keep_prev) differs = differs || (kept != (keep_prev[k] != 0));
             }
-            kept = r == j || !(sqrt(ss) < eps);
-            keep[k] = kept ? 1 : 0;
+            for (int q = 0; q < bc; ++q) {
+                double cs = 0.0;
+                if (kept) {
+                    const double* col = blk + static_cast<int64_t>(q) * br;
+                    for (int p = 0; p < br; ++p) cs += fabs(col[p]);
+                    if (r == j) diag[q] = col[q];
+                }
+                cs = warp_sum(cs);
+                if (lane == 0) colsum[q] += cs;
+            }
         }
-        for (int q = 0; q < bc; ++q) {
-            double cs = 0.0;
-            if (kept) {
-                const double* col = blk + static_cast<int64_t>(q) * br;
-                for (int p = 0; p < br; ++p) cs += fabs(col[p]);
-                if (r == j) diag[q] = col[q];
-            }
-            cs = warp_sum(cs);
-            if (lane == 0) colsum[q] += cs;
+        __syncwarp();
+        double lo = INFINITY, hi = -INFINITY;
+        for (int q = lane; q < bc; q += 32) {
+            const double d = diag[q], rad = colsum[q] - fabs(d);
+            lo = fmin(lo, d - rad);
+            hi = fmax(hi, d + rad);
+        }
+        finite = __all_sync(0xffffffffu, finite);
+        differs = __any_sync(0xffffffffu, differs);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            lohi[2 * j] = lo;
+            lohi[2 * j + 1] = hi;
+            if (!finite) atomicCAS(&sc->status, kOk, kErrNonfinite);
+            if (differs) atomicOr(&sc->changed, 1);
         }
     }
-    __syncwarp();
+    // the last block: bracket of the filtered H over all columns
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_s = atomicAdd(&sc->filter_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
     double lo = INFINITY, hi = -INFINITY;
-    for (int q = lane; q < bc; q += 32) {
-        const double d = diag[q], rad = colsum[q] - fabs(d);
-        lo = fmin(lo, d - rad);
-        hi = fmax(hi, d + rad);
+    for (int c = threadIdx.x; c < n_cols; c += blockDim.x) {
+        lo = fmin(lo, __ldcg(lohi + 2 * c));
+        hi = fmax(hi, __ldcg(lohi + 2 * c + 1));
     }
-    finite = __all_sync(0xffffffffu, finite);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     if (lane == 0) {
-        lohi[2 * j] = lo;
-        lohi[2 * j + 1] = hi;
-        if (!finite) atomicCAS(status, kOk, kErrNonfinite);
+        mm_s[0][warp] = lo;
+        mm_s[1][warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
+            lo = fmin(lo, mm_s[0][w]);
+            hi = fmax(hi, mm_s[1][w]);
+        }
+        lo = fmin(lo, mm_s[0][0]);
+        hi = fmax(hi, mm_s[1][0]);
+        sc->br_lo = lo;
+        sc->br_hi = hi;
+        sc->mu0 = 0.5 * (lo + hi);
+        sc->filter_done = 0u;
     }
 }
 
-// *changed |= 1 when the keep flags differ from those of the current filtered pattern.
-__global__ void k_keep_changed(const uint8_t* __restrict__ keep, const uint8_t* __restrict__ prev, int64_t n, int* changed) {
-    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n;
-         k += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        if (keep[k] != prev[k]) {
-            atomicOr(changed, 1);
-            return;
-        }
-}
-
-cudaError_t launch_keep_changed(const uint8_t* keep, const uint8_t* prev, int64_t n, int* changed, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 1024));
-    k_keep_changed<<<grid, 256, 0, st>>>(keep, prev, n, changed);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
-                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep, int* status,
-                                     float* H32, double* lohi, cudaStream_t st) {
+                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep,
+                                     const uint8_t* keep_prev, float* H32, double* lohi, DevScalars* sc,
+                                     cudaStream_t st) {
     if (n_cols <= 0) return cudaSuccess;
     const int grid = static_cast<int>((static_cast<int64_t>(n_cols) * 32 + 255) / 256);
     const size_t smem = sizeof(double) * 2 * static_cast<size_t>(bmax) * 8;
@@ -118,7 +146,8 @@ cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, co
         cudaError_t e = cudaFuncSetAttribute(k_filter_gershgorin, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
-    k_filter_gershgorin<<<grid, 256, smem, st>>>(H, col_ptr, row_idx, voff, bsize, n_cols, eps, keep, status, H32, lohi, bmax);
+    k_filter_gershgorin<<<grid, 256, smem, st>>>(H, col_ptr, row_idx, voff, bsize, n_cols, eps, keep, keep_prev, H32, lohi,
+                                                 bmax, sc);
     return cudaGetLastError();
 }
 
@@ -146,7 +175,7 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
     __shared__ double warp_max_s[8];
     __shared__ float stat_s[8][7];  // per warp: F2, Da, Ds, Dq, Rs (sums), Dm, Rm (maxima)
     __shared__ float x_s[kModelFeatures], h1_s[kModelHidden], y_s[2][2];
-    const R mu = static_cast<R>(mu_d);
+    const R mu = static_cast<R>(ex.mu_dev ? *ex.mu_dev : mu_d);
     const SubDesc s = subs[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int* rows = reinterpret_cast<int*>(gsm);  // R_j
@@ -361,69 +390,64 @@ cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nbl
     return launch_gather<float>(subs, n_subs, max_nblk, max_ld, max_bs, pv, H32, mu, T32, bound, ex, st);
 }
 
-// One CTA per submatrix: scatter of the saved owner columns (Fig. 2 step (iii)).
+// Deterministic sums of partial[0, n_cols) by one block (each thread adds a fixed
+// strided subset in order, then a fixed tree) into sc->trace, sc->energy.
+__device__ void sum_partials(const double2* partial, int n_cols, DevScalars* sc, double* scratch) {
+    double tr = 0.0, en = 0.0;
+    for (int c = threadIdx.x; c < n_cols; c += blockDim.x) {
+        const double2 p = __ldcg(partial + c);
+        tr += p.x;
+        en += p.y;
+    }
+    tr = block_sum(tr, scratch);
+    en = block_sum(en, scratch);
+    if (threadIdx.x == 0) {
+        sc->trace = tr;
+        sc->energy = en;
+    }
+}
+
+// One CTA per submatrix: scatter of the saved owner columns (Fig. 2 step (iii)),
+// then (the last CTA) the sums of a8.
 __global__ void __launch_bounds__(256) k_scatter_owner(const SubDesc* __restrict__ subs, PatternView pv,
                                                        const float* __restrict__ xown, const double* __restrict__ H,
-                                                       double* __restrict__ D, double2* __restrict__ partial) {
+                                                       double* __restrict__ D, double2* __restrict__ partial, int n_cols,
+                                                       DevScalars* sc) {
     extern __shared__ int ls_smem[];
     __shared__ double scratch[32];
+    __shared__ bool last_s;
     const SubDesc s = subs[blockIdx.x];
     const float* x = xown + s.x_off;
     auto xcol = [&](int q, int i) -> double { return static_cast<double>(x[static_cast<int64_t>(q) * s.n + i]); };
     finish_column(s, pv, H, D, partial, xcol, ls_smem, scratch);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_s = atomicAdd(&sc->scatter_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
+    sum_partials(partial, n_cols, sc, scratch);
+    if (threadIdx.x == 0) {
+        sc->scatter_done = 0u;
+        sc->ns_counter = 0;  // the Newton-Schulz launch before this one is complete
+    }
 }
 
 cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
-                                 const float* xown, const double* H, double* D, double2* partial, cudaStream_t st) {
+                                 const float* xown, const double* H, double* D, double2* partial, int n_cols,
+                                 DevScalars* sc, cudaStream_t st) {
     const size_t smem = sizeof(int) * (static_cast<size_t>(max_nblk) + 1);
-    k_scatter_owner<<<n_subs, 256, smem, st>>>(subs, pv, xown, H, D, partial);
+    k_scatter_owner<<<n_subs, 256, smem, st>>>(subs, pv, xown, H, D, partial, n_cols, sc);
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(1024) k_reduce(const double2* __restrict__ partial, const double* __restrict__ lohi,
-                                                 int n_cols, double* out) {
+__global__ void __launch_bounds__(1024) k_reduce(const double2* __restrict__ partial, int n_cols, DevScalars* sc) {
     __shared__ double scratch[32];
-    __shared__ double mm[2][32];
-    double tr = 0.0, en = 0.0, lo = INFINITY, hi = -INFINITY;
-    for (int j = threadIdx.x; j < n_cols; j += blockDim.x) {
-        const double2 p = partial[j];
-        tr += p.x;
-        en += p.y;
-        if (lohi) {
-            lo = fmin(lo, lohi[2 * j]);
-            hi = fmax(hi, lohi[2 * j + 1]);
-        }
-    }
-    tr = block_sum(tr, scratch);
-    en = block_sum(en, scratch);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    if (lane == 0) {
-        mm[0][warp] = lo;
-        mm[1][warp] = hi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        out[0] = tr;
-        out[1] = en;
-        if (lohi) {
-            double l = INFINITY, h = -INFINITY;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                l = fmin(l, mm[0][w]);
-                h = fmax(h, mm[1][w]);
-            }
-            out[2] = l;
-            out[3] = h;
-        }
-    }
+    sum_partials(partial, n_cols, sc, scratch);
 }
 
-cudaError_t launch_reduce(const double2* partial, const double* lohi, int n_cols, double* out, cudaStream_t st) {
-    k_reduce<<<1, 1024, 0, st>>>(partial, lohi, n_cols, out);
+cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cudaStream_t st) {
+    k_reduce<<<1, 256, 0, st>>>(partial, n_cols, sc);
     return cudaGetLastError();
 }
 

@@ -76,12 +76,14 @@ struct smx_ctx {
     int64_t t_elems = 0, x_elems = 0;
 
     // device buffers
-    DevBuf d_H, d_H32, d_voff, d_row_idx, d_col_ptr, d_bs, d_keep, d_keep_prev, d_changed;
-    double br_lo = 0.0, br_hi = 0.0;  // Gershgorin bracket of the filtered H (from the last analyse)
-    int32_t* h_small = nullptr;       // pinned: status, changed flag, then the bracket (4 doubles)
+    DevBuf d_H, d_H32, d_voff, d_row_idx, d_col_ptr, d_bs, d_keep, d_keep_prev;
+    double br_lo = 0.0, br_hi = 0.0;  // Gershgorin bracket of the filtered H (from the last filter)
+    bool filter_compared = false;     // the last filter launch compared its flags with the current pattern
+    DevBuf d_sc;                      // DevScalars: status, flags, bracket, trace and energy
+    DevScalars* h_sc = nullptr;       // pinned copy, filled by fetch()
     DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order;
     DevBuf d_T, d_W1, d_W2, d_ws, d_D, d_xown;
-    DevBuf d_bound, d_iters, d_partial, d_lohi, d_out, d_out_br, d_status, d_counter, d_work_n3;
+    DevBuf d_bound, d_iters, d_partial, d_lohi, d_work_n3;
     uint8_t* h_keep_pinned = nullptr;
 
     // tensor-core workspace
@@ -112,7 +114,7 @@ struct smx_ctx {
     int adam_t = 0;
     int64_t n_samples = 0, cap_samples = 0;
     DevBuf d_params, d_mst, d_vst, d_partial_mlp, d_feat, d_pred, d_labels, d_gersh, d_prev_ratio, d_sq_ratio,
-        d_fallback, d_loss, d_sx, d_st, d_fit_x, d_fit_t, d_grad;
+        d_loss, d_sx, d_st, d_fit_x, d_fit_t, d_grad;
 };
 
 // ---------------------------------------------------------------------------
@@ -213,38 +215,63 @@ static smx_status get_encoder(smx_ctx* c) {
 }
 
 // Filter (a1), the Gershgorin bracket of the filtered H, and symbolic analysis (a2).
-static smx_status analyse(smx_ctx* c) {
-    cudaStream_t st = c->stream;
-    SMX_CUDA(cudaMemsetAsync(c->d_status.p, 0, sizeof(int), st));
-    SMX_CUDA(cudaMemsetAsync(c->d_changed.p, 0, sizeof(int), st));
+static DevScalars* scalars(smx_ctx* c) { return dp<DevScalars>(c->d_sc); }
+
+// Clears the status word, the change flag and the fallback count (once per call that launches work).
+static smx_status reset_flags(smx_ctx* c) {
+    SMX_CUDA(cudaMemsetAsync(&scalars(c)->status, 0, 3 * sizeof(int), c->stream));
+    return SMX_OK;
+}
+
+static void accumulate_timers(smx_ctx* c);
+
+// Copies the device scalars to h_sc (one copy) and waits for the stream.
+static smx_status fetch(smx_ctx* c) {
+    SMX_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    SMX_CUDA(cudaStreamSynchronize(c->stream));
+    accumulate_timers(c);
+    return SMX_OK;
+}
+
+// a1 on the device (asynchronous): keep flags, FP32 copy of H, the bracket and,
+// against the current filtered pattern, the change flag.
+static smx_status launch_filter(smx_ctx* c) {
+    c->filter_compared = c->analysed && c->eps > 0.0;  // without a threshold every block is kept
     SMX_CUDA(launch_filter_gershgorin(dp<double>(c->d_H), dp<int64_t>(c->d_col_ptr), dp<int32_t>(c->d_row_idx),
                                       dp<int64_t>(c->d_voff), dp<int32_t>(c->d_bs), c->B, c->bmax, c->eps,
-                                      dp<uint8_t>(c->d_keep),
-                                      dp<int>(c->d_status), dp<float>(c->d_H32), dp<double>(c->d_lohi), st));
-    SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), dp<double>(c->d_lohi), c->B, dp<double>(c->d_out_br), st));
-    c->kernel_launches += 2;
-    // with a threshold the filtered pattern may change: compared on the device, the flags
-    // are read back only when it did (or the first time)
-    const bool compare = c->analysed && c->eps > 0.0;
-    if (compare) {
-        SMX_CUDA(launch_keep_changed(dp<uint8_t>(c->d_keep), dp<uint8_t>(c->d_keep_prev), c->nnzb, dp<int>(c->d_changed), st));
-        c->kernel_launches += 1;
-    }
-    SMX_CUDA(cudaMemcpyAsync(c->h_small, c->d_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SMX_CUDA(cudaMemcpyAsync(c->h_small + 1, c->d_changed.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SMX_CUDA(cudaMemcpyAsync(c->h_small + 2, c->d_out_br.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    SMX_CUDA(cudaStreamSynchronize(st));
-    if (c->h_small[0] == kErrNonfinite) return SMX_ERR_NONFINITE;
-    {
-        double br[4];
-        std::memcpy(br, c->h_small + 2, sizeof(br));
-        c->br_lo = br[2];
-        c->br_hi = br[3];
-    }
-    if (c->analysed && (!compare || c->h_small[1] == 0)) {
+                                      dp<uint8_t>(c->d_keep), c->filter_compared ? dp<uint8_t>(c->d_keep_prev) : nullptr,
+                                      dp<float>(c->d_H32), dp<double>(c->d_lohi), scalars(c), c->stream));
+    c->kernel_launches += 1;
+    return SMX_OK;
+}
+
+static smx_status compact(smx_ctx* c);
+
+// After a filter launch and a fetch: errors, the bracket, and the host-side
+// compaction of the filtered pattern when it changed (or the first time).
+static smx_status after_filter(smx_ctx* c) {
+    if (c->h_sc->status == kErrNonfinite) return SMX_ERR_NONFINITE;
+    c->br_lo = c->h_sc->br_lo;
+    c->br_hi = c->h_sc->br_hi;
+    if (c->analysed && (!c->filter_compared || c->h_sc->changed == 0)) {
         c->dirty = false;
         return SMX_OK;  // same filtered pattern
     }
+    return compact(c);
+}
+
+// a1 + a2, synchronous (clears the flags first).
+static smx_status analyse(smx_ctx* c) {
+    SMX_TRY(reset_flags(c));
+    SMX_TRY(launch_filter(c));
+    SMX_TRY(fetch(c));
+    return after_filter(c);
+}
+
+// a2: the filtered pattern from the keep flags on the device, symbolic sets of
+// every submatrix, chunks and processing order (host), uploaded.
+static smx_status compact(smx_ctx* c) {
+    cudaStream_t st = c->stream;
     SMX_CUDA(cudaMemcpyAsync(c->h_keep_pinned, c->d_keep.p, c->nnzb, cudaMemcpyDeviceToHost, st));
     SMX_CUDA(cudaStreamSynchronize(st));
     c->keep.assign(c->h_keep_pinned, c->h_keep_pinned + c->nnzb);
@@ -365,7 +392,7 @@ static double tau_for(int precision) {
 
 // Adds the device time of the Newton-Schulz launches recorded since the last
 // call; the stream must be synchronised.
-static void accumulate_timers(smx_ctx* c) {
+void accumulate_timers(smx_ctx* c) {
     for (size_t i = 0; i < c->ns_pending; ++i) {
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, c->ns_events[i].first, c->ns_events[i].second) == cudaSuccess)
@@ -404,13 +431,14 @@ static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const Gathe
     return SMX_OK;
 }
 
-static smx_status build_at(smx_ctx* c, double mu) {
+// mu_on_device: the gather reads mu from the device scalars (the midpoint the
+// filter just computed) instead of the argument.
+static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
     cudaStream_t st = c->stream;
     const int B = c->B;
-    SMX_CUDA(cudaMemsetAsync(c->d_status.p, 0, sizeof(int), st));
+    DevScalars* sc = scalars(c);
     SMX_CUDA(cudaEventRecord(c->ev0, st));
-    SMX_CUDA(cudaMemsetAsync(c->d_fallback.p, 0, sizeof(int), st));
     const PatternView pv = pattern_view(c);
     if (c->precision == SMX_FP64) {
         SMX_TRY(ensure(c->d_W1, c->d_T.bytes));
@@ -425,6 +453,7 @@ static smx_status build_at(smx_ctx* c, double mu) {
         const int j0 = c->chunk_start[k], m = c->chunk_start[k + 1] - j0;
         GatherExtras ex;
         ex.gersh = dp<double>(c->d_gersh) + j0;
+        if (mu_on_device) ex.mu_dev = &sc->mu0;
         if (c->model_on) {  // learned bound: features and prediction inside the gather (checked in the NS kernel)
             ex.prev_ratio = dp<float>(c->d_prev_ratio) + j0;
             ex.params = dp<float>(c->d_params);
@@ -448,8 +477,8 @@ static smx_status build_at(smx_ctx* c, double mu) {
             a.gersh = dp<double>(c->d_gersh) + j0;
             a.sq_ratio = dp<float>(c->d_sq_ratio) + j0;
             a.use_model = c->model_on ? 1 : 0;
-            a.fallbacks = dp<int>(c->d_fallback);
-            a.status = dp<int>(c->d_status);
+            a.fallbacks = &sc->fallbacks;
+            a.status = &sc->status;
             a.pv = pv;
             a.H = dp<double>(c->d_H);
             a.D = dp<double>(c->d_D);
@@ -462,7 +491,7 @@ static smx_status build_at(smx_ctx* c, double mu) {
             a.subs = subs;  // indexed by block column through the order slice
             a.order = dp<int32_t>(c->d_order) + j0;
             a.n_subs = m;
-            a.work_counter = dp<int>(c->d_counter);
+            a.work_counter = &sc->ns_counter;
             a.T = dp<float>(c->d_T);
             a.bound = dp<double>(c->d_bound);
             a.ws = c->d_ws.p;
@@ -475,8 +504,8 @@ static smx_status build_at(smx_ctx* c, double mu) {
             a.gersh = dp<double>(c->d_gersh);
             a.sq_ratio = dp<float>(c->d_sq_ratio);
             a.use_model = c->model_on ? 1 : 0;
-            a.fallbacks = dp<int>(c->d_fallback);
-            a.status = dp<int>(c->d_status);
+            a.fallbacks = &sc->fallbacks;
+            a.status = &sc->status;
             a.pv = pv;
             a.H = dp<double>(c->d_H);
             a.D = dp<double>(c->d_D);
@@ -486,15 +515,17 @@ static smx_status build_at(smx_ctx* c, double mu) {
             SMX_CUDA(launch_ns_tc(a, c->precision, c->tmap, c->max_nblk, st));
             SMX_CUDA(cudaEventRecord(ns1, st));
             SMX_CUDA(launch_scatter_owner(subs + j0, m, c->max_nblk, pv, dp<float>(c->d_xown), dp<double>(c->d_H),
-                                          dp<double>(c->d_D), dp<double2>(c->d_partial), st));
+                                          dp<double>(c->d_D), dp<double2>(c->d_partial), B, sc, st));
             c->kernel_launches += 1;
         }
         c->kernel_launches += 1;
         c->ns_launches += 1;
     }
-    SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), nullptr, B, dp<double>(c->d_out), st));
+    if (c->precision == SMX_FP64) {  // the tensor-core scatter sums the partials itself
+        SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), B, sc, st));
+        c->kernel_launches += 1;
+    }
     SMX_CUDA(cudaEventRecord(c->ev1, st));
-    c->kernel_launches += 1;
     c->sq_valid = true;
     c->built = true;
     c->last_mu = mu;
@@ -502,11 +533,8 @@ static smx_status build_at(smx_ctx* c, double mu) {
 }
 
 static smx_status read_status(smx_ctx* c) {
-    int status = 0;
-    SMX_CUDA(cudaMemcpyAsync(&status, c->d_status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    SMX_CUDA(cudaStreamSynchronize(c->stream));
-    accumulate_timers(c);
-    return static_cast<smx_status>(status);
+    SMX_TRY(fetch(c));
+    return static_cast<smx_status>(c->h_sc->status);
 }
 
 // ---------------------------------------------------------------------------
@@ -576,16 +604,13 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if ((s = ensure(c->d_D, vb)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_keep, c->nnzb)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_keep_prev, c->nnzb)) != SMX_OK) return fail(s);
-    if ((s = ensure(c->d_changed, sizeof(int))) != SMX_OK) return fail(s);
-    if (cudaMallocHost(&c->h_small, 64) != cudaSuccess) return fail(SMX_ERR_OOM);
+    if ((s = ensure(c->d_sc, sizeof(DevScalars))) != SMX_OK) return fail(s);
+    if (cudaMallocHost(&c->h_sc, sizeof(DevScalars)) != cudaSuccess) return fail(SMX_ERR_OOM);
+    if (cudaMemsetAsync(c->d_sc.p, 0, sizeof(DevScalars), c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
     if ((s = ensure(c->d_bound, sizeof(double) * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_iters, sizeof(int32_t) * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_partial, sizeof(double2) * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_lohi, sizeof(double) * 2 * n_block_cols)) != SMX_OK) return fail(s);
-    if ((s = ensure(c->d_out, sizeof(double) * 4)) != SMX_OK) return fail(s);
-    if ((s = ensure(c->d_out_br, sizeof(double) * 4)) != SMX_OK) return fail(s);
-    if ((s = ensure(c->d_status, sizeof(int))) != SMX_OK) return fail(s);
-    if ((s = ensure(c->d_counter, sizeof(int))) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_work_n3, sizeof(unsigned long long))) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_gersh, sizeof(double) * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_sq_ratio, sizeof(float) * n_block_cols)) != SMX_OK) return fail(s);
@@ -593,7 +618,6 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if ((s = ensure(c->d_feat, sizeof(float) * kModelFeatures * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_pred, sizeof(float) * 2 * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_labels, sizeof(float) * 2 * n_block_cols)) != SMX_OK) return fail(s);
-    if ((s = ensure(c->d_fallback, sizeof(int))) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_loss, sizeof(float))) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_params, sizeof(float) * kModelParams)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_mst, sizeof(float) * kModelParams)) != SMX_OK) return fail(s);
@@ -605,7 +629,6 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if (cudaMemsetAsync(c->d_work_n3.p, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
     if (cudaMallocHost(&c->h_keep_pinned, c->nnzb > 0 ? c->nnzb : 1) != cudaSuccess) return fail(SMX_ERR_OOM);
     if (cudaMemcpyAsync(c->d_H.p, values, vb, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
-    if (cudaMemsetAsync(c->d_status.p, 0, sizeof(int), c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
     if (cudaMemsetAsync(c->d_iters.p, 0, sizeof(int32_t) * n_block_cols, c->stream) != cudaSuccess)
         return fail(SMX_ERR_CUDA);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(SMX_ERR_CUDA);
@@ -699,6 +722,7 @@ smx_status smx_build_density(smx_ctx* c) {
     if (!c) return SMX_ERR_ARG;
     DeviceGuard g(c->device);
     c->bisection_steps = 0;
+    SMX_TRY(reset_flags(c));
     return build_at(c, c->mu);
 }
 
@@ -707,19 +731,48 @@ smx_status smx_solve_mu(smx_ctx* c) {
     if (!c->have_ne || c->col_hi >= 0) return SMX_ERR_STATE;  // a shard's trace is partial
     DeviceGuard g(c->device);
     if (c->n_e < 0.0 || c->n_e > static_cast<double>(c->N)) return SMX_ERR_NOBRACKET;
-    if (c->dirty || !c->analysed) SMX_TRY(analyse(c));  // the bracket comes with the filter
-    double lo = c->br_lo, hi = c->br_hi;
+    SMX_TRY(reset_flags(c));
     c->bisection_steps = 0;
-    for (int step = 0; step < c->max_steps; ++step) {
+    double lo = 0.0, hi = 0.0;
+    int step = 0;
+    if (c->analysed && c->dirty) {
+        // New values on a known pattern: the filter and the first bisection step (at the
+        // midpoint the filter leaves on the device, on the current filtered pattern) go
+        // out together and come back in one read.  If the filter changed the pattern,
+        // the step is discarded and taken again on the new one.
+        SMX_TRY(launch_filter(c));
+        c->dirty = false;  // the build below runs on the current filtered pattern
+        SMX_TRY(build_at(c, 0.0, true));
+        SMX_TRY(fetch(c));
+        const bool changed = c->filter_compared && c->h_sc->changed != 0;
+        SMX_TRY(after_filter(c));  // errors of the filter, bracket, compaction when changed
+        lo = c->br_lo;
+        hi = c->br_hi;
+        c->bisection_steps = 1;
+        if (changed) {
+            SMX_TRY(reset_flags(c));  // the step is taken again on the new pattern
+        } else {
+            c->last_mu = c->h_sc->mu0;  // the device's 0.5 (lo + hi)
+            step = 1;
+            if (c->h_sc->status != SMX_OK) return static_cast<smx_status>(c->h_sc->status);
+            const double tr = c->h_sc->trace;
+            if (std::fabs(tr - c->n_e) <= c->tol) return SMX_OK;
+            if (tr < c->n_e) lo = c->last_mu; else hi = c->last_mu;
+        }
+    } else {
+        if (c->dirty || !c->analysed) SMX_TRY(analyse(c));  // the bracket comes with the filter
+        lo = c->br_lo;
+        hi = c->br_hi;
+    }
+    for (; step < c->max_steps; ++step) {
         const double mid = 0.5 * (lo + hi);
         SMX_TRY(build_at(c, mid));
         ++c->bisection_steps;
-        double tr[2];
-        SMX_CUDA(cudaMemcpyAsync(tr, c->d_out.p, sizeof(tr), cudaMemcpyDeviceToHost, c->stream));
         const smx_status ds = read_status(c);
         if (ds != SMX_OK) return ds;
-        if (std::fabs(tr[0] - c->n_e) <= c->tol) break;
-        if (tr[0] < c->n_e) lo = mid; else hi = mid;
+        const double tr = c->h_sc->trace;
+        if (std::fabs(tr - c->n_e) <= c->tol) break;
+        if (tr < c->n_e) lo = mid; else hi = mid;
     }
     return SMX_OK;
 }
@@ -728,12 +781,10 @@ smx_status smx_get_trace(smx_ctx* c, double* trace_D, double* trace_DH, double* 
     if (!c) return SMX_ERR_ARG;
     if (!c->built) return SMX_ERR_STATE;
     DeviceGuard g(c->device);
-    double out[2];
-    SMX_CUDA(cudaMemcpyAsync(out, c->d_out.p, sizeof(out), cudaMemcpyDeviceToHost, c->stream));
     const smx_status ds = read_status(c);
     if (ds != SMX_OK) return ds;
-    if (trace_D) *trace_D = out[0];
-    if (trace_DH) *trace_DH = out[1];
+    if (trace_D) *trace_D = c->h_sc->trace;
+    if (trace_DH) *trace_DH = c->h_sc->energy;
     if (mu) *mu = c->last_mu;
     return SMX_OK;
 }
@@ -774,12 +825,10 @@ smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
     DeviceGuard g(c->device);
     std::vector<int32_t> it(c->B);
     unsigned long long work = 0;
-    int fallbacks = 0;
-    SMX_CUDA(cudaMemcpyAsync(&fallbacks, c->d_fallback.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     SMX_CUDA(cudaMemcpyAsync(it.data(), c->d_iters.p, sizeof(int32_t) * c->B, cudaMemcpyDeviceToHost, c->stream));
     SMX_CUDA(cudaMemcpyAsync(&work, c->d_work_n3.p, sizeof(work), cudaMemcpyDeviceToHost, c->stream));
-    SMX_CUDA(cudaStreamSynchronize(c->stream));
-    accumulate_timers(c);
+    SMX_TRY(fetch(c));
+    const int fallbacks = c->h_sc->fallbacks;
     std::memset(out, 0, sizeof(*out));
     out->n_block_cols = c->B;
     const int32_t lo = c->col_lo, hi = c->col_hi < 0 ? c->B : c->col_hi;
@@ -1081,12 +1130,12 @@ void smx_destroy(smx_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep_prev, &c->d_changed, &c->d_keep, &c->d_fcol_ptr,
+    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep_prev, &c->d_sc, &c->d_keep, &c->d_fcol_ptr,
                       &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
                       &c->d_W2, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
-                      &c->d_out, &c->d_out_br, &c->d_status, &c->d_counter, &c->d_work_n3,
+                      &c->d_work_n3,
                       &c->d_params, &c->d_mst, &c->d_vst, &c->d_partial_mlp, &c->d_feat, &c->d_pred, &c->d_labels,
-                      &c->d_gersh, &c->d_prev_ratio, &c->d_sq_ratio, &c->d_fallback, &c->d_loss, &c->d_sx, &c->d_st,
+                      &c->d_gersh, &c->d_prev_ratio, &c->d_sq_ratio, &c->d_loss, &c->d_sx, &c->d_st,
                       &c->d_fit_x, &c->d_fit_t, &c->d_grad};
     for (DevBuf* b : bufs) release(*b);
     for (auto& pr : c->ns_events) {
@@ -1094,7 +1143,7 @@ void smx_destroy(smx_ctx* c) {
         cudaEventDestroy(pr.second);
     }
     if (c->h_keep_pinned) cudaFreeHost(c->h_keep_pinned);
-    if (c->h_small) cudaFreeHost(c->h_small);
+    if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;

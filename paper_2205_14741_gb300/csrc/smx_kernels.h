@@ -9,15 +9,30 @@
 
 namespace smx {
 
-// a1 + bracket: per block column j, keep flags of its blocks (Frobenius norm
-// >= eps, diagonal always), non-finite check, FP32 copy of H, and the
-// Gershgorin interval of the filtered column (lohi[2j], lohi[2j + 1]).
-cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
-                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep, int* status,
-                                     float* H32, double* lohi, cudaStream_t st);
+// Small device-side state of a context, read back by the host in one copy.
+struct DevScalars {
+    double trace, energy;  // a8: trace(D) and trace(D H) of the last build
+    double br_lo, br_hi;   // Gershgorin bracket of the filtered H (a9)
+    double mu0;            // 0.5 (br_lo + br_hi): the first bisection step
+    double pad0;
+    int status;            // first error recorded by a kernel (kOk = 0)
+    int changed;           // the keep flags differ from the current filtered pattern
+    int fallbacks;         // learned-bound fallbacks since the last reset
+    int ns_counter;        // job counter of the tensor-core Newton-Schulz kernel (reset by the scatter)
+    unsigned int filter_done, scatter_done;  // last-block tickets (each reset by its last block)
+    int pad1[2];
+};
 
-// *changed |= 1 when keep differs from prev (the flags of the current filtered pattern).
-cudaError_t launch_keep_changed(const uint8_t* keep, const uint8_t* prev, int64_t n, int* changed, cudaStream_t st);
+// a1 + bracket: per block column j, keep flags of its blocks (Frobenius norm
+// >= eps, diagonal always), non-finite check (sc->status), FP32 copy of H and
+// the Gershgorin interval of the filtered column (lohi[2j], lohi[2j + 1]);
+// with keep_prev, sc->changed = 1 when a flag differs from it.  The last
+// block writes the bracket (min and max over the columns) and its midpoint
+// to sc->br_lo, br_hi, mu0.
+cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
+                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep,
+                                     const uint8_t* keep_prev, float* H32, double* lohi, DevScalars* sc,
+                                     cudaStream_t st);
 
 // Optional outputs of the gather, per submatrix (pointers offset like subs; null = not wanted).
 struct GatherExtras {
@@ -27,6 +42,7 @@ struct GatherExtras {
     const float* params = nullptr;       // learned bound: parameters; when set, b_j is the model's
     float* pred = nullptr;               // ... and its two predictions
     float margin = 0.0f;                 // ... b_j = G_j clamp(pred_0, 0.02, 1) (1 + margin) / 1.2
+    const double* mu_dev = nullptr;      // when set, mu is read from here (on the device) instead
 };
 
 // a3 + a4: T_j = H[R_j, R_j] - mu I into the FP64 staging buffer, then the
@@ -41,10 +57,9 @@ cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nbl
                                     const PatternView& pv, const float* H32, double mu, float* T32, double* bound,
                                     const GatherExtras& ex, cudaStream_t st);
 
-// a8: deterministic sums of the per-column partials -> out[0] = trace(D),
-// out[1] = trace(D H); also min/max of the column Gershgorin bounds into
-// out[2], out[3] when lohi != nullptr.
-cudaError_t launch_reduce(const double2* partial, const double* lohi, int n_cols, double* out, cudaStream_t st);
+// a8 (FP64 form): deterministic sums of the per-column partials ->
+// sc->trace = trace(D), sc->energy = trace(D H).
+cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cudaStream_t st);
 
 // a5/a6 (FP64 plain form) + a7: Newton-Schulz in FP64, then scatter.
 struct NsFp64Args {
@@ -75,7 +90,7 @@ struct NsTcArgs {
     const SubDesc* subs;
     const int32_t* order;  // processing order (largest first)
     int n_subs;
-    int* work_counter;     // zeroed by the launcher
+    int* work_counter;     // zero at launch (the scatter that follows resets it)
     const float* T;        // FP32 staging of T_j - mu I (leading dimension SubDesc::ld)
     double* bound;         // in: initial bound b_j (X0 = T_j / b_j); out: effective bound after rescaling
     void* ws;              // 16-bit workspace: n_slots * 6 buffers of ld x ld
@@ -100,9 +115,12 @@ struct NsTcArgs {
 cudaError_t launch_ns_tc(const NsTcArgs& a, int precision, const CUtensorMap& tmap, int max_nblk, cudaStream_t st);
 
 // a7 + a8 for the tensor-core path: D[R_j, j] = 1/2 (E_j - X[:, own]) from the
-// saved owner columns, with the per-column trace / energy partials (FP64).
+// saved owner columns, with the per-column trace / energy partials (FP64);
+// the last block sums partial[0, n_cols) in a fixed order into sc->trace,
+// sc->energy and resets sc->ns_counter for the next Newton-Schulz launch.
 cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
-                                 const float* xown, const double* H, double* D, double2* partial, cudaStream_t st);
+                                 const float* xown, const double* H, double* D, double2* partial, int n_cols,
+                                 DevScalars* sc, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // learned spectral bound (k_bound_model.cu)

@@ -263,3 +263,44 @@ def test_errors_are_reported():
         assert ei.value.status == _lib.ERR_NOBRACKET
         with pytest.raises(SmxError):
             c.get_trace()  # no successful build yet
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x3"])
+def test_solve_mu_over_snapshots_with_changing_pattern(prec):
+    """One context through an MD-like trajectory whose filtered pattern changes at every
+    snapshot (and one snapshot with a NaN): each solve equals a fresh context's, bit for
+    bit, and the oracle's bisection (the first step is taken before the pattern change is
+    known and taken again on the new pattern)."""
+    from paper_2205_14741_gb300 import SmxError, _lib
+    from synth import md_trajectory
+
+    eps, n_e = 1e-2, 384.0
+    snaps = list(md_trajectory(128, 6, 6.0, 1.5, seed=21, n_snap=4, step_sigma=0.15, fixed_pattern=True))
+    nnz = []
+    with _ctx(snaps[0], prec, eps) as c:
+        c.set_electron_count(n_e, max_steps=30, tol=1e-2)
+        for k, sn in enumerate(snaps):
+            if k == 2:  # a bad snapshot in between: reported, and the context stays usable
+                bad = sn.values.copy()
+                bad[17] = np.nan
+                c.set_values(bad)
+                with pytest.raises(SmxError) as ei:
+                    c.solve_mu()
+                assert ei.value.status == _lib.ERR_NONFINITE
+            c.set_values(sn.values)
+            c.solve_mu()
+            tr, en, mu = c.get_trace()
+            d = c.get_density().copy()
+            col_ptr, _ = c.get_pattern()
+            nnz.append(int(col_ptr[-1]))
+            with _ctx(sn, prec, eps) as f:
+                f.set_electron_count(n_e, max_steps=30, tol=1e-2)
+                f.solve_mu()
+                assert f.get_trace() == (tr, en, mu)
+                assert np.array_equal(f.get_density(), d)
+            cp, ri, v, _ = O.filter_blocks(sn.block_size, sn.col_ptr, sn.row_idx, sn.values, eps)
+            mu_or, res, _ = O.bisect_mu(sn.block_size, cp, ri, v, n_e, max_steps=30, tol=1e-2)
+            # the bracket's row sums are added in another order on the device: mu agrees to rounding
+            assert abs(mu - mu_or) <= 1e-12
+            assert abs(en - res.energy) <= TOL_E[prec] * abs(res.energy)
+    assert len(set(nnz)) == len(nnz)  # the filtered pattern changed at every snapshot
