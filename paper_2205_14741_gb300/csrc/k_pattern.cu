@@ -152,25 +152,30 @@ cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, co
 }
 
 // One CTA per submatrix; T_j is row-major with leading dimension s.ld (zero
-// in columns [n, ld)).  Warp w assembles the rows of block rows c = w, w + 8,
-// ...: the blocks of H's column R_j[c] whose rows lie in R_j are listed once
-// per block row (position a in R_j, value offset); row x = start(c) + q of T_j
-// then takes, from each listed block (R_j[a], R_j[c]) (column-major), its
-// column q -- T_j is symmetric, so that column is row x restricted to block a.
-// The row is put together in shared memory and written once, coalesced, with
-// its absolute sum for the Gershgorin bound b_j = max_x sum_y |T[x][y]|, and
-// the row statistics of the learned bound's features.
+// in columns [n, ld)).  Warp w takes the block rows c = w, w + 8, ... of T_j.
+// T_j is symmetric, so block row c is block column c transposed: the blocks
+// of H's column R_j[c] whose rows lie in R_j, listed by local block a in a
+// per-warp table (value offset, or -1 for a block dropped by the filter).
+// Rows x = start(c) + q are then written column by column: the lane of
+// column y reads element (y - start(a), q) of block (R_j[a], R_j[c]) straight
+// from H (a = the local block of y; consecutive y of a block are consecutive
+// in memory) for up to eight rows q at once, and the stores are coalesced.
+// Each row's absolute sum (Gershgorin bound b_j = max_x sum_y |T[x][y]|) and
+// the feature statistics are taken as the row is written, lane-strided over
+// y, then reduced over the warp (a fixed order).
 //
 // Learned bound (optional): features of A = T_j - mu I (all over G except f6,
 // f8): f0 ||A||_F/sqrt(n), f1 max|A_rr|, f2 mean|A_rr|, f3 std(A_rr), f4 max_r
 // R_r, f5 mean_r R_r (R_r = sum_{c != r} |A_rc|), f6 n/256, f7 mean A_rr, f8
 // the previous step's ratio; then the 9 -> 64 -> 64 -> 2 tanh network with the
 // parameters rounded to FP16, and b_j = G clamp(rho_hat/G, 0.02, 1) (1 + margin)/1.2.
+constexpr int kGatherRows = 8;  // rows of a block row written together
+
 template <class R>
 __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict__ subs, PatternView pv,
                                                       const R* __restrict__ H, double mu_d, R* __restrict__ T,
-                                                      double* __restrict__ bound, int ld_max, int nblk_max, int nw,
-                                                      int rg, GatherExtras ex) {
+                                                      double* __restrict__ bound, int nblk_max, int n_max,
+                                                      GatherExtras ex) {
     extern __shared__ __align__(16) unsigned char gsm[];
     __shared__ double warp_max_s[8];
     __shared__ float stat_s[8][7];  // per warp: F2, Da, Ds, Dq, Rs (sums), Dm, Rm (maxima)
@@ -178,100 +183,112 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
     const R mu = static_cast<R>(ex.mu_dev ? *ex.mu_dev : mu_d);
     const SubDesc s = subs[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int* rows = reinterpret_cast<int*>(gsm);  // R_j
-    int* ls = rows + nblk_max;                // local starts, nblk + 1 entries
-    const size_t head = (static_cast<size_t>(2 * nblk_max + 1) * sizeof(int) + 15) & ~size_t(15);
-    const size_t lists = (static_cast<size_t>(nblk_max) * (sizeof(int64_t) + sizeof(int)) + 15) & ~size_t(15);
-    const size_t per_warp = lists + rg * ((static_cast<size_t>(ld_max) * sizeof(R) + 15) & ~size_t(15));
-    unsigned char* wbase = gsm + head + warp * per_warp;
-    int64_t* vo_list = reinterpret_cast<int64_t*>(wbase);
-    int* a_list = reinterpret_cast<int*>(wbase + static_cast<size_t>(nblk_max) * sizeof(int64_t));
-    R* rowbuf = reinterpret_cast<R*>(wbase + lists);
+    int64_t* tab = reinterpret_cast<int64_t*>(gsm) + static_cast<size_t>(warp) * nblk_max;  // per warp
+    int* rows = reinterpret_cast<int*>(reinterpret_cast<int64_t*>(gsm) + static_cast<size_t>(8) * nblk_max);  // R_j
+    int* ls = rows + nblk_max;      // local starts, nblk + 1 entries
+    int* cblk = ls + nblk_max + 1;  // local block of each local column, n entries
     for (int a = tid; a < s.nblk; a += blockDim.x) {
         rows[a] = pv.frow_idx[s.fptr + a];
         ls[a] = pv.lstart[s.fptr + a];
     }
     if (tid == 0) ls[s.nblk] = s.n;
     __syncthreads();
+    for (int y = tid; y < s.n; y += blockDim.x) {
+        int lo = 0, hi = s.nblk - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (ls[mid] <= y) lo = mid; else hi = mid - 1;
+        }
+        cblk[y] = lo;
+    }
+    __syncthreads();
 
     R* t = T + s.t_off;
     double m = 0.0;
     float f2 = 0.f, da = 0.f, ds = 0.f, dq = 0.f, rs = 0.f, dm = 0.f, rm = 0.f;  // feature statistics
-    for (int c = warp; c < s.nblk && warp < nw; c += nw) {  // nw warps own a row buffer each
+    for (int c = warp; c < s.nblk; c += 8) {
         const int col = rows[c];
         const int bc = ls[c + 1] - ls[c];
+        // tab[a] = value offset of block (R_j[a], col), -1 when the filter dropped it
+        for (int a = lane; a < s.nblk; a += 32) tab[a] = -1;
+        __syncwarp();
         const int64_t k0 = pv.fcol_ptr[col], k1 = pv.fcol_ptr[col + 1];
-        // the blocks of column col inside R_j
-        int cnt = 0;
-        for (int64_t kb = k0; kb < k1; kb += 32) {
-            const int64_t k = kb + lane;
-            int a = -1;
-            if (k < k1) {
-                const int r = pv.frow_idx[k];
-                int lo = 0, hi = s.nblk - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (rows[mid] < r) lo = mid + 1; else hi = mid;
-                }
-                if (rows[lo] == r) a = lo;
+        for (int64_t k = k0 + lane; k < k1; k += 32) {
+            const int r = pv.frow_idx[k];
+            int lo = 0, hi = s.nblk - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (rows[mid] < r) lo = mid + 1; else hi = mid;
             }
-            const unsigned found = __ballot_sync(0xffffffffu, a >= 0);
-            if (a >= 0) {
-                const int pos = cnt + __popc(found & ((1u << lane) - 1u));
-                a_list[pos] = a;
-                vo_list[pos] = pv.fvoff[k];
-            }
-            cnt += __popc(found);
+            if (rows[lo] == r) tab[lo] = pv.fvoff[k];
         }
         __syncwarp();
-        // rows q0 .. q0 + rg - 1 of the block row together: the listed blocks' columns are
-        // loaded in one pass (a lane per block) into rg row buffers
-        for (int q0 = 0; q0 < bc; q0 += rg) {
-          const int nq = min(rg, bc - q0);
-          for (int y = lane; y < nq * s.ld; y += 32) rowbuf[y] = R(0);
-          __syncwarp();
-          for (int e = lane; e < cnt; e += 32) {  // a lane per listed block: columns q0.. of block (R_j[a], col)
-              const int a = a_list[e];
-              const int br = ls[a + 1] - ls[a];
-              const R* src = H + vo_list[e] + static_cast<int64_t>(q0) * br;
-              R* dst = rowbuf + ls[a];
-              for (int qq = 0; qq < nq; ++qq)
-                  for (int p = 0; p < br; ++p) {
-                      R v = src[qq * br + p];
-                      if (a == c && p == q0 + qq) v -= mu;
-                      dst[qq * s.ld + p] = v;
-                  }
-          }
-          __syncwarp();
-          for (int qq = 0; qq < nq; ++qq) {
-            const int q = q0 + qq;
-            const R* rowq = rowbuf + qq * s.ld;
-            R* trow = t + static_cast<int64_t>(ls[c] + q) * s.ld;
-            R acc = R(0);
-            float sq = 0.f;
+        for (int q0 = 0; q0 < bc; q0 += kGatherRows) {
+            const int nq = min(kGatherRows, bc - q0);
+            R acc[kGatherRows];
+            float sq[kGatherRows];
+            R dsel = R(0);  // this lane's diagonal entry of the group, if it holds one
+#pragma unroll
+            for (int qq = 0; qq < kGatherRows; ++qq) {
+                acc[qq] = R(0);
+                sq[qq] = 0.f;
+            }
+            const int dcol = ls[c] + q0;  // column of row q0's diagonal entry
             for (int y = lane; y < s.ld; y += 32) {
-                const R v = rowq[y];
-                trow[y] = v;
-                acc += fabs(v);
-                sq = fmaf(static_cast<float>(v), static_cast<float>(v), sq);
+                R v[kGatherRows];
+#pragma unroll
+                for (int qq = 0; qq < kGatherRows; ++qq) v[qq] = R(0);
+                if (y < s.n) {
+                    const int a = cblk[y];
+                    const int64_t vo = tab[a];
+                    if (vo >= 0) {
+                        const int br = ls[a + 1] - ls[a];
+                        const R* src = H + vo + (y - ls[a]) + static_cast<int64_t>(q0) * br;
+#pragma unroll
+                        for (int qq = 0; qq < kGatherRows; ++qq)
+                            if (qq < nq) v[qq] = src[static_cast<int64_t>(qq) * br];
+                    }
+                }
+                const int dq_ = y - dcol;  // row of the group whose diagonal is column y
+                if (dq_ >= 0 && dq_ < nq) {
+#pragma unroll
+                    for (int qq = 0; qq < kGatherRows; ++qq)
+                        if (qq == dq_) {
+                            v[qq] -= mu;
+                            dsel = v[qq];
+                        }
+                }
+#pragma unroll
+                for (int qq = 0; qq < kGatherRows; ++qq)
+                    if (qq < nq) {
+                        t[static_cast<int64_t>(dcol + qq) * s.ld + y] = v[qq];
+                        acc[qq] += fabs(v[qq]);
+                        sq[qq] = fmaf(static_cast<float>(v[qq]), static_cast<float>(v[qq]), sq[qq]);
+                    }
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            for (int qq = 0; qq < kGatherRows; ++qq) {
+                if (qq >= nq) break;
+                R a_ = acc[qq];
+                float s_ = sq[qq];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a_ += __shfl_xor_sync(0xffffffffu, a_, o);
+                    s_ += __shfl_xor_sync(0xffffffffu, s_, o);
+                }
+                const float d = static_cast<float>(__shfl_sync(0xffffffffu, dsel, (dcol + qq) & 31));
+                m = fmax(m, static_cast<double>(a_));
+                const float ad = fabsf(d), rr = static_cast<float>(a_) - ad;
+                f2 += s_;
+                da += ad;
+                ds += d;
+                dq = fmaf(d, d, dq);
+                rs += rr;
+                dm = fmaxf(dm, ad);
+                rm = fmaxf(rm, rr);
             }
-            m = fmax(m, static_cast<double>(acc));
-            const float d = static_cast<float>(rowq[ls[c] + q]), ad = fabsf(d), rr = static_cast<float>(acc) - ad;
-            f2 += sq;
-            da += ad;
-            ds += d;
-            dq = fmaf(d, d, dq);
-            rs += rr;
-            dm = fmaxf(dm, ad);
-            rm = fmaxf(rm, rr);
-          }
-          __syncwarp();
         }
+        __syncwarp();
     }
     if (lane == 0) {
         warp_max_s[warp] = m;
@@ -360,34 +377,29 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
 }
 
 template <class R>
-static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, int max_bs, const PatternView& pv,
+static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
                                  const R* H, double mu, R* T, double* bound, const GatherExtras& ex, cudaStream_t st) {
-    const size_t head = (static_cast<size_t>(2 * max_nblk + 1) * sizeof(int) + 15) & ~size_t(15);
-    const size_t lists = (static_cast<size_t>(max_nblk) * (sizeof(int64_t) + sizeof(int)) + 15) & ~size_t(15);
-    // rows per warp buffer: up to the largest block size, 8 warps within 200 KB of shared memory
-    const size_t row_bytes = (static_cast<size_t>(max_ld) * sizeof(R) + 15) & ~size_t(15);
-    const size_t budget = (200u << 10) / 8;
-    const int rg = static_cast<int>(std::max<size_t>(1, std::min<size_t>(static_cast<size_t>(max_bs),
-                                                                          budget > lists ? (budget - lists) / row_bytes : 1)));
-    const size_t per_warp = lists + rg * row_bytes;
-    const int nw = static_cast<int>(std::max<size_t>(1, std::min<size_t>(8, (200u << 10) / per_warp)));
-    const size_t smem = head + nw * per_warp;
-    cudaError_t e = cudaFuncSetAttribute(k_gather_bound<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    k_gather_bound<R><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound, max_ld, max_nblk, nw, rg, ex);
+    // per-warp block tables, R_j, local starts and the local block of every column
+    const size_t smem = static_cast<size_t>(8) * max_nblk * sizeof(int64_t) +
+                        (static_cast<size_t>(2 * max_nblk + 1) + static_cast<size_t>(max_n)) * sizeof(int);
+    if (smem > (48u << 10)) {
+        cudaError_t e = cudaFuncSetAttribute(k_gather_bound<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    k_gather_bound<R><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound, max_nblk, max_n, ex);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, int max_bs, const PatternView& pv,
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
                                 const double* H, double mu, double* T, double* bound, const GatherExtras& ex,
                                 cudaStream_t st) {
-    return launch_gather<double>(subs, n_subs, max_nblk, max_ld, max_bs, pv, H, mu, T, bound, ex, st);
+    return launch_gather<double>(subs, n_subs, max_nblk, max_n, pv, H, mu, T, bound, ex, st);
 }
 
-cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, int max_bs,
-                                    const PatternView& pv, const float* H32, double mu, float* T32, double* bound,
-                                    const GatherExtras& ex, cudaStream_t st) {
-    return launch_gather<float>(subs, n_subs, max_nblk, max_ld, max_bs, pv, H32, mu, T32, bound, ex, st);
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
+                                    const float* H32, double mu, float* T32, double* bound, const GatherExtras& ex,
+                                    cudaStream_t st) {
+    return launch_gather<float>(subs, n_subs, max_nblk, max_n, pv, H32, mu, T32, bound, ex, st);
 }
 
 // Deterministic sums of partial[0, n_cols) by one block (each thread adds a fixed

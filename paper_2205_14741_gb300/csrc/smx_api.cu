@@ -418,13 +418,12 @@ static smx_status ns_event_pair(smx_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
 // a3 + a4 for block columns [j0, j0 + m) into the staging buffer.
 static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const GatherExtras& ex) {
     const PatternView pv = pattern_view(c);
-    const int max_ld = static_cast<int>(round_up(c->max_n, 4));
     SubDesc* subs = dp<SubDesc>(c->d_subs);
     if (c->precision == SMX_FP64) {
-        SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, max_ld, c->bmax, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
+        SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, c->max_n, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
                                      dp<double>(c->d_bound) + j0, ex, c->stream));
     } else {
-        SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, max_ld, c->bmax, pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
+        SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, c->max_n, pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
                                          dp<double>(c->d_bound) + j0, ex, c->stream));
     }
     c->kernel_launches += 1;

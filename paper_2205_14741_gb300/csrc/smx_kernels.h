@@ -48,14 +48,14 @@ struct GatherExtras {
 // a3 + a4: T_j = H[R_j, R_j] - mu I into the FP64 staging buffer, then the
 // Gershgorin bound b_j = max row abs-sum of T_j (>= spectral radius), or the
 // learned bound (extras.params).
-cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, int max_bs, const PatternView& pv,
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
                                 const double* H, double mu, double* T, double* bound, const GatherExtras& ex,
                                 cudaStream_t st);
 // The same in FP32 (tensor-core path): T32 from the FP32 copy of H; the bound
 // is enlarged by 1e-5 relative to cover FP32 summation.
-cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_ld, int max_bs,
-                                    const PatternView& pv, const float* H32, double mu, float* T32, double* bound,
-                                    const GatherExtras& ex, cudaStream_t st);
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
+                                    const float* H32, double mu, float* T32, double* bound, const GatherExtras& ex,
+                                    cudaStream_t st);
 
 // a8 (FP64 form): deterministic sums of the per-column partials ->
 // sc->trace = trace(D), sc->energy = trace(D H).
