@@ -674,12 +674,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
                 tmem_wait_st();
             };
-            // drain: X'_t = alpha C (its padding is zero already) -> rows of buffer zo, or into the image
-            auto drain = [&](int t, uint32_t acc, float alpha, int zo, bool to_image, uint32_t hi_dst) {
+            // drain: X'_t = alpha C (its padding is zero already) into the image (hi at hi_dst)
+            auto drain = [&](int t, uint32_t acc, float alpha, uint32_t hi_dst) {
                 const int row = 128 * t + 32 * q + lane;
-                if (row - lane >= kpad) return;
-                uint16_t* out_hi = ws + static_cast<int64_t>(zo) * buf + static_cast<int64_t>(row) * a.ld;
-                uint16_t* out_lo = out_hi + buf;
+                if (row - lane >= kpad) return;  // the warp's rows are all padding (kpad is a multiple of 32)
 #pragma unroll 1
                 for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
                     uint32_t raw[32];
@@ -691,24 +689,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
-                    if (to_image) {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const uint32_t off = img_offset(row, c0 + 8 * u, RB);
-                            *reinterpret_cast<uint4*>(smem + hi_dst + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
-                            if constexpr (NB == 2)
-                                *reinterpret_cast<uint4*>(smem + lo_off + off) =
-                                    make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
-                        }
-                    } else {
-                        uint4* dh = reinterpret_cast<uint4*>(out_hi + c0);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) dh[u] = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
-                        if constexpr (NB == 2) {
-                            uint4* dlo = reinterpret_cast<uint4*>(out_lo + c0);
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) dlo[u] = make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
-                        }
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t off = img_offset(row, c0 + 8 * u, RB);
+                        *reinterpret_cast<uint4*>(smem + hi_dst + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                        if constexpr (NB == 2)
+                            *reinterpret_cast<uint4*>(smem + lo_off + off) =
+                                make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
                     }
                 }
             };
@@ -747,24 +734,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                         for (int u = 0; u < 4; ++u)
                             *reinterpret_cast<uint4*>(smem + lo_off + img_offset(row, c0 + 8 * u, RB)) =
                                 make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
-                    }
-                }
-            };
-            // ... or, after the last iteration, tile 0 of X' into the slot's X buffer zo
-            auto spill0 = [&](int zo, uint32_t hi_src) {
-                const int row = 32 * q + lane;
-                uint16_t* out_hi = ws + static_cast<int64_t>(zo) * buf + static_cast<int64_t>(row) * a.ld;
-                uint16_t* out_lo = out_hi + buf;
-#pragma unroll 1
-                for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
-                    uint32_t lw[16];
-                    if constexpr (NB == 2) tmem_ld16(L + lane_off + c0 / 2, lw);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        reinterpret_cast<uint4*>(out_hi + c0)[u] =
-                            *reinterpret_cast<const uint4*>(smem + hi_src + img_offset(row, c0 + 8 * u, RB));
-                        if constexpr (NB == 2)
-                            reinterpret_cast<uint4*>(out_lo + c0)[u] = make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
                     }
                 }
             };
@@ -844,7 +813,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 const uint32_t TA = tmem_base, TB = tmem_base + 160, TC = tmem_base + 320;
                 const uint32_t q0_reg = mtiles > 1 ? TC : TB;
                 for (int it = 0; it < a.max_iter; ++it) {
-                    const int zn = cur ? zx0 : zx1;
                     // A = Z - shift I and X' = alpha A X: shift = 3, alpha = -1/2 (Y = 3/2 I - 1/2 Z);
                     // at iteration 0 shift = 3/c^2, alpha = -c^3/2 (the a-posteriori scaling c)
                     float alpha = -0.5f, shift = 3.0f;
@@ -902,12 +870,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     else mma_wait();
                     __syncthreads();
                     if (*abortp) break;
-                    // into the image when the iteration continues, else to the slot's X buffer
+                    // into the image (the last X too: its owner columns are saved from there)
                     const bool last = conv_s || bad_s || it + 1 == a.max_iter;
-                    drain(0, q0_reg, alpha, zn, !last, hi_off);
-                    if (mtiles > 1) drain(1, TA, alpha, zn, !last, hi_off);
-                    if (last) fence_proxy_async_global();
-                    else fence_proxy_async_smem();
+                    drain(0, q0_reg, alpha, hi_off);
+                    if (mtiles > 1) drain(1, TA, alpha, hi_off);
+                    fence_proxy_async_smem();
                     tc_fence_before();
                     __syncthreads();
                     cur ^= 1;
@@ -919,7 +886,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 // image is double-buffered and tile 0's X' lo half waits in tensor memory (L)
                 const uint32_t P = tmem_base, Q = tmem_base + 192;
                 for (int it = 0; it < a.max_iter; ++it) {
-                    const int zn = cur ? zx0 : zx1;
                     float alpha = -0.5f, shift = 3.0f;
                     if (it == 0) {
                         // Z_t = X0_t X0 for both tiles, the bound, then tile 1 is multiplied again
@@ -975,17 +941,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     // tile 0 is in the next hi image and (lo) in tensor memory
                     const uint32_t hi_next = NB == 2 ? (hi_off == img_bytes ? 2 * img_bytes : img_bytes)
                                                      : (hi_off == 0 ? img_bytes : 0);
-                    if (last) {
-                        spill0(zn, hi_next);
-                        drain(1, Q, alpha, zn, false, hi_next);
-                        fence_proxy_async_global();
-                    } else {
-                        drain(1, Q, alpha, zn, true, hi_next);
-                        fill_lo0();
-                        fence_proxy_async_smem();
-                        hi_off = hi_next;
-                        img_hi = smem_base + hi_off;
-                    }
+                    drain(1, Q, alpha, hi_next);
+                    fill_lo0();
+                    fence_proxy_async_smem();
+                    hi_off = hi_next;
+                    img_hi = smem_base + hi_off;
                     tc_fence_before();
                     __syncthreads();
                     cur ^= 1;
@@ -1122,15 +1082,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         // save columns own .. own + b_j of the final X (the method keeps the
         // columns; the iterate is symmetric only up to rounding) for the scatter
         {
-            const uint16_t* fh = ws + static_cast<int64_t>(cur ? zx1 : zx0) * buf;
-            const uint16_t* fl = fh + buf;
             float* dst = a.xown + s.x_off;
-            for (int e = tid; e < s.n * s.bown; e += blockDim.x) {
-                const int q = e / s.n, i = e - q * s.n;
-                const int64_t o = static_cast<int64_t>(i) * a.ld + s.own + q;
-                float x = from16<PREC>(fh[o]);
-                if constexpr (NB == 2) x += from16<PREC>(fl[o]);
-                dst[e] = x;
+            if (resident) {  // the final X is the shared-memory image
+                for (int e = tid; e < s.n * s.bown; e += blockDim.x) {
+                    const int q = e / s.n, i = e - q * s.n;
+                    const uint32_t off = img_offset(i, s.own + q, RB);
+                    float x = from16<PREC>(*reinterpret_cast<const uint16_t*>(smem + hi_off + off));
+                    if constexpr (NB == 2) x += from16<PREC>(*reinterpret_cast<const uint16_t*>(smem + lo_off + off));
+                    dst[e] = x;
+                }
+            } else {
+                const uint16_t* fh = ws + static_cast<int64_t>(cur ? zx1 : zx0) * buf;
+                const uint16_t* fl = fh + buf;
+                for (int e = tid; e < s.n * s.bown; e += blockDim.x) {
+                    const int q = e / s.n, i = e - q * s.n;
+                    const int64_t o = static_cast<int64_t>(i) * a.ld + s.own + q;
+                    float x = from16<PREC>(fh[o]);
+                    if constexpr (NB == 2) x += from16<PREC>(fl[o]);
+                    dst[e] = x;
+                }
             }
         }
         __syncthreads();
