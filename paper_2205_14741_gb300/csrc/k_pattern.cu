@@ -172,7 +172,7 @@ cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, co
 constexpr int kGatherRows = 8;  // rows of a block row written together
 
 template <class R>
-__global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict__ subs, PatternView pv,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(const SubDesc* __restrict__ subs, PatternView pv,
                                                       const R* __restrict__ H, double mu_d, R* __restrict__ T,
                                                       double* __restrict__ bound, int nblk_max, int n_max,
                                                       GatherExtras ex) {
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
     int64_t* tab = reinterpret_cast<int64_t*>(gsm) + static_cast<size_t>(warp) * nblk_max;  // per warp
     int* rows = reinterpret_cast<int*>(reinterpret_cast<int64_t*>(gsm) + static_cast<size_t>(8) * nblk_max);  // R_j
     int* ls = rows + nblk_max;      // local starts, nblk + 1 entries
-    int* cblk = ls + nblk_max + 1;  // local block of each local column, n entries
+    int* cinfo = ls + nblk_max + 1;  // per local column y: local block a (bits 16-31), its size (8-15), y - start(a) (0-7)
     for (int a = tid; a < s.nblk; a += blockDim.x) {
         rows[a] = pv.frow_idx[s.fptr + a];
         ls[a] = pv.lstart[s.fptr + a];
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
             const int mid = (lo + hi + 1) >> 1;
             if (ls[mid] <= y) lo = mid; else hi = mid - 1;
         }
-        cblk[y] = lo;
+        cinfo[y] = (lo << 16) | ((ls[lo + 1] - ls[lo]) << 8) | (y - ls[lo]);
     }
     __syncthreads();
 
@@ -239,11 +239,11 @@ __global__ void __launch_bounds__(256) k_gather_bound(const SubDesc* __restrict_
 #pragma unroll
                 for (int qq = 0; qq < kGatherRows; ++qq) v[qq] = R(0);
                 if (y < s.n) {
-                    const int a = cblk[y];
-                    const int64_t vo = tab[a];
+                    const int ci = cinfo[y];
+                    const int64_t vo = tab[ci >> 16];
                     if (vo >= 0) {
-                        const int br = ls[a + 1] - ls[a];
-                        const R* src = H + vo + (y - ls[a]) + static_cast<int64_t>(q0) * br;
+                        const int br = (ci >> 8) & 0xff;
+                        const R* src = H + vo + (ci & 0xff) + static_cast<int64_t>(q0) * br;
 #pragma unroll
                         for (int qq = 0; qq < kGatherRows; ++qq)
                             if (qq < nq) v[qq] = src[static_cast<int64_t>(qq) * br];
