@@ -47,6 +47,9 @@ constexpr int kEpiWarps = 8;
 // (the A factor of Y X); only X' goes through L2.
 constexpr int kResKpad = 192;
 constexpr uint32_t kABytes = 128 * 128;  // 128 rows x 64 K x 2 B
+// On-chip prologue: T_j's rows pass through two staging buffers after the images (at most
+// 2 x 72 KB; the second hi image of the double-buffered form is free until iteration 0).
+constexpr uint32_t kStageOff = 144u * 1024u;
 
 template <int PREC>
 struct TcCfg {
@@ -61,6 +64,10 @@ struct TcCfg {
     static constexpr size_t kResSmem = static_cast<size_t>(kNb + 1) * 9 * 8192 + 8192;
     static constexpr size_t kDynSmem = 1024 + (static_cast<size_t>(kStages) * kStage > kResSmem
                                                    ? static_cast<size_t>(kStages) * kStage : kResSmem);
+    // each of the on-chip prologue's two staging buffers: what the allocation leaves after kStageOff
+    static constexpr uint32_t kStageBuf = static_cast<uint32_t>((kDynSmem - 1024 - kStageOff) / 2) & ~15u;
+    static_assert(kDynSmem - 1024 >= kStageOff + 2 * static_cast<size_t>(kStageBuf) && kStageBuf >= 16u * 1024u,
+                  "staging buffers inside the allocation");
 };
 
 // Shared-memory descriptor of a B tile in the MN-major 128-byte-swizzled
@@ -195,6 +202,14 @@ __device__ __forceinline__ uint64_t sdesc_mn_sw128_lbo(uint32_t saddr, uint32_t 
 __device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
+
+// 16-byte asynchronous copy global -> shared (no registers), its group commit and wait.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Orders this thread's generic shared-memory writes before later async-proxy
 // (tensor-core) reads issued after a barrier.
@@ -513,7 +528,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
 
         // prologue: X0 = (T_j - mu I) / b_j in FP32, zero-padded to kpad x kpad, split hi/lo,
         // into the shared-memory image (on-chip form) or the slot's X buffer
-        {
+        if (resident) {
+            // rows of T_j through two shared-memory buffers by asynchronous 16-byte copies: the
+            // copy of a batch of rows overlaps the split of the batch before
+            const float inv_b = static_cast<float>(1.0 / a.bound[j]);
+            const float* t = a.T + s.t_off;
+            const int row_chunks = s.ld / 4;  // 16-byte chunks per row of T_j
+            const int per = max(1, min(s.n, static_cast<int>(C::kStageBuf / (16u * row_chunks))));  // rows per batch
+            const int batches = (s.n + per - 1) / per;
+            auto issue = [&](int bi) {  // batch bi into buffer bi & 1 (every thread commits one group)
+                if (bi < batches) {
+                    const int r0 = bi * per, nr = min(per, s.n - r0);
+                    uint8_t* buf_s = smem + kStageOff + (bi & 1) * C::kStageBuf;
+                    const float* src = t + static_cast<int64_t>(r0) * s.ld;
+                    for (int c = tid; c < nr * row_chunks; c += kThreads) cp_async16(buf_s + 16 * c, src + 4 * c);
+                }
+                cp_async_commit();
+            };
+            issue(0);
+            issue(1);
+            const int per_row = kpad / 8;
+            for (int bi = 0; bi < batches; ++bi) {
+                cp_async_wait<1>();  // this thread's copies of batch bi are done (bi + 1 may be pending)
+                __syncthreads();     // ... and every thread's
+                const int r0 = bi * per, r1 = bi + 1 == batches ? kpad : min(s.n, r0 + per);  // the last batch pads to kpad
+                const float* buf_s = reinterpret_cast<const float*>(smem + kStageOff + (bi & 1) * C::kStageBuf);
+                for (int e = tid; e < (r1 - r0) * per_row; e += kThreads) {
+                    const int rr = e / per_row, c0 = (e - rr * per_row) * 8, r = r0 + rr;
+                    float x[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) x[i] = 0.0f;
+                    // rows of T are zero in [n, ld); rows n .. kpad - 1 of the image are zero
+                    if (r < s.n) {
+                        const float4* src = reinterpret_cast<const float4*>(buf_s + static_cast<int64_t>(rr) * s.ld + c0);
+                        if (c0 + 4 <= s.ld) {
+                            const float4 v = src[0];
+                            x[0] = v.x * inv_b; x[1] = v.y * inv_b; x[2] = v.z * inv_b; x[3] = v.w * inv_b;
+                        }
+                        if (c0 + 8 <= s.ld) {
+                            const float4 v = src[1];
+                            x[4] = v.x * inv_b; x[5] = v.y * inv_b; x[6] = v.z * inv_b; x[7] = v.w * inv_b;
+                        }
+                    }
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int i = 0; i < 8; i += 2) split2<PREC, NB>(x[i], x[i + 1], hw[i >> 1], lw[i >> 1]);
+                    const uint32_t off = img_offset(r, c0, RB);
+                    *reinterpret_cast<uint4*>(smem + hi_off + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    if constexpr (NB == 2)
+                        *reinterpret_cast<uint4*>(smem + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+                __syncthreads();  // buffer bi & 1 is free again
+                issue(bi + 2);
+            }
+            cp_async_wait<0>();
+            fence_proxy_async_smem();
+            if (tid == 0) { conv_s = 0; bad_s = 0; }
+            __syncthreads();
+        } else {
             const float inv_b = static_cast<float>(1.0 / a.bound[j]);
             const float* t = a.T + s.t_off;
             uint16_t* xh = ws + static_cast<int64_t>(zx0) * buf;
@@ -544,20 +616,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int i = 0; i < 8; i += 2) split2<PREC, NB>(x[i], x[i + 1], hw[i >> 1], lw[i >> 1]);
-                    if (resident) {
-                        const uint32_t off = img_offset(r, c0, RB);
-                        *reinterpret_cast<uint4*>(smem + hi_off + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        if constexpr (NB == 2)
-                            *reinterpret_cast<uint4*>(smem + lo_off + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                    } else {
-                        *reinterpret_cast<uint4*>(xh + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        if constexpr (NB == 2)
-                            *reinterpret_cast<uint4*>(xl + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                    }
+                    *reinterpret_cast<uint4*>(xh + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    if constexpr (NB == 2)
+                        *reinterpret_cast<uint4*>(xl + static_cast<int64_t>(r) * a.ld + c0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 }
             }
-            if (resident) fence_proxy_async_smem();
-            else fence_proxy_async_global();
+            fence_proxy_async_global();
             if (tid == 0) { conv_s = 0; bad_s = 0; }
             __syncthreads();
         }
