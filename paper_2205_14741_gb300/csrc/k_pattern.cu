@@ -14,92 +14,112 @@
 
 namespace smx {
 
-// a1 + the Gershgorin bracket of a9, one warp per block column j of the input
-// pattern, a lane per block: each block's Frobenius norm decides whether it is
-// kept (diagonal blocks always), its values are checked for finiteness and
-// copied to FP32; then, per column q of the block column, the absolute sums of
-// the kept blocks' columns are reduced over the lanes (H is symmetric: these
-// are the row sums), giving the column's Gershgorin interval
-// [min_q (d_q - r_q), max_q (d_q + r_q)] (d_q the diagonal entry, r_q the sum
-// without it).  With keep_prev the new flags are compared with the current
-// filtered pattern's.  The last block to finish takes the minimum and maximum
-// over the columns: the bracket of the whole filtered H and its midpoint.
-// Deterministic: every sum has a fixed order, minima and maxima are exact.
-__global__ void __launch_bounds__(256) k_filter_gershgorin(const double* __restrict__ H, const int64_t* __restrict__ col_ptr,
-                                                           const int32_t* __restrict__ row_idx,
-                                                           const int64_t* __restrict__ voff,
-                                                           const int32_t* __restrict__ bsize, int n_cols, double eps,
-                                                           uint8_t* __restrict__ keep, const uint8_t* __restrict__ keep_prev,
-                                                           float* __restrict__ H32, double* __restrict__ lohi, int bmax,
-                                                           DevScalars* sc) {
-    extern __shared__ double fg_smem[];  // per warp: column sums and diagonal entries, bmax each
+// a1 + the Gershgorin bracket of a9 in two passes.
+//
+// Pass 1, eight threads per block k of the input pattern (thread q takes the
+// block's columns q, q + 8, ...): the column's values are checked for
+// finiteness and copied to FP32, its sum of squares and of absolute values
+// taken; the block's Frobenius norm (squares summed over its columns in a
+// fixed tree) decides whether it is kept (diagonal blocks always), against
+// keep_prev when given.  The column absolute sums of a kept block (zero for a
+// dropped one) go to csum[k][q] (stride bmax), the diagonal block's diagonal
+// to diag[j][q].
+__global__ void __launch_bounds__(256) k_filter_blocks(const double* __restrict__ H, const int64_t* __restrict__ voff,
+                                                       const int32_t* __restrict__ row_idx,
+                                                       const int32_t* __restrict__ bcol,
+                                                       const int32_t* __restrict__ bsize, int64_t nnzb, int bmax,
+                                                       double eps, uint8_t* __restrict__ keep,
+                                                       const uint8_t* __restrict__ keep_prev, float* __restrict__ H32,
+                                                       double* __restrict__ csum, double* __restrict__ diag,
+                                                       DevScalars* sc) {
+    const int64_t k = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 3;
+    const int q0 = threadIdx.x & 7;
+    const bool on = k < nnzb;  // the 8-lane group is uniform
+    int j = 0, r = 0, br = 0, bc = 0;
+    if (on) {
+        j = bcol[k];
+        r = row_idx[k];
+        br = bsize[r];
+        bc = bsize[j];
+    }
+    double ss = 0.0;
+    bool finite = true;
+    for (int q = q0; q < bc; q += 8) {
+        const double* col = H + voff[k] + static_cast<int64_t>(q) * br;
+        float* col32 = H32 + voff[k] + static_cast<int64_t>(q) * br;
+        double cs = 0.0;
+        for (int p0 = 0; p0 < br; p0 += 8) {  // eight loads in flight, then their use
+            double v[8];
+#pragma unroll
+            for (int p = 0; p < 8; ++p) v[p] = p0 + p < br ? col[p0 + p] : 0.0;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                if (p0 + p >= br) break;
+                ss = fma(v[p], v[p], ss);
+                cs += fabs(v[p]);
+                finite = finite && isfinite(v[p]);
+                col32[p0 + p] = __double2float_rn(v[p]);
+            }
+        }
+        csum[k * bmax + q] = cs;  // masked below once the block's fate is known
+        if (r == j) diag[static_cast<int64_t>(j) * bmax + q] = col[q];
+    }
+    // the block's sum of squares over its eight lanes (a fixed tree)
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const bool kept = on && (r == j || !(sqrt(ss) < eps));
+    if (on) {
+        if (!kept)
+            for (int q = q0; q < bc; q += 8) csum[k * bmax + q] = 0.0;
+        if (q0 == 0) {
+            keep[k] = kept ? 1 : 0;
+            if (keep_prev && kept != (keep_prev[k] != 0)) atomicOr(&sc->changed, 1);
+        }
+        if (!finite) atomicCAS(&sc->status, kOk, kErrNonfinite);
+    }
+}
+
+// Pass 2, a warp per block column j: per column q the sum over the column's
+// blocks of csum (lane-strided, then a fixed tree), the Gershgorin interval
+// [min_q (d_q - r_q), max_q (d_q + r_q)] (H symmetric: column sums are row
+// sums; r_q without the diagonal entry d_q) into lohi; the last block takes the
+// minimum and maximum over the columns: the bracket of the filtered H and its
+// midpoint.
+__global__ void __launch_bounds__(256) k_filter_columns(const int64_t* __restrict__ col_ptr,
+                                                        const int32_t* __restrict__ bsize, int n_cols, int bmax,
+                                                        const double* __restrict__ csum, const double* __restrict__ diag,
+                                                        double* __restrict__ lohi, DevScalars* sc) {
     __shared__ double mm_s[2][8];
     __shared__ bool last_s;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (j < n_cols) {
-        double* colsum = fg_smem + static_cast<size_t>(warp) * 2 * bmax;
-        double* diag = colsum + bmax;
         const int bc = bsize[j];
-        for (int q = lane; q < bc; q += 32) colsum[q] = diag[q] = 0.0;
-        __syncwarp();
         const int64_t k0 = col_ptr[j], k1 = col_ptr[j + 1];
-        bool finite = true, differs = false;
-        for (int64_t kb = k0; kb < k1; kb += 32) {
-            const int64_t k = kb + lane;
-            int r = -1, br = 0;
-            bool kept = false;
-            const double* blk = nullptr;
-            if (k < k1) {
-                r = row_idx[k];
-                br = bsize[r];
-                blk = H + voff[k];
-                float* blk32 = H32 + voff[k];
-                const int sz = br * bc;
-                double ss = 0.0;
-                for (int e = 0; e < sz; ++e) {
-                    const double v = blk[e];
-                    ss = fma(v, v, ss);
-                    finite = finite && isfinite(v);
-                    blk32[e] = __double2float_rn(v);
-                }
-                kept = r == j || !(sqrt(ss) < eps);
-                keep[k] = kept ? 1 : 0;
-                if (keep_prev) differs = differs || (kept != (keep_prev[k] != 0));
-            }
-            for (int q = 0; q < bc; ++q) {
-                double cs = 0.0;
-                if (kept) {
-                    const double* col = blk + static_cast<int64_t>(q) * br;
-                    for (int p = 0; p < br; ++p) cs += fabs(col[p]);
-                    if (r == j) diag[q] = col[q];
-                }
-                cs = warp_sum(cs);
-                if (lane == 0) colsum[q] += cs;
-            }
-        }
-        __syncwarp();
         double lo = INFINITY, hi = -INFINITY;
-        for (int q = lane; q < bc; q += 32) {
-            const double d = diag[q], rad = colsum[q] - fabs(d);
-            lo = fmin(lo, d - rad);
-            hi = fmax(hi, d + rad);
-        }
-        finite = __all_sync(0xffffffffu, finite);
-        differs = __any_sync(0xffffffffu, differs);
+        for (int q0 = 0; q0 < bc; q0 += 8) {  // eight columns' loads in flight
+            double cs[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            for (int qq = 0; qq < 8; ++qq) cs[qq] = 0.0;
+            for (int64_t k = k0 + lane; k < k1; k += 32) {
+#pragma unroll
+                for (int qq = 0; qq < 8; ++qq)
+                    if (q0 + qq < bc) cs[qq] += csum[k * bmax + q0 + qq];
+            }
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq) {
+                if (q0 + qq >= bc) break;
+                const double c_ = warp_sum(cs[qq]);
+                const double d = diag[static_cast<int64_t>(j) * bmax + q0 + qq], rad = c_ - fabs(d);
+                lo = fmin(lo, d - rad);
+                hi = fmax(hi, d + rad);
+            }
         }
         if (lane == 0) {
             lohi[2 * j] = lo;
             lohi[2 * j + 1] = hi;
-            if (!finite) atomicCAS(&sc->status, kOk, kErrNonfinite);
-            if (differs) atomicOr(&sc->changed, 1);
         }
     }
-    // the last block: bracket of the filtered H over all columns
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last_s = atomicAdd(&sc->filter_done, 1u) == gridDim.x - 1;
@@ -122,12 +142,10 @@ __global__ void __launch_bounds__(256) k_filter_gershgorin(const double* __restr
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
+        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
             lo = fmin(lo, mm_s[0][w]);
             hi = fmax(hi, mm_s[1][w]);
         }
-        lo = fmin(lo, mm_s[0][0]);
-        hi = fmax(hi, mm_s[1][0]);
         sc->br_lo = lo;
         sc->br_hi = hi;
         sc->mu0 = 0.5 * (lo + hi);
@@ -135,19 +153,18 @@ __global__ void __launch_bounds__(256) k_filter_gershgorin(const double* __restr
     }
 }
 
-cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
-                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep,
-                                     const uint8_t* keep_prev, float* H32, double* lohi, DevScalars* sc,
-                                     cudaStream_t st) {
+cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int32_t* bcol,
+                                     const int64_t* voff, const int32_t* bsize, int n_cols, int64_t nnzb, int bmax,
+                                     double eps, uint8_t* keep, const uint8_t* keep_prev, float* H32, double* csum,
+                                     double* diag, double* lohi, DevScalars* sc, cudaStream_t st) {
     if (n_cols <= 0) return cudaSuccess;
-    const int grid = static_cast<int>((static_cast<int64_t>(n_cols) * 32 + 255) / 256);
-    const size_t smem = sizeof(double) * 2 * static_cast<size_t>(bmax) * 8;
-    if (smem > (48u << 10)) {
-        cudaError_t e = cudaFuncSetAttribute(k_filter_gershgorin, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-    }
-    k_filter_gershgorin<<<grid, 256, smem, st>>>(H, col_ptr, row_idx, voff, bsize, n_cols, eps, keep, keep_prev, H32, lohi,
-                                                 bmax, sc);
+    const int64_t g1 = (nnzb * 8 + 255) / 256;
+    k_filter_blocks<<<static_cast<unsigned>(g1), 256, 0, st>>>(H, voff, row_idx, bcol, bsize, nnzb, bmax, eps, keep, keep_prev,
+                                                               H32, csum, diag, sc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int g2 = static_cast<int>((static_cast<int64_t>(n_cols) * 32 + 255) / 256);
+    k_filter_columns<<<g2, 256, 0, st>>>(col_ptr, bsize, n_cols, bmax, csum, diag, lohi, sc);
     return cudaGetLastError();
 }
 

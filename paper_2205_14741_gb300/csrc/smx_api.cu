@@ -76,7 +76,7 @@ struct smx_ctx {
     int64_t t_elems = 0, x_elems = 0;
 
     // device buffers
-    DevBuf d_H, d_H32, d_voff, d_row_idx, d_col_ptr, d_bs, d_keep, d_keep_prev;
+    DevBuf d_H, d_H32, d_voff, d_row_idx, d_col_ptr, d_bs, d_keep, d_keep_prev, d_bcol, d_csum, d_diag;
     double br_lo = 0.0, br_hi = 0.0;  // Gershgorin bracket of the filtered H (from the last filter)
     bool filter_compared = false;     // the last filter launch compared its flags with the current pattern
     DevBuf d_sc;                      // DevScalars: status, flags, bracket, trace and energy
@@ -238,10 +238,12 @@ static smx_status fetch(smx_ctx* c) {
 static smx_status launch_filter(smx_ctx* c) {
     c->filter_compared = c->analysed && c->eps > 0.0;  // without a threshold every block is kept
     SMX_CUDA(launch_filter_gershgorin(dp<double>(c->d_H), dp<int64_t>(c->d_col_ptr), dp<int32_t>(c->d_row_idx),
-                                      dp<int64_t>(c->d_voff), dp<int32_t>(c->d_bs), c->B, c->bmax, c->eps,
-                                      dp<uint8_t>(c->d_keep), c->filter_compared ? dp<uint8_t>(c->d_keep_prev) : nullptr,
-                                      dp<float>(c->d_H32), dp<double>(c->d_lohi), scalars(c), c->stream));
-    c->kernel_launches += 1;
+                                      dp<int32_t>(c->d_bcol), dp<int64_t>(c->d_voff), dp<int32_t>(c->d_bs), c->B, c->nnzb,
+                                      c->bmax, c->eps, dp<uint8_t>(c->d_keep),
+                                      c->filter_compared ? dp<uint8_t>(c->d_keep_prev) : nullptr, dp<float>(c->d_H32),
+                                      dp<double>(c->d_csum), dp<double>(c->d_diag), dp<double>(c->d_lohi), scalars(c),
+                                      c->stream));
+    c->kernel_launches += 2;
     return SMX_OK;
 }
 
@@ -597,6 +599,9 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if ((s = upload(c->d_row_idx, c->row_idx, c->stream)) != SMX_OK) return fail(s);
     if ((s = upload(c->d_col_ptr, c->col_ptr, c->stream)) != SMX_OK) return fail(s);
     if ((s = upload(c->d_bs, c->bs, c->stream)) != SMX_OK) return fail(s);
+    if ((s = upload(c->d_bcol, c->bcol, c->stream)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_csum, sizeof(double) * std::max<int64_t>(1, c->nnzb) * c->bmax)) != SMX_OK) return fail(s);
+    if ((s = ensure(c->d_diag, sizeof(double) * static_cast<size_t>(n_block_cols) * c->bmax)) != SMX_OK) return fail(s);
     const size_t vb = static_cast<size_t>(c->n_values) * sizeof(double);
     if ((s = ensure(c->d_H, vb)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_H32, vb / 2)) != SMX_OK) return fail(s);
@@ -1129,7 +1134,7 @@ void smx_destroy(smx_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep_prev, &c->d_sc, &c->d_keep, &c->d_fcol_ptr,
+    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep_prev, &c->d_sc, &c->d_bcol, &c->d_csum, &c->d_diag, &c->d_keep, &c->d_fcol_ptr,
                       &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
                       &c->d_W2, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
                       &c->d_work_n3,

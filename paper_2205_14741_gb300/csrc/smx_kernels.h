@@ -23,16 +23,16 @@ struct DevScalars {
     int pad1[2];
 };
 
-// a1 + bracket: per block column j, keep flags of its blocks (Frobenius norm
-// >= eps, diagonal always), non-finite check (sc->status), FP32 copy of H and
-// the Gershgorin interval of the filtered column (lohi[2j], lohi[2j + 1]);
-// with keep_prev, sc->changed = 1 when a flag differs from it.  The last
-// block writes the bracket (min and max over the columns) and its midpoint
-// to sc->br_lo, br_hi, mu0.
-cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
-                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep,
-                                     const uint8_t* keep_prev, float* H32, double* lohi, DevScalars* sc,
-                                     cudaStream_t st);
+// a1 + bracket: keep flags of every block (Frobenius norm >= eps, diagonal
+// always), non-finite check (sc->status), FP32 copy of H and the Gershgorin
+// interval of every filtered column (lohi[2j], lohi[2j + 1]); with keep_prev,
+// sc->changed = 1 when a flag differs from it.  The bracket (min and max over
+// the columns) and its midpoint go to sc->br_lo, br_hi, mu0.  csum (nnzb x
+// bmax) and diag (n_cols x bmax) are scratch.
+cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int32_t* bcol,
+                                     const int64_t* voff, const int32_t* bsize, int n_cols, int64_t nnzb, int bmax,
+                                     double eps, uint8_t* keep, const uint8_t* keep_prev, float* H32, double* csum,
+                                     double* diag, double* lohi, DevScalars* sc, cudaStream_t st);
 
 // Optional outputs of the gather, per submatrix (pointers offset like subs; null = not wanted).
 struct GatherExtras {
