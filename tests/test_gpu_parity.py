@@ -304,3 +304,28 @@ def test_solve_mu_over_snapshots_with_changing_pattern(prec):
             assert abs(mu - mu_or) <= 1e-12
             assert abs(en - res.energy) <= TOL_E[prec] * abs(res.energy)
     assert len(set(nnz)) == len(nnz)  # the filtered pattern changed at every snapshot
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x3"])
+def test_stored_oracle_values(prec):
+    """The CUDA path against the oracle values stored in tests/golden (no oracle run here)."""
+    from tests.test_golden import load_golden
+
+    g = load_golden()
+    s = make_workload("water32")
+    with _ctx(s, prec) as c:
+        c.set_mu(0.0)
+        c.build_density()
+        d = c.get_density()
+        tr, en, _ = c.get_trace()
+        c.set_electron_count(96.0, max_steps=30, tol=0.5)
+        c.solve_mu()
+        tr_b, _, mu_b = c.get_trace()
+        steps = c.get_stats()["bisection_steps"]
+    for k, v in g["d"].items():
+        assert abs(d[k] - v) <= TOL_D[prec], (k, d[k], v)
+    assert abs(en - g["energy"]) <= TOL_E[prec] * abs(g["energy"])
+    assert abs(tr - g["trace"]) <= (1e-9 if prec == "fp64" else 1e-3)
+    # the bracket's sums are taken in another order on the device: mu agrees to rounding
+    assert abs(mu_b - g["bisect_mu"]) <= 1e-12 and steps == int(g["bisect_steps"])
+    assert abs(tr_b - g["bisect_trace"]) <= (1e-9 if prec == "fp64" else 1e-3)

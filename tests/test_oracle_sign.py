@@ -88,3 +88,21 @@ def test_gershgorin_hand_values_and_enclosure():
         assert lo <= lam[0] and lam[-1] <= hi
     lo, hi = O.gershgorin_bounds(np.diag([-2.0, 7.0]))
     assert (lo, hi) == (-2.0, 7.0)
+
+
+@pytest.mark.parametrize("n", [1, 4, 23])
+def test_block_sign_identity_eq12(n):
+    # Eq. 12: for a symmetric positive definite A, sign([[0, A], [I, 0]]) = [[0, A^1/2], [A^-1/2, 0]].
+    # The left side goes through the oracle's sign of a (non-symmetric) 2n x 2n matrix by the
+    # Newton iteration; the right side is built from A's eigendecomposition (a library routine).
+    rng = np.random.default_rng(77 + n)
+    g = rng.normal(size=(n, n))
+    a = g @ g.T + n * np.eye(n)
+    w, v = np.linalg.eigh(a)
+    root = (v * np.sqrt(w)) @ v.T
+    iroot = (v / np.sqrt(w)) @ v.T
+    m = np.block([[np.zeros((n, n)), a], [np.eye(n), np.zeros((n, n))]])
+    s = O.sign_newton(m)
+    ref = np.block([[np.zeros((n, n)), root], [iroot, np.zeros((n, n))]])
+    assert np.max(np.abs(s - ref)) <= 1e-10 * max(1.0, float(np.max(np.abs(ref))))
+    assert np.max(np.abs(root @ iroot - np.eye(n))) < 1e-12
