@@ -5,8 +5,8 @@ reference that the CUDA path is checked against. Only the test suite, the
 package's smoke check and the benchmark's CPU-baseline leg may import it; the
 product path never does, and shares no code with it.
 
-Parity status of each function is listed in ``oracle/submatrix.py`` and
-``oracle/mlp.py``; every function there is pinned by tests in
+Parity status of each function is listed in ``oracle/submatrix.py``,
+``oracle/functions.py`` and ``oracle/mlp.py``; every function there is pinned by tests in
 ``tests/test_oracle_*.py`` against closed forms, invariants, brute force or
 independent algorithms.
 """
@@ -26,3 +26,4 @@ from .submatrix import (  # noqa: F401
     dense_density,
     SubmatrixResult,
 )
+from .functions import FUNCTIONS, apply_eig, coupled_newton_schulz, function_submatrix  # noqa: F401

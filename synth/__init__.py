@@ -12,6 +12,7 @@ from .water import (  # noqa: F401
     make_workload,
     make_lattice_system,
     make_mixed_block_system,
+    make_overlap_system,
     make_slab_system,
     md_trajectory,
     keyed_normals,

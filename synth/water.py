@@ -229,6 +229,21 @@ def make_lattice_system(n_mol: int, b: int, r_c: float, ell: float, seed: int,
     return sysm
 
 
+def make_overlap_system(n_mol: int, b: int, r_c: float, ell: float, seed: int, spacing: float = 3.1,
+                        jitter: float = 0.3, sigma: float = 0.05, diag_spread: float = 0.05) -> BlockCSC:
+    """Overlap-like symmetric positive definite matrix with the lattice system's block pattern:
+    diagonal blocks I + diag_spread * (G + G^T)/2 (G standard normal), off-diagonal blocks
+    N(0, sigma) exp(-d/ell) as in the Hamiltonian stand-in.  With the defaults every Gershgorin
+    disc of the water-like patterns stays well right of zero (checked where it is used)."""
+    rng = np.random.default_rng(seed)
+    pos, box = lattice_positions(n_mol, spacing, jitter, rng)
+    g = rng.standard_normal((n_mol, b, b))
+    diag = np.eye(b)[None, :, :] + diag_spread * 0.5 * (g + g.transpose(0, 2, 1))
+    sysm = _assemble(pos, box, b, diag, seed, r_c, ell, sigma)
+    sysm.meta = dict(kind="overlap", n_mol=n_mol, b=b, r_c=r_c, ell=ell, seed=seed)
+    return sysm
+
+
 def make_slab_system(n_mol: int, b: int, r_c: float, ell: float, seed: int, box=(50.0, 50.0, 200.0),
                      width: float = 8.0, hard_core: float = 2.0, sigma: float = 0.1) -> BlockCSC:
     """Water/vacuum slab: bulk density 1/3.1^3 per cubic Angstrom ramping to zero across two interfaces."""
