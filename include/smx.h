@@ -80,6 +80,20 @@ typedef enum {
     SMX_BF16 = 3
 } smx_precision;
 
+/* Matrix function a build computes (Fig. 2 is generic in f).
+ *   SMX_FN_DENSITY  D = 1/2 (I - sign(H - mu I)) (Eq. 14 with S = I), the default;
+ *   SMX_FN_INV_SQRT (H - mu I)^(-1/2) and SMX_FN_SQRT (H - mu I)^(1/2) for a
+ *                   symmetric positive definite H - mu I (an overlap matrix with
+ *                   mu = 0, the step before the non-orthogonal form of Eq. 14):
+ *                   per block column the owner columns of f(T_j - mu I), by the
+ *                   sign iteration of the Eq. 12 block matrix [[0, A], [I, 0]]
+ *                   written per block (coupled Newton-Schulz). */
+typedef enum {
+    SMX_FN_DENSITY = 0,
+    SMX_FN_INV_SQRT = 1,
+    SMX_FN_SQRT = 2
+} smx_function;
+
 /* Statistics of the last build (or the last bisection step). */
 typedef struct {
     int32_t n_block_cols;       /* number of submatrices */
@@ -93,7 +107,8 @@ typedef struct {
     int32_t n_noconv;           /* submatrices that hit the iteration cap */
     int32_t n_bound_fallback;   /* submatrices whose learned bound failed the safe check */
     int32_t bisection_steps;    /* builds done by the last smx_solve_mu (a first step taken again counts twice) */
-    double flops_ns;            /* algorithmic flops of the last build: sum_j 4 n_j^3 iters_j */
+    double flops_ns;            /* algorithmic flops of the last build: sum_j 4 n_j^3 iters_j
+                                   (6 n_j^3 iters_j for the function forms: three products a step) */
     double ms_last_build;       /* device time of the last build (CUDA events), ms */
     double mu;                  /* mu of the last build */
     int32_t precision;          /* smx_precision of the bulk phase */
@@ -103,7 +118,8 @@ typedef struct {
     int64_t ns_launches;        /* launches of the Newton-Schulz kernel */
     double ns_ms_total;         /* their summed device time (CUDA events on the context stream), ms */
     double ns_work_n3;          /* sum over submatrices and launches of n_j^3 * iterations_j;
-                                   4 * ns_work_n3 is the algorithmic Newton-Schulz flop count */
+                                   4 * ns_work_n3 is the algorithmic Newton-Schulz flop count
+                                   (6 * for the function forms) */
 } smx_stats;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -166,6 +182,15 @@ smx_status smx_set_electron_count(smx_ctx* ctx, double n_e, int32_t max_steps, d
 /* Arithmetic of the Newton-Schulz iteration; fp64_final_iters (0..4) FP64
  * iterations follow the bulk phase when bulk != SMX_FP64.  Errors: SMX_ERR_ARG. */
 smx_status smx_set_precision(smx_ctx* ctx, smx_precision bulk, int32_t fp64_final_iters);
+
+/* The matrix function of the following builds.  The function forms run in
+ * FP64 only (a build in another precision returns SMX_ERR_UNSUPPORTED) and
+ * ignore the learned bound; their result is read with smx_get_density, and
+ * smx_get_trace reports its trace and its sum of products with H over the
+ * stored entries.  A submatrix that is not positive definite ends in
+ * SMX_ERR_NOCONV or SMX_ERR_NONFINITE.  smx_solve_mu needs SMX_FN_DENSITY
+ * (SMX_ERR_STATE otherwise).  Errors: SMX_ERR_ARG (unknown f). */
+smx_status smx_set_function(smx_ctx* ctx, smx_function f);
 
 /* Builds D at the current fixed mu (Fig. 2 steps (i)-(iii) and Eq. 14):
  * filter (if values or threshold changed), gather, spectral bound, scaling,

@@ -18,6 +18,9 @@ OK, ERR_ARG, ERR_PATTERN, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_NOCONV, ERR_NOBR
 # smx_precision
 FP64, FP16X3, FP16, BF16 = range(4)
 PRECISIONS = {"fp64": FP64, "fp16x3": FP16X3, "fp16": FP16, "bf16": BF16}
+# smx_function: matrix function of a build
+FN_DENSITY, FN_INV_SQRT, FN_SQRT = 0, 1, 2
+FUNCTIONS = {"density": FN_DENSITY, "inv_sqrt": FN_INV_SQRT, "sqrt": FN_SQRT}
 # learned spectral bound
 BOUND_MODEL_FEATURES = 9
 BOUND_MODEL_PARAMS = 4930
@@ -66,6 +69,7 @@ SIGNATURES = {
     "smx_set_mu": (C.c_int, [C.c_void_p, C.c_double]),
     "smx_set_electron_count": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_double]),
     "smx_set_precision": (C.c_int, [C.c_void_p, C.c_int, C.c_int32]),
+    "smx_set_function": (C.c_int, [C.c_void_p, C.c_int]),
     "smx_build_density": (C.c_int, [C.c_void_p]),
     "smx_solve_mu": (C.c_int, [C.c_void_p]),
     "smx_get_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -103,6 +103,48 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
 
     int done = 0;
     bool conv = false, bad = false;
+    if (a.function != kFnDensity) {
+        // f = A^-1/2 or A^1/2 for a symmetric positive definite A = T_j - mu I: the sign
+        // iteration of the Eq. 12 block matrix [[0, A/b], [I, 0]] written per block (the
+        // coupled Newton-Schulz iteration), Y <- Y T, Z <- T Z, T = 3/2 I - 1/2 Z Y, from
+        // Y = A/b (now in X, eigenvalues in (0, 1] with b >= rho(A)) and Z = I; Y -> (A/b)^1/2,
+        // Z -> (A/b)^-1/2.  The residual ||Z Y - I||_F comes with the first product; the
+        // stopping rule is the sign iteration's.
+        double* Yb = X;
+        double* Zb = Y;
+        double* Tb = Z;
+        double* Nb = a.W3 + s.t_off;
+        for (int r = threadIdx.x / 32; r < n; r += 8)
+            for (int c = threadIdx.x & 31; c < n; c += 32) Zb[static_cast<int64_t>(r) * ld + c] = r == c ? 1.0 : 0.0;
+        __syncthreads();
+        for (int it = 0; it < a.max_iter; ++it) {
+            double r2 = gemm_fp64(Zb, Yb, Tb, n, ld, 1, As, Bs);  // T = 3/2 I - 1/2 Z Y
+            r2 = block_sum(r2, scratch);
+            gemm_fp64(Yb, Tb, Nb, n, ld, 2, As, Bs);  // Y' = Y T
+            __syncthreads();
+            gemm_fp64(Tb, Zb, Yb, n, ld, 2, As, Bs);  // Z' = T Z into Y's buffer
+            __syncthreads();
+            double* old_z = Zb;
+            Zb = Yb;
+            Yb = Nb;
+            Nb = old_z;
+            done = it + 1;
+            if (!isfinite(r2)) { bad = true; break; }
+            if (it > 0 && sqrt(r2) <= a.tau) { conv = true; break; }
+        }
+        if (threadIdx.x == 0) {
+            a.iters[s.col] = done;
+            atomicAdd(a.work_n3, static_cast<unsigned long long>(n) * n * n * done);
+            if (bad) atomicCAS(a.status, kOk, kErrNonfinite);
+            else if (!conv) atomicCAS(a.status, kOk, kErrNoconv);
+        }
+        // A^-1/2 = Z / sqrt(b), A^1/2 = sqrt(b) Y (both symmetric: row own + q is column own + q)
+        const double* F = a.function == kFnInvSqrt ? Zb : Yb;
+        const double fs = a.function == kFnInvSqrt ? 1.0 / sqrt(a.bound[blockIdx.x]) : sqrt(a.bound[blockIdx.x]);
+        auto frow = [&](int q, int i) -> double { return fs * F[static_cast<int64_t>(s.own + q) * ld + i]; };
+        finish_column(s, a.pv, a.H, a.D, a.partial, frow, ls_smem, scratch, false);
+        return;
+    }
     for (int it = 0; it < a.max_iter; ++it) {
         double r2 = 1.0, oscale = 1.0;
         if (it == 0) {

@@ -64,6 +64,7 @@ struct smx_ctx {
     double n_e = 0.0, tol = 0.5;
     int max_steps = 30;
     int precision = SMX_FP64;
+    int function = SMX_FN_DENSITY;
     int fp64_final = 0;
 
     // filtered pattern + submatrices
@@ -82,7 +83,7 @@ struct smx_ctx {
     DevBuf d_sc;                      // DevScalars: status, flags, bracket, trace and energy
     DevScalars* h_sc = nullptr;       // pinned copy, filled by fetch()
     DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order;
-    DevBuf d_T, d_W1, d_W2, d_ws, d_D, d_xown;
+    DevBuf d_T, d_W1, d_W2, d_W3, d_ws, d_D, d_xown;
     DevBuf d_bound, d_iters, d_partial, d_lohi, d_work_n3;
     uint8_t* h_keep_pinned = nullptr;
 
@@ -435,15 +436,18 @@ static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const Gathe
 // mu_on_device: the gather reads mu from the device scalars (the midpoint the
 // filter just computed) instead of the argument.
 static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
+    if (c->function != SMX_FN_DENSITY && c->precision != SMX_FP64) return SMX_ERR_UNSUPPORTED;
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
     cudaStream_t st = c->stream;
     const int B = c->B;
     DevScalars* sc = scalars(c);
+    const bool model = c->model_on && c->function == SMX_FN_DENSITY;  // the function forms start from G_j
     SMX_CUDA(cudaEventRecord(c->ev0, st));
     const PatternView pv = pattern_view(c);
     if (c->precision == SMX_FP64) {
         SMX_TRY(ensure(c->d_W1, c->d_T.bytes));
         SMX_TRY(ensure(c->d_W2, c->d_T.bytes));
+        if (c->function != SMX_FN_DENSITY) SMX_TRY(ensure(c->d_W3, c->d_T.bytes));
     } else {
         SMX_TRY(prepare_tc_workspace(c));
         SMX_TRY(ensure(c->d_xown, static_cast<size_t>(c->x_elems) * sizeof(float)));
@@ -455,7 +459,7 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
         GatherExtras ex;
         ex.gersh = dp<double>(c->d_gersh) + j0;
         if (mu_on_device) ex.mu_dev = &sc->mu0;
-        if (c->model_on) {  // learned bound: features and prediction inside the gather (checked in the NS kernel)
+        if (model) {  // learned bound: features and prediction inside the gather (checked in the NS kernel)
             ex.prev_ratio = dp<float>(c->d_prev_ratio) + j0;
             ex.params = dp<float>(c->d_params);
             ex.margin = kModelMargin;
@@ -470,6 +474,8 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             a.T = dp<double>(c->d_T);
             a.W1 = dp<double>(c->d_W1);
             a.W2 = dp<double>(c->d_W2);
+            a.W3 = c->function != SMX_FN_DENSITY ? dp<double>(c->d_W3) : nullptr;
+            a.function = c->function;
             a.bound = dp<double>(c->d_bound) + j0;
             a.tau = tau_for(SMX_FP64);
             a.max_iter = 100;
@@ -477,7 +483,7 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             a.work_n3 = dp<unsigned long long>(c->d_work_n3);
             a.gersh = dp<double>(c->d_gersh) + j0;
             a.sq_ratio = dp<float>(c->d_sq_ratio) + j0;
-            a.use_model = c->model_on ? 1 : 0;
+            a.use_model = model ? 1 : 0;
             a.fallbacks = &sc->fallbacks;
             a.status = &sc->status;
             a.pv = pv;
@@ -504,7 +510,7 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             a.work_n3 = dp<unsigned long long>(c->d_work_n3);
             a.gersh = dp<double>(c->d_gersh);
             a.sq_ratio = dp<float>(c->d_sq_ratio);
-            a.use_model = c->model_on ? 1 : 0;
+            a.use_model = model ? 1 : 0;
             a.fallbacks = &sc->fallbacks;
             a.status = &sc->status;
             a.pv = pv;
@@ -722,6 +728,12 @@ smx_status smx_set_precision(smx_ctx* c, smx_precision bulk, int32_t fp64_final_
     return SMX_OK;
 }
 
+smx_status smx_set_function(smx_ctx* c, smx_function f) {
+    if (!c || (f != SMX_FN_DENSITY && f != SMX_FN_INV_SQRT && f != SMX_FN_SQRT)) return SMX_ERR_ARG;
+    c->function = f;
+    return SMX_OK;
+}
+
 smx_status smx_build_density(smx_ctx* c) {
     if (!c) return SMX_ERR_ARG;
     DeviceGuard g(c->device);
@@ -733,6 +745,7 @@ smx_status smx_build_density(smx_ctx* c) {
 smx_status smx_solve_mu(smx_ctx* c) {
     if (!c) return SMX_ERR_ARG;
     if (!c->have_ne || c->col_hi >= 0) return SMX_ERR_STATE;  // a shard's trace is partial
+    if (c->function != SMX_FN_DENSITY) return SMX_ERR_STATE;  // bisection on the density matrix only
     DeviceGuard g(c->device);
     if (c->n_e < 0.0 || c->n_e > static_cast<double>(c->N)) return SMX_ERR_NOBRACKET;
     SMX_TRY(reset_flags(c));
@@ -851,7 +864,8 @@ smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
         out->iters_max = std::max(out->iters_max, it[j]);
         dsum += n;
         isum += it[j];
-        flops += 4.0 * n * static_cast<double>(n) * n * it[j];
+        // two products per step for the sign iteration, three for the coupled one of the function forms
+        flops += (c->function == SMX_FN_DENSITY ? 4.0 : 6.0) * n * static_cast<double>(n) * n * it[j];
         if (it[j] >= 100) ++noconv;
     }
     out->dim_mean = dsum / (hi - lo);
@@ -1136,7 +1150,7 @@ void smx_destroy(smx_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep_prev, &c->d_sc, &c->d_bcol, &c->d_csum, &c->d_diag, &c->d_keep, &c->d_fcol_ptr,
                       &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
-                      &c->d_W2, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
+                      &c->d_W2, &c->d_W3, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
                       &c->d_work_n3,
                       &c->d_params, &c->d_mst, &c->d_vst, &c->d_partial_mlp, &c->d_feat, &c->d_pred, &c->d_labels,
                       &c->d_gersh, &c->d_prev_ratio, &c->d_sq_ratio, &c->d_loss, &c->d_sx, &c->d_st,

@@ -14,11 +14,13 @@ namespace smx {
 // partial[col] = (trace of the diagonal block of D, sum over column j of D .* H).
 //
 // xrow(q, i) must return X[own + q][i] as double.  All threads of the block
-// call this function; smem_ls must hold room for s.nblk + 1 ints.
+// call this function; smem_ls must hold room for s.nblk + 1 ints.  With
+// density = false the columns of X themselves are written (another matrix
+// function f on the same machinery: F[R_j, j] = f(T_j)[:, own ..]).
 template <class XRow>
 __device__ void finish_column(const SubDesc& s, const PatternView& pv, const double* __restrict__ H,
                               double* __restrict__ D, double2* __restrict__ partial, XRow xrow, int* smem_ls,
-                              double* red_scratch) {
+                              double* red_scratch, bool density = true) {
     for (int a = threadIdx.x; a < s.nblk; a += blockDim.x) smem_ls[a] = pv.lstart[s.fptr + a];
     if (threadIdx.x == 0) smem_ls[s.nblk] = s.n;
     __syncthreads();
@@ -38,7 +40,7 @@ __device__ void finish_column(const SubDesc& s, const PatternView& pv, const dou
         const int p = i - smem_ls[lo];
         const int64_t off = pv.fvoff[k] + static_cast<int64_t>(q) * br + p;
         const bool diag = (i == s.own + q);
-        const double d = 0.5 * ((diag ? 1.0 : 0.0) - xrow(q, i));
+        const double d = density ? 0.5 * ((diag ? 1.0 : 0.0) - xrow(q, i)) : xrow(q, i);
         D[off] = d;
         if (diag) tr += d;
         en += d * H[off];

@@ -62,12 +62,18 @@ cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nbl
 cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cudaStream_t st);
 
 // a5/a6 (FP64 plain form) + a7: Newton-Schulz in FP64, then scatter.
+// Matrix function of a build (values of smx_function): 0 = the density matrix
+// 1/2 (I - sign(A)), 1 = A^-1/2, 2 = A^1/2 (A = T_j - mu I symmetric positive definite).
+enum : int { kFnDensity = 0, kFnInvSqrt = 1, kFnSqrt = 2 };
+
 struct NsFp64Args {
     const SubDesc* subs;
     int n_subs;
     double* T;   // FP64 staging buffer (overwritten: X0 = T / b)
     double* W1;  // FP64 work buffers laid out like T
     double* W2;
+    double* W3;  // a third one for the function forms (coupled iteration), else unused
+    int function;  // kFnDensity, kFnInvSqrt or kFnSqrt
     double* bound;  // in: initial bound b_j; out: effective bound after the a-posteriori rescale
     double tau;
     int max_iter;
