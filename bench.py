@@ -33,6 +33,7 @@ WORKLOAD_TEXT = {
     "water4096x23": "4096 molecules, 23x23 blocks (N=94208), cutoff 7 A, decay 2 A, filter 1e-6, mu by bisection",
 }
 L2_FLUSH_BYTES = 256 << 20
+FP64_PEAK_TFLOPS = 1.2  # DFMA throughput measured on this machine's GB300 (register-resident FMA loop)
 METRIC = "density matrices/s (mu-solved), mixed precision vs FP64 plain at <=1e-5 error on D"
 
 
@@ -229,6 +230,64 @@ def learned_scaling(args, stream):
     }
 
 
+def function_leg(args, stream, flush, check):
+    """S^-1/2 of a 1024-molecule overlap-like matrix (6x6 blocks, cutoff 6 A) in FP64 through the
+    same filter / gather / Newton-Schulz / scatter path (the coupled form of Eq. 12).  Timed per
+    build with CUDA events, L2 flushed between builds; rate against the FP64 pipe; sampled columns
+    against the oracle's eigendecomposition when ``check``."""
+    import torch
+
+    from paper_2205_14741_gb300 import SubmatrixDensity
+    from synth import make_overlap_system
+
+    s = make_overlap_system(1024, 6, 6.0, 1.5, 41)
+    c = SubmatrixDensity.from_system(s, stream=stream.cuda_stream)
+    try:
+        c.set_precision("fp64")
+        c.set_function("inv_sqrt")
+        c.set_mu(0.0)
+        for _ in range(args.warmup):
+            c.build_density()
+        torch.cuda.synchronize()
+        c.reset_counters()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.function_steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            c.build_density()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        st = c.get_stats()
+        got = c.get_density()
+        dims, iters, _ = c.get_submatrix_info()
+    finally:
+        c.close()
+    tflops = 6.0 * st["ns_work_n3"] / (ms / 1e3) / 1e12  # work counter: sum over the timed builds
+    out = {"value": args.function_steps / (ms / 1e3), "unit": "S^-1/2 per s", "ms_per_build": ms / args.function_steps,
+           "workload": "1024 water-like molecules, overlap-like SPD matrix, 6x6 blocks (N=6144), cutoff 6 A, "
+                       "decay 1.5 A, no filtering, mu = 0",
+           "iters_mean": st["iters_mean"], "dims_mean": float(np.mean(dims)),
+           "tflops": tflops, "fp64_peak_tflops": FP64_PEAK_TFLOPS,
+           "frac_of_fp64_peak": tflops / FP64_PEAK_TFLOPS,
+           "note": "flops = sum over the timed builds of sum_j 6 n_j^3 iters_j (coupled iteration: three "
+                   "products of n_j x n_j) over their summed event time; "
+                   "FP64 peak = DFMA rate measured on this GB300 by a register-resident FMA loop"}
+    if check:
+        import oracle as O
+
+        rng = np.random.default_rng(0)
+        cols = sorted(set(np.argsort(dims)[-2:].tolist()) | set(rng.choice(s.n_blocks, 6, replace=False).tolist()))
+        res = O.function_submatrix(s.block_size, s.col_ptr, s.row_idx, s.values, "inv_sqrt", columns=cols)
+        off = O.block_value_offsets(s.block_size, s.col_ptr, s.row_idx)
+        err = max(float(np.max(np.abs(got[off[s.col_ptr[j]]:off[s.col_ptr[j + 1]]]
+                                      - res.values[off[s.col_ptr[j]]:off[s.col_ptr[j + 1]]]))) for j in cols)
+        out["max_abs_err_vs_oracle"] = err
+        out["checked_columns"] = len(cols)
+    return out
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -414,6 +473,11 @@ def run_ours(args):
                 "submatrix_tflops": 4.0 * st64["ns_work_n3"] / (ms64 / 1e3) / 1e12,
                 "max_abs_diff_vs_mixed": float(np.max(np.abs(d64 - d_gpu)))}
 
+    # -- a function form on the same machinery: A^-1/2 of an overlap matrix (FP64) --
+    funcs = None
+    if not args.no_functions:
+        funcs = function_leg(args, stream, flush, rank == 0 and not args.no_cpu)
+
     # -- accuracy and CPU baseline (rank 0, oracle on a bounded sample) ---------
     cpu = None
     acc = None
@@ -456,6 +520,7 @@ def run_ours(args):
                        "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
             "submatrix_tflops": submatrix_tflops,
             "fp64_plain": fp64,
+            "inv_sqrt_fp64": funcs,
             "speedup_mixed_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "accuracy": acc,
             "roofline": roofline,
@@ -489,6 +554,8 @@ def main():
     ap.add_argument("--ref-columns", type=int, default=128)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-functions", action="store_true", help="skip the A^-1/2 (FP64) leg")
+    ap.add_argument("--function-steps", type=int, default=3)
     ap.add_argument("--learned-snapshots", type=int, default=200,
                     help="trajectory length of the learned-bound report (0 skips it)")
     ap.add_argument("--learned-epochs", type=int, default=40)

@@ -6,7 +6,7 @@ package's smoke check and the benchmark's CPU-baseline leg may import it; the
 product path never does, and shares no code with it.
 
 Parity status of each function is listed in ``oracle/submatrix.py``,
-``oracle/functions.py`` and ``oracle/mlp.py``; every function there is pinned by tests in
+``oracle/functions.py``, ``oracle/nonorth.py`` and ``oracle/mlp.py``; every function there is pinned by tests in
 ``tests/test_oracle_*.py`` against closed forms, invariants, brute force or
 independent algorithms.
 """
@@ -27,3 +27,11 @@ from .submatrix import (  # noqa: F401
     SubmatrixResult,
 )
 from .functions import FUNCTIONS, apply_eig, coupled_newton_schulz, function_submatrix  # noqa: F401
+from .nonorth import (  # noqa: F401
+    sign_pencil,
+    density_pencil,
+    density_nonorth_submatrix,
+    nonorth_bracket,
+    bisect_mu_nonorth,
+    take_blocks,
+)

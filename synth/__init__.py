@@ -13,6 +13,7 @@ from .water import (  # noqa: F401
     make_lattice_system,
     make_mixed_block_system,
     make_overlap_system,
+    make_nonorth_pair,
     make_slab_system,
     md_trajectory,
     keyed_normals,

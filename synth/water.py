@@ -244,6 +244,28 @@ def make_overlap_system(n_mol: int, b: int, r_c: float, ell: float, seed: int, s
     return sysm
 
 
+def make_nonorth_pair(n_mol: int, b: int, r_c: float, ell: float, seed: int, spacing: float = 3.1,
+                      jitter: float = 0.3, sigma_h: float = 0.1, sigma_s: float = 0.05,
+                      diag_spread: float = 0.05):
+    """A Kohn-Sham-like H and an overlap-like S of one molecular geometry, in a non-orthogonal
+    basis: both on the block pattern of the pairs within r_c.  H as in the lattice system
+    (two bands of on-site energies, off-diagonal N(0, sigma_h) exp(-d/ell)); S with diagonal
+    blocks I + diag_spread (G + G^T)/2 and off-diagonal N(0, sigma_s) exp(-d/ell) from a
+    second key stream, so that S is not a multiple of H off the diagonal.  Returns (H, S)
+    as two BlockCSC with identical patterns."""
+    rng = np.random.default_rng(seed)
+    pos, box = lattice_positions(n_mol, spacing, jitter, rng)
+    diag_h = _diag_blocks(n_mol, b, rng)
+    g = rng.standard_normal((n_mol, b, b))
+    diag_s = np.eye(b)[None, :, :] + diag_spread * 0.5 * (g + g.transpose(0, 2, 1))
+    pairs = _pairs_within(pos, box, r_c)[:2] if np.isfinite(r_c) else np.triu_indices(n_mol, k=1)
+    h = _assemble(pos, box, b, diag_h, seed, r_c, ell, sigma_h, pairs=pairs)
+    s = _assemble(pos, box, b, diag_s, seed + 0x5A17, r_c, ell, sigma_s, pairs=pairs)
+    h.meta = dict(kind="nonorth_h", n_mol=n_mol, b=b, r_c=r_c, ell=ell, seed=seed)
+    s.meta = dict(kind="nonorth_s", n_mol=n_mol, b=b, r_c=r_c, ell=ell, seed=seed)
+    return h, s
+
+
 def make_slab_system(n_mol: int, b: int, r_c: float, ell: float, seed: int, box=(50.0, 50.0, 200.0),
                      width: float = 8.0, hard_core: float = 2.0, sigma: float = 0.1) -> BlockCSC:
     """Water/vacuum slab: bulk density 1/3.1^3 per cubic Angstrom ramping to zero across two interfaces."""
