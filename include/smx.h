@@ -192,6 +192,26 @@ smx_status smx_set_precision(smx_ctx* ctx, smx_precision bulk, int32_t fp64_fina
  * (SMX_ERR_STATE otherwise).  Errors: SMX_ERR_ARG (unknown f). */
 smx_status smx_set_function(smx_ctx* ctx, smx_function f);
 
+/* Non-orthogonal basis (Eq. 14 with an overlap S != I).  values: S on the
+ * block pattern given to smx_create, in the same layout as H (n_values
+ * doubles, host or device memory per on_device; copied, the caller keeps
+ * ownership); NULL returns the context to S = I.  The following builds
+ * compute, per block column j on the filtered pattern of H (S is taken on the
+ * same pattern), P_j = 1/2 (I - sign(A_S^-1 A_H - mu I)) A_S^-1 with
+ * A_H = H[R_j, R_j], A_S = S[R_j, R_j], as P_j = 1/2 L (I - sign(M - mu I)) L
+ * with L = A_S^-1/2 (coupled Newton-Schulz iteration, Eq. 12) and
+ * M = L A_H L, and write the owner columns P[R_j, j].  L and M are computed once
+ * per (H, S, filtered pattern) and kept (2 sum_j n_j ld_j doubles); each
+ * bisection step then runs the sign iteration on M - mu I.  smx_get_trace
+ * reports tr(P S) = sum_pq P_pq S_pq over the stored entries (the electron
+ * count that smx_solve_mu matches) and sum_pq P_pq H_pq; the bisection
+ * bracket is the union of the Gershgorin intervals of the M_j.  Supported for
+ * SMX_FN_DENSITY in SMX_FP64 on a single staging chunk (SMX_ERR_UNSUPPORTED
+ * from the build otherwise).  An S whose submatrices are not positive definite
+ * ends in SMX_ERR_NOCONV or SMX_ERR_NONFINITE.  Errors: SMX_ERR_ARG,
+ * SMX_ERR_NONFINITE (host values), SMX_ERR_OOM, SMX_ERR_CUDA. */
+smx_status smx_set_overlap(smx_ctx* ctx, const double* values, int32_t on_device);
+
 /* Builds D at the current fixed mu (Fig. 2 steps (i)-(iii) and Eq. 14):
  * filter (if values or threshold changed), gather, spectral bound, scaling,
  * Newton-Schulz, scatter, trace and energy.  Asynchronous on the context

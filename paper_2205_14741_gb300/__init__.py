@@ -125,6 +125,17 @@ class SubmatrixDensity:
         check(self._lib.smx_set_function(self._ctx, FUNCTIONS[f] if isinstance(f, str) else int(f)),
               "smx_set_function")
 
+    def set_overlap(self, values=None, on_device: bool = False):
+        """Overlap S on the input pattern (non-orthogonal form of Eq. 14; see smx_set_overlap);
+        None returns to S = I."""
+        if values is None:
+            check(self._lib.smx_set_overlap(self._ctx, None, 0), "smx_set_overlap")
+        elif on_device:
+            check(self._lib.smx_set_overlap(self._ctx, _ptr(values), 1), "smx_set_overlap")
+        else:
+            v = np.ascontiguousarray(values, dtype=np.float64)
+            check(self._lib.smx_set_overlap(self._ctx, _ptr(v), 0), "smx_set_overlap")
+
     # -- work ---------------------------------------------------------------
     def build_density(self):
         check(self._lib.smx_build_density(self._ctx), "smx_build_density")

@@ -84,6 +84,97 @@ __device__ double gemm_fp64(const double* __restrict__ A, const double* __restri
     return r2;
 }
 
+// The sign iteration of the Eq. 12 block matrix [[0, A], [I, 0]] written per block (the
+// coupled Newton-Schulz iteration): T = 3/2 I - 1/2 Z Y, Y <- Y T, Z <- T Z from Y = A (in Yb,
+// eigenvalues in (0, 1]) and Z = I (set here); Y -> A^1/2, Z -> A^-1/2.  The residual
+// ||Z Y - I||_F comes with the first product; the stopping rule is the sign iteration's.  On
+// return Yb and Zb point to the final iterates; the four n x n buffers rotate.  Returns the
+// number of steps.
+__device__ int coupled_ns(double*& Yb, double*& Zb, double*& Tb, double*& Nb, int n, int ld, int max_iter, double tau,
+                          double (*As)[kTile + 1], double (*Bs)[kTile + 1], double* scratch, bool& conv, bool& bad) {
+    for (int r = threadIdx.x / 32; r < n; r += 8)
+        for (int c = threadIdx.x & 31; c < n; c += 32) Zb[static_cast<int64_t>(r) * ld + c] = r == c ? 1.0 : 0.0;
+    __syncthreads();
+    int done = 0;
+    conv = bad = false;
+    for (int it = 0; it < max_iter; ++it) {
+        double r2 = gemm_fp64(Zb, Yb, Tb, n, ld, 1, As, Bs);  // T = 3/2 I - 1/2 Z Y
+        r2 = block_sum(r2, scratch);
+        gemm_fp64(Yb, Tb, Nb, n, ld, 2, As, Bs);  // Y' = Y T
+        __syncthreads();
+        gemm_fp64(Tb, Zb, Yb, n, ld, 2, As, Bs);  // Z' = T Z into Y's buffer
+        __syncthreads();
+        double* old_z = Zb;
+        Zb = Yb;
+        Yb = Nb;
+        Nb = old_z;
+        done = it + 1;
+        if (!isfinite(r2)) { bad = true; break; }
+        if (it > 0 && sqrt(r2) <= tau) { conv = true; break; }
+    }
+    return done;
+}
+
+// Gershgorin interval (lo, hi) of an n x n matrix held row by row.
+__device__ double2 gershgorin_interval(const double* M, int n, int ld, double* scratch) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int r = warp; r < n; r += 8) {
+        double acc = 0.0;
+        for (int c = lane; c < n; c += 32) acc += c == r ? 0.0 : fabs(M[static_cast<int64_t>(r) * ld + c]);
+        acc = warp_sum(acc);
+        const double d = M[static_cast<int64_t>(r) * ld + r];
+        lo = fmin(lo, d - acc);
+        hi = fmax(hi, d + acc);
+    }
+    lo = -warp_max(-lo);
+    hi = warp_max(hi);
+    if (lane == 0) {
+        scratch[warp] = lo;
+        scratch[8 + warp] = hi;
+    }
+    __syncthreads();
+    double2 out = make_double2(INFINITY, -INFINITY);
+    for (int w = 0; w < 8; ++w) {
+        out.x = fmin(out.x, scratch[w]);
+        out.y = fmax(out.y, scratch[8 + w]);
+    }
+    __syncthreads();
+    return out;
+}
+
+// C[i][q] = sum_k A[i][k] Bt[q][k] for i < n, q < m: a product with a thin right factor given
+// by its rows (Bt = the transposed factor, m rows of length n, leading dimension ldb), C with
+// leading dimension m.  mode 1 writes Bt[q][i] - C[i][q] instead; scale multiplies the result.
+// A warp per row i, eight columns q at a time.
+__device__ void thin_product(const double* __restrict__ A, int lda, const double* __restrict__ Bt, int ldb, int n, int m,
+                             double* __restrict__ C, int mode, double scale) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+    for (int i = warp; i < n; i += 8) {
+        const double* ai = A + static_cast<int64_t>(i) * lda;
+        for (int q0 = 0; q0 < m; q0 += 8) {
+            double acc[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc[t] = 0.0;
+            for (int k = lane; k < n; k += 32) {
+                const double x = ai[k];
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (q0 + t < m) acc[t] = fma(x, Bt[static_cast<int64_t>(q0 + t) * ldb + k], acc[t]);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const double v = warp_sum(acc[t]);
+                if (lane == 0 && q0 + t < m) {
+                    const double r = mode == 1 ? Bt[static_cast<int64_t>(q0 + t) * ldb + i] - v : v;
+                    C[static_cast<int64_t>(i) * m + q0 + t] = scale * r;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
@@ -96,6 +187,33 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
     double* X = a.T + s.t_off;
     double* Y = a.W1 + s.t_off;
     double* Z = a.W2 + s.t_off;
+    if (a.Mc) {
+        // non-orthogonal form: the sign iteration runs on M_j - mu I with M_j = L_j A_H L_j
+        // (L_j = A_S^-1/2, from the setup kernel); its Gershgorin bound starts the iteration
+        const double* M = a.Mc + s.t_off;
+        const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+        double rmax = 0.0;
+        for (int r = warp; r < n; r += 8) {
+            double acc = 0.0;
+            for (int c = lane; c < n; c += 32) {
+                const double v = M[static_cast<int64_t>(r) * ld + c] - (r == c ? a.mu : 0.0);
+                X[static_cast<int64_t>(r) * ld + c] = v;
+                acc += fabs(v);
+            }
+            rmax = fmax(rmax, warp_sum(acc));
+        }
+        rmax = warp_max(rmax);
+        if (lane == 0) scratch[warp] = rmax;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = 0.0;
+            for (int w = 0; w < 8; ++w) b = fmax(b, scratch[w]);
+            b = b > 0.0 ? b : 1.0;
+            a.bound[blockIdx.x] = b;
+            a.gersh[blockIdx.x] = b;
+        }
+        __syncthreads();
+    }
     const double inv_b = 1.0 / a.bound[blockIdx.x];
     for (int r = threadIdx.x / 32; r < n; r += 8)
         for (int c = threadIdx.x & 31; c < n; c += 32) X[static_cast<int64_t>(r) * ld + c] *= inv_b;
@@ -104,34 +222,12 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
     int done = 0;
     bool conv = false, bad = false;
     if (a.function != kFnDensity) {
-        // f = A^-1/2 or A^1/2 for a symmetric positive definite A = T_j - mu I: the sign
-        // iteration of the Eq. 12 block matrix [[0, A/b], [I, 0]] written per block (the
-        // coupled Newton-Schulz iteration), Y <- Y T, Z <- T Z, T = 3/2 I - 1/2 Z Y, from
-        // Y = A/b (now in X, eigenvalues in (0, 1] with b >= rho(A)) and Z = I; Y -> (A/b)^1/2,
-        // Z -> (A/b)^-1/2.  The residual ||Z Y - I||_F comes with the first product; the
-        // stopping rule is the sign iteration's.
+        // f = A^-1/2 or A^1/2 for a symmetric positive definite A = T_j - mu I (now A/b in X)
         double* Yb = X;
         double* Zb = Y;
         double* Tb = Z;
         double* Nb = a.W3 + s.t_off;
-        for (int r = threadIdx.x / 32; r < n; r += 8)
-            for (int c = threadIdx.x & 31; c < n; c += 32) Zb[static_cast<int64_t>(r) * ld + c] = r == c ? 1.0 : 0.0;
-        __syncthreads();
-        for (int it = 0; it < a.max_iter; ++it) {
-            double r2 = gemm_fp64(Zb, Yb, Tb, n, ld, 1, As, Bs);  // T = 3/2 I - 1/2 Z Y
-            r2 = block_sum(r2, scratch);
-            gemm_fp64(Yb, Tb, Nb, n, ld, 2, As, Bs);  // Y' = Y T
-            __syncthreads();
-            gemm_fp64(Tb, Zb, Yb, n, ld, 2, As, Bs);  // Z' = T Z into Y's buffer
-            __syncthreads();
-            double* old_z = Zb;
-            Zb = Yb;
-            Yb = Nb;
-            Nb = old_z;
-            done = it + 1;
-            if (!isfinite(r2)) { bad = true; break; }
-            if (it > 0 && sqrt(r2) <= a.tau) { conv = true; break; }
-        }
+        done = coupled_ns(Yb, Zb, Tb, Nb, n, ld, a.max_iter, a.tau, As, Bs, scratch, conv, bad);
         if (threadIdx.x == 0) {
             a.iters[s.col] = done;
             atomicAdd(a.work_n3, static_cast<unsigned long long>(n) * n * n * done);
@@ -238,13 +334,101 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
         else if (!conv) atomicCAS(a.status, kOk, kErrNoconv);
     }
     const double* Xf = X;
+    if (a.Mc) {
+        // P_j[:, own] = 1/2 L (I - X) L[:, own] = 1/2 L (W - X W), W = L[:, own] (rows own..
+        // of the symmetric L): Eq. 14 with sign(A_S^-1 A_H - mu I) = L sign(M - mu I) L^-1
+        // and A_S^-1 = L L.  Two thin products into the free buffers Y (U) and Z (P_own).
+        const double* L = a.Lc + s.t_off;
+        double* U = Y;
+        double* Pown = Z;
+        thin_product(Xf, ld, L + static_cast<int64_t>(s.own) * ld, ld, n, s.bown, U, 1, 1.0);
+        // second factor given by rows: U^T (bown x n) is U read with stride bown
+        const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+        for (int i = warp; i < n; i += 8) {
+            const double* li = L + static_cast<int64_t>(i) * ld;
+            for (int q0 = 0; q0 < s.bown; q0 += 8) {
+                double acc[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc[t] = 0.0;
+                for (int k = lane; k < n; k += 32) {
+                    const double x = li[k];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        if (q0 + t < s.bown) acc[t] = fma(x, U[static_cast<int64_t>(k) * s.bown + q0 + t], acc[t]);
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const double v = warp_sum(acc[t]);
+                    if (lane == 0 && q0 + t < s.bown) Pown[static_cast<int64_t>(i) * s.bown + q0 + t] = 0.5 * v;
+                }
+            }
+        }
+        __syncthreads();
+        auto prow = [&](int q, int i) -> double { return Pown[static_cast<int64_t>(i) * s.bown + q]; };
+        finish_column(s, a.pv, a.H, a.D, a.partial, prow, ls_smem, scratch, false, a.Sv);
+        return;
+    }
     auto xrow = [&](int q, int i) -> double { return Xf[static_cast<int64_t>(s.own + q) * ld + i]; };
     finish_column(s, a.pv, a.H, a.D, a.partial, xrow, ls_smem, scratch);
+}
+
+// Setup of the non-orthogonal form for one (H, S) pair, a CTA per submatrix: from A_S (in Lc)
+// and A_H (in Mc), both gathered without shift, L = A_S^-1/2 by the coupled iteration (into
+// Lc) and M = L A_H L, symmetrised (into Mc), and the Gershgorin interval of M.
+__global__ void __launch_bounds__(256) k_nonorth_setup(NonorthSetupArgs a) {
+    __shared__ double As[kKc][kTile + 1];
+    __shared__ double Bs[kKc][kTile + 1];
+    __shared__ double scratch[32];
+    const SubDesc s = a.subs[blockIdx.x];
+    const int n = s.n, ld = s.ld;
+    double* Lc = a.Lc + s.t_off;
+    double* Mc = a.Mc + s.t_off;
+    double* Yb = a.T + s.t_off;
+    double* Zb = a.W1 + s.t_off;
+    double* Tb = a.W2 + s.t_off;
+    double* Nb = a.W3 + s.t_off;
+    const double b = a.bound_s[blockIdx.x];
+    const double inv_b = b > 0.0 ? 1.0 / b : 0.0;
+    for (int r = threadIdx.x / 32; r < n; r += 8)
+        for (int c = threadIdx.x & 31; c < n; c += 32)
+            Yb[static_cast<int64_t>(r) * ld + c] = Lc[static_cast<int64_t>(r) * ld + c] * inv_b;
+    __syncthreads();
+    bool conv = false, bad = false;
+    const int done = coupled_ns(Yb, Zb, Tb, Nb, n, ld, a.max_iter, a.tau, As, Bs, scratch, conv, bad);
+    if (threadIdx.x == 0) {
+        a.iters[s.col] = done;
+        if (bad || !(b > 0.0)) atomicCAS(a.status, kOk, kErrNonfinite);
+        else if (!conv) atomicCAS(a.status, kOk, kErrNoconv);
+    }
+    const double ls = b > 0.0 ? 1.0 / sqrt(b) : 0.0;  // A_S^-1/2 = Z / sqrt(b)
+    for (int r = threadIdx.x / 32; r < n; r += 8)
+        for (int c = threadIdx.x & 31; c < n; c += 32)
+            Lc[static_cast<int64_t>(r) * ld + c] = ls * Zb[static_cast<int64_t>(r) * ld + c];
+    __syncthreads();
+    gemm_fp64(Mc, Lc, Tb, n, ld, 2, As, Bs);  // A_H L
+    __syncthreads();
+    gemm_fp64(Lc, Tb, Nb, n, ld, 2, As, Bs);  // L A_H L
+    __syncthreads();
+    for (int r = threadIdx.x / 32; r < n; r += 8)
+        for (int c = threadIdx.x & 31; c < n; c += 32)
+            Mc[static_cast<int64_t>(r) * ld + c] =
+                0.5 * (Nb[static_cast<int64_t>(r) * ld + c] + Nb[static_cast<int64_t>(c) * ld + r]);
+    __syncthreads();
+    const double2 g = gershgorin_interval(Mc, n, ld, scratch);
+    if (threadIdx.x == 0) {
+        a.lohi[2 * blockIdx.x] = g.x;
+        a.lohi[2 * blockIdx.x + 1] = g.y;
+    }
 }
 
 cudaError_t launch_ns_fp64(const NsFp64Args& a, int max_nblk, cudaStream_t st) {
     const size_t smem = sizeof(int) * (static_cast<size_t>(max_nblk) + 1);
     k_ns_fp64<<<a.n_subs, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nonorth_setup(const NonorthSetupArgs& a, cudaStream_t st) {
+    k_nonorth_setup<<<a.n_subs, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -110,6 +110,11 @@ struct smx_ctx {
     int32_t col_lo = 0, col_hi = -1;          // block columns this context builds (a shard); col_hi < 0: all
     int64_t t_chunk_max = 0;                  // elements of the largest chunk
 
+    // non-orthogonal form (Eq. 14 with an overlap S on the pattern of H)
+    bool have_S = false, nonorth_ready = false;
+    DevBuf d_S, d_Lc, d_Mc, d_nlohi, d_setup_iters;
+    double nbr_lo = 0.0, nbr_hi = 0.0;  // bracket: the Gershgorin intervals of all M_j
+
     // learned spectral bound
     bool model_ready = false, model_on = false, sq_valid = false;
     int adam_t = 0;
@@ -265,6 +270,7 @@ static smx_status after_filter(smx_ctx* c) {
 
 // a1 + a2, synchronous (clears the flags first).
 static smx_status analyse(smx_ctx* c) {
+    c->nonorth_ready = false;  // L_j and M_j follow the values of H and the filtered pattern
     SMX_TRY(reset_flags(c));
     SMX_TRY(launch_filter(c));
     SMX_TRY(fetch(c));
@@ -433,15 +439,76 @@ static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const Gathe
     return SMX_OK;
 }
 
+static smx_status read_status(smx_ctx* c);
+
+// Setup of the non-orthogonal form for the current (H, S) and filtered pattern:
+// A_S and A_H gathered without shift, L_j = A_S^-1/2 and M_j = L_j A_H L_j kept
+// for every block column, and the bisection bracket from the Gershgorin
+// intervals of the M_j.  Synchronous (reads the bracket back).
+static smx_status nonorth_setup(smx_ctx* c) {
+    if (c->chunk_start.size() != 2) return SMX_ERR_UNSUPPORTED;  // L_j and M_j of every column stay resident
+    cudaStream_t st = c->stream;
+    const size_t tb = static_cast<size_t>(c->t_elems) * sizeof(double);
+    SMX_TRY(ensure(c->d_W1, tb));
+    SMX_TRY(ensure(c->d_W2, tb));
+    SMX_TRY(ensure(c->d_W3, tb));
+    SMX_TRY(ensure(c->d_Lc, tb));
+    SMX_TRY(ensure(c->d_Mc, tb));
+    SMX_TRY(ensure(c->d_nlohi, sizeof(double) * 2 * c->B));
+    SMX_TRY(ensure(c->d_setup_iters, sizeof(int32_t) * c->B));
+    const int j0 = c->chunk_start[0], m = c->chunk_start[1] - j0;
+    const PatternView pv = pattern_view(c);
+    SubDesc* subs = dp<SubDesc>(c->d_subs) + j0;
+    GatherExtras ex;
+    SMX_CUDA(launch_gather_bound(subs, m, c->max_nblk, c->max_n, pv, dp<double>(c->d_S), 0.0, dp<double>(c->d_Lc),
+                                 dp<double>(c->d_bound) + j0, ex, st));
+    SMX_CUDA(launch_gather_bound(subs, m, c->max_nblk, c->max_n, pv, dp<double>(c->d_H), 0.0, dp<double>(c->d_Mc),
+                                 dp<double>(c->d_gersh) + j0, ex, st));
+    NonorthSetupArgs a;
+    a.subs = subs;
+    a.n_subs = m;
+    a.Lc = dp<double>(c->d_Lc);
+    a.Mc = dp<double>(c->d_Mc);
+    a.T = dp<double>(c->d_T);
+    a.W1 = dp<double>(c->d_W1);
+    a.W2 = dp<double>(c->d_W2);
+    a.W3 = dp<double>(c->d_W3);
+    a.bound_s = dp<double>(c->d_bound) + j0;
+    a.tau = tau_for(SMX_FP64);
+    a.max_iter = 100;
+    a.iters = dp<int32_t>(c->d_setup_iters);
+    a.lohi = dp<double>(c->d_nlohi);
+    a.status = &scalars(c)->status;
+    SMX_CUDA(launch_nonorth_setup(a, st));
+    c->kernel_launches += 3;
+    std::vector<double> lohi(2 * static_cast<size_t>(m));
+    SMX_CUDA(cudaMemcpyAsync(lohi.data(), c->d_nlohi.p, sizeof(double) * lohi.size(), cudaMemcpyDeviceToHost, st));
+    const smx_status ds = read_status(c);  // synchronises
+    if (ds != SMX_OK) return ds;
+    double lo = lohi[0], hi = lohi[1];
+    for (int j = 1; j < m; ++j) {
+        lo = std::min(lo, lohi[2 * j]);
+        hi = std::max(hi, lohi[2 * j + 1]);
+    }
+    if (!std::isfinite(lo) || !std::isfinite(hi)) return SMX_ERR_NONFINITE;
+    c->nbr_lo = lo;
+    c->nbr_hi = hi;
+    c->nonorth_ready = true;
+    return SMX_OK;
+}
+
 // mu_on_device: the gather reads mu from the device scalars (the midpoint the
 // filter just computed) instead of the argument.
 static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
     if (c->function != SMX_FN_DENSITY && c->precision != SMX_FP64) return SMX_ERR_UNSUPPORTED;
+    if (c->have_S && (c->function != SMX_FN_DENSITY || c->precision != SMX_FP64 || mu_on_device))
+        return SMX_ERR_UNSUPPORTED;  // the non-orthogonal form: density matrix, FP64
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
+    if (c->have_S && !c->nonorth_ready) SMX_TRY(nonorth_setup(c));
     cudaStream_t st = c->stream;
     const int B = c->B;
     DevScalars* sc = scalars(c);
-    const bool model = c->model_on && c->function == SMX_FN_DENSITY;  // the function forms start from G_j
+    const bool model = c->model_on && c->function == SMX_FN_DENSITY && !c->have_S;  // other forms start from G_j
     SMX_CUDA(cudaEventRecord(c->ev0, st));
     const PatternView pv = pattern_view(c);
     if (c->precision == SMX_FP64) {
@@ -464,7 +531,7 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             ex.params = dp<float>(c->d_params);
             ex.margin = kModelMargin;
         }
-        SMX_TRY(gather_chunk(c, j0, m, mu, ex));
+        if (!c->have_S) SMX_TRY(gather_chunk(c, j0, m, mu, ex));  // the non-orthogonal form starts from M_j
         cudaEvent_t ns0, ns1;
         SMX_TRY(ns_event_pair(c, &ns0, &ns1));
         if (c->precision == SMX_FP64) {
@@ -490,6 +557,12 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             a.H = dp<double>(c->d_H);
             a.D = dp<double>(c->d_D);
             a.partial = dp<double2>(c->d_partial);
+            if (c->have_S) {
+                a.Mc = dp<double>(c->d_Mc);
+                a.Lc = dp<double>(c->d_Lc);
+                a.Sv = dp<double>(c->d_S);
+                a.mu = mu;
+            }
             SMX_CUDA(cudaEventRecord(ns0, st));
             SMX_CUDA(launch_ns_fp64(a, c->max_nblk, st));
             SMX_CUDA(cudaEventRecord(ns1, st));
@@ -728,6 +801,27 @@ smx_status smx_set_precision(smx_ctx* c, smx_precision bulk, int32_t fp64_final_
     return SMX_OK;
 }
 
+smx_status smx_set_overlap(smx_ctx* c, const double* values, int32_t on_device) {
+    if (!c) return SMX_ERR_ARG;
+    DeviceGuard g(c->device);
+    c->nonorth_ready = false;
+    c->built = false;
+    if (!values) {
+        c->have_S = false;
+        release(c->d_Lc);
+        release(c->d_Mc);
+        return SMX_OK;
+    }
+    if (!on_device)
+        for (int64_t i = 0; i < c->n_values; ++i)
+            if (!std::isfinite(values[i])) return SMX_ERR_NONFINITE;
+    SMX_TRY(ensure(c->d_S, static_cast<size_t>(c->n_values) * sizeof(double)));
+    SMX_CUDA(cudaMemcpyAsync(c->d_S.p, values, static_cast<size_t>(c->n_values) * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    c->have_S = true;
+    return SMX_OK;
+}
+
 smx_status smx_set_function(smx_ctx* c, smx_function f) {
     if (!c || (f != SMX_FN_DENSITY && f != SMX_FN_INV_SQRT && f != SMX_FN_SQRT)) return SMX_ERR_ARG;
     c->function = f;
@@ -752,7 +846,7 @@ smx_status smx_solve_mu(smx_ctx* c) {
     c->bisection_steps = 0;
     double lo = 0.0, hi = 0.0;
     int step = 0;
-    if (c->analysed && c->dirty) {
+    if (c->analysed && c->dirty && !c->have_S) {
         // New values on a known pattern: the filter and the first bisection step (at the
         // midpoint the filter leaves on the device, on the current filtered pattern) go
         // out together and come back in one read.  If the filter changed the pattern,
@@ -780,6 +874,12 @@ smx_status smx_solve_mu(smx_ctx* c) {
         if (c->dirty || !c->analysed) SMX_TRY(analyse(c));  // the bracket comes with the filter
         lo = c->br_lo;
         hi = c->br_hi;
+        if (c->have_S) {  // the pencil's bracket comes with the setup
+            if (c->function != SMX_FN_DENSITY || c->precision != SMX_FP64) return SMX_ERR_UNSUPPORTED;
+            if (!c->nonorth_ready) SMX_TRY(nonorth_setup(c));
+            lo = c->nbr_lo;
+            hi = c->nbr_hi;
+        }
     }
     for (; step < c->max_steps; ++step) {
         const double mid = 0.5 * (lo + hi);
@@ -1154,7 +1254,8 @@ void smx_destroy(smx_ctx* c) {
                       &c->d_work_n3,
                       &c->d_params, &c->d_mst, &c->d_vst, &c->d_partial_mlp, &c->d_feat, &c->d_pred, &c->d_labels,
                       &c->d_gersh, &c->d_prev_ratio, &c->d_sq_ratio, &c->d_loss, &c->d_sx, &c->d_st,
-                      &c->d_fit_x, &c->d_fit_t, &c->d_grad};
+                      &c->d_fit_x, &c->d_fit_t, &c->d_grad, &c->d_S, &c->d_Lc, &c->d_Mc, &c->d_nlohi,
+                      &c->d_setup_iters};
     for (DevBuf* b : bufs) release(*b);
     for (auto& pr : c->ns_events) {
         cudaEventDestroy(pr.first);

@@ -16,11 +16,14 @@ namespace smx {
 // xrow(q, i) must return X[own + q][i] as double.  All threads of the block
 // call this function; smem_ls must hold room for s.nblk + 1 ints.  With
 // density = false the columns of X themselves are written (another matrix
-// function f on the same machinery: F[R_j, j] = f(T_j)[:, own ..]).
+// function f on the same machinery: F[R_j, j] = f(T_j)[:, own ..]).  With a
+// trace_weight W (laid out like H) the first partial is sum over the column of
+// D .* W instead of the diagonal's trace (tr(P S) of the non-orthogonal form).
 template <class XRow>
 __device__ void finish_column(const SubDesc& s, const PatternView& pv, const double* __restrict__ H,
                               double* __restrict__ D, double2* __restrict__ partial, XRow xrow, int* smem_ls,
-                              double* red_scratch, bool density = true) {
+                              double* red_scratch, bool density = true,
+                              const double* __restrict__ trace_weight = nullptr) {
     for (int a = threadIdx.x; a < s.nblk; a += blockDim.x) smem_ls[a] = pv.lstart[s.fptr + a];
     if (threadIdx.x == 0) smem_ls[s.nblk] = s.n;
     __syncthreads();
@@ -42,7 +45,8 @@ __device__ void finish_column(const SubDesc& s, const PatternView& pv, const dou
         const bool diag = (i == s.own + q);
         const double d = density ? 0.5 * ((diag ? 1.0 : 0.0) - xrow(q, i)) : xrow(q, i);
         D[off] = d;
-        if (diag) tr += d;
+        if (trace_weight) tr += d * trace_weight[off];
+        else if (diag) tr += d;
         en += d * H[off];
     }
     tr = block_sum(tr, red_scratch);

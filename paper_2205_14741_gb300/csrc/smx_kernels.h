@@ -79,7 +79,7 @@ struct NsFp64Args {
     int max_iter;
     int32_t* iters;
     unsigned long long* work_n3;  // += n_j^3 * iters_j per submatrix
-    const double* gersh;   // Gershgorin bound G_j of T_j - mu I
+    double* gersh;         // Gershgorin bound G_j of T_j - mu I (written here in the non-orthogonal form)
     float* sq_ratio;       // out: sqrt(max_r sum_c |(A^2)_rc|) / G_j, the Gershgorin bound of A^2 (next-step feature)
     int use_model;         // the initial bound came from the learned model: keep it when the check passes
     int* fallbacks;        // count of submatrices whose learned bound failed the check
@@ -88,8 +88,35 @@ struct NsFp64Args {
     const double* H;
     double* D;
     double2* partial;
+    // non-orthogonal form (Eq. 14 with S != I), all null otherwise: the iteration starts from
+    // M_j - mu I (T is not read; bound and gersh are written), the owner columns of
+    // P_j = 1/2 L_j (I - X) L_j are scattered, and the trace is sum P_pq S_pq
+    const double* Mc = nullptr;  // M_j = L_j A_H L_j, laid out like T
+    const double* Lc = nullptr;  // L_j = A_S^-1/2, laid out like T
+    const double* Sv = nullptr;  // S in the input value layout
+    double mu = 0.0;
 };
 cudaError_t launch_ns_fp64(const NsFp64Args& a, int max_nblk, cudaStream_t st);
+
+// Setup of the non-orthogonal form, once per (H, S): L_j = A_S^-1/2 (coupled iteration) and
+// M_j = L_j A_H L_j with its Gershgorin interval, a CTA per submatrix.
+struct NonorthSetupArgs {
+    const SubDesc* subs;
+    int n_subs;
+    double* Lc;             // in: A_S = S[R_j, R_j]; out: L_j
+    double* Mc;             // in: A_H = H[R_j, R_j]; out: M_j (symmetrised)
+    double* T;              // work buffers laid out like Lc
+    double* W1;
+    double* W2;
+    double* W3;
+    const double* bound_s;  // Gershgorin bound of A_S (>= its largest eigenvalue)
+    double tau;
+    int max_iter;
+    int32_t* iters;         // out: steps of the coupled iteration per block column
+    double* lohi;           // out: [2 * n_subs] Gershgorin interval of M_j
+    int* status;
+};
+cudaError_t launch_nonorth_setup(const NonorthSetupArgs& a, cudaStream_t st);
 
 // a5 (tcgen05 tensor cores) + a7.
 struct NsTcArgs {
