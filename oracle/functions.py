@@ -1,16 +1,17 @@
-"""Other matrix functions on the submatrix machinery (Fig. 2 is generic in f).
+"""Other matrix functions on the submatrix machinery (Fig. 2 is generic in f): A^-1/2, A^1/2, A^-1.
 
 TEST INFRASTRUCTURE ONLY: the reference the CUDA path's function forms are
 checked against.  Only tests, the smoke check and the benchmark's CPU-baseline
 leg use it.
 
 For a symmetric positive definite H (an overlap matrix, say) the submatrix
-method gives sparse approximations of H^(-1/2) and H^(1/2): for every block
+method gives sparse approximations of H^(-1/2), H^(1/2) and H^(-1): for every block
 column j the dense submatrix A_j = T_j - mu I (Fig. 2 step (i)), f(A_j) by
 eigendecomposition (step (ii)), and the columns of block j of f(A_j) into the
 result (step (iii)).  Section 3 obtains these functions from the sign function
-through Eq. 12, sign([[0, A], [I, 0]]) = [[0, A^1/2], [A^-1/2, 0]]; the GPU
-path iterates that identity, this oracle evaluates f on the eigenvalues.
+through Eq. 12, sign([[0, A], [I, 0]]) = [[0, A^1/2], [A^-1/2, 0]] (the inverse
+as the square of A^-1/2); the GPU path iterates that identity, this oracle
+evaluates f on the eigenvalues.
 
 Readings: f acts on T_j - mu I (mu = 0 for H itself); the result has exactly
 the filtered pattern of H; its "trace" is the sum of the diagonal entries of
@@ -19,8 +20,9 @@ the diagonal blocks and its "energy" the sum over stored entries F_pq H_pq
 
 Parity status: pinned by tests/test_oracle_functions.py (diagonal and
 block-diagonal inputs, a full pattern against the dense function computed
-from numpy's eigh, F A F = I on a full pattern, and an independent coupled
-Newton-Schulz iteration of Eq. 12 on small submatrices).
+from numpy's eigh, F A F = I and F A = I on a full pattern, the inverse
+against a library solve, and an independent coupled Newton-Schulz iteration
+of Eq. 12 on small submatrices).
 """
 
 from __future__ import annotations
@@ -29,7 +31,7 @@ import numpy as np
 
 from .submatrix import SubmatrixResult, _block, block_value_offsets, gather_submatrix, submatrix_rows
 
-FUNCTIONS = ("inv_sqrt", "sqrt")
+FUNCTIONS = ("inv_sqrt", "sqrt", "inv")
 
 
 def apply_eig(a: np.ndarray, f: str) -> np.ndarray:
@@ -37,7 +39,7 @@ def apply_eig(a: np.ndarray, f: str) -> np.ndarray:
     lam, v = np.linalg.eigh(a)
     if np.min(lam) <= 0.0:
         raise ValueError("the matrix is not positive definite")
-    g = lam ** -0.5 if f == "inv_sqrt" else np.sqrt(lam)
+    g = {"inv_sqrt": lam ** -0.5, "sqrt": np.sqrt(lam), "inv": 1.0 / lam}[f]
     return (v * g) @ v.T
 
 

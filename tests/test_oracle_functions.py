@@ -1,4 +1,4 @@
-"""Pins for the oracle's submatrix matrix functions (oracle/functions.py): A^-1/2 and A^1/2.
+"""Pins for the oracle's submatrix matrix functions (oracle/functions.py): A^-1/2, A^1/2, A^-1.
 
 Each check is independent of the oracle's eigendecomposition formula: a diagonal input
 (elementwise powers), the dense function of a full pattern from numpy's eigh of the whole
@@ -23,7 +23,10 @@ def test_overlap_generator_is_positive_definite():
     assert lo > 0.3 and np.allclose(a, a.T)
 
 
-@pytest.mark.parametrize("f", ["inv_sqrt", "sqrt"])
+POWER = {"inv_sqrt": -0.5, "sqrt": 0.5, "inv": -1.0}
+
+
+@pytest.mark.parametrize("f", ["inv_sqrt", "sqrt", "inv"])
 def test_diagonal_blocks_elementwise(f):
     # block-diagonal with diagonal blocks: f is the elementwise power
     s = make_lattice_system(8, 3, 0.0, 1.5, 9)  # cutoff 0: diagonal blocks only
@@ -33,7 +36,7 @@ def test_diagonal_blocks_elementwise(f):
         blk = np.diag(d[3 * j:3 * j + 3])
         vals[9 * j:9 * j + 9] = blk.T.reshape(-1)
     res = O.function_submatrix(s.block_size, s.col_ptr, s.row_idx, vals, f)
-    p = -0.5 if f == "inv_sqrt" else 0.5
+    p = POWER[f]
     ref = np.zeros_like(vals)
     for j in range(8):
         ref[9 * j:9 * j + 9] = np.diag(d[3 * j:3 * j + 3] ** p).T.reshape(-1)
@@ -41,17 +44,20 @@ def test_diagonal_blocks_elementwise(f):
     assert abs(res.trace - np.sum(d ** p)) < 1e-12
 
 
-@pytest.mark.parametrize("f", ["inv_sqrt", "sqrt"])
+@pytest.mark.parametrize("f", ["inv_sqrt", "sqrt", "inv"])
 def test_full_pattern_equals_dense_function(f):
     s = _system(np.inf)
     a = O.to_dense(s.block_size, s.col_ptr, s.row_idx, s.values)
     lam, v = np.linalg.eigh(a)
-    dense = (v * (lam ** (-0.5 if f == "inv_sqrt" else 0.5))) @ v.T
+    dense = (v * (lam ** POWER[f])) @ v.T
     res = O.function_submatrix(s.block_size, s.col_ptr, s.row_idx, s.values, f)
     got = O.to_dense(s.block_size, s.col_ptr, s.row_idx, res.values)
     assert np.max(np.abs(got - dense)) < 1e-12
     if f == "inv_sqrt":
         assert np.max(np.abs(got @ a @ got - np.eye(a.shape[0]))) < 1e-12
+    if f == "inv":
+        assert np.max(np.abs(got @ a - np.eye(a.shape[0]))) < 1e-12
+        assert np.max(np.abs(got - np.linalg.solve(a, np.eye(a.shape[0])))) < 1e-12
 
 
 def test_block_diagonal_is_exact():
