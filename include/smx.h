@@ -87,11 +87,14 @@ typedef enum {
  *                   mu = 0, the step before the non-orthogonal form of Eq. 14):
  *                   per block column the owner columns of f(T_j - mu I), by the
  *                   sign iteration of the Eq. 12 block matrix [[0, A], [I, 0]]
- *                   written per block (coupled Newton-Schulz). */
+ *                   written per block (coupled Newton-Schulz);
+ *   SMX_FN_INV      (H - mu I)^(-1) for the same inputs: the square of the
+ *                   iteration's (H - mu I)^(-1/2), owner columns only. */
 typedef enum {
     SMX_FN_DENSITY = 0,
     SMX_FN_INV_SQRT = 1,
-    SMX_FN_SQRT = 2
+    SMX_FN_SQRT = 2,
+    SMX_FN_INV = 3
 } smx_function;
 
 /* Statistics of the last build (or the last bisection step). */

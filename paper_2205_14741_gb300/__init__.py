@@ -15,7 +15,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (BF16, BOUND_MODEL_FEATURES, BOUND_MODEL_PARAMS, FN_DENSITY, FN_INV_SQRT, FN_SQRT,  # noqa: F401
+from ._lib import (BF16, BOUND_MODEL_FEATURES, BOUND_MODEL_PARAMS, FN_DENSITY, FN_INV, FN_INV_SQRT, FN_SQRT,  # noqa: F401
                    FP16, FP16X3, FP64, FUNCTIONS, PRECISIONS, SmxError, Stats, check)
 
 
@@ -120,7 +120,7 @@ class SubmatrixDensity:
         check(self._lib.smx_set_precision(self._ctx, p, int(fp64_final_iters)), "smx_set_precision")
 
     def set_function(self, f="density"):
-        """Matrix function of the following builds: "density" (default), "inv_sqrt" or "sqrt"
+        """Matrix function of the following builds: "density" (default), "inv_sqrt", "sqrt" or "inv"
         (FP64 form; see smx_set_function)."""
         check(self._lib.smx_set_function(self._ctx, FUNCTIONS[f] if isinstance(f, str) else int(f)),
               "smx_set_function")

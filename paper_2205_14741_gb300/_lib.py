@@ -19,8 +19,8 @@ OK, ERR_ARG, ERR_PATTERN, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_NOCONV, ERR_NOBR
 FP64, FP16X3, FP16, BF16 = range(4)
 PRECISIONS = {"fp64": FP64, "fp16x3": FP16X3, "fp16": FP16, "bf16": BF16}
 # smx_function: matrix function of a build
-FN_DENSITY, FN_INV_SQRT, FN_SQRT = 0, 1, 2
-FUNCTIONS = {"density": FN_DENSITY, "inv_sqrt": FN_INV_SQRT, "sqrt": FN_SQRT}
+FN_DENSITY, FN_INV_SQRT, FN_SQRT, FN_INV = 0, 1, 2, 3
+FUNCTIONS = {"density": FN_DENSITY, "inv_sqrt": FN_INV_SQRT, "sqrt": FN_SQRT, "inv": FN_INV}
 # learned spectral bound
 BOUND_MODEL_FEATURES = 9
 BOUND_MODEL_PARAMS = 4930

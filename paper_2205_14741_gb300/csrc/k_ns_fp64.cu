@@ -234,6 +234,16 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
             if (bad) atomicCAS(a.status, kOk, kErrNonfinite);
             else if (!conv) atomicCAS(a.status, kOk, kErrNoconv);
         }
+        if (a.function == kFnInv) {
+            // A^-1 = (A^-1/2)^2 = Z Z / b: its owner columns Z Z[:, own] / b (Z symmetric, so
+            // the thin factor is given by rows own ..), into the free buffer T
+            thin_product(Zb, ld, Zb + static_cast<int64_t>(s.own) * ld, ld, n, s.bown, Tb, 0,
+                         1.0 / a.bound[blockIdx.x]);
+            const double* U = Tb;
+            auto irow = [&](int q, int i) -> double { return U[static_cast<int64_t>(i) * s.bown + q]; };
+            finish_column(s, a.pv, a.H, a.D, a.partial, irow, ls_smem, scratch, false);
+            return;
+        }
         // A^-1/2 = Z / sqrt(b), A^1/2 = sqrt(b) Y (both symmetric: row own + q is column own + q)
         const double* F = a.function == kFnInvSqrt ? Zb : Yb;
         const double fs = a.function == kFnInvSqrt ? 1.0 / sqrt(a.bound[blockIdx.x]) : sqrt(a.bound[blockIdx.x]);

@@ -823,7 +823,7 @@ smx_status smx_set_overlap(smx_ctx* c, const double* values, int32_t on_device) 
 }
 
 smx_status smx_set_function(smx_ctx* c, smx_function f) {
-    if (!c || (f != SMX_FN_DENSITY && f != SMX_FN_INV_SQRT && f != SMX_FN_SQRT)) return SMX_ERR_ARG;
+    if (!c || (f != SMX_FN_DENSITY && f != SMX_FN_INV_SQRT && f != SMX_FN_SQRT && f != SMX_FN_INV)) return SMX_ERR_ARG;
     c->function = f;
     return SMX_OK;
 }

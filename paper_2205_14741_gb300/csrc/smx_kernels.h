@@ -64,7 +64,7 @@ cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cu
 // a5/a6 (FP64 plain form) + a7: Newton-Schulz in FP64, then scatter.
 // Matrix function of a build (values of smx_function): 0 = the density matrix
 // 1/2 (I - sign(A)), 1 = A^-1/2, 2 = A^1/2 (A = T_j - mu I symmetric positive definite).
-enum : int { kFnDensity = 0, kFnInvSqrt = 1, kFnSqrt = 2 };
+enum : int { kFnDensity = 0, kFnInvSqrt = 1, kFnSqrt = 2, kFnInv = 3 };
 
 struct NsFp64Args {
     const SubDesc* subs;

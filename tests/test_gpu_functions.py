@@ -1,4 +1,4 @@
-"""GPU parity of the function forms (FP64): per-submatrix A^-1/2 and A^1/2 of an overlap-like
+"""GPU parity of the function forms (FP64): per-submatrix A^-1/2, A^1/2 and A^-1 of an overlap-like
 symmetric positive definite matrix against oracle/functions.py (eigendecomposition), and the
 error paths.  Tolerance: the FP64 form's 1e-10 max-abs, as for the density matrix."""
 
@@ -29,7 +29,7 @@ def _ctx(sysm, f, prec="fp64"):
     return c
 
 
-@pytest.mark.parametrize("f", ["inv_sqrt", "sqrt"])
+@pytest.mark.parametrize("f", ["inv_sqrt", "sqrt", "inv"])
 def test_functions_match_oracle(f):
     s = make_overlap_system(64, 6, 5.0, 1.5, 31)
     with _ctx(s, f) as c:
