@@ -59,8 +59,9 @@ struct TcCfg {
     static constexpr int kStages = (PREC == 1) ? 2 : 4;    // smem ring depth
     static constexpr uint32_t kStage = kNb * (kABytes + kBBytes);
     static constexpr int kFmt = (PREC == 3) ? 1 : 0;       // 0 = FP16, 1 = BF16
-    // the streamed form's stages, or the on-chip form's images: for kpad = 192 two hi images
-    // and a lo image of 72 KB each plus 8 KB read past the end by the last row tile's MMAs
+    // the streamed form's stages, or the on-chip form's data: for kpad = 192 the hi and lo
+    // images (72 KB each), the corner operand Bz (hi and lo, 24 KB each) and 8 KB read past the
+    // lo image by the last row tile's MMAs, inside a reserve of three images plus 8 KB
     static constexpr size_t kResSmem = static_cast<size_t>(kNb + 1) * 9 * 8192 + 8192;
     static constexpr size_t kDynSmem = 1024 + (static_cast<size_t>(kStages) * kStage > kResSmem
                                                    ? static_cast<size_t>(kStages) * kStage : kResSmem);
@@ -521,10 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         const bool resident = kpad <= kResKpad;
         const int RB = (kpad + 63) >> 6;
         const uint32_t img_bytes = static_cast<uint32_t>(RB * RB) * 8192u;
-        // kpad in (160, 192]: the hi image is double-buffered (X' is written while X is read)
-        const bool dbl = resident && kpad > 160;
-        uint32_t hi_off = dbl ? (NB == 2 ? img_bytes : 0u) : 0u;  // current hi image
-        const uint32_t lo_off = dbl ? 0u : img_bytes;            // lo image (split form)
+        const uint32_t hi_off = 0u, lo_off = img_bytes;  // hi image, lo image (split form)
 
         // prologue: X0 = (T_j - mu I) / b_j in FP32, zero-padded to kpad x kpad, split hi/lo,
         // into the shared-memory image (on-chip form) or the slot's X buffer
@@ -629,41 +627,65 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         int cur = 0, done = 0;
         if (resident) {
             // ---------------------------------------------------------------
-            // On-chip form.  Per iteration and 128-row tile t:
-            //   Z_t <- X_t X          (A and B from the shared-memory image)
-            //   Z_t <- A-operand form of Z_t - shift I (hi, lo packed 16-bit, in place)
-            //   Q_t <- (Z_t - shift I) X   (A from tensor memory, B from the image)
-            //   X'_t = alpha Q_t      into the image once every product of the
+            // On-chip form.  Per iteration, for the 128-row tile 0:
+            //   Z_0 <- X_0 X          (A and B from the shared-memory image)
+            //   Z_0 <- A-operand form of Z_0 - shift I (hi, lo packed 16-bit, in place)
+            //   Q_0 <- (Z_0 - shift I) X   (A from tensor memory, B from the image)
+            //   X'_0 = alpha Q_0      into the image once every product of the
             //                         iteration has read it
+            // and for the rows past 128 (kpad > 128) only the corner [128 .., 128 ..] of
+            // each product, the rest being tile 0's columns transposed (see below).
             // Y X = X Y (Y is a polynomial in X).  Iteration 0 forms Z = X0^2 for
-            // every tile, bounds rho(Z), and continues with shift = 3/c^2 and
+            // every row, bounds rho(Z), and continues with shift = 3/c^2 and
             // alpha = -c^3/2; later iterations use shift = 3, alpha = -1/2.  All 12
             // warps share the tensor-memory passes: warp w serves lanes 32 (w mod 4)
             // and the 32-column chunks c0 = 32 (w / 4) + 96 k; each pass loads its
             // next chunk while the current one is converted.
             // ---------------------------------------------------------------
-            const bool onchip = kpad <= 160;
             const int mtiles = (kpad + 127) >> 7;
             const int ksteps = kpad >> 4;
             const uint32_t idesc = idesc_f16(128, kpad, C::kFmt) | idesc_b_mn;
-            const uint32_t smem_base = smem_u32(smem), img_lo = smem_base + lo_off;
-            uint32_t img_hi = smem_base + hi_off;  // moves with hi_off (double-buffered form)
-            const uint32_t L = tmem_base + 384;    // double-buffered form: lo of tile 0's X' (96 columns)
+            const uint32_t smem_base = smem_u32(smem), img_lo = smem_base + lo_off, img_hi = smem_base + hi_off;
+            // two row tiles (kpad in (128, 192]): tile 1 holds the wc = kpad - 128 last rows
+            const int wc = kpad - 128;
+            const uint32_t idesc_w = idesc_f16(128, wc > 0 ? wc : 32, C::kFmt) | idesc_b_mn;
+            const uint32_t idesc_128 = idesc_f16(128, 128, C::kFmt) | idesc_b_mn;
+            // Bz = (Z - shift I)[:, 128 ..] as an MN-major B operand (kpad K rows, one 64-column
+            // block; hi boxes, then lo boxes) after the images; iteration 0's row-sum scratch at
+            // 160 KB is used only before Bz is written
+            const uint32_t bz_off = static_cast<uint32_t>(NB) * img_bytes;
+            const uint32_t bz_hi = smem_base + bz_off, bz_lo = bz_hi + static_cast<uint32_t>(RB) * 8192u;
             float* rpart_s = reinterpret_cast<float*>(smem + 160 * 1024);  // [3][kResKpad], iteration 0 only
             float* rsum_s = rpart_s + 3 * kResKpad;
             float* rs2_s = rsum_s + kResKpad;
             const uint32_t lbo = static_cast<uint32_t>(RB) * 8192u;
             const int q = warp & 3, part = warp >> 2;
             const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
-            auto issue_xx = [&](int t, uint32_t d) {  // d <- X_t X
+            // d <- X_t X[:, col0 ..] (col0 a multiple of 64; N from idn)
+            auto issue_xx_cols = [&](int t, uint32_t d, int col0, uint32_t idn) {
+                const uint32_t cb = static_cast<uint32_t>(col0 >> 6) * lbo;
                 for (int kk = 0; kk < ksteps; ++kk) {
                     const uint32_t aoff = static_cast<uint32_t>(((kk >> 2) * RB + 2 * t) * 8192 + (kk & 3) * 32);
-                    const uint32_t boff = static_cast<uint32_t>((kk >> 2) * 8192 + (kk & 3) * 2048);
+                    const uint32_t boff = static_cast<uint32_t>((kk >> 2) * 8192 + (kk & 3) * 2048) + cb;
                     const uint64_t ah = sdesc_sw128(img_hi + aoff), bh = sdesc_mn_sw128_lbo(img_hi + boff, lbo);
-                    tc_mma_f16(d, ah, bh, idesc, kk ? 1u : 0u);
+                    tc_mma_f16(d, ah, bh, idn, kk ? 1u : 0u);
                     if constexpr (NB == 2) {
-                        tc_mma_f16(d, ah, sdesc_mn_sw128_lbo(img_lo + boff, lbo), idesc, 1u);
-                        tc_mma_f16(d, sdesc_sw128(img_lo + aoff), bh, idesc, 1u);
+                        tc_mma_f16(d, ah, sdesc_mn_sw128_lbo(img_lo + boff, lbo), idn, 1u);
+                        tc_mma_f16(d, sdesc_sw128(img_lo + aoff), bh, idn, 1u);
+                    }
+                }
+            };
+            auto issue_xx = [&](int t, uint32_t d) { issue_xx_cols(t, d, 0, idesc); };  // d <- X_t X
+            // d <- X_1 Bz: rows 128 .. of X (the image) times (Z - shift I)[:, 128 ..] (N = wc)
+            auto issue_cyx = [&](uint32_t d) {
+                for (int kk = 0; kk < ksteps; ++kk) {
+                    const uint32_t aoff = static_cast<uint32_t>(((kk >> 2) * RB + 2) * 8192 + (kk & 3) * 32);
+                    const uint32_t boff = static_cast<uint32_t>((kk >> 2) * 8192 + (kk & 3) * 2048);
+                    const uint64_t ah = sdesc_sw128(img_hi + aoff), bh = sdesc_mn_sw128_lbo(bz_hi + boff, lbo);
+                    tc_mma_f16(d, ah, bh, idesc_w, kk ? 1u : 0u);
+                    if constexpr (NB == 2) {
+                        tc_mma_f16(d, ah, sdesc_mn_sw128_lbo(bz_lo + boff, lbo), idesc_w, 1u);
+                        tc_mma_f16(d, sdesc_sw128(img_lo + aoff), bh, idesc_w, 1u);
                     }
                 }
             };
@@ -704,7 +726,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             // convert: accumulator at acc -> A = C - shift I in place, each 32-column chunk becoming
             // 16 columns of packed hi pairs and 16 of lo pairs; with resid, r2 += ||C - I||_F^2 over
             // the thread's entries (the n x n block; the padding contributes nothing)
-            auto convert = [&](int t, uint32_t acc, float shift, bool resid, float& r2) {
+            // to_bz (two-tile form, tile 0): the chunks at columns >= 128 also go to Bz (rows 0 .. 127),
+            // and their residual counts twice (Z is symmetric: the block below the diagonal block)
+            auto convert = [&](int t, uint32_t acc, float shift, bool resid, float& r2, bool to_bz = false) {
                 const int row0 = 128 * t + 32 * q;  // the warp's first row
                 if (row0 >= kpad) return;
                 const bool live = row0 + lane < s.n;
@@ -730,16 +754,65 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                             sq = fmaf(e, e, sq);
                         }
                     }
-                    if (resid) r2 += sq;
+                    const bool bz = to_bz && c0 >= 128;
+                    if (resid) r2 += bz ? 2.0f * sq : sq;
                     uint32_t w[32];
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], w[i >> 1], w[16 + (i >> 1)]);
                     tmem_st32(acc + lane_off + c0, w);
+                    if (bz) {
+                        const int row = row0 + lane;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const uint32_t off = bz_off + img_offset(row, c0 - 128 + 8 * u, RB);
+                            *reinterpret_cast<uint4*>(smem + off) = make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+                            if constexpr (NB == 2)
+                                *reinterpret_cast<uint4*>(smem + off + RB * 8192) =
+                                    make_uint4(w[16 + 4 * u], w[17 + 4 * u], w[18 + 4 * u], w[19 + 4 * u]);
+                        }
+                    }
                 }
                 tmem_wait_st();
             };
+            // the corner Z[128 .., 128 ..] (accumulator at acc, wc columns; lanes = rows - 128):
+            // (Z - shift I) into Bz rows 128 .. kpad - 1; residual once
+            auto convert_corner = [&](uint32_t acc, float shift, bool resid, float& r2) {
+                const int crow0 = 32 * q;  // the warp's first corner row
+                if (crow0 >= wc) return;
+                const int row = 128 + crow0 + lane;
+                const bool live = row < s.n;
+#pragma unroll 1
+                for (int c0 = 32 * part; c0 < wc; c0 += 96) {
+                    uint32_t raw[32];
+                    tmem_ld32_issue(acc + lane_off + c0, raw);
+                    tmem_wait_ld_regs(raw);
+                    float y[32], sq = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float v = __uint_as_float(raw[i]);
+                        const bool d = (c0 == crow0) && (i == lane) && live;
+                        const float e = d ? v - 1.0f : v;
+                        y[i] = d ? v - shift : v;
+                        sq = fmaf(e, e, sq);
+                    }
+                    if (resid) r2 += sq;
+                    uint32_t hw[16], lw[16];
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t off = bz_off + img_offset(row, c0 + 8 * u, RB);
+                        *reinterpret_cast<uint4*>(smem + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                        if constexpr (NB == 2)
+                            *reinterpret_cast<uint4*>(smem + off + RB * 8192) =
+                                make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
+                    }
+                }
+            };
             // drain: X'_t = alpha C (its padding is zero already) into the image (hi at hi_dst)
-            auto drain = [&](int t, uint32_t acc, float alpha, uint32_t hi_dst) {
+            // transpose (two-tile form, tile 0): the chunks at columns >= 128 are also written as
+            // rows 128 .. of the image (X' is symmetric), element by element
+            auto drain = [&](int t, uint32_t acc, float alpha, uint32_t hi_dst, bool transpose = false) {
                 const int row = 128 * t + 32 * q + lane;
                 if (row - lane >= kpad) return;  // the warp's rows are all padding (kpad is a multiple of 32)
 #pragma unroll 1
@@ -761,14 +834,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                             *reinterpret_cast<uint4*>(smem + lo_off + off) =
                                 make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
                     }
+                    if (transpose && c0 >= 128) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const uint32_t off = img_offset(c0 + i, row, RB);  // element (c0 + i, row)
+                            const int sh = (i & 1) * 16;                       // pairs hold the even column low
+                            *reinterpret_cast<uint16_t*>(smem + hi_dst + off) = static_cast<uint16_t>(hw[i >> 1] >> sh);
+                            if constexpr (NB == 2)
+                                *reinterpret_cast<uint16_t*>(smem + lo_off + off) = static_cast<uint16_t>(lw[i >> 1] >> sh);
+                        }
+                    }
                 }
             };
-            // Double-buffered form, tile 0 of X' while the image is still read: hi into the next
-            // hi image, lo (packed pairs, 16 columns per 32-column chunk) into tensor memory at L.
-            auto drain_split0 = [&](uint32_t acc, float alpha, uint32_t hi_dst) {
-                const int row = 32 * q + lane;
+            // the corner of X' = alpha C (accumulator at acc, wc columns) into rows and columns 128 ..
+            auto drain_corner = [&](uint32_t acc, float alpha) {
+                const int crow0 = 32 * q;
+                if (crow0 >= wc) return;
+                const int row = 128 + crow0 + lane;
 #pragma unroll 1
-                for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
+                for (int c0 = 32 * part; c0 < wc; c0 += 96) {
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + lane_off + c0, raw);
                     tmem_wait_ld_regs(raw);
@@ -779,36 +863,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        *reinterpret_cast<uint4*>(smem + hi_dst + img_offset(row, c0 + 8 * u, RB)) =
-                            make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
-                    if constexpr (NB == 2) tmem_st16(L + lane_off + c0 / 2, lw);
-                }
-                tmem_wait_st();
-            };
-            // ... then, once the image is free: the lo half from tensor memory into the lo image
-            auto fill_lo0 = [&]() {
-                if constexpr (NB == 2) {
-                    const int row = 32 * q + lane;
-#pragma unroll 1
-                    for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
-                        uint32_t lw[16];
-                        tmem_ld16(L + lane_off + c0 / 2, lw);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            *reinterpret_cast<uint4*>(smem + lo_off + img_offset(row, c0 + 8 * u, RB)) =
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t off = img_offset(row, 128 + c0 + 8 * u, RB);
+                        *reinterpret_cast<uint4*>(smem + hi_off + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                        if constexpr (NB == 2)
+                            *reinterpret_cast<uint4*>(smem + lo_off + off) =
                                 make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
                     }
                 }
             };
             // scan: rpart_s[part, row] = sum_c |C_rc| w_c over this thread's columns (w = 1 when null)
-            auto scan = [&](int t, uint32_t acc, const float* w) {
+            // (with acc_hi != 0 the columns >= 128 come from acc_hi instead: the two-tile form's tile 1)
+            auto scan = [&](int t, uint32_t acc, const float* w, uint32_t acc_hi = 0u) {
                 const int row = 128 * t + 32 * q + lane;
                 float sum = 0.0f;
 #pragma unroll 1
                 for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
                     uint32_t raw[32];
-                    tmem_ld32_issue(acc + lane_off + c0, raw);
+                    tmem_ld32_issue((acc_hi != 0u && c0 >= 128 ? acc_hi + (c0 - 128) : acc + c0) + lane_off, raw);
                     tmem_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
@@ -827,9 +899,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
 
             // it = 0: the bound on rho(Z) from the first products' row sums (tile 0 in z0, tile 1
             // in z1; after a barrier) and the a-posteriori scaling c = 1.2/s (every thread gets c)
-            auto start_scale = [&](uint32_t z0, uint32_t z1) -> float {
+            auto start_scale = [&](uint32_t z0, uint32_t z1, uint32_t z1_hi = 0u) -> float {
                 scan(0, z0, nullptr);
-                if (mtiles > 1) scan(1, z1, nullptr);
+                if (mtiles > 1) scan(1, z1, nullptr, z1_hi);
                 gather_parts(rsum_s);
                 float rmax = 0.0f;
                 for (int r = tid; r < s.n; r += kThreads) rmax = fmaxf(rmax, rsum_s[r]);
@@ -840,7 +912,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     for (int r = tid; r < s.n; r += kThreads) rsum_s[r] = fmaxf(rsum_s[r], 1e-12f * rmax);
                     __syncthreads();
                     scan(0, z0, rsum_s);
-                    if (mtiles > 1) scan(1, z1, rsum_s);
+                    if (mtiles > 1) scan(1, z1, rsum_s, z1_hi);
                     gather_parts(rs2_s);
                     float qm = 0.0f;
                     for (int r = tid; r < s.n; r += kThreads) qm = fmaxf(qm, rs2_s[r] / rsum_s[r]);
@@ -867,15 +939,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 else if (sqrt(rr) <= a.tau) conv_s = 1;
             };
 
-            if (onchip) {
-                // kpad <= 160: three tensor-memory regions TA, TB, TC.  Per iteration
-                //   Z_0 -> TA and Z_1 -> TB back to back, each on its own barrier;
-                //   TA -> A operand of tile 0 while Z_1 is multiplied; Q_0 = A_0 X -> TC;
-                //   TB -> A operand of tile 1 while Q_0 is multiplied; Q_1 = A_1 X -> TA
-                //   (free once Q_0 is done); X' = alpha Q of both tiles into the image.
-                // With a single tile: Z_0 -> TA, Q_0 -> TB.
-                const uint32_t TA = tmem_base, TB = tmem_base + 160, TC = tmem_base + 320;
-                const uint32_t q0_reg = mtiles > 1 ? TC : TB;
+            if (mtiles == 1) {
+                // kpad <= 128, one row tile.  Per iteration: Z -> TA; TA -> A operand of
+                // Z - shift I; Q = A X -> TB; X' = alpha Q into the image.
+                const uint32_t TA = tmem_base, TB = tmem_base + 160;
                 for (int it = 0; it < a.max_iter; ++it) {
                     // A = Z - shift I and X' = alpha A X: shift = 3, alpha = -1/2 (Y = 3/2 I - 1/2 Z);
                     // at iteration 0 shift = 3/c^2, alpha = -c^3/2 (the a-posteriori scaling c)
@@ -884,17 +951,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                         tc_fence_after();
                         issue_xx(0, TA);
                         tc_commit(&mma_bar);
-                        if (mtiles > 1) {
-                            issue_xx(1, TB);
-                            tc_commit(&mma_bar2);
-                        }
                     }
-                    mma_wait();  // Z_0
+                    mma_wait();  // Z
                     if (it == 0) {
-                        if (mtiles > 1) mma_wait2();  // Z_1
                         __syncthreads();
                         if (*abortp) break;
-                        const float c = start_scale(TA, TB);
+                        const float c = start_scale(TA, 0u);
                         shift = 3.0f / (c * c);
                         alpha = -0.5f * c * c * c;
                     }
@@ -903,41 +965,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     if (*abortp) break;
                     float r2 = 0.0f;
                     convert(0, TA, shift, it > 0, r2);
-                    if (mtiles == 1) {
-                        r2 = warp_sum_f(r2);
-                        if (lane == 0) resid_s2[warp] = r2;
-                    }
+                    r2 = warp_sum_f(r2);
+                    if (lane == 0) resid_s2[warp] = r2;
                     tc_fence_before();
                     __syncthreads();
                     if (warp == 1 && lane == 0) {
                         tc_fence_after();
-                        issue_yx(TA, q0_reg);
+                        issue_yx(TA, TB);
                         tc_commit(&mma_bar);
                     }
-                    if (mtiles > 1) {
-                        if (it > 0) mma_wait2();  // Z_1, multiplied while tile 0 was converted
-                        convert(1, TB, shift, it > 0, r2);
-                        r2 = warp_sum_f(r2);
-                        if (lane == 0) resid_s2[warp] = r2;
-                        tc_fence_before();
-                        mma_wait();  // Q_0: TA is free
-                        __syncthreads();
-                        if (*abortp) break;
-                        if (warp == 1 && lane == 0) {
-                            tc_fence_after();
-                            issue_yx(TB, TA);
-                            tc_commit(&mma_bar2);
-                        }
-                    }
                     if (tid == 0 && it > 0) decide();
-                    if (mtiles > 1) mma_wait2();  // the last second product
-                    else mma_wait();
+                    mma_wait();
                     __syncthreads();
                     if (*abortp) break;
                     // into the image (the last X too: its owner columns are saved from there)
                     const bool last = conv_s || bad_s || it + 1 == a.max_iter;
-                    drain(0, q0_reg, alpha, hi_off);
-                    if (mtiles > 1) drain(1, TA, alpha, hi_off);
+                    drain(0, TB, alpha, hi_off);
                     fence_proxy_async_smem();
                     tc_fence_before();
                     __syncthreads();
@@ -946,70 +989,74 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     if (last) break;
                 }
             } else {
-                // kpad in (160, 192]: P = Y_t (then its A operand), Q = the second product; the hi
-                // image is double-buffered and tile 0's X' lo half waits in tensor memory (L)
-                const uint32_t P = tmem_base, Q = tmem_base + 192;
+                // kpad in (128, 192]: tile 0 = rows 0 .. 127, tile 1 = the wc = kpad - 128 rows
+                // after them.  Z = X X and Q = (Z - shift I) X are symmetric (X commutes with
+                // Z), so tile 1's rows are tile 0's columns 128 .. transposed except for the
+                // corner [128 .., 128 ..]; only the corners are multiplied for tile 1, with N = wc:
+                //   Z_0 = X_0 X -> TA (N = kpad), Z_c = X_1 X[:, 128 ..] -> TB (N = wc);
+                //   TA -> A operand of Z_0 - shift I, its columns 128 .. also into Bz (rows
+                //   0 .. 127), while Z_c is multiplied; Q_0 = A X -> TC;
+                //   Z_c - shift I -> Bz rows 128 .. while Q_0 is multiplied; Q_c = X_1 Bz -> TB;
+                //   X' = alpha Q: tile 0 into the image, its columns 128 .. also as rows 128 ..
+                //   (transposed), and the corner.
+                // Iteration 0 also forms tile 1's columns 0 .. 127 (-> R1, N = 128) for the
+                // row sums of the bound.  Tensor memory: TA, TB, R1 and TC = the last kpad
+                // columns (TC overlaps R1 only when kpad = 192, and R1 is dead by then).
+                const uint32_t TA = tmem_base, TB = tmem_base + kpad, R1 = TB + wc, TC = tmem_base + 512 - kpad;
                 for (int it = 0; it < a.max_iter; ++it) {
                     float alpha = -0.5f, shift = 3.0f;
+                    if (warp == 1 && lane == 0) {
+                        tc_fence_after();
+                        issue_xx(0, TA);
+                        if (it == 0) issue_xx_cols(1, R1, 0, idesc_128);
+                        tc_commit(&mma_bar);
+                        issue_xx_cols(1, TB, 128, idesc_w);
+                        tc_commit(&mma_bar2);
+                    }
+                    mma_wait();  // Z_0 (and R1)
                     if (it == 0) {
-                        // Z_t = X0_t X0 for both tiles, the bound, then tile 1 is multiplied again
-                        if (warp == 1 && lane == 0) {
-                            tc_fence_after();
-                            issue_xx(0, P);
-                            issue_xx(1, Q);
-                            tc_commit(&mma_bar);
-                        }
-                        mma_wait();
+                        mma_wait2();  // Z_c
                         __syncthreads();
                         if (*abortp) break;
-                        const float c = start_scale(P, Q);
+                        const float c = start_scale(TA, R1, TB);
                         shift = 3.0f / (c * c);
                         alpha = -0.5f * c * c * c;
-                        tc_fence_before();
-                        __syncthreads();
                     }
+                    tc_fence_before();
+                    __syncthreads();
+                    if (*abortp) break;
                     float r2 = 0.0f;
-                    for (int t = 0; t < mtiles; ++t) {
-                        const bool g1 = !(it == 0 && t == 0);  // Z_0 is already in P
-                        if (g1 && warp == 1 && lane == 0) {
-                            tc_fence_after();
-                            issue_xx(t, P);
-                            tc_commit(&mma_bar);
-                        }
-                        const uint32_t hi_next = NB == 2 ? (hi_off == img_bytes ? 2 * img_bytes : img_bytes)
-                                                         : (hi_off == 0 ? img_bytes : 0);
-                        if (t == 1) drain_split0(Q, alpha, hi_next);  // overlaps the product
-                        if (g1) mma_wait();
-                        tc_fence_before();
-                        __syncthreads();
-                        if (*abortp) break;
-                        convert(t, P, shift, it > 0, r2);
-                        if (t == mtiles - 1) {
-                            r2 = warp_sum_f(r2);
-                            if (lane == 0) resid_s2[warp] = r2;
-                        }
-                        tc_fence_before();
-                        __syncthreads();
-                        if (warp == 1 && lane == 0) {
-                            tc_fence_after();
-                            issue_yx(P, Q);
-                            tc_commit(&mma_bar);
-                        }
-                        if (t == mtiles - 1 && tid == 0 && it > 0) decide();
-                        mma_wait();
-                        __syncthreads();
-                        if (*abortp) break;
+                    convert(0, TA, shift, it > 0, r2, true);
+                    fence_proxy_async_smem();  // Bz rows 0 .. 127 (read by Q_c's products)
+                    tc_fence_before();
+                    __syncthreads();
+                    if (warp == 1 && lane == 0) {
+                        tc_fence_after();
+                        issue_yx(TA, TC);
+                        tc_commit(&mma_bar);
                     }
+                    if (it > 0) mma_wait2();  // Z_c, multiplied while tile 0 was converted
+                    convert_corner(TB, shift, it > 0, r2);
+                    r2 = warp_sum_f(r2);
+                    if (lane == 0) resid_s2[warp] = r2;
+                    fence_proxy_async_smem();  // Bz rows 128 ..
+                    tc_fence_before();
+                    __syncthreads();
+                    if (*abortp) break;
+                    if (warp == 1 && lane == 0) {
+                        tc_fence_after();
+                        issue_cyx(TB);
+                        tc_commit(&mma_bar2);
+                    }
+                    if (tid == 0 && it > 0) decide();
+                    mma_wait();   // Q_0
+                    mma_wait2();  // Q_c
+                    __syncthreads();
                     if (*abortp) break;
                     const bool last = conv_s || bad_s || it + 1 == a.max_iter;
-                    // tile 0 is in the next hi image and (lo) in tensor memory
-                    const uint32_t hi_next = NB == 2 ? (hi_off == img_bytes ? 2 * img_bytes : img_bytes)
-                                                     : (hi_off == 0 ? img_bytes : 0);
-                    drain(1, Q, alpha, hi_next);
-                    fill_lo0();
+                    drain(0, TC, alpha, hi_off, true);
+                    drain_corner(TB, alpha);
                     fence_proxy_async_smem();
-                    hi_off = hi_next;
-                    img_hi = smem_base + hi_off;
                     tc_fence_before();
                     __syncthreads();
                     cur ^= 1;
