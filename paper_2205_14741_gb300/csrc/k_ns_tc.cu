@@ -810,9 +810,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
             };
             // drain: X'_t = alpha C (its padding is zero already) into the image (hi at hi_dst)
-            // transpose (two-tile form, tile 0): the chunks at columns >= 128 are also written as
-            // rows 128 .. of the image (X' is symmetric), element by element
-            auto drain = [&](int t, uint32_t acc, float alpha, uint32_t hi_dst, bool transpose = false) {
+            auto drain = [&](int t, uint32_t acc, float alpha, uint32_t hi_dst) {
                 const int row = 128 * t + 32 * q + lane;
                 if (row - lane >= kpad) return;  // the warp's rows are all padding (kpad is a multiple of 32)
 #pragma unroll 1
@@ -834,15 +832,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                             *reinterpret_cast<uint4*>(smem + lo_off + off) =
                                 make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
                     }
-                    if (transpose && c0 >= 128) {
+                }
+            };
+            // two-tile form: the columns 128 .. of tile 0 of X' = alpha C as rows 128 .. of the
+            // image (X' is symmetric), element by element
+            auto drain_t = [&](uint32_t acc, float alpha) {
+                const int row = 32 * q + lane;
+#pragma unroll 1
+                for (int c0 = 128 + 32 * part; c0 < kpad; c0 += 96) {
+                    uint32_t raw[32];
+                    tmem_ld32_issue(acc + lane_off + c0, raw);
+                    tmem_wait_ld_regs(raw);
+                    uint32_t hw[16], lw[16];
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const uint32_t off = img_offset(c0 + i, row, RB);  // element (c0 + i, row)
-                            const int sh = (i & 1) * 16;                       // pairs hold the even column low
-                            *reinterpret_cast<uint16_t*>(smem + hi_dst + off) = static_cast<uint16_t>(hw[i >> 1] >> sh);
-                            if constexpr (NB == 2)
-                                *reinterpret_cast<uint16_t*>(smem + lo_off + off) = static_cast<uint16_t>(lw[i >> 1] >> sh);
-                        }
+                    for (int i = 0; i < 32; i += 2)
+                        split2<PREC, NB>(alpha * __uint_as_float(raw[i]), alpha * __uint_as_float(raw[i + 1]), hw[i >> 1], lw[i >> 1]);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const uint32_t off = img_offset(c0 + i, row, RB);  // element (c0 + i, row)
+                        const int sh = (i & 1) * 16;                       // pairs hold the even column low
+                        *reinterpret_cast<uint16_t*>(smem + hi_off + off) = static_cast<uint16_t>(hw[i >> 1] >> sh);
+                        if constexpr (NB == 2)
+                            *reinterpret_cast<uint16_t*>(smem + lo_off + off) = static_cast<uint16_t>(lw[i >> 1] >> sh);
                     }
                 }
             };
@@ -997,8 +1008,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 //   TA -> A operand of Z_0 - shift I, its columns 128 .. also into Bz (rows
                 //   0 .. 127), while Z_c is multiplied; Q_0 = A X -> TC;
                 //   Z_c - shift I -> Bz rows 128 .. while Q_0 is multiplied; Q_c = X_1 Bz -> TB;
-                //   X' = alpha Q: tile 0 into the image, its columns 128 .. also as rows 128 ..
-                //   (transposed), and the corner.
+                //   X' = alpha Q: tile 0 into the image while Q_c is multiplied (Q_c reads only
+                //   rows 128 .. of the image and Bz; its A tile's rows past kpad, whose results are
+                //   dropped, may see the new values), then tile 0's columns 128 .. as rows 128 ..
+                //   (transposed) and the corner.
                 // Iteration 0 also forms tile 1's columns 0 .. 127 (-> R1, N = 128) for the
                 // row sums of the bound.  Tensor memory: TA, TB, R1 and TC = the last kpad
                 // columns (TC overlaps R1 only when kpad = 192, and R1 is dead by then).
@@ -1050,11 +1063,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     }
                     if (tid == 0 && it > 0) decide();
                     mma_wait();   // Q_0
+                    drain(0, TC, alpha, hi_off);
                     mma_wait2();  // Q_c
                     __syncthreads();
                     if (*abortp) break;
                     const bool last = conv_s || bad_s || it + 1 == a.max_iter;
-                    drain(0, TC, alpha, hi_off, true);
+                    drain_t(TC, alpha);
                     drain_corner(TB, alpha);
                     fence_proxy_async_smem();
                     tc_fence_before();
