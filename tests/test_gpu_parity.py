@@ -329,3 +329,44 @@ def test_stored_oracle_values(prec):
     # the bracket's sums are taken in another order on the device: mu agrees to rounding
     assert abs(mu_b - g["bisect_mu"]) <= 1e-12 and steps == int(g["bisect_steps"])
     assert abs(tr_b - g["bisect_trace"]) <= (1e-9 if prec == "fp64" else 1e-3)
+
+
+# Full patterns whose one submatrix has n just past, inside and at the ends of the two-row-tile
+# on-chip range (128, 192], and one past it (streamed form): the second tile is formed from
+# the first's columns plus a corner product; n - 128 = 1 leaves a single live corner row.
+TILE_EDGE_SIZES = {129: [43, 43, 43], 130: [43, 43, 44], 145: [29] * 5, 159: [40, 40, 40, 39], 160: [40] * 4,
+                   161: [40, 40, 40, 41], 176: [44] * 4, 191: [48, 48, 48, 47], 192: [48] * 4,
+                   193: [48, 48, 48, 49]}
+
+
+@pytest.mark.parametrize("n", sorted(TILE_EDGE_SIZES))
+@pytest.mark.parametrize("prec,bound", [("fp16x3", TOL_D["fp16x3"]), ("fp16", 2e-2), ("bf16", 1e-1)])
+def test_second_row_tile_edges(n, prec, bound):
+    from paper_2205_14741_gb300 import SmxError, _lib
+
+    sizes = TILE_EDGE_SIZES[n]
+    assert sum(sizes) == n
+    s = make_mixed_block_system(sizes, r_c=np.inf, ell=1.5, seed=40 + n)
+    with _ctx(s, prec) as c:
+        c.set_mu(0.0)
+        c.build_density()
+        try:
+            d = c.get_density()
+        except SmxError as e:
+            # single-pass BF16 (8-bit mantissa): past n ~ 160 the residual ||X^2 - I||_F can
+            # stall above its stopping threshold 5e-2, which the kernel reports as
+            # non-convergence (the split and single-pass FP16 forms converge at every size here)
+            if prec == "bf16" and n > 160 and e.status == _lib.ERR_NOCONV:
+                pytest.xfail("BF16 residual floor above its stopping threshold at this size")
+            raise
+        tr, en, _ = c.get_trace()
+        st = c.get_stats()
+    assert st["dim_min"] == n and st["dim_max"] == n
+    d_or, res, _ = oracle_in_input_layout(s, 0.0, 0.0)
+    # one submatrix is the whole matrix: the oracle's result is the dense projector
+    h = O.to_dense(s.block_size, s.col_ptr, s.row_idx, s.values)
+    assert np.max(np.abs(O.to_dense(s.block_size, s.col_ptr, s.row_idx, d_or) - O.dense_density(h, 0.0))) <= 1e-12
+    if prec == "fp16x3":
+        _check(d, tr, en, d_or, res, prec)
+    else:
+        assert float(np.max(np.abs(d - d_or))) <= bound
