@@ -810,7 +810,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
             };
             // drain: X'_t = alpha C (its padding is zero already) into the image (hi at hi_dst)
-            auto drain = [&](int t, uint32_t acc, float alpha, uint32_t hi_dst) {
+            // keep_a: also leave X' in the accumulator columns as the packed A operand (16 columns
+            // of hi pairs, then 16 of lo pairs per 32-column chunk) of the next iteration's X X
+            auto drain = [&](int t, uint32_t acc, float alpha, uint32_t hi_dst, bool keep_a = false) {
                 const int row = 128 * t + 32 * q + lane;
                 if (row - lane >= kpad) return;  // the warp's rows are all padding (kpad is a multiple of 32)
 #pragma unroll 1
@@ -832,28 +834,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                             *reinterpret_cast<uint4*>(smem + lo_off + off) =
                                 make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
                     }
+                    if (keep_a) {
+                        uint32_t w[32];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            w[i] = hw[i];
+                            w[16 + i] = lw[i];
+                        }
+                        tmem_st32(acc + lane_off + c0, w);
+                    }
                 }
+                if (keep_a) tmem_wait_st();
             };
-            // two-tile form: the columns 128 .. of tile 0 of X' = alpha C as rows 128 .. of the
-            // image (X' is symmetric), element by element
-            auto drain_t = [&](uint32_t acc, float alpha) {
+            // two-tile form: the columns 128 .. of tile 0 of X' as rows 128 .. of the image (X' is
+            // symmetric), element by element, from the packed operand that drain left at acc
+            auto drain_t = [&](uint32_t acc) {
                 const int row = 32 * q + lane;
 #pragma unroll 1
                 for (int c0 = 128 + 32 * part; c0 < kpad; c0 += 96) {
-                    uint32_t raw[32];
-                    tmem_ld32_issue(acc + lane_off + c0, raw);
-                    tmem_wait_ld_regs(raw);
-                    uint32_t hw[16], lw[16];
-#pragma unroll
-                    for (int i = 0; i < 32; i += 2)
-                        split2<PREC, NB>(alpha * __uint_as_float(raw[i]), alpha * __uint_as_float(raw[i + 1]), hw[i >> 1], lw[i >> 1]);
+                    uint32_t w[32];
+                    tmem_ld32_issue(acc + lane_off + c0, w);
+                    tmem_wait_ld_regs(w);
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const uint32_t off = img_offset(c0 + i, row, RB);  // element (c0 + i, row)
                         const int sh = (i & 1) * 16;                       // pairs hold the even column low
-                        *reinterpret_cast<uint16_t*>(smem + hi_off + off) = static_cast<uint16_t>(hw[i >> 1] >> sh);
+                        *reinterpret_cast<uint16_t*>(smem + hi_off + off) = static_cast<uint16_t>(w[i >> 1] >> sh);
                         if constexpr (NB == 2)
-                            *reinterpret_cast<uint16_t*>(smem + lo_off + off) = static_cast<uint16_t>(lw[i >> 1] >> sh);
+                            *reinterpret_cast<uint16_t*>(smem + lo_off + off) = static_cast<uint16_t>(w[16 + (i >> 1)] >> sh);
                     }
                 }
             };
@@ -1008,7 +1016,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 //   TA -> A operand of Z_0 - shift I, its columns 128 .. also into Bz (rows
                 //   0 .. 127), while Z_c is multiplied; Q_0 = A X -> TC;
                 //   Z_c - shift I -> Bz rows 128 .. while Q_0 is multiplied; Q_c = X_1 Bz -> TB;
-                //   X' = alpha Q: tile 0 into the image while Q_c is multiplied (Q_c reads only
+                //   X' = alpha Q: tile 0 into the image (and, packed, back into TC as the A operand
+                //   of the next Z_0, so that after iteration 0 the first product reads A from
+                //   tensor memory) while Q_c is multiplied (Q_c reads only
                 //   rows 128 .. of the image and Bz; its A tile's rows past kpad, whose results are
                 //   dropped, may see the new values), then tile 0's columns 128 .. as rows 128 ..
                 //   (transposed) and the corner.
@@ -1020,7 +1030,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     float alpha = -0.5f, shift = 3.0f;
                     if (warp == 1 && lane == 0) {
                         tc_fence_after();
-                        issue_xx(0, TA);
+                        if (it == 0) issue_xx(0, TA);
+                        else issue_yx(TC, TA);  // X_0 as the operand the last drain left in TC
                         if (it == 0) issue_xx_cols(1, R1, 0, idesc_128);
                         tc_commit(&mma_bar);
                         issue_xx_cols(1, TB, 128, idesc_w);
@@ -1063,12 +1074,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     }
                     if (tid == 0 && it > 0) decide();
                     mma_wait();   // Q_0
-                    drain(0, TC, alpha, hi_off);
+                    drain(0, TC, alpha, hi_off, true);
                     mma_wait2();  // Q_c
+                    tc_fence_before();
                     __syncthreads();
+                    tc_fence_after();
                     if (*abortp) break;
                     const bool last = conv_s || bad_s || it + 1 == a.max_iter;
-                    drain_t(TC, alpha);
+                    drain_t(TC);
                     drain_corner(TB, alpha);
                     fence_proxy_async_smem();
                     tc_fence_before();
