@@ -690,8 +690,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
             };
             // A in tensor memory from column at: per 32 K values, 16 columns hi then 16 lo
-            auto issue_yx = [&](uint32_t at, uint32_t d) {  // d <- A X
-                for (int kk = 0; kk < ksteps; ++kk) {
+            // d <- A X over the K steps [k0, k1) (k0 = 0 starts the accumulator)
+            auto issue_yx_k = [&](uint32_t at, uint32_t d, int k0, int k1) {
+                for (int kk = k0; kk < k1; ++kk) {
                     const uint32_t boff = static_cast<uint32_t>((kk >> 2) * 8192 + (kk & 3) * 2048);
                     const uint32_t ah = at + 32 * (kk >> 1) + 8 * (kk & 1);
                     const uint64_t bh = sdesc_mn_sw128_lbo(img_hi + boff, lbo);
@@ -702,6 +703,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     }
                 }
             };
+            auto issue_yx = [&](uint32_t at, uint32_t d) { issue_yx_k(at, d, 0, ksteps); };  // d <- A X
             auto mma_wait = [&]() {  // all threads
                 mbar_wait(&mma_bar, mma_ph & 1u, &abort_s, a.status);
                 ++mma_ph;
@@ -1018,7 +1020,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 //   Z_c - shift I -> Bz rows 128 .. while Q_0 is multiplied; Q_c = X_1 Bz -> TB;
                 //   X' = alpha Q: tile 0 into the image (and, packed, back into TC as the A operand
                 //   of the next Z_0, so that after iteration 0 the first product reads A from
-                //   tensor memory) while Q_c is multiplied (Q_c reads only
+                //   tensor memory; the next Z_0 starts over K rows 0 .. 127 as soon as Q_c is
+                //   done) while Q_c is multiplied (Q_c reads only
                 //   rows 128 .. of the image and Bz; its A tile's rows past kpad, whose results are
                 //   dropped, may see the new values), then tile 0's columns 128 .. as rows 128 ..
                 //   (transposed) and the corner.
@@ -1028,11 +1031,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 const uint32_t TA = tmem_base, TB = tmem_base + kpad, R1 = TB + wc, TC = tmem_base + 512 - kpad;
                 for (int it = 0; it < a.max_iter; ++it) {
                     float alpha = -0.5f, shift = 3.0f;
-                    if (warp == 1 && lane == 0) {
+                    if (it == 0 && warp == 1 && lane == 0) {  // later iterations: issued at the end of the previous one
                         tc_fence_after();
-                        if (it == 0) issue_xx(0, TA);
-                        else issue_yx(TC, TA);  // X_0 as the operand the last drain left in TC
-                        if (it == 0) issue_xx_cols(1, R1, 0, idesc_128);
+                        issue_xx(0, TA);
+                        issue_xx_cols(1, R1, 0, idesc_128);
                         tc_commit(&mma_bar);
                         issue_xx_cols(1, TB, 128, idesc_w);
                         tc_commit(&mma_bar2);
@@ -1075,17 +1077,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     if (tid == 0 && it > 0) decide();
                     mma_wait();   // Q_0
                     drain(0, TC, alpha, hi_off, true);
+                    fence_proxy_async_smem();  // rows 0 .. 127 of the image (read by the next Z_0)
                     mma_wait2();  // Q_c
                     tc_fence_before();
                     __syncthreads();
                     tc_fence_after();
                     if (*abortp) break;
                     const bool last = conv_s || bad_s || it + 1 == a.max_iter;
+                    // the next Z_0 = X_0 X over K rows 0 .. 127 (image rows 0 .. 127 and the packed
+                    // X_0 in TC are final) while rows 128 .. are written; issued by warp 10, which
+                    // has no rows or chunks in the two passes below, so its wait for the MMA queue
+                    // delays no pass
+                    if (!last && warp == 10 && lane == 0) issue_yx_k(TC, TA, 0, 8);
                     drain_t(TC);
                     drain_corner(TB, alpha);
                     fence_proxy_async_smem();
                     tc_fence_before();
                     __syncthreads();
+                    if (!last && warp == 10 && lane == 0) {
+                        tc_fence_after();
+                        issue_yx_k(TC, TA, 8, ksteps);  // K rows 128 ..
+                        tc_commit(&mma_bar);
+                        issue_xx_cols(1, TB, 128, idesc_w);  // the next Z_c, after Z_0 in the queue
+                        tc_commit(&mma_bar2);
+                    }
                     cur ^= 1;
                     done = it + 1;
                     if (last) break;
