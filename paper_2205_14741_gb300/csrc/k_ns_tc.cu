@@ -730,12 +730,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             // the thread's entries (the n x n block; the padding contributes nothing)
             // to_bz (two-tile form, tile 0): the chunks at columns >= 128 also go to Bz (rows 0 .. 127),
             // and their residual counts twice (Z is symmetric: the block below the diagonal block)
+            // In the two-tile form (to_bz) warp 10 is still issuing the corner product Z_c when
+            // this pass starts, so its chunks go to the other two warps of its lane quadrant
+            // (warps 2 and 6 take every other chunk).
             auto convert = [&](int t, uint32_t acc, float shift, bool resid, float& r2, bool to_bz = false) {
                 const int row0 = 128 * t + 32 * q;  // the warp's first row
                 if (row0 >= kpad) return;
                 const bool live = row0 + lane < s.n;
+                const bool shared2 = to_bz && q == 2;  // quadrant 2 without warp 10
+                if (shared2 && part == 2) return;
+                const int cstep = shared2 ? 64 : 96;
 #pragma unroll 1
-                for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
+                for (int c0 = 32 * part; c0 < kpad; c0 += cstep) {
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + lane_off + c0, raw);
                     tmem_wait_ld_regs(raw);
@@ -1047,10 +1053,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                         const float c = start_scale(TA, R1, TB);
                         shift = 3.0f / (c * c);
                         alpha = -0.5f * c * c * c;
+                        tc_fence_before();
+                        __syncthreads();
+                        if (*abortp) break;
                     }
-                    tc_fence_before();
-                    __syncthreads();
-                    if (*abortp) break;
+                    // later iterations: no barrier here (each thread waited for Z_0 itself; the
+                    // abort flag is checked after the next barrier but one), so the conversion
+                    // starts while warp 10 is still issuing Z_c
                     float r2 = 0.0f;
                     convert(0, TA, shift, it > 0, r2, true);
                     fence_proxy_async_smem();  // Bz rows 0 .. 127 (read by Q_c's products)
