@@ -11,17 +11,17 @@ What it computes (the paper, Section 2 and Section 3):
   A = V diag(lambda) V^T this equals V diag(sign(lambda)) V^T, which is how
   this oracle evaluates it (eigendecomposition by LAPACK through numpy; the
   iterative methods are the GPU path's business).
-* Fig. 2, the submatrix method: (i) for every column build a dense submatrix
-  from the rows that are non-zero in that column, (ii) apply the matrix
-  function to each dense submatrix, (iii) insert the relevant result columns
-  into the sparse result.
+* Fig. 2, the submatrix method: (i) one dense submatrix per column, made of
+  the rows stored in that column, (ii) the matrix function of each dense
+  submatrix, (iii) the columns of each result that belong to its column
+  written back into the sparse result.
 
 Readings where the paper is silent (the same readings bind the GPU path):
 
 * granularity is the block column: block column j gives the submatrix
   T_j = H[R_j, R_j], R_j = sorted block rows stored in column j of the
   filtered H; blocks of H[R_j, R_j] that are not stored are zero;
-* "relevant result columns" are the columns of block j only, over all rows
+* the result columns kept are the columns of block j only, over all rows
   of R_j: D[R_j, j] = 1/2 (E_j - sign(T_j - mu I)[:, cols of j]);
 * filtering drops an off-diagonal block when its Frobenius norm is strictly
   below eps; diagonal blocks are always kept;
