@@ -45,3 +45,20 @@ def test_trajectory_pattern_changes_smoothly():
 def test_spectrum_matrix():
     a = spectrum_matrix(20, np.linspace(-1, 1, 20), seed=1)
     assert np.allclose(np.linalg.eigvalsh(a), np.linspace(-1, 1, 20), atol=1e-13)
+
+
+def test_nonorth_pair_shares_the_pattern_and_s_is_positive_definite():
+    from synth import make_nonorth_pair
+
+    h, s = make_nonorth_pair(64, 6, 6.0, 1.5, 11)
+    assert np.array_equal(h.col_ptr, s.col_ptr) and np.array_equal(h.row_idx, s.row_idx)
+    hd = O.to_dense(h.block_size, h.col_ptr, h.row_idx, h.values)
+    sd = O.to_dense(s.block_size, s.col_ptr, s.row_idx, s.values)
+    assert np.allclose(hd, hd.T) and np.allclose(sd, sd.T)
+    lo, _ = O.gershgorin_bounds(sd)
+    assert lo > 0.1  # every Gershgorin disc of S well right of zero
+    # S's off-diagonal blocks come from their own key stream, not from H's
+    off = ~np.eye(hd.shape[0], dtype=bool) & (hd != 0)
+    assert abs(np.corrcoef(hd[off], sd[off])[0, 1]) < 0.1
+    h2, s2 = make_nonorth_pair(64, 6, 6.0, 1.5, 11)
+    assert np.array_equal(h.values, h2.values) and np.array_equal(s.values, s2.values)
