@@ -32,7 +32,7 @@
 //                residual ||X^2 - I||_F^2 in FP32, split to hi/lo, 16-byte
 //                stores to the slot (L2-resident)
 // On-chip form (up to 192): all 12 warps share the tensor-memory passes; one
-// lane of warp 1 issues the MMAs.
+// lane of warp 1 issues the MMAs (of warp 10 the next iteration's in two-tile form).
 #include "smx_finish.cuh"
 #include "smx_kernels.h"
 
