@@ -170,7 +170,11 @@ smx_status smx_set_staging_limit(smx_ctx* ctx, uint64_t bytes);
 smx_status smx_set_column_range(smx_ctx* ctx, int32_t j0, int32_t j1);
 
 /* Gershgorin interval [lo, hi] of the whole filtered H (Eq. 14's mu lies in
- * it): the bisection bracket.  Synchronises.  Errors: SMX_ERR_ARG, SMX_ERR_CUDA. */
+ * it): the bisection bracket.  With an overlap set (smx_set_overlap) the
+ * bracket of the non-orthogonal form instead: the union of the Gershgorin
+ * intervals of all M_j (runs the setup if needed); SMX_ERR_UNSUPPORTED on a
+ * column-range shard (the shard knows only its own M_j) or outside FP64.
+ * Synchronises.  Errors: SMX_ERR_ARG, SMX_ERR_CUDA, SMX_ERR_UNSUPPORTED. */
 smx_status smx_get_gershgorin_interval(smx_ctx* ctx, double* lo, double* hi);
 
 /* Fixed chemical potential mu (Eq. 14) for smx_build_density.  Errors: SMX_ERR_ARG (non-finite). */

@@ -771,6 +771,15 @@ smx_status smx_get_gershgorin_interval(smx_ctx* c, double* lo, double* hi) {
     if (!c || !lo || !hi) return SMX_ERR_ARG;
     DeviceGuard g(c->device);
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));  // the bracket comes with the filter
+    if (c->have_S) {
+        // the non-orthogonal form brackets mu by the Gershgorin intervals of its M_j, known only
+        // for the context's own block columns: no common bracket for shards
+        if (c->col_hi >= 0 || c->precision != SMX_FP64) return SMX_ERR_UNSUPPORTED;
+        if (!c->nonorth_ready) SMX_TRY(nonorth_setup(c));
+        *lo = c->nbr_lo;
+        *hi = c->nbr_hi;
+        return SMX_OK;
+    }
     *lo = c->br_lo;
     *hi = c->br_hi;
     return SMX_OK;

@@ -198,3 +198,18 @@ def test_errors():
             c.build_density()
             c.get_trace()
         assert ei.value.status in (_lib.ERR_NOCONV, _lib.ERR_NONFINITE)
+
+
+def test_bracket_is_the_pencils_and_not_offered_to_shards():
+    from paper_2205_14741_gb300 import SmxError, _lib
+
+    h, s = make_nonorth_pair(48, 6, 5.0, 1.5, 18)
+    lo_or, hi_or = O.nonorth_bracket(h.block_size, h.col_ptr, h.row_idx, h.values, s.values)
+    with _ctx(h, s.values) as c:
+        lo, hi = c.get_gershgorin_interval()
+        # L_j from the coupled iteration against the oracle's eigendecomposition: rounding only
+        assert abs(lo - lo_or) <= 1e-12 * abs(lo_or) and abs(hi - hi_or) <= 1e-12 * abs(hi_or)
+        c.set_column_range(0, 24)
+        with pytest.raises(SmxError) as ei:
+            c.get_gershgorin_interval()
+        assert ei.value.status == _lib.ERR_UNSUPPORTED
