@@ -6,7 +6,12 @@ symbolic analysis, then the mu bisection, each bisection step a full build
 energy).  The default workload is 1024 water-like molecules with 6x6 blocks
 (N = 6144), filter 1e-5, bisection to trace(D) = 3072.
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+Prints one JSON line (rank 0).  Besides the headline it reports the FP64 plain
+form, the learned bound's effect on an MD-like trajectory, and two FP64 forms
+beside the hot path on 1024-molecule inputs: S^-1/2 of an overlap-like matrix
+(``inv_sqrt_fp64``) and the mu-solved non-orthogonal density matrix of an
+(H, S) pair (``nonorth_fp64``), each with a sampled check against the oracle
+(``--no-functions`` skips them).  ``--impl reference`` times the FP64 CPU oracle
 on the same workload instead (bounded column samples, extrapolated).
 """
 
