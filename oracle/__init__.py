@@ -6,7 +6,7 @@ package's smoke check and the benchmark's CPU-baseline leg may import it; the
 product path never does, and shares no code with it.
 
 Parity status of each function is listed in ``oracle/submatrix.py``,
-``oracle/functions.py``, ``oracle/nonorth.py`` and ``oracle/mlp.py``; every function there is pinned by tests in
+``oracle/functions.py``, ``oracle/nonorth.py``, ``oracle/fermi.py`` and ``oracle/mlp.py``; every function there is pinned by tests in
 ``tests/test_oracle_*.py`` against closed forms, invariants, brute force or
 independent algorithms.
 """
@@ -35,3 +35,4 @@ from .nonorth import (  # noqa: F401
     bisect_mu_nonorth,
     take_blocks,
 )
+from .fermi import fermi_dense, fermi_submatrix  # noqa: F401
