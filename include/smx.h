@@ -142,14 +142,17 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
                       const int64_t* col_ptr, const int32_t* row_idx, const double* values,
                       void* cuda_stream);
 
-/* Replaces the values of H (same input pattern, e.g. the next MD snapshot).
+/* Replaces the values of H (same input pattern, e.g. the next MD snapshot;
+ * the input of Fig. 2, which Section 4 revisits at every step of a run).
  *  values    : double[] of the same length as in smx_create.
  *  on_device : 0 = host pointer, 1 = device pointer (read on the context stream).
  * The filter is re-applied at the next build.  Errors: SMX_ERR_ARG, SMX_ERR_CUDA. */
 smx_status smx_set_values(smx_ctx* ctx, const double* values, int32_t on_device);
 
-/* Block filter: an off-diagonal block whose Frobenius norm is strictly below
- * eps is dropped from H (and from D); diagonal blocks are always kept.
+/* Block filter (the sparse, filtered matrices of Section 3 that Fig. 2 takes
+ * as input; the paper prints no rule, so this library reads it as): an
+ * off-diagonal block whose Frobenius norm is strictly below eps is dropped
+ * from H (and from D); diagonal blocks are always kept.
  * eps >= 0.  Errors: SMX_ERR_ARG. */
 smx_status smx_set_filter_threshold(smx_ctx* ctx, double eps);
 
@@ -180,8 +183,10 @@ smx_status smx_get_gershgorin_interval(smx_ctx* ctx, double* lo, double* hi);
 /* Fixed chemical potential mu (Eq. 14) for smx_build_density.  Errors: SMX_ERR_ARG (non-finite). */
 smx_status smx_set_mu(smx_ctx* ctx, double mu);
 
-/* Electron count for smx_solve_mu: bisection on trace(D(mu)) = n_e inside the
- * Gershgorin interval of the filtered H; stops when |trace - n_e| <= tol or
+/* Electron count for smx_solve_mu, which sets Eq. 14's mu (the paper does not
+ * say how; this library reads it as a bisection): bisection on
+ * trace(D(mu)) = n_e inside the Gershgorin interval of the filtered H, with
+ * trace(D) counting orbitals (no spin factor); stops when |trace - n_e| <= tol or
  * after max_steps builds (1..200).  The result is the last evaluated mu.
  * Errors: SMX_ERR_ARG. */
 smx_status smx_set_electron_count(smx_ctx* ctx, double n_e, int32_t max_steps, double tol);
@@ -227,8 +232,8 @@ smx_status smx_set_overlap(smx_ctx* ctx, const double* values, int32_t on_device
  * SMX_ERR_UNSUPPORTED (a submatrix larger than this build handles). */
 smx_status smx_build_density(smx_ctx* ctx);
 
-/* Finds mu by bisection (see smx_set_electron_count) and leaves the last
- * build's D in the context.  Synchronises once per bisection step.  With new
+/* Finds Eq. 14's mu by bisection (see smx_set_electron_count) and leaves the
+ * last build's D in the context.  Synchronises once per bisection step.  With new
  * values on an analysed context the filter and the first step (at the
  * bracket's midpoint, computed on the device) are issued together and read
  * back once; if the filter changed the filtered pattern, that step is taken
@@ -238,22 +243,31 @@ smx_status smx_build_density(smx_ctx* ctx);
 smx_status smx_solve_mu(smx_ctx* ctx);
 
 /* trace(D), trace(D H) (the band-structure energy, unshifted H) and mu of the
- * last build.  Any argument may be NULL.  Synchronises the stream and returns
+ * last build, D being Eq. 14's density matrix assembled by Fig. 2 (trace(D)
+ * sums the diagonals of the diagonal blocks; trace(D H) sums D_pq H_pq over
+ * the stored entries of the filtered pattern).  Any argument may be NULL.  Synchronises the stream and returns
  * latched device errors.  Errors: SMX_ERR_STATE (no build yet). */
 smx_status smx_get_trace(smx_ctx* ctx, double* trace_D, double* trace_DH, double* mu);
 
-/* Copies D of the last build, laid out exactly like the input values
- * (input pattern; blocks dropped by the filter are zero).
+/* Copies D of the last build (Fig. 2 step (iii): the kept columns of each
+ * f(T_j), inserted into D, which has the filtered pattern of H and no fill-in
+ * of its own), laid out exactly like the input values (input pattern; blocks
+ * dropped by the filter are zero).
  *  values_out : double[] of the input value count; host or device pointer.
  *  on_device  : 0 = host pointer (synchronises), 1 = device pointer (async).
  * Errors: SMX_ERR_ARG, SMX_ERR_STATE, SMX_ERR_CUDA, latched device errors. */
 smx_status smx_get_density(smx_ctx* ctx, double* values_out, int32_t on_device);
 
-/* Filtered pattern of the last build.  col_ptr: host int64[B+1]; row_idx: host
- * int32[nnzb_filtered] (size from smx_get_stats), either may be NULL. */
+/* Filtered pattern of the last build (the pattern of H after the block filter
+ * of smx_set_filter_threshold, which D shares; it fixes the index sets R_j of
+ * Fig. 2).  col_ptr: host int64[B+1]; row_idx: host int32[nnzb_filtered]
+ * (size from smx_get_stats), either may be NULL. */
 smx_status smx_get_pattern(smx_ctx* ctx, int64_t* col_ptr, int32_t* row_idx);
 
-/* Statistics of the last build (see smx_stats).  Synchronises. */
+/* Statistics of the last build (see smx_stats): the submatrix dimensions of
+ * Fig. 2, the iterations of the Eq. 13 iteration (two products of n_j x n_j
+ * matrices each, hence 4 n_j^3 flops), fallbacks of the learned bound
+ * (Section 4) and device timings.  Synchronises. */
 smx_status smx_get_stats(smx_ctx* ctx, smx_stats* out);
 
 /* ---------------------------------------------------------------------------
@@ -333,15 +347,16 @@ smx_status smx_reset_counters(smx_ctx* ctx);
  * b_j used for X0 = (T_j - mu I)/b_j.  Synchronises. */
 smx_status smx_get_submatrix_info(smx_ctx* ctx, int32_t* dims, int32_t* iters, double* bounds);
 
-/* Dense density matrix without any device allocation (the paper has no
- * counterpart; this serves callers that cannot allocate device memory at the
- * time they need the result: code running while a stream is captured into a
- * CUDA graph, plug-ins whose host framework owns the whole device pool, and
- * latency-critical loops that must not enter the allocator, which can
- * synchronise the device).
+/* Dense density matrix without any device allocation.  The paper has no
+ * counterpart: this call serves callers that cannot allocate device memory
+ * when they need the result, such as plug-ins whose host framework's caching
+ * allocator owns the whole device pool, and latency-critical loops that must
+ * not enter the driver's allocator (cudaMalloc/cudaFree can synchronise the
+ * device).
  * Computes D = 1/2 (I - sign(H - mu I)) of one dense symmetric H by FP64
- * Newton-Schulz iteration with a Gershgorin scaling (one CTA; same arithmetic
- * as the FP64 form of smx_build_density).
+ * Newton-Schulz iteration with a Gershgorin scaling (Eq. 13 and Eq. 14 with
+ * S = I on a single dense matrix; one CTA; same arithmetic as the FP64 form
+ * of smx_build_density).
  *  h_dev       : device double[n*n], row-major, symmetric (read only).
  *  n           : 1 <= n <= 256; larger n returns SMX_ERR_ARG.
  *  mu          : finite chemical potential.
@@ -349,13 +364,16 @@ smx_status smx_get_submatrix_info(smx_ctx* ctx, int32_t* dims, int32_t* iters, d
  *  cuda_stream : stream to run on (NULL = legacy default stream).
  * Work matrices live in one fixed __device__ array of 3*256*256 + 4 doubles
  * (about 1.5 MiB) that every GPU which loads the library keeps until the
- * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress), so make the first call on each device
- * before any stream capture.  All calls share the array: calls whose work
- * overlaps on a GPU (other streams, other host threads) race and must be
- * serialised by the caller.  The call synchronises the stream to report
- * errors: SMX_ERR_ARG, SMX_ERR_CUDA, SMX_ERR_UNSUPPORTED (device index >= 64),
- * SMX_ERR_NONFINITE, SMX_ERR_NOCONV. */
+ * process exits.  The first call on a device (and the first after a device
+ * reset) looks up that array's device address (cudaGetSymbolAddress), so
+ * make the first call on each device before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (every call
+ * overwrites what it reads): calls whose work overlaps on a GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The call waits for its stream (a copy of the status to the host and a
+ * stream synchronisation) and returns: SMX_ERR_ARG, SMX_ERR_CUDA,
+ * SMX_ERR_UNSUPPORTED (device index >= 64), SMX_ERR_NONFINITE,
+ * SMX_ERR_NOCONV. */
 smx_status smx_dense_density_noalloc(const double* h_dev, int32_t n, double mu, double* d_dev,
                                      void* cuda_stream);
 

@@ -30,12 +30,13 @@ def _ptr(a):
 def dense_density_noalloc(h_dev, n: int, mu: float, d_dev, stream: int | None = None) -> None:
     """D = 1/2 (I - sign(H - mu I)) of one dense symmetric n x n matrix (n <= 256), no device allocation.
 
-    For callers that cannot allocate device memory (graph capture, a host
-    framework that owns the pool, allocation-free loops).  ``h_dev`` and
-    ``d_dev`` are caller-owned CUDA tensors (row-major doubles).  The library
-    keeps its work matrices in one fixed device array shared by all calls:
-    make the first call on a device before any stream capture, and do not let
-    calls overlap on the GPU.
+    For callers that cannot allocate device memory when they need the result
+    (a plug-in whose host framework owns the device pool, a loop that must not
+    enter the allocator).  ``h_dev`` and ``d_dev`` are caller-owned CUDA
+    tensors (row-major doubles).  The library keeps its work matrices in one
+    fixed device array shared by all calls: make the first call on a device
+    before any stream capture, and do not let calls overlap on the GPU.  The
+    call waits for its stream to return the status.
     """
     lib = _lib.load()
     check(lib.smx_dense_density_noalloc(_ptr(h_dev), int(n), float(mu), _ptr(d_dev), C.c_void_p(stream or 0)),

@@ -447,15 +447,15 @@ cudaError_t launch_nonorth_setup(const NonorthSetupArgs& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Allocation-free dense entry point (no counterpart in the paper).
 //
-// Some callers cannot allocate device memory when they need a result: code
-// that runs while a CUDA stream is being captured into a graph (cudaMalloc is
-// not allowed there), plug-ins inside a framework whose caching allocator owns
-// the whole device pool, and latency-critical loops that must never enter the
-// driver's allocator (cudaMalloc/cudaFree can synchronise the device).
+// Some callers cannot allocate device memory when they need a result:
+// plug-ins inside a host framework whose caching allocator already owns the
+// whole device pool (a cudaMalloc of their own would fail or fragment it),
+// and latency-critical loops that must never enter the driver's allocator
+// (cudaMalloc/cudaFree can synchronise the device and take milliseconds).
 // smx_dense_density_noalloc serves them: it takes caller-owned input and
 // output buffers and keeps its Newton-Schulz work matrices in the fixed
 // device array below, which every GPU that loads this library holds until the
-// process exits.
+// process exits.  The call itself synchronises its stream to return the status.
 // ---------------------------------------------------------------------------
 
 #include <cmath>
@@ -536,7 +536,26 @@ __global__ void __launch_bounds__(256) k_dense_density_noalloc(const double* __r
 
 namespace {
 std::mutex g_noalloc_mutex;
+// per device: the array's device address and the context it was looked up in
 double* g_noalloc_ptr[smx::kNoAllocMaxDevices] = {};
+CUcontext g_noalloc_ctx[smx::kNoAllocMaxDevices] = {};
+
+// The current driver context, through the runtime's driver entry point (no link to libcuda).
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(p);
+    });
+    CUcontext c = nullptr;
+    if (fn) fn(&c);
+    return c;
+}
 }  // namespace
 
 extern "C" smx_status smx_dense_density_noalloc(const double* h_dev, int32_t n, double mu, double* d_dev,
@@ -548,12 +567,16 @@ extern "C" smx_status smx_dense_density_noalloc(const double* h_dev, int32_t n, 
     double* scratch = nullptr;
     {
         // set-up once per device, with that device current: the host-side name
-        // of a __device__ array is not a device address, so look the address up
+        // of a __device__ array is not a device address, so look the address up.
+        // A device reset (cudaDeviceReset) replaces the context and reloads the
+        // module, so the lookup is repeated when the current context changed.
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
+        const CUcontext cur = current_context();
+        if (!g_noalloc_ptr[dev] || g_noalloc_ctx[dev] != cur) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, smx::g_noalloc_scratch) != cudaSuccess || !p) return SMX_ERR_CUDA;
             g_noalloc_ptr[dev] = static_cast<double*>(p);
+            g_noalloc_ctx[dev] = cur;
         }
         scratch = g_noalloc_ptr[dev];
     }

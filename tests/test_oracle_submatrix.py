@@ -188,6 +188,23 @@ def test_trace_energy_from_dense_bookkeeping():
     assert np.all(d[h == 0.0] == 0.0)
 
 
+def test_global_gershgorin_hand_values_and_dense_agreement():
+    # hand matrix (dense rows written out from the blocks above):
+    #   row 0: [1, .5, .3, 1e-4, 0]   -> 1 -/+ 0.8001
+    #   row 1: [.5, -1, -.4, 0, 1e-4] -> -1 -/+ 0.9001
+    #   row 2: [.3, -.4, .2, 0, 0]    -> 0.2 -/+ 0.7
+    #   rows 3, 4: one 1e-4 each      -> 0 -/+ 1e-4
+    bs, cp, ri, v, _ = _hand_matrix()
+    lo, hi = O.global_gershgorin(bs, cp, ri, v)
+    assert abs(lo - (-1.9001)) < 1e-15 and abs(hi - 1.8001) < 1e-15
+    # the bracket of the bisection equals the dense Gershgorin interval (itself pinned by hand
+    # values) on the filtered water32 and on a ragged-block system
+    for s in [make_workload("water32"), make_lattice_system(12, 4, 5.0, 1.5, 7)]:
+        bs, cp, ri, v = _filtered(s, 1e-3)
+        assert O.global_gershgorin(bs, cp, ri, v) == pytest.approx(
+            O.gershgorin_bounds(O.to_dense(bs, cp, ri, v)), abs=1e-13)
+
+
 def test_trace_nondecreasing_in_mu_and_bisection():
     s = make_workload("water32")
     bs, cp, ri, v = _filtered(s)

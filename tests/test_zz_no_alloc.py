@@ -1,12 +1,12 @@
 """The allocation-free dense entry point, through the C ABI.
 
 smx_dense_density_noalloc is for callers that cannot allocate device memory
-when they need a density matrix (work running inside a CUDA-graph capture,
-plug-ins whose framework owns the device pool, allocation-free loops).  Its
-result must match the regular entry point, smx_build_density, on a system
-whose single submatrix is the whole matrix, call after call: the shared
-fixed work array keeps the previous call's contents, which must not leak
-into the next result.
+when they need a density matrix (plug-ins whose host framework owns the
+device pool, loops that must not enter the allocator).  Its result must match
+the regular entry point, smx_build_density, on a system whose single
+submatrix is the whole matrix, and the oracle's dense density matrix, call
+after call: the shared fixed work array keeps the previous call's contents,
+which must not leak into the next result.
 
 This file is named so that pytest collects it after every other test file.
 """
@@ -51,6 +51,29 @@ def test_no_alloc_matches_build_density_on_consecutive_calls():
         d = d_dev.cpu().numpy()
         err = float(np.max(np.abs(d - d_ref)))
         assert err <= TOL_FP64, f"call {call}: max|D_noalloc - D_build| = {err:.3e}"
+        err_or = float(np.max(np.abs(d - O.dense_density(h, mu))))
+        assert err_or <= TOL_FP64, f"call {call}: max|D_noalloc - D_oracle| = {err_or:.3e}"
+
+
+def test_no_alloc_reports_nonfinite_input_then_recovers():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_14741_gb300 import _lib
+
+    lib = _lib.load()
+    s = make_workload("water32")
+    h = O.to_dense(s.block_size, s.col_ptr, s.row_idx, s.values)
+    bad = h.copy()
+    bad[3, 5] = bad[5, 3] = np.nan
+    d_dev = torch.empty(h.shape, dtype=torch.float64, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for hh, want in [(bad, _lib.ERR_NONFINITE), (h, _lib.OK)]:
+        h_dev = torch.from_numpy(hh).cuda()
+        st = lib.smx_dense_density_noalloc(C.c_void_p(h_dev.data_ptr()), s.n, 0.0, C.c_void_p(d_dev.data_ptr()),
+                                           stream)
+        assert st == want
+    err = float(np.max(np.abs(d_dev.cpu().numpy() - O.dense_density(h, 0.0))))
+    assert err <= TOL_FP64
 
 
 def test_no_alloc_rejects_oversized_input():
