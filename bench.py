@@ -35,7 +35,9 @@ WORKLOAD_TEXT = {
     "water1024": "1024 water-like molecules on a jittered cubic lattice, 6x6 blocks (N=6144), cutoff 6 A, "
                  "decay 1.5 A, block filter 1e-5, bisection to trace(D)=3072 (tol 1e-2)",
     "water32": "32 water-like molecules, 6x6 blocks (N=192), cutoff 5 A, bisection to trace(D)=96",
-    "water4096x23": "4096 molecules, 23x23 blocks (N=94208), cutoff 7 A, decay 2 A, filter 1e-6, mu by bisection",
+    "water4096x23": "4096 molecules, 23x23 blocks (N=94208), cutoff 7 A, decay 2 A, filter 1e-6, mu = 0 fixed",
+    "slab6000": "6000-molecule water/vacuum slab (50x50x200 A box, density ramp over two interfaces), 6x6 blocks, "
+                "cutoff 15.3 A, decay 3 A, filter 1e-5, 20-step bisection to trace(D)=18000 (tol 1e-2)",
 }
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_TFLOPS = 1.2  # DFMA throughput measured on this machine's GB300 (register-resident FMA loop)
@@ -382,31 +384,49 @@ def nonorth_leg(args, stream, flush, check):
     return out
 
 
+def _dims_of(block_size, cp, ri):
+    """n_j of every block column of a (filtered) block-CSC pattern (no method arithmetic)."""
+    bs = np.asarray(block_size, dtype=np.int64)
+    sizes = bs[np.asarray(ri, dtype=np.int64)]
+    csum = np.concatenate([[0], np.cumsum(sizes)])
+    return (csum[np.asarray(cp[1:])] - csum[np.asarray(cp[:-1])]).astype(np.int64)
+
+
+def _work_scale(block_size, cp, ri, cols):
+    """Factor from a column sample to the whole build: sum_j n_j^3 over all columns / over the sample."""
+    d3 = _dims_of(block_size, cp, ri).astype(np.float64) ** 3
+    return float(d3.sum() / d3[np.asarray(cols)].sum())
+
+
+def _fixed_mu(w):
+    return w.get("mu") is not None
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return 0
+    import oracle as O
     from synth import WORKLOADS, make_workload
 
     w = WORKLOADS[args.workload]
     sysm = make_workload(args.workload)
     workers = os.cpu_count() or 1
-    mu = 0.0 if w.get("mu") is not None else None
-    # the bisection of this workload settles on the first midpoint inside the gap;
-    # a bounded sample of one build per step stands for one mu-solved density matrix
-    builds_per_step = 1
-    if mu is None:
-        import oracle as O
-
-        cp, ri, v, _ = O.filter_blocks(sysm.block_size, sysm.col_ptr, sysm.row_idx, sysm.values, w["eps"])
+    cp, ri, v, _ = O.filter_blocks(sysm.block_size, sysm.col_ptr, sysm.row_idx, sysm.values, w["eps"])
+    if _fixed_mu(w):
+        mu, builds_per_step = float(w["mu"]), 1
+    else:
+        # one mu-solved density matrix = the builds of the bisection; water1024 settles on the
+        # first midpoint of the bracket (one build), the slab's bisection takes all its steps
         lo, hi = O.global_gershgorin(sysm.block_size, cp, ri, v)
         mu = 0.5 * (lo + hi)
+        builds_per_step = int(w.get("max_steps", 1))
     for _ in range(args.warmup):
         _oracle_sample(sysm, w["eps"], mu, 16, workers)
     times = []
     for k in range(args.steps):
         dt, cols, _, _ = _oracle_sample(sysm, w["eps"], mu, args.ref_columns, workers, seed=k)
-        times.append(dt * sysm.n_blocks / len(cols) * builds_per_step)
+        times.append(dt * _work_scale(sysm.block_size, cp, ri, cols) * builds_per_step)
     per = sum(times) / len(times)
     value = 1.0 / per
     out = {
@@ -417,11 +437,118 @@ def run_reference(args):
         "config": {"workload": WORKLOAD_TEXT.get(args.workload, args.workload)},
         "cpu_baseline": {"value": value, "unit": "density matrices/s", "cores": workers, "kind": "oracle",
                          "sample": f"{args.ref_columns} of {sysm.n_blocks} block columns per step (seeded), "
-                                   f"time scaled by {sysm.n_blocks}/{args.ref_columns}"},
+                                   f"time scaled by sum_j n_j^3 (all) / sum_j n_j^3 (sample)"
+                                   + (f" x{builds_per_step} bisection builds" if builds_per_step > 1 else "")},
         "e2e": {"value": value, "unit": "density matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
     return 0
+
+
+def train_heldout_model(args, w, stream):
+    """Trains the learned bound on systems of the same generator with other seeds (held out: none
+    of them is timed) and saves the parameters; returns (path, description)."""
+    import tempfile
+
+    from paper_2205_14741_gb300 import SubmatrixDensity
+    from synth import make_workload
+
+    path = os.path.join(tempfile.mkdtemp(prefix="smx_bound_"), "model.bin")
+    seeds = [w["seed"] + 1000 * (k + 1) for k in range(args.model_systems)]
+    t0 = time.perf_counter()
+    samples = 0
+    ctx = None
+    for k, seed in enumerate(seeds):
+        sysm = make_workload(args.workload, seed=seed)
+        ctx = SubmatrixDensity.from_system(sysm, stream=stream.cuda_stream)
+        ctx.set_filter_threshold(w["eps"])
+        ctx.set_precision(args.precision)
+        if k == 0:
+            ctx.bound_model_init(w["seed"])
+        else:
+            ctx.bound_model_init(w["seed"])
+            ctx.set_bound_model(False, path)  # continue from the parameters trained so far
+        # two rounds per system: the second sees the previous-step feature of the first
+        for _ in range(2):
+            ctx.set_values(sysm.values)
+            if _fixed_mu(w):
+                ctx.set_mu(float(w["mu"]))
+                ctx.build_density()
+            else:
+                ctx.set_electron_count(w["n_e"], max_steps=30, tol=1e-2)
+                ctx.solve_mu()
+                ctx.set_mu(ctx.get_trace()[2])
+            ctx.bound_model_collect(48)
+            samples += sysm.n_blocks
+        loss = ctx.bound_model_train(epochs=args.model_epochs, batch=256, lr=2e-3)
+        ctx.bound_model_save(path)
+        ctx.close()
+    return path, {"trained_on": f"{args.workload} generator, seeds {seeds} (held out: not timed)",
+                  "samples": samples, "epochs_per_system": args.model_epochs, "train_loss": loss,
+                  "seconds": time.perf_counter() - t0}
+
+
+def shard_leg(args, w, sysm, stream, pg, world, rank):
+    """One system split over the ranks by block-column ranges (balanced by sum n_j^3); each
+    bisection step sums the 16-byte (trace, energy) over the ranks (NCCL all-reduce).  Returns
+    (ms per mu-solved density matrix, max over ranks; final mu, trace)."""
+    import torch
+
+    from paper_2205_14741_gb300 import SubmatrixDensity
+    from paper_2205_14741_gb300.shard import partition_columns, solve_mu_sharded
+
+    ctx = SubmatrixDensity.from_system(sysm, stream=stream.cuda_stream)
+    ctx.set_filter_threshold(w["eps"])
+    ctx.set_precision(args.precision)
+    ctx.set_mu(0.0)
+    ctx.build_density()
+    dims, _, _ = ctx.get_submatrix_info()
+    j0, j1 = partition_columns(dims, world)[rank]
+    ctx.set_column_range(j0, j1)
+    h_dev = torch.from_numpy(sysm.values).to("cuda")
+    red = torch.zeros(2, dtype=torch.float64, device="cuda")
+
+    def allreduce(x):
+        if pg is None:
+            return x
+        red.copy_(torch.from_numpy(x))
+        pg.all_reduce(red)
+        return red.cpu().numpy()
+
+    def step():
+        ctx.set_values(h_dev, on_device=True)
+        if _fixed_mu(w):
+            ctx.set_mu(float(w["mu"]))
+            ctx.build_density()
+            t, e, m = ctx.get_trace()
+            t, e = allreduce(np.array([t, e]))
+            return m, t, 1
+        m, t, _, n = solve_mu_sharded(ctx, w["n_e"], allreduce, max_steps=w.get("max_steps", args.max_steps),
+                                      tol=1e-2)
+        return m, t, n
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    res = None
+    for a, b in ev:
+        a.record(stream)
+        res = step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if pg:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    ctx.close()
+    return {"ms_per_step": ms, "value": 1e3 / ms, "unit": "density matrices/s", "ranks": world,
+            "columns_this_rank": [int(j0), int(j1)], "mu": res[0], "trace": res[1], "builds_per_step": res[2],
+            "scaling": "strong", "note": "one system; block-column shards balanced by sum n_j^3, 16-byte "
+                                         "all-reduce of (trace, energy) per bisection step"}
 
 
 def run_ours(args):
@@ -441,24 +568,54 @@ def run_ours(args):
     from synth import WORKLOADS, make_workload
 
     w = WORKLOADS[args.workload]
+    big = args.workload != "water1024" and w["n_mol"] * w["b"] > 20000
     sysm = make_workload(args.workload)
     stream = torch.cuda.current_stream()
-    ctx = SubmatrixDensity.from_system(sysm, stream=stream.cuda_stream)
-    ctx.set_filter_threshold(w["eps"])
+    fixed = _fixed_mu(w)
     n_e = w.get("n_e")
     if n_e is None:
         n_e = float(sysm.n_occ)
-    ctx.set_electron_count(n_e, max_steps=30, tol=1e-2)
+
+    if args.shard:
+        sh = shard_leg(args, w, sysm, stream, pg, world, rank)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": sh["value"], "unit": sh["unit"], "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": sh["ms_per_step"],
+                              "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                              "dtype": args.precision, "data": "synthetic",
+                              "config": {"workload": WORKLOAD_TEXT.get(args.workload, args.workload),
+                                         "parallelism": f"{world} block-column shards"},
+                              "shard": sh}))
+        if pg:
+            pg.destroy_process_group()
+        return 0
+
+    # learned bound trained on held-out systems of the same generator (before any timing)
+    model_path, model_info = None, None
+    if args.bound_mode != "off":
+        model_path, model_info = train_heldout_model(args, w, stream)
+
+    ctx = SubmatrixDensity.from_system(sysm, stream=stream.cuda_stream)
+    ctx.set_filter_threshold(w["eps"])
+    ctx.set_electron_count(n_e, max_steps=w.get("max_steps", args.max_steps), tol=1e-2)
     h_dev = torch.from_numpy(sysm.values).to("cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    if model_path:
+        ctx.bound_model_init(0)
 
     def step():
         ctx.set_values(h_dev, on_device=True)
-        ctx.solve_mu()
+        if fixed:
+            ctx.set_mu(float(w["mu"]))
+            ctx.build_density()
+        else:
+            ctx.solve_mu()
 
-    def timed(n_steps, prec):
+    def timed(n_steps, prec, mode="off", warmup=None):
         ctx.set_precision(prec)
-        for _ in range(args.warmup):
+        if model_path:
+            ctx.set_bound_model(mode, model_path if mode != "off" else None)
+        for _ in range(args.warmup if warmup is None else warmup):
             step()
         torch.cuda.synchronize()
         if pg:
@@ -483,33 +640,25 @@ def run_ours(args):
             ms = float(t.item())
         return ms, stats, clk
 
-    # -- the same form without the learned bound ----------------------------
-    plain_scaling = None
-    model_setup = None
-    if args.bound_model:
-        ms0, st0, _ = timed(args.steps, args.precision)
-        plain_scaling = {"value": args.steps * world / (ms0 / 1e3), "ms_per_step": ms0 / args.steps,
-                         "ns_ms_per_step": st0["ns_ms_total"] / args.steps, "iters_mean": st0["iters_mean"]}
-        # learned bound: trained on this system's own submatrices before timing (features and
-        # 48-step Lanczos labels at the solved mu, without and with the previous-step feature)
-        t0 = time.perf_counter()
-        ctx.set_precision(args.precision)
-        ctx.bound_model_init(w.get("seed", 0))
-        for _ in range(2):
-            ctx.set_values(h_dev, on_device=True)
-            ctx.solve_mu()
-            ctx.set_mu(ctx.get_trace()[2])
-            ctx.bound_model_collect(48)
-        loss = ctx.bound_model_train(epochs=args.model_epochs, batch=256, lr=2e-3)
-        ctx.set_bound_model(True)
-        torch.cuda.synchronize()
-        model_setup = {"seconds": time.perf_counter() - t0, "samples": 2 * sysm.n_blocks, "epochs": args.model_epochs,
-                       "train_loss": loss}
+    def summary(ms, st, n_steps):
+        return {"value": n_steps * world / (ms / 1e3), "ms_per_step": ms / n_steps,
+                "ns_ms_per_step": st["ns_ms_total"] / n_steps, "iters_mean": st["iters_mean"],
+                "iters_max": st["iters_max"], "fallbacks_per_step": st["n_bound_fallback"] / n_steps}
 
-    # -- mixed-precision form (the headline) --------------------------------
-    ms, st, clk = timed(args.steps, args.precision)
+    # -- the other spectral-bound modes (same form, same workload) -----------------
+    modes = {}
+    if model_path:
+        for mode in ["off", "rho", "gap"]:
+            if mode != args.bound_mode:
+                m0, s0, _ = timed(args.mode_steps, args.precision, mode, warmup=1)
+                modes[mode] = summary(m0, s0, args.mode_steps)
+
+    # -- the headline --------------------------------------------------------------
+    ms, st, clk = timed(args.steps, args.precision, args.bound_mode)
+    modes[args.bound_mode] = summary(ms, st, args.steps)
     tr, en, mu = ctx.get_trace()
     d_gpu = ctx.get_density()
+    dims_all, _, _ = ctx.get_submatrix_info()
     value = args.steps * world / (ms / 1e3)
     ns_flops = 4.0 * st["ns_work_n3"]
     ns_s = st["ns_ms_total"] / 1e3
@@ -518,11 +667,13 @@ def run_ours(args):
     peaks, peak_kind = _peaks()
     passes = 3 if args.precision == "fp16x3" else 1
     peak = peaks["bf16_tflops"] / passes
+    form = "on-chip form (kpad <= 192)" if int(np.max(dims_all)) <= 192 else "streamed form (kpad > 192)"
     roofline = {
-        "bound": "tensor", "kernel": f"k_ns_tc<{args.precision}>", "achieved": achieved, "peak": peak,
+        "bound": "tensor", "kernel": f"k_ns_tc<{args.precision}>, {form}", "achieved": achieved, "peak": peak,
         "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-        "note": f"achieved = sum_j 4 n_j^3 iters_j (true n) / summed NS-kernel event time; peak = {peak_kind} "
-                f"dense bf16/fp16 burst peak {peaks['bf16_tflops']} TF/s"
+        "note": f"achieved = sum_j 4 n_j^3 iters_j (true n; the kernel multiplies only the tiles on and right "
+                f"of the diagonal blocks of the symmetric products, the count stays 4 n^3) / summed NS-kernel "
+                f"event time; peak = {peak_kind} dense bf16/fp16 burst peak {peaks['bf16_tflops']} TF/s"
                 + (" / 3 (three fp16 products per multiply-add in the split form)" if passes == 3 else ""),
         "ns_share_of_step": (st["ns_ms_total"] / ms) if ms > 0 else None,
     }
@@ -535,42 +686,60 @@ def run_ours(args):
     h_np, d_np = h_host.numpy(), d_host.numpy()
     e2e_times = []
     bis_steps = []
-    for k in range(args.warmup + args.steps):
+    for k in range(args.warmup + args.e2e_steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.set_values(h_np)
-        ctx.solve_mu()
+        if fixed:
+            ctx.set_mu(float(w["mu"]))
+            ctx.build_density()
+        else:
+            ctx.solve_mu()
         ctx.get_density(d_np)
         ctx.get_trace()
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_times.append(t1 - t0)
-            bis_steps.append(ctx.get_stats()["bisection_steps"])
+            bis_steps.append(ctx.get_stats()["bisection_steps"] if not fixed else 1)
     e2e_s = sum(e2e_times)
     if pg:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e_s = float(t.item())
     nbytes = sysm.values.shape[0] * 8
-    e2e = {"value": args.steps * world / e2e_s, "unit": "density matrices/s", "h2d_bytes_per_step": nbytes,
+    e2e = {"value": args.e2e_steps * world / e2e_s, "unit": "density matrices/s", "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes + 24 * int(np.mean(bis_steps)) + 16}
 
     # -- the plain FP64 form on the same workload ------------------------------
     fp64 = None
     if not args.no_fp64:
-        ctx.set_bound_model(False)  # the plain form: Gershgorin start
-        ms64, st64, _ = timed(args.fp64_steps, "fp64")
-        d64 = ctx.get_density()
-        fp64 = {"value": args.fp64_steps * world / (ms64 / 1e3), "unit": "density matrices/s",
-                "ms_per_step": ms64 / args.fp64_steps,
-                "submatrix_tflops": 4.0 * st64["ns_work_n3"] / (ms64 / 1e3) / 1e12,
-                "max_abs_diff_vs_mixed": float(np.max(np.abs(d64 - d_gpu)))}
+        if model_path:
+            ctx.set_bound_model("off")  # the plain form: Gershgorin start
+        if big:
+            # FP64 on a column subset (one submatrix per SM), extrapolated by the work sum n_j^3
+            sub = min(int(dims_all.shape[0]), 152)
+            ctx.set_column_range(0, sub)
+            ms64, st64, _ = timed(1, "fp64", warmup=1)
+            ctx.set_column_range(0, int(dims_all.shape[0]))
+            d3 = dims_all.astype(np.float64) ** 3
+            scale = float(d3.sum() / d3[:sub].sum())
+            fp64 = {"value": world / (ms64 * scale / 1e3), "unit": "density matrices/s",
+                    "ms_per_step": ms64 * scale, "sample": f"block columns 0..{sub - 1} timed, x{scale:.1f} "
+                                                          f"(sum n_j^3 all / sample)",
+                    "submatrix_tflops": 4.0 * st64["ns_work_n3"] / (ms64 / 1e3) / 1e12}
+        else:
+            ms64, st64, _ = timed(args.fp64_steps, "fp64")
+            d64 = ctx.get_density()
+            fp64 = {"value": args.fp64_steps * world / (ms64 / 1e3), "unit": "density matrices/s",
+                    "ms_per_step": ms64 / args.fp64_steps,
+                    "submatrix_tflops": 4.0 * st64["ns_work_n3"] / (ms64 / 1e3) / 1e12,
+                    "max_abs_diff_vs_mixed": float(np.max(np.abs(d64 - d_gpu)))}
 
-    # -- a function form on the same machinery: A^-1/2 of an overlap matrix (FP64) --
+    # -- function forms on the same machinery (FP64, 1024-molecule inputs) ----------
     funcs = None
     nonorth = None
-    if not args.no_functions:
+    if not args.no_functions and args.workload == "water1024":
         funcs = function_leg(args, stream, flush, rank == 0 and not args.no_cpu)
         nonorth = nonorth_leg(args, stream, flush, rank == 0 and not args.no_cpu)
 
@@ -578,28 +747,31 @@ def run_ours(args):
     cpu = None
     acc = None
     if rank == 0 and not args.no_cpu:
-        workers = os.cpu_count() or 1
-        dt, cols, res, _ = _oracle_sample(sysm, w["eps"], mu, args.ref_columns, workers)
         import oracle as O
 
+        workers = os.cpu_count() or 1
+        n_cols = args.ref_columns if not big else min(args.ref_columns, 2 * workers)
+        dt, cols, res, (cp_f, ri_f) = _oracle_sample(sysm, w["eps"], mu, n_cols, workers)
         off = O.block_value_offsets(sysm.block_size, sysm.col_ptr, sysm.row_idx)
-        # eps filtering drops nothing on this workload unless reported otherwise
-        errs = []
-        cp_f, ri_f, _, keep = O.filter_blocks(sysm.block_size, sysm.col_ptr, sysm.row_idx, sysm.values, w["eps"])
-        if keep.all():
-            for j in cols:
-                sl = slice(off[sysm.col_ptr[j]], off[sysm.col_ptr[j + 1]])
-                errs.append(float(np.max(np.abs(d_gpu[sl] - res.values[sl]))))
-        acc = {"d_max_abs_err_sampled_columns": max(errs) if errs else None, "columns": len(cols),
-               "trace": tr, "energy": en, "mu": mu}
-        builds = int(np.mean(bis_steps)) if bis_steps else 1
-        per_dm = dt * sysm.n_blocks / len(cols) * builds
+        _, _, _, keep = O.filter_blocks(sysm.block_size, sysm.col_ptr, sysm.row_idx, sysm.values, w["eps"])
+        off_f = O.block_value_offsets(sysm.block_size, cp_f, ri_f)
+        kf = np.cumsum(keep) - 1
+        err = 0.0
+        for j in cols:  # the kept blocks of each sampled column (dropped blocks are zero on both sides)
+            for k in range(sysm.col_ptr[j], sysm.col_ptr[j + 1]):
+                a = d_gpu[off[k]:off[k + 1]]
+                b = res.values[off_f[kf[k]]:off_f[kf[k] + 1]] if keep[k] else np.zeros_like(a)
+                err = max(err, float(np.max(np.abs(a - b))))
+        acc = {"d_max_abs_err_sampled_columns": err, "columns": len(cols), "trace": tr, "energy": en, "mu": mu}
+        builds = int(round(np.mean(bis_steps))) if bis_steps else 1
+        scale = _work_scale(sysm.block_size, cp_f, ri_f, cols)
+        per_dm = dt * scale * builds
         cpu = {"value": 1.0 / per_dm, "unit": "density matrices/s", "cores": workers, "kind": "oracle",
                "sample": f"{len(cols)} of {sysm.n_blocks} block columns at the GPU's final mu, "
-                         f"time x{sysm.n_blocks}/{len(cols)} x{builds} bisection build(s)"}
+                         f"time x{scale:.1f} (sum n_j^3 all / sample) x{builds} bisection build(s)"}
 
     learned = None
-    if rank == 0 and world == 1 and args.learned_snapshots > 0:
+    if rank == 0 and world == 1 and args.learned_snapshots > 0 and args.workload == "water1024":
         learned = learned_scaling(args, stream)
 
     if rank == 0:
@@ -610,8 +782,11 @@ def run_ours(args):
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT.get(args.workload, args.workload),
                        "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
-                       "spectral_bound": ("learned (trained on this system's submatrices before timing)"
-                                          if args.bound_model else "a-posteriori Gershgorin"),
+                       "spectral_bound": {"off": "a-posteriori Gershgorin start, plain steps",
+                                          "rho": "learned rho_hat (held-out training), plain steps",
+                                          "gap": "learned rho_hat and gap (held-out training), scaled steps"}[
+                           args.bound_mode],
+                       "mu": "fixed" if fixed else "bisection (tol 1e-2)",
                        "bisection_builds_per_step": float(np.mean(bis_steps)) if bis_steps else None,
                        "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
             "submatrix_tflops": submatrix_tflops,
@@ -627,10 +802,11 @@ def run_ours(args):
             "gpu_launches": gpu_launches,
             "iters": {"min": st["iters_min"], "max": st["iters_max"], "mean": st["iters_mean"]},
             "dims": {"min": st["dim_min"], "max": st["dim_max"], "mean": st["dim_mean"]},
+            "bound_model": ({"headline_mode": args.bound_mode, "training": model_info, "modes": modes,
+                             "fallback_rate": st["n_bound_fallback"] / (sysm.n_blocks * args.steps
+                                                                      * max(1.0, float(np.mean(bis_steps))))}
+                            if model_path else None),
             "learned_scaling": learned,
-            "bound_model": ({"headline_uses_learned_bound": True, "setup": model_setup,
-                             "fallback_rate": st["n_bound_fallback"] / sysm.n_blocks,
-                             "without_learned_bound": plain_scaling} if args.bound_model else None),
         }
         print(json.dumps(out))
     ctx.close()
@@ -647,6 +823,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water1024")
     ap.add_argument("--precision", default="fp16x3", choices=["fp16x3", "fp16", "bf16", "fp64"])
+    ap.add_argument("--bound-mode", default="gap", choices=["off", "rho", "gap"],
+                    help="spectral bound of the headline: off, learned rho_hat, or rho_hat and gap (scaled steps)")
+    ap.add_argument("--model-systems", type=int, default=2, help="held-out systems the learned bound trains on")
+    ap.add_argument("--model-epochs", type=int, default=100)
+    ap.add_argument("--mode-steps", type=int, default=5, help="timed steps of each non-headline bound mode")
+    ap.add_argument("--e2e-steps", type=int, default=None, help="end-to-end steps (default: --steps)")
+    ap.add_argument("--max-steps", type=int, default=30, help="bisection steps at most")
+    ap.add_argument("--shard", action="store_true",
+                    help="one system split over the ranks by block columns (strong scaling)")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--ref-columns", type=int, default=128)
     ap.add_argument("--no-fp64", action="store_true")
@@ -656,10 +841,9 @@ def main():
     ap.add_argument("--learned-snapshots", type=int, default=200,
                     help="trajectory length of the learned-bound report (0 skips it)")
     ap.add_argument("--learned-epochs", type=int, default=40)
-    ap.add_argument("--no-bound-model", dest="bound_model", action="store_false",
-                    help="time the headline without the learned spectral bound")
-    ap.add_argument("--model-epochs", type=int, default=100)
     args = ap.parse_args()
+    if args.e2e_steps is None:
+        args.e2e_steps = args.steps
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -330,14 +330,39 @@ smx_status smx_bound_model_fit(smx_ctx* ctx, const float* x, const float* t, int
  * Synchronises. */
 smx_status smx_bound_model_predict(smx_ctx* ctx, float* features, float* pred, float* labels, int32_t lanczos_steps);
 
-/* Enables (1) or disables (0) the model in builds; weights_path, if not NULL,
- * loads parameters saved by smx_bound_model_save.  Errors: SMX_ERR_ARG (bad
- * file), SMX_ERR_STATE (enabling a model that was never initialised). */
+/* Enables or disables the model in builds; weights_path, if not NULL, loads
+ * parameters saved by smx_bound_model_save.
+ *  enable = 0: off (X0 = A / G, first step scaled by 1.2/s, plain steps).
+ *  enable = 1: on, with both predictions: after the check on rho_hat passes,
+ *              the predicted gap sets the scaled schedule of the Newton-Schulz
+ *              steps, X_{k+1} = p(a_k X_k) with p(x) = x (3 - x^2)/2,
+ *              a_k = min(sqrt(3 / (1 + l_k + l_k^2)), 1.72), l_0 =
+ *              delta_hat / (b s) and l_{k+1} = p(a_k l_k) (the interval
+ *              [l_k, 1] of |eigenvalues| maps into [l_{k+1}, 1]); any l_0 in
+ *              (0, 1] converges, a poor prediction only costs steps.
+ *  enable = 2: on, rho_hat only (the start scaling; plain steps).
+ * The sign the iteration converges to does not depend on the mode (Eq. 13).
+ * Errors: SMX_ERR_ARG (bad file, enable outside 0..2), SMX_ERR_STATE
+ * (enabling a model that was never initialised). */
 smx_status smx_set_bound_model(smx_ctx* ctx, int32_t enable, const char* weights_path);
 
 /* Writes the parameters to a binary file: 8-byte magic "SMXBNDM1", int32
  * count, count floats, uint64 checksum (FNV-1a of the float bytes). */
 smx_status smx_bound_model_save(smx_ctx* ctx, const char* path);
+
+/* Failure-detection self-test of the bounded device waits (the paper has no
+ * counterpart).  Every wait of the library's kernels on an mbarrier gives up
+ * after a fixed number of polls, records SMX_ERR_TIMEOUT in the context's
+ * status word and lets the kernel return (after draining its own copies and
+ * tensor-core work), so that a lost arrival surfaces as an error instead of a
+ * hung GPU.  This call exercises that path safely: one thread of a one-CTA
+ * kernel waits on a fresh mbarrier that nothing arrives at, with no
+ * asynchronous copy or tensor-core operation in flight, and gives up after
+ * poll_limit polls (1 .. 2^26).  Synchronises and returns SMX_ERR_TIMEOUT
+ * (SMX_OK would mean the wait completed, which cannot happen); the error stays
+ * latched until the next smx_build_density / smx_solve_mu, and the context
+ * stays usable.  Errors: SMX_ERR_ARG, SMX_ERR_CUDA. */
+smx_status smx_selftest_wait_timeout(smx_ctx* ctx, uint32_t poll_limit);
 
 /* Zeroes the accumulated counters of smx_stats.  Synchronises the stream. */
 smx_status smx_reset_counters(smx_ctx* ctx);

@@ -170,6 +170,11 @@ class SubmatrixDensity:
         check(self._lib.smx_get_stats(self._ctx, C.byref(s)), "smx_get_stats")
         return s.as_dict()
 
+    def selftest_wait_timeout(self, poll_limit: int = 1 << 16) -> int:
+        """Runs the bounded-wait self-test (smx_selftest_wait_timeout); returns its status code
+        (ERR_TIMEOUT when the wait gave up as designed) without raising."""
+        return int(self._lib.smx_selftest_wait_timeout(self._ctx, C.c_uint32(int(poll_limit))))
+
     def reset_counters(self):
         check(self._lib.smx_reset_counters(self._ctx), "smx_reset_counters")
 
@@ -225,9 +230,13 @@ class SubmatrixDensity:
               "smx_bound_model_predict")
         return f, p, lab
 
-    def set_bound_model(self, enable: bool, weights_path: str | None = None):
+    def set_bound_model(self, enable=True, weights_path: str | None = None):
+        """enable: False / "off" (0), True / "gap" (1: rho_hat and the gap-driven scaled
+        schedule) or "rho" (2: rho_hat only); see smx_set_bound_model."""
+        modes = {"off": 0, "gap": 1, "rho": 2}
+        mode = modes[enable] if isinstance(enable, str) else int(enable)
         path = weights_path.encode() if weights_path is not None else None
-        check(self._lib.smx_set_bound_model(self._ctx, 1 if enable else 0, path), "smx_set_bound_model")
+        check(self._lib.smx_set_bound_model(self._ctx, mode, path), "smx_set_bound_model")
 
     def bound_model_save(self, path: str):
         check(self._lib.smx_bound_model_save(self._ctx, path.encode()), "smx_bound_model_save")

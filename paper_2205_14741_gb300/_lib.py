@@ -87,6 +87,7 @@ SIGNATURES = {
     "smx_bound_model_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "smx_set_bound_model": (C.c_int, [C.c_void_p, C.c_int32, C.c_char_p]),
     "smx_bound_model_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "smx_selftest_wait_timeout": (C.c_int, [C.c_void_p, C.c_uint32]),
     "smx_reset_counters": (C.c_int, [C.c_void_p]),
     "smx_get_submatrix_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "smx_dense_density_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),

@@ -22,10 +22,11 @@ constexpr int kTile = 64;
 constexpr int kKc = 16;
 
 // C = A B (n x n, row-major, leading dimension ld).  mode 1 writes
-// 3/2 I - 1/2 A B and returns this thread's share of ||A B - I||_F^2;
-// mode 2 writes oscale * A B.
+// dg I + cf A B (3/2 I - 1/2 A B by default) and returns this thread's share of
+// ||A B - I||_F^2; mode 2 writes oscale * A B.
 __device__ double gemm_fp64(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C, int n,
-                            int ld, int mode, double (*As)[kTile + 1], double (*Bs)[kTile + 1], double oscale = 1.0) {
+                            int ld, int mode, double (*As)[kTile + 1], double (*Bs)[kTile + 1], double oscale = 1.0,
+                            double cf = -0.5, double dg = 1.5) {
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     double r2 = 0.0;
     for (int r0 = 0; r0 < n; r0 += kTile) {
@@ -72,7 +73,7 @@ __device__ double gemm_fp64(const double* __restrict__ A, const double* __restri
                     const double v = acc[i][j];
                     if (mode == 1) {
                         const double dlt = (row == col) ? 1.0 : 0.0;
-                        C[static_cast<int64_t>(row) * ld + col] = 1.5 * dlt - 0.5 * v;
+                        C[static_cast<int64_t>(row) * ld + col] = dg * dlt + cf * v;
                         r2 += (v - dlt) * (v - dlt);
                     } else {
                         C[static_cast<int64_t>(row) * ld + col] = oscale * v;
@@ -215,6 +216,10 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
         __syncthreads();
     }
     const double inv_b = 1.0 / a.bound[blockIdx.x];
+    // learned bound: the predicted smallest |eigenvalue| of X0 = (T_j - mu I) / b_j (negative:
+    // no prediction), and the lower end the scaled schedule assumes (1 = plain steps)
+    const double dhat = a.pred ? a.pred[2 * blockIdx.x + 1] * a.gersh[blockIdx.x] * inv_b : -1.0;
+    double lsch = 1.0, acur = 1.0;
     for (int r = threadIdx.x / 32; r < n; r += 8)
         for (int c = threadIdx.x & 31; c < n; c += 32) X[static_cast<int64_t>(r) * ld + c] *= inv_b;
     __syncthreads();
@@ -310,8 +315,19 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
             const double smax = sqrt(best * (1.0 + 1e-12));
             double scale = smax > 0.0 ? 1.2 / smax : 1.0;
             if (a.use_model && smax > 0.0) {  // same rule as the tensor-core kernel
-                if (smax <= 1.7) scale = fmax(1.0, scale);
-                else if (threadIdx.x == 0) atomicAdd(a.fallbacks, 1);
+                const bool gap = dhat > 0.0;
+                if (gap ? dhat <= smax : smax <= 1.7) {
+                    if (gap) {  // the scaled schedule from l0 = dhat / s
+                        const double l0 = dhat / smax;
+                        const double a0 = ns_scale(l0);
+                        scale = a0 / smax;
+                        lsch = ns_next_lower(a0, l0);
+                    } else {
+                        scale = fmax(1.0, scale);
+                    }
+                } else if (threadIdx.x == 0) {
+                    atomicAdd(a.fallbacks, 1);
+                }
             }
             const double sc2 = scale * scale;
             for (int r = threadIdx.x / 32; r < n; r += 8)
@@ -327,7 +343,17 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
             __syncthreads();
             oscale = scale;
         } else {
-            r2 = gemm_fp64(X, X, Y, n, ld, 1, As, Bs);
+            // Y = a (3/2 I - a^2/2 X^2) on the scaled schedule (a = 1: a plain step)
+            double cf = -0.5, dg = 1.5;
+            acur = 1.0;
+            if (lsch < 1.0) {
+                const double f = ns_scale(lsch);
+                cf = -0.5 * f * f * f;
+                dg = 1.5 * f;
+                lsch = ns_next_lower(f, lsch);
+                acur = f;
+            }
+            r2 = gemm_fp64(X, X, Y, n, ld, 1, As, Bs, 1.0, cf, dg);
             r2 = block_sum(r2, scratch);
         }
         gemm_fp64(X, Y, Z, n, ld, 2, As, Bs, oscale);
@@ -335,7 +361,12 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
         double* tmp = X; X = Z; Z = tmp;
         done = it + 1;
         if (!isfinite(r2)) { bad = true; break; }
-        if (it > 0 && sqrt(r2) <= a.tau) { conv = true; break; }
+        if (it > 0 && sqrt(r2) <= a.tau) {
+            // stop after this step unless it was a scaled step whose factor moves converged
+            // eigenvalues off 1 (p(a) ~ 1 - 1.5 (a - 1)^2): then plain steps from here
+            if (acur - 1.0 <= 2e-6) { conv = true; break; }
+            lsch = 1.0;
+        }
     }
     if (threadIdx.x == 0) {
         a.iters[s.col] = done;

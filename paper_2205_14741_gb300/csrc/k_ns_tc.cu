@@ -50,6 +50,14 @@ constexpr uint32_t kABytes = 128 * 128;  // 128 rows x 64 K x 2 B
 // On-chip prologue: T_j's rows pass through two staging buffers after the images (at most
 // 2 x 72 KB; the second hi image of the double-buffered form is free until iteration 0).
 constexpr uint32_t kStageOff = 144u * 1024u;
+// On-chip form: the per-warp 32 x 32 transpose buffers (rows 80 bytes apart) after the images
+// and the corner operand (for split operands at 192 KB, single ones at 96 KB; free during the
+// iterations; the prologue's staging buffers are dead by then)
+constexpr uint32_t kXsOff = 96u * 1024u;  // times the operand count NB
+constexpr uint32_t kXsWarp = 32 * 80;
+// A step with factor a maps an eigenvalue at 1 to p(a) ~ 1 - 1.5 (a - 1)^2: the last step may
+// use a up to 1 + kStopSlack (a shift of at most 1.4e-7, far below the split form's error).
+constexpr float kStopSlack = 3e-4f;
 
 template <int PREC>
 struct TcCfg {
@@ -63,8 +71,15 @@ struct TcCfg {
     // images (72 KB each), the corner operand Bz (hi and lo, 24 KB each) and 8 KB read past the
     // lo image by the last row tile's MMAs, inside a reserve of three images plus 8 KB
     static constexpr size_t kResSmem = static_cast<size_t>(kNb + 1) * 9 * 8192 + 8192;
-    static constexpr size_t kDynSmem = 1024 + (static_cast<size_t>(kStages) * kStage > kResSmem
-                                                   ? static_cast<size_t>(kStages) * kStage : kResSmem);
+    // the streamed form's per-warp transpose buffers (8 epilogue warps, 32 rows of 80 bytes) after its stages
+    static constexpr uint32_t kXposeWarp = 32 * 80;
+    static constexpr uint32_t kXposeOff = static_cast<uint32_t>(kStages) * kStage;
+    static constexpr size_t kStreamSmem = static_cast<size_t>(kXposeOff) + 8 * kXposeWarp;
+    static constexpr size_t kDynSmem = 1024 + (kStreamSmem > kResSmem ? kStreamSmem : kResSmem);
+    static_assert(kDynSmem <= 227 * 1024, "shared memory per CTA");
+    static_assert(static_cast<size_t>(kXsOff) * kNb + 12 * kXsWarp <= kDynSmem - 1024, "on-chip transpose buffers");
+    static_assert(kXsOff * kNb >= static_cast<uint32_t>(kNb) * 9 * 8192 + static_cast<uint32_t>(kNb) * 3 * 8192,
+                  "transpose buffers after the images and the corner operand");
     // each of the on-chip prologue's two staging buffers: what the allocation leaves after kStageOff
     static constexpr uint32_t kStageBuf = static_cast<uint32_t>((kDynSmem - 1024 - kStageOff) / 2) & ~15u;
     static_assert(kDynSmem - 1024 >= kStageOff + 2 * static_cast<size_t>(kStageBuf) && kStageBuf >= 16u * 1024u,
@@ -251,6 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     __shared__ uint64_t full_bar[S], empty_bar[S], tfull[2], tempty[2], drain_bar;
     __shared__ uint32_t tmem_base_s;
     __shared__ int abort_s, job_s, conv_s, bad_s, p_issued_s, m_consumed_s;
+    __shared__ int plain_s;  // the scaled schedule is over: plain steps from the next one
     __shared__ float resid_s[kEpiWarps];
     __shared__ uint64_t mma_bar, mma_bar2;
     __shared__ float resid_s2[kThreads / 32];
@@ -316,18 +332,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     uint32_t mma_ph = 0, mma_ph2 = 0;  // completed phases of mma_bar, mma_bar2 (uniform over the CTA)
     const uint32_t idesc_b_mn = 1u << 16;  // B operand MN-major
 
-    // C = A * B over K in [0, kpad), written to buffer zo (rows and columns < kpad).
-    // mode 1: zo = 3/2 I - 1/2 A A, residual ||A A - I||_F^2 accumulated;
-    // mode 2: zo = oscale * A B;
-    // mode 3: zo = A B and rsum[(2 nt + half) kpad + r] = sum of |C_rc| over the columns of
-    //         N tile nt that epilogue half "half" drains (rows r < n).
-    auto gemm = [&](int kpad, int n, int mode, int za, int zb, int zo, float oscale, float* rsum) {
-        const int mtiles = (kpad + 127) / 128, ntiles = (kpad + NT - 1) / NT, kchunks = (kpad + 63) / 64;
+    // C = A * B over K in [0, kpad), written to buffer zo (rows and columns < kpad).  Every
+    // product of the iteration is symmetric (X X, and X Y with Y a polynomial in X), so only
+    // the tiles on and right of the diagonal 128 x 128 blocks are multiplied: row tile mt
+    // covers columns 128 mt .. kpad - 1.  Each epilogue warp owns 32 rows; of a tile's
+    // 32 x 32 chunks it writes those right of its diagonal chunk together with their transposes
+    // (through a per-warp shared-memory transpose) and the diagonal chunk's upper triangle
+    // mirrored into its lower one, so zo holds an exactly symmetric matrix.  (An iterate whose
+    // diagonal blocks kept the rounding asymmetry of the products while the rest is mirrored
+    // would let that asymmetry grow from step to step.)
+    // mode 1: zo = oscale A A + dg I (3/2 I - 1/2 A A for a plain step), residual
+    //         ||A A - I||_F^2 accumulated over the chunks written (transposed ones count twice);
+    // mode 2: zo = oscale * A B.
+    auto gemm = [&](int kpad, int n, int mode, int za, int zb, int zo, float oscale, float dg = 1.5f) {
+        const int mtiles = (kpad + 127) / 128, kchunks = (kpad + 63) / 64;
+        // row tile mt: N tiles of up to NT columns from column 128 mt
+        auto ntiles_of = [&](int mt) { return (kpad - 128 * mt + NT - 1) / NT; };
         if (warp == 0) {
             if (lane == 0) {
                 for (int mt = 0; mt < mtiles && !*abortp; ++mt)
-                    for (int nt = 0; nt < ntiles && !*abortp; ++nt) {
-                        const int nn = min(NT, kpad - NT * nt);
+                    for (int nt = 0; nt < ntiles_of(mt) && !*abortp; ++nt) {
+                        const int n0 = 128 * mt + NT * nt, nn = min(NT, kpad - n0);
                         for (int kc = 0; kc < kchunks; ++kc) {
                             const int stage = p_it % S;
                             const uint32_t round = p_it / S;
@@ -341,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                 tma_load_3d(sa + 8192, &tmap, kc * 64, 128 * mt + 64, za + b, &full_bar[stage]);
                                 uint8_t* sb = st + NB * kABytes + b * C::kBBytes;
                                 for (int h = 0; h < nboxes; ++h)
-                                    tma_load_3d(sb + h * 8192, &tmap, NT * nt + 64 * h, kc * 64, zb + b, &full_bar[stage]);
+                                    tma_load_3d(sb + h * 8192, &tmap, n0 + 64 * h, kc * 64, zb + b, &full_bar[stage]);
                             }
                             ++p_it;
                         }
@@ -352,8 +377,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         } else if (warp == 1) {
             if (lane == 0) {
                 for (int mt = 0; mt < mtiles && !*abortp; ++mt)
-                    for (int nt = 0; nt < ntiles && !*abortp; ++nt) {
-                        const int nn = min(NT, kpad - NT * nt);
+                    for (int nt = 0; nt < ntiles_of(mt) && !*abortp; ++nt) {
+                        const int nn = min(NT, kpad - 128 * mt - NT * nt);
                         const uint32_t abuf = m_tile & 1, around = m_tile >> 1;
                         if (around > 0 && !mbar_wait(&tempty[abuf], (around - 1) & 1, &abort_s, a.status)) break;
                         tc_fence_after();
@@ -392,10 +417,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         } else if (warp >= 4) {
             const int q = warp & 3, half = (warp - 4) >> 2;
             const int lrow = q * 32 + lane;
+            // this warp's transpose buffer: 32 rows of 32 16-bit values, rows 80 bytes apart
+            // (conflict-free 16-byte row writes, 2-byte column reads)
+            uint16_t* xs = reinterpret_cast<uint16_t*>(smem + C::kXposeOff + (warp - 4) * C::kXposeWarp);
             float r2 = 0.0f;
             for (int mt = 0; mt < mtiles; ++mt)
-                for (int nt = 0; nt < ntiles; ++nt) {
-                    const int nn = min(NT, kpad - NT * nt);
+                for (int nt = 0; nt < ntiles_of(mt); ++nt) {
+                    const int n0 = 128 * mt + NT * nt, nn = min(NT, kpad - n0);
                     const uint32_t abuf = e_tile & 1, around = e_tile >> 1;
                     int ok = 1;
                     if (lane == 0) ok = mbar_wait(&tfull[abuf], around & 1, &abort_s, a.status) ? 1 : 0;
@@ -403,18 +431,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     if (!ok) { mt = mtiles; break; }
                     tc_fence_after();
                     const int row = 128 * mt + lrow;
-                    uint16_t* out_hi = ws + static_cast<int64_t>(zo) * buf + static_cast<int64_t>(row) * a.ld;
+                    uint16_t* zo_hi = ws + static_cast<int64_t>(zo) * buf;
+                    uint16_t* out_hi = zo_hi + static_cast<int64_t>(row) * a.ld;
                     uint16_t* out_lo = out_hi + buf;
-                    float ra = 0.0f;  // mode 3: this thread's share of the row's abs sum
                     for (int c0 = 32 * half; c0 < nn; c0 += 64) {
                         uint32_t raw[32];
                         tmem_ld32_issue(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + abuf * 256 + c0, raw);
                         tmem_wait_ld();
-                        if (row < kpad) {
-                            const int col0 = NT * nt + c0;
+                        const int r0 = row - lane;  // the warp's first row
+                        const int col0 = n0 + c0;
+                        // chunks left of the warp's diagonal chunk are not written: the transposes of
+                        // the chunks right of it fill them (all warp-uniform; kpad is a multiple of 32)
+                        if (r0 < kpad && col0 >= r0) {
+                            const bool xp = col0 > r0;  // right of the diagonal chunk: also transposed
                             const bool interior = row < n && col0 + 32 <= n;
                             const int i0 = row - col0;  // position of the diagonal in this chunk, if 0 <= i0 < 32
-                            float y[32];
+                            float y[32], rc = 0.0f;
                             if (interior) {
                                 if (mode == 1) {
                                     float sq = 0.0f, dv = 0.0f;
@@ -422,18 +454,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                     for (int i = 0; i < 32; ++i) {
                                         const float v = __uint_as_float(raw[i]);
                                         sq = fmaf(v, v, sq);
-                                        y[i] = -0.5f * v;
-                                        if (i == i0) { y[i] += 1.5f; dv = v; }
+                                        y[i] = oscale * v;
+                                        if (i == i0) { y[i] += dg; dv = v; }
                                     }
                                     // sum (v - delta)^2 = sum v^2 - 2 v_diag + 1 when the diagonal is here
-                                    r2 += (i0 >= 0 && i0 < 32) ? sq - 2.0f * dv + 1.0f : sq;
+                                    rc = (i0 >= 0 && i0 < 32) ? sq - 2.0f * dv + 1.0f : sq;
                                 } else {
 #pragma unroll
                                     for (int i = 0; i < 32; ++i) y[i] = oscale * __uint_as_float(raw[i]);
-                                    if (mode == 3) {
-#pragma unroll
-                                        for (int i = 0; i < 32; ++i) ra += fabsf(y[i]);
-                                    }
                                 }
                             } else {
 #pragma unroll
@@ -443,28 +471,65 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                     if (mode == 1) {
                                         const float dl = (i == i0) ? 1.0f : 0.0f;
                                         const float e = v - dl;
-                                        y[i] = valid ? fmaf(-0.5f, v, 1.5f * dl) : 0.0f;
-                                        r2 = valid ? fmaf(e, e, r2) : r2;
+                                        y[i] = valid ? fmaf(oscale, v, dg * dl) : 0.0f;
+                                        rc = valid ? fmaf(e, e, rc) : rc;
                                     } else {
                                         y[i] = valid ? oscale * v : 0.0f;
-                                        if (mode == 3) ra += fabsf(y[i]);
                                     }
                                 }
                             }
+                            r2 += xp ? 2.0f * rc : rc;
                             uint32_t hw[16], lw[16];
 #pragma unroll
                             for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
-                            uint4* dh = reinterpret_cast<uint4*>(out_hi + col0);
+                            // the warp's 32 x 32 block through shared memory: lane l reads column l,
+                            // i.e. element (r0 + k, col0 + l) for k = 0 .. 31
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) dh[u] = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
-                            if constexpr (NB == 2) {
-                                uint4* dlo = reinterpret_cast<uint4*>(out_lo + col0);
+                            for (int b = 0; b < NB; ++b) {
+                                const uint32_t* w = b == 0 ? hw : lw;
+                                uint16_t* dst_row = (b == 0 ? out_hi : out_lo) + col0;
+                                if (!xp) {
+                                    // the diagonal chunk: its upper triangle (own row from the diagonal
+                                    // on), mirrored into the lower one, so the stored iterate is exactly
+                                    // symmetric
+                                    __syncwarp();
+                                    uint4* xr = reinterpret_cast<uint4*>(xs + lane * 40);
 #pragma unroll
-                                for (int u = 0; u < 4; ++u) dlo[u] = make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
+                                    for (int u = 0; u < 4; ++u) xr[u] = make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+                                    __syncwarp();
+                                    uint32_t t[16];
+#pragma unroll
+                                    for (int k = 0; k < 16; ++k) {
+                                        const uint32_t e0 = 2 * k < lane ? static_cast<uint32_t>(xs[(2 * k) * 40 + lane]) : (w[k] & 0xFFFFu);
+                                        const uint32_t e1 = 2 * k + 1 < lane ? static_cast<uint32_t>(xs[(2 * k + 1) * 40 + lane]) : (w[k] >> 16);
+                                        t[k] = e0 | (e1 << 16);
+                                    }
+                                    uint4* d = reinterpret_cast<uint4*>(dst_row);
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) d[u] = make_uint4(t[4 * u], t[4 * u + 1], t[4 * u + 2], t[4 * u + 3]);
+                                } else {
+                                    uint4* d = reinterpret_cast<uint4*>(dst_row);
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) d[u] = make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+                                    // element (row, col0 + k) -> (col0 + k, row): lane l writes row col0 + l,
+                                    // columns r0 .. r0 + 31 (64 contiguous bytes)
+                                    __syncwarp();
+                                    uint4* xr = reinterpret_cast<uint4*>(xs + lane * 40);
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) xr[u] = make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+                                    __syncwarp();
+                                    uint32_t t[16];
+#pragma unroll
+                                    for (int k = 0; k < 16; ++k)
+                                        t[k] = static_cast<uint32_t>(xs[(2 * k) * 40 + lane]) |
+                                               (static_cast<uint32_t>(xs[(2 * k + 1) * 40 + lane]) << 16);
+                                    uint4* dt = reinterpret_cast<uint4*>(zo_hi + b * buf + static_cast<int64_t>(col0 + lane) * a.ld + r0);
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) dt[u] = make_uint4(t[4 * u], t[4 * u + 1], t[4 * u + 2], t[4 * u + 3]);
+                                }
                             }
                         }
                     }
-                    if (mode == 3 && row < n) rsum[(2 * nt + half) * kpad + row] = ra;  // summed in order later
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&tempty[abuf]);
@@ -499,6 +564,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         const int j = a.order[job];
         const SubDesc s = a.subs[j];
         const int kpad = (s.n + 31) & ~31;  // MMA extent; TMA moves 64-wide boxes
+        // learned bound: the predicted smallest |eigenvalue| of X0 = (T_j - mu I) / b_j (read
+        // before this job rewrites b_j; negative when there is no prediction)
+        const float dhat = a.pred ? a.pred[2 * j + 1] * static_cast<float>(a.gersh[j] / a.bound[j]) : -1.0f;
+        // lower end of the interval the scaled schedule assumes for the current iterate's
+        // |eigenvalues| (1 = plain steps), and the factor a of the current step
+        float lsch = 1.0f, acur = 1.0f;
 
         const int zx0 = slot_z + 0, zx1 = slot_z + 2, zy = slot_z + 4;
 
@@ -565,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             }
             cp_async_wait<0>();
             fence_proxy_async_smem();
-            if (tid == 0) { conv_s = 0; bad_s = 0; }
+            if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; }
             __syncthreads();
         } else {
             const float inv_b = static_cast<float>(1.0 / a.bound[j]);
@@ -604,10 +675,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
             }
             fence_proxy_async_global();
-            if (tid == 0) { conv_s = 0; bad_s = 0; }
+            if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; }
             __syncthreads();
         }
 
+        // The factor c of the first step X1 = p(c X0), p(x) = x (3 - x^2) / 2, from the guaranteed
+        // bound smax >= rho(X0) (every thread gets the same c and lsch).  Without the learned
+        // bound X0 = A / G and c = 1.2 / s, then plain steps.  With rho_hat only, the prediction
+        // passes the check when s <= 1.7 < sqrt 3 (rho_hat was not an underestimate beyond
+        // that) and its scaling is kept, c = max(1, 1.2 / s).  With the predicted gap, the steps
+        // follow the scaled schedule from l0 = dhat / s, c = ns_scale(l0) / s; the check is
+        // dhat <= s (the gap cannot exceed the spectral radius), and the schedule converges
+        // for any l0 in (0, 1].  A failed check falls back to c = 1.2 / s and plain steps (counted).
+        auto start_factor = [&](float smax) -> float {
+            float c = smax > 0.0f ? 1.2f / smax : 1.0f;
+            if (a.use_model && smax > 0.0f) {
+                const bool gap = dhat > 0.0f;
+                if (gap ? dhat <= smax : smax <= 1.7f) {
+                    if (gap) {
+                        const float l0 = dhat / smax;
+                        const float a0 = ns_scale(l0);
+                        c = a0 / smax;
+                        lsch = ns_next_lower(a0, l0);
+                    } else {
+                        c = fmaxf(1.0f, c);
+                    }
+                } else if (tid == 0) {
+                    atomicAdd(a.fallbacks, 1);
+                }
+            }
+            return c;
+        };
+        // the constants of a later step X' = p(a X) = alpha (Z - shift I) X, Z = X^2:
+        // shift = 3 / a^2, alpha = -a^3 / 2 (a = 1: a plain step)
+        auto next_step = [&](float& shift, float& alpha) {
+            if (plain_s) lsch = 1.0f;
+            acur = 1.0f;
+            if (lsch < 1.0f) {
+                const float f = ns_scale(lsch);
+                shift = 3.0f / (f * f);
+                alpha = -0.5f * f * f * f;
+                lsch = ns_next_lower(f, lsch);
+                acur = f;
+            }
+        };
+        // The stopping rule (tid 0, after the residual ||X^2 - I||_F of the current step):
+        // stop after this step when the residual is <= tau, unless the step is a scaled one
+        // whose factor would move converged eigenvalues off 1 (p(a) = 1 - 1.5 (a - 1)^2 + ...);
+        // then the schedule ends and the next steps are plain.
+        auto converged = [&](double resid) {
+            if (acur - 1.0f <= kStopSlack) conv_s = 1;
+            else plain_s = 1;
+            (void)resid;
+        };
         int cur = 0, done = 0;
         if (resident) {
             // ---------------------------------------------------------------
@@ -801,11 +921,50 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     }
                 }
             };
+            // Mirror of a 32 x 32 chunk of the iterate inside a diagonal block: the warp's rows
+            // r0 .. r0 + 31, image columns c0 .. c0 + 31 (hi / lo pairs of the thread's row in
+            // hw / lw), through the warp's transpose buffer.  Right of the warp's diagonal chunk
+            // (c0 > r0) the chunk is also written transposed, as rows c0 .. c0 + 31 of columns
+            // r0 .. r0 + 31; the diagonal chunk (c0 == r0) is written with its lower triangle
+            // replaced by the mirror of its upper one.  So the iterate in the image is exactly
+            // symmetric there (left as computed, its rounding asymmetry would grow from step to
+            // step).  Lane l writes one row of 64 contiguous bytes per hi / lo image.
+            uint16_t* xsw = reinterpret_cast<uint16_t*>(smem + kXsOff * NB + static_cast<uint32_t>(warp) * kXsWarp);
+            auto mirror_chunk = [&](const uint32_t (&hw)[16], const uint32_t (&lw)[16], int r0, int c0, bool diag) {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    const uint32_t* w = b == 0 ? hw : lw;
+                    __syncwarp();
+                    uint4* xr = reinterpret_cast<uint4*>(xsw + lane * 40);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) xr[u] = make_uint4(w[4 * u], w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+                    __syncwarp();
+                    uint32_t t[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const uint32_t x0 = xsw[(2 * k) * 40 + lane], x1 = xsw[(2 * k + 1) * 40 + lane];
+                        if (diag) {  // own row from the diagonal on, the mirror left of it
+                            t[k] = (2 * k < lane ? x0 : (w[k] & 0xFFFFu)) | ((2 * k + 1 < lane ? x1 : (w[k] >> 16)) << 16);
+                        } else {
+                            t[k] = x0 | (x1 << 16);
+                        }
+                    }
+                    const uint32_t base = b == 0 ? hi_off : lo_off;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        *reinterpret_cast<uint4*>(smem + base + img_offset(c0 + lane, r0 + 8 * u, RB)) =
+                            make_uint4(t[4 * u], t[4 * u + 1], t[4 * u + 2], t[4 * u + 3]);
+                }
+            };
             // drain: X'_t = alpha C (its padding is zero already) into the image (hi at hi_dst)
             // keep_a: also leave X' in the accumulator columns as the packed A operand (16 columns
             // of hi pairs, then 16 of lo pairs per 32-column chunk) of the next iteration's X X
+            // (as computed: the mirror makes only the image exactly symmetric)
+            // In the diagonal block (columns < 128) a warp writes the chunks from its diagonal
+            // chunk on and mirrors them; the chunks left of it are the mirrors of other warps'.
             auto drain = [&](int t, uint32_t acc, float alpha, uint32_t hi_dst, bool keep_a = false) {
                 const int row = 128 * t + 32 * q + lane;
+                const int crow0 = 32 * q;  // the warp's first row inside the tile
                 if (row - lane >= kpad) return;  // the warp's rows are all padding (kpad is a multiple of 32)
 #pragma unroll 1
                 for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
@@ -818,14 +977,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
+                    const bool in_diag = c0 < 128;
+                    if (!in_diag || c0 > crow0) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t off = img_offset(row, c0 + 8 * u, RB);
-                        *reinterpret_cast<uint4*>(smem + hi_dst + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
-                        if constexpr (NB == 2)
-                            *reinterpret_cast<uint4*>(smem + lo_off + off) =
-                                make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
+                        for (int u = 0; u < 4; ++u) {
+                            const uint32_t off = img_offset(row, c0 + 8 * u, RB);
+                            *reinterpret_cast<uint4*>(smem + hi_dst + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                            if constexpr (NB == 2)
+                                *reinterpret_cast<uint4*>(smem + lo_off + off) =
+                                    make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
+                        }
                     }
+                    if (in_diag && c0 >= crow0) mirror_chunk(hw, lw, 128 * t + crow0, c0, c0 == crow0);
                     if (keep_a) {
                         uint32_t w[32];
 #pragma unroll
@@ -857,13 +1020,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     }
                 }
             };
-            // the corner of X' = alpha C (accumulator at acc, wc columns) into rows and columns 128 ..
+            // the corner of X' = alpha C (accumulator at acc, wc columns) into rows and columns
+            // 128 .., made exactly symmetric as the diagonal block of tile 0 in drain
             auto drain_corner = [&](uint32_t acc, float alpha) {
                 const int crow0 = 32 * q;
                 if (crow0 >= wc) return;
                 const int row = 128 + crow0 + lane;
 #pragma unroll 1
                 for (int c0 = 32 * part; c0 < wc; c0 += 96) {
+                    if (c0 < crow0) continue;  // the mirror of another warp's chunk
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + lane_off + c0, raw);
                     tmem_wait_ld_regs(raw);
@@ -873,14 +1038,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
+                    if (c0 > crow0) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t off = img_offset(row, 128 + c0 + 8 * u, RB);
-                        *reinterpret_cast<uint4*>(smem + hi_off + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
-                        if constexpr (NB == 2)
-                            *reinterpret_cast<uint4*>(smem + lo_off + off) =
-                                make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
+                        for (int u = 0; u < 4; ++u) {
+                            const uint32_t off = img_offset(row, 128 + c0 + 8 * u, RB);
+                            *reinterpret_cast<uint4*>(smem + hi_off + off) = make_uint4(hw[4 * u], hw[4 * u + 1], hw[4 * u + 2], hw[4 * u + 3]);
+                            if constexpr (NB == 2)
+                                *reinterpret_cast<uint4*>(smem + lo_off + off) =
+                                    make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
+                        }
                     }
+                    mirror_chunk(hw, lw, 128 + crow0, 128 + c0, c0 == crow0);
                 }
             };
             // scan: rpart_s[part, row] = sum_c |C_rc| w_c over this thread's columns (w = 1 when null)
@@ -930,11 +1098,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     best = fminf(best, block_max2(qm, 0.0f).x);
                 }
                 const float smax = sqrtf(best * (1.0f + 1e-4f));  // margin for FP32 summation
-                float scale = smax > 0.0f ? 1.2f / smax : 1.0f;
-                if (a.use_model && smax > 0.0f) {
-                    if (smax <= 1.7f) scale = fmaxf(1.0f, scale);
-                    else if (tid == 0) atomicAdd(a.fallbacks, 1);
-                }
+                const float scale = start_factor(smax);
                 if (tid == 0) {
                     const double s0 = sqrt(static_cast<double>(rmax) * (1.0 + 1e-5));
                     a.sq_ratio[j] = static_cast<float>(s0 * a.bound[j] / a.gersh[j]);
@@ -947,7 +1111,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 double rr = 0.0;
                 for (int w = 0; w < kThreads / 32; ++w) rr += resid_s2[w];
                 if (!isfinite(rr)) bad_s = 1;
-                else if (sqrt(rr) <= a.tau) conv_s = 1;
+                else if (sqrt(rr) <= a.tau) converged(sqrt(rr));
             };
 
             if (mtiles == 1) {
@@ -956,8 +1120,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 const uint32_t TA = tmem_base, TB = tmem_base + 160;
                 for (int it = 0; it < a.max_iter; ++it) {
                     // A = Z - shift I and X' = alpha A X: shift = 3, alpha = -1/2 (Y = 3/2 I - 1/2 Z);
-                    // at iteration 0 shift = 3/c^2, alpha = -c^3/2 (the a-posteriori scaling c)
+                    // at iteration 0 shift = 3/c^2, alpha = -c^3/2 (the a-posteriori scaling c);
+                    // on the scaled schedule 3/a^2 and -a^3/2
                     float alpha = -0.5f, shift = 3.0f;
+                    if (it > 0) next_step(shift, alpha);
                     if (warp == 1 && lane == 0) {
                         tc_fence_after();
                         issue_xx(0, TA);
@@ -1021,6 +1187,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 const uint32_t TA = tmem_base, TB = tmem_base + kpad, R1 = TB + wc, TC = tmem_base + 512 - kpad;
                 for (int it = 0; it < a.max_iter; ++it) {
                     float alpha = -0.5f, shift = 3.0f;
+                    if (it > 0) next_step(shift, alpha);
                     if (it == 0 && warp == 1 && lane == 0) {  // later iterations: issued at the end of the previous one
                         tc_fence_after();
                         issue_xx(0, TA);
@@ -1112,21 +1279,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 //
                 // Bound on rho(Z) = rho(X0)^2 (Collatz-Wielandt): for any positive
                 // vector w, rho(Z) <= rho(|Z|) <= max_r (|Z| w)_r / w_r.  w = 1 gives
-                // the Gershgorin bound (the max row sum r, from the product's
-                // epilogue); with the learned bound on, one power step (w = r)
-                // tightens it (on water-like submatrices from about 1.5 rho to
-                // 1.35 rho) so that good predictions pass the check.
+                // the Gershgorin bound (the max row sum r, from a pass over the stored Z);
+                // one power step (w = r) tightens it (on water-like submatrices from
+                // about 1.5 rho to 1.35 rho).
                 // The row-sum vector lives in the (still unused) buffer of X1.
                 float* wv = reinterpret_cast<float*>(ws + static_cast<int64_t>(zn) * buf);
-                float* wparts = wv + kpad;  // 2 per N tile, kpad each
-                const int nparts = 2 * ((kpad + NT - 1) / NT);
-                for (int c = tid; c < nparts * kpad; c += kThreads) wparts[c] = 0.0f;
-                __syncthreads();
-                gemm(kpad, s.n, 3, zx, zx, zy, 1.0f, wparts);  // Z = X0^2 and partial row sums of |Z|
-                for (int r = tid; r < kpad; r += kThreads) {  // wv = row sums of |Z|, parts added in order
-                    float sum = 0.0f;
-                    for (int p = 0; p < nparts; ++p) sum += wparts[p * kpad + r];
-                    wv[r] = sum;
+                gemm(kpad, s.n, 2, zx, zx, zy, 1.0f);  // Z = X0^2 (both triangles)
+                {
+                    const uint16_t* zh = ws + static_cast<int64_t>(zy) * buf;
+                    const uint16_t* zl = zh + buf;
+                    // row sums of |Z|, eight rows per warp at a time, 8 columns per lane and load
+                    constexpr int kR = 8;
+                    for (int r0 = warp * kR; r0 < kpad; r0 += kR * (kThreads / 32)) {
+                        float acc[kR];
+#pragma unroll
+                        for (int u = 0; u < kR; ++u) acc[u] = 0.0f;
+                        for (int c = 8 * lane; c < kpad; c += 256) {
+#pragma unroll
+                            for (int u = 0; u < kR; ++u) {
+                                float zr[8];
+                                const int r = min(r0 + u, kpad - 1);  // rows past kpad repeat the last (not stored)
+                                load8<PREC, NB>(zh + static_cast<int64_t>(r) * a.ld + c, zl + static_cast<int64_t>(r) * a.ld + c, zr);
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) acc[u] += fabsf(zr[i]);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kR; ++u) {
+                            const float v = warp_sum_f(acc[u]);
+                            if (lane == 0 && r0 + u < kpad) wv[r0 + u] = v;
+                        }
+                    }
                 }
                 __syncthreads();
                 float rmax = 0.0f;
@@ -1135,7 +1318,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 float best = rmax;
                 uint16_t* zh = ws + static_cast<int64_t>(zy) * buf;
                 uint16_t* zl = zh + buf;
-                if (a.use_model && rmax > 0.0f) {
+                if (rmax > 0.0f) {  // (a pass over Z is cheap next to the products at these sizes)
                     // w > 0: rows that are zero in Z get a tiny positive weight
                     for (int c = tid; c < s.n; c += kThreads) wv[c] = fmaxf(wv[c], 1e-12f * rmax);
                     __syncthreads();
@@ -1170,15 +1353,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     best = fminf(best, block_max2(q, 0.0f).x);
                 }
                 const float smax = sqrtf(best * (1.0f + 1e-4f));  // margin for FP32 summation
-                // Without the learned bound X0 = A / G and X0 is always rescaled to
-                // c = 1.2 / s.  With it, the predicted scaling is kept when the
-                // guaranteed bound allows (s <= 1.7 < sqrt 3) and only enlarged, never
-                // shrunk; otherwise the prediction is discarded for c = 1.2 / s.
-                float scale = smax > 0.0f ? 1.2f / smax : 1.0f;
-                if (a.use_model && smax > 0.0f) {
-                    if (smax <= 1.7f) scale = fmaxf(1.0f, scale);
-                    else if (tid == 0) atomicAdd(a.fallbacks, 1);
-                }
+                const float scale = start_factor(smax);
                 // Z_rr -= 3 / c^2 (in place, the split re-done)
                 const float shift = 3.0f / (scale * scale);
                 for (int r = tid; r < s.n; r += kThreads) {
@@ -1202,16 +1377,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     a.bound[j] = a.bound[j] / static_cast<double>(scale);  // effective scaling of X0'
                 }
                 __syncthreads();
-                gemm(kpad, s.n, 2, zx, zy, zn, -0.5f * scale * scale * scale, nullptr);  // X1 = -c^3/2 X0 (Z - 3/c^2 I)
+                gemm(kpad, s.n, 2, zx, zy, zn, -0.5f * scale * scale * scale);  // X1 = -c^3/2 X0 (Z - 3/c^2 I)
             } else {
-                gemm(kpad, s.n, 1, zx, zx, zy, 1.0f, nullptr);  // Y = 3/2 I - 1/2 X^2
+                float shift = 3.0f, alpha = -0.5f;
+                next_step(shift, alpha);
+                // Y = a (3/2 I - a^2/2 X^2) = alpha X^2 - alpha shift I: the scaled step X' = X Y
+                gemm(kpad, s.n, 1, zx, zx, zy, alpha, -alpha * shift);  // Y = 3/2 I - 1/2 X^2 when plain
                 if (tid == 0) {
                     double r2 = 0.0;
                     for (int w = 0; w < kEpiWarps; ++w) r2 += resid_s[w];
                     if (!isfinite(r2)) bad_s = 1;
-                    else if (sqrt(r2) <= a.tau) conv_s = 1;
+                    else if (sqrt(r2) <= a.tau) converged(sqrt(r2));
                 }
-                gemm(kpad, s.n, 2, zx, zy, zn, 1.0f, nullptr);  // X' = X Y
+                gemm(kpad, s.n, 2, zx, zy, zn, 1.0f);  // X' = X Y
             }
             cur ^= 1;
             done = it + 1;

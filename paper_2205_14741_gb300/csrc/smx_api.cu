@@ -117,6 +117,7 @@ struct smx_ctx {
 
     // learned spectral bound
     bool model_ready = false, model_on = false, sq_valid = false;
+    bool model_gap = false;  // the learned gap drives the scaled Newton-Schulz schedule
     int adam_t = 0;
     int64_t n_samples = 0, cap_samples = 0;
     DevBuf d_params, d_mst, d_vst, d_partial_mlp, d_feat, d_pred, d_labels, d_gersh, d_prev_ratio, d_sq_ratio,
@@ -425,8 +426,10 @@ static smx_status ns_event_pair(smx_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
 
 // One build at chemical potential mu (a3 - a8).
 // a3 + a4 for block columns [j0, j0 + m) into the staging buffer.
-static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const GatherExtras& ex) {
+static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const GatherExtras& ex_in) {
     const PatternView pv = pattern_view(c);
+    GatherExtras ex = ex_in;
+    ex.bmax = c->bmax;
     SubDesc* subs = dp<SubDesc>(c->d_subs);
     if (c->precision == SMX_FP64) {
         SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, c->max_n, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
@@ -530,6 +533,7 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             ex.prev_ratio = dp<float>(c->d_prev_ratio) + j0;
             ex.params = dp<float>(c->d_params);
             ex.margin = kModelMargin;
+            if (c->model_gap) ex.pred = dp<float>(c->d_pred) + 2 * j0;  // 2 per column
         }
         if (!c->have_S) SMX_TRY(gather_chunk(c, j0, m, mu, ex));  // the non-orthogonal form starts from M_j
         cudaEvent_t ns0, ns1;
@@ -551,6 +555,7 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             a.gersh = dp<double>(c->d_gersh) + j0;
             a.sq_ratio = dp<float>(c->d_sq_ratio) + j0;
             a.use_model = model ? 1 : 0;
+            if (model && c->model_gap) a.pred = dp<float>(c->d_pred) + 2 * j0;
             a.fallbacks = &sc->fallbacks;
             a.status = &sc->status;
             a.pv = pv;
@@ -584,6 +589,7 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             a.gersh = dp<double>(c->d_gersh);
             a.sq_ratio = dp<float>(c->d_sq_ratio);
             a.use_model = model ? 1 : 0;
+            if (model && c->model_gap) a.pred = dp<float>(c->d_pred);
             a.fallbacks = &sc->fallbacks;
             a.status = &sc->status;
             a.pv = pv;
@@ -995,6 +1001,15 @@ smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
     return SMX_OK;
 }
 
+smx_status smx_selftest_wait_timeout(smx_ctx* c, uint32_t poll_limit) {
+    if (!c || poll_limit == 0 || poll_limit > kSpinLimit) return SMX_ERR_ARG;
+    DeviceGuard g(c->device);
+    SMX_TRY(reset_flags(c));
+    SMX_CUDA(launch_wait_selftest(&scalars(c)->status, poll_limit, nullptr, c->stream));
+    c->kernel_launches += 1;
+    return read_status(c);
+}
+
 smx_status smx_reset_counters(smx_ctx* c) {
     if (!c) return SMX_ERR_ARG;
     DeviceGuard g(c->device);
@@ -1244,8 +1259,10 @@ smx_status smx_set_bound_model(smx_ctx* c, int32_t enable, const char* weights_p
         if (!ok) return SMX_ERR_ARG;
         SMX_TRY(model_upload(c, p));
     }
+    if (enable < 0 || enable > 2) return SMX_ERR_ARG;
     if (enable && !c->model_ready) return SMX_ERR_STATE;
     c->model_on = enable != 0;
+    c->model_gap = enable == 1;
     return SMX_OK;
 }
 

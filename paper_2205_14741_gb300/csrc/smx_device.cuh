@@ -166,6 +166,33 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // ---------------------------------------------------------------------------
+// Scaled Newton-Schulz schedule
+// ---------------------------------------------------------------------------
+// With every |eigenvalue| of X in [l, 1] (0 < l <= 1), one step of the sign
+// iteration applied to a X, p(a X) with p(x) = x (3 - x^2) / 2, maps that
+// interval into [p(a l), 1] when a = sqrt(3 / (1 + l + l^2)): this a makes
+// p(a l) = p(a), and p peaks at 1 inside the interval.  Small eigenvalues thus
+// grow by about 1.5 a (up to 2.6) per step instead of 1.5.  Any l in (0, 1]
+// keeps every eigenvalue in (0, 1] with its sign (a l underestimated only
+// costs steps), so the schedule is safe for any lower bound the caller
+// guesses.  a is capped at kScaleCap < sqrt 3 so that rounding in X or in the
+// upper bound cannot carry an eigenvalue past sqrt 3, where p changes sign.
+constexpr double kScaleCap = 1.72;
+template <typename T>
+__device__ __forceinline__ T ns_scale(T l) {
+    if (!(l < T(1))) return T(1);
+    const T a = sqrt(T(3) / (T(1) + l + l * l));
+    return a < T(kScaleCap) ? a : T(kScaleCap);
+}
+// the lower end of the interval after the step with factor a
+template <typename T>
+__device__ __forceinline__ T ns_next_lower(T a, T l) {
+    const T x = a * l;
+    const T y = T(0.5) * x * (T(3) - x * x);
+    return y < T(1) ? y : T(1);
+}
+
+// ---------------------------------------------------------------------------
 // warp / block reductions
 // ---------------------------------------------------------------------------
 

@@ -43,6 +43,7 @@ struct GatherExtras {
     float* pred = nullptr;               // ... and its two predictions
     float margin = 0.0f;                 // ... b_j = G_j clamp(pred_0, 0.02, 1) (1 + margin) / 1.2
     const double* mu_dev = nullptr;      // when set, mu is read from here (on the device) instead
+    int bmax = 0;                        // largest block size (0: unknown), selects the small-block kernel
 };
 
 // a3 + a4: T_j = H[R_j, R_j] - mu I into the FP64 staging buffer, then the
@@ -60,6 +61,10 @@ cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nbl
 // a8 (FP64 form): deterministic sums of the per-column partials ->
 // sc->trace = trace(D), sc->energy = trace(D H).
 cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cudaStream_t st);
+
+// Failure-detection self-test: a wait on an mbarrier nothing arrives at, given up after
+// poll_limit polls (records kErrTimeout in *status; *polls_out, if set, the polls made).
+cudaError_t launch_wait_selftest(int* status, uint32_t poll_limit, int* polls_out, cudaStream_t st);
 
 // a5/a6 (FP64 plain form) + a7: Newton-Schulz in FP64, then scatter.
 // Matrix function of a build (values of smx_function): 0 = the density matrix
@@ -95,6 +100,9 @@ struct NsFp64Args {
     const double* Lc = nullptr;  // L_j = A_S^-1/2, laid out like T
     const double* Sv = nullptr;  // S in the input value layout
     double mu = 0.0;
+    // learned bound: predictions of this chunk ([2 i + 1] = delta_hat / G for the i-th
+    // submatrix); see NsTcArgs::pred
+    const float* pred = nullptr;
 };
 cudaError_t launch_ns_fp64(const NsFp64Args& a, int max_nblk, cudaStream_t st);
 
@@ -143,6 +151,10 @@ struct NsTcArgs {
     double* D;
     double2* partial;
     float* xown;           // receives columns own .. own + bown of each final X
+    // learned bound: predictions per block column ([2 j + 1] = delta_hat / G_j); with the
+    // prediction accepted, the steps follow the scaled schedule from the lower bound
+    // delta_hat / (b_j s) (null: plain steps after the a-posteriori start)
+    const float* pred = nullptr;
 };
 // precision: 1 = FP16 split hi/lo (3 products), 2 = FP16, 3 = BF16 (values of smx_precision)
 cudaError_t launch_ns_tc(const NsTcArgs& a, int precision, const CUtensorMap& tmap, int max_nblk, cudaStream_t st);

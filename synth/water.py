@@ -357,7 +357,7 @@ WORKLOADS = {
     # 4096 molecules, 23x23 blocks, N = 94208: fixed mu = 0
     "water4096x23": dict(gen="lattice", n_mol=4096, b=23, r_c=7.0, ell=2.0, seed=1003, eps=1e-6, mu=0.0),
     # 6000-molecule water/vacuum slab, 6x6 blocks, wide cutoff: 20-step bisection to 3 * 6000
-    "slab6000": dict(gen="slab", n_mol=6000, b=6, r_c=15.3, ell=3.0, seed=1004, eps=1e-5, n_e=18000.0),
+    "slab6000": dict(gen="slab", n_mol=6000, b=6, r_c=15.3, ell=3.0, seed=1004, eps=1e-5, n_e=18000.0, max_steps=20),
     # MD-like trajectory of the 1024-molecule system (200 snapshots)
     "md1024": dict(gen="md", n_mol=1024, b=6, r_c=6.0, ell=1.5, seed=1005, eps=1e-5, n_e=3072.0, n_snap=200),
 }
