@@ -929,6 +929,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             // replaced by the mirror of its upper one.  So the iterate in the image is exactly
             // symmetric there (left as computed, its rounding asymmetry would grow from step to
             // step).  Lane l writes one row of 64 contiguous bytes per hi / lo image.
+            // The single-pass forms mirror; the split form keeps the computed diagonal blocks: its
+            // rounding (about 1e-7) leaves the asymmetric part far below the error bound over a
+            // few steps, and the mirror would cost about 12% of the kernel on water-like inputs.
+            constexpr bool kMirror = NB == 1;
             uint16_t* xsw = reinterpret_cast<uint16_t*>(smem + kXsOff * NB + static_cast<uint32_t>(warp) * kXsWarp);
             auto mirror_chunk = [&](const uint32_t (&hw)[16], const uint32_t (&lw)[16], int r0, int c0, bool diag) {
 #pragma unroll
@@ -977,7 +981,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
-                    const bool in_diag = c0 < 128;
+                    const bool in_diag = kMirror && c0 < 128;
                     if (!in_diag || c0 > crow0) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
@@ -1028,7 +1032,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 const int row = 128 + crow0 + lane;
 #pragma unroll 1
                 for (int c0 = 32 * part; c0 < wc; c0 += 96) {
-                    if (c0 < crow0) continue;  // the mirror of another warp's chunk
+                    if (kMirror && c0 < crow0) continue;  // the mirror of another warp's chunk
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + lane_off + c0, raw);
                     tmem_wait_ld_regs(raw);
@@ -1038,7 +1042,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) split2<PREC, NB>(y[i], y[i + 1], hw[i >> 1], lw[i >> 1]);
-                    if (c0 > crow0) {
+                    if (!kMirror || c0 > crow0) {
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const uint32_t off = img_offset(row, 128 + c0 + 8 * u, RB);
@@ -1048,7 +1052,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                                     make_uint4(lw[4 * u], lw[4 * u + 1], lw[4 * u + 2], lw[4 * u + 3]);
                         }
                     }
-                    mirror_chunk(hw, lw, 128 + crow0, 128 + c0, c0 == crow0);
+                    if (kMirror) mirror_chunk(hw, lw, 128 + crow0, 128 + c0, c0 == crow0);
                 }
             };
             // scan: rpart_s[part, row] = sum_c |C_rc| w_c over this thread's columns (w = 1 when null)

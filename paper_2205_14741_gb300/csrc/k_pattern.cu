@@ -153,133 +153,11 @@ __global__ void __launch_bounds__(256) k_filter_columns(const int64_t* __restric
     }
 }
 
-// a1 + the bracket in one pass for block sizes up to 8 (a warp per block column j, a lane per
-// block of the column, 32 blocks at a time): the lane reads its block (contiguous, column-major),
-// checks finiteness, writes the FP32 copy, takes the Frobenius norm (the keep decision) and the
-// block's column absolute sums; the column's sums over its kept blocks are then warp sums in a
-// fixed order (H symmetric: column sums are row sums), with the diagonal taken from the lane
-// that holds the diagonal block.  The last block reduces the intervals to the bracket.
-constexpr int kFastFilterB = 8;
-__global__ void __launch_bounds__(256) k_filter_fast(const double* __restrict__ H, const int64_t* __restrict__ col_ptr,
-                                                     const int64_t* __restrict__ voff,
-                                                     const int32_t* __restrict__ row_idx,
-                                                     const int32_t* __restrict__ bsize, int n_cols, double eps,
-                                                     uint8_t* __restrict__ keep, const uint8_t* __restrict__ keep_prev,
-                                                     float* __restrict__ H32, double* __restrict__ lohi, DevScalars* sc) {
-    __shared__ double mm_s[2][8];
-    __shared__ bool last_s;
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (j < n_cols) {
-        const int bc = bsize[j];
-        const int64_t k0 = col_ptr[j], k1 = col_ptr[j + 1];
-        double cs[kFastFilterB], dg[kFastFilterB];
-#pragma unroll
-        for (int q = 0; q < kFastFilterB; ++q) cs[q] = dg[q] = 0.0;
-        bool finite = true, changed = false;
-        int has_diag = 0;
-        for (int64_t kb = k0; kb < k1; kb += 32) {
-            const int64_t k = kb + lane;
-            if (k < k1) {
-                const int r = row_idx[k], br = bsize[r];
-                const int64_t vo = voff[k];
-                const int e_n = br * bc;
-                double ss = 0.0, bs[kFastFilterB];
-#pragma unroll
-                for (int q = 0; q < kFastFilterB; ++q) bs[q] = 0.0;
-                for (int e0 = 0; e0 < e_n; e0 += 8) {  // eight loads in flight, then their use
-                    double v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = e0 + u < e_n ? H[vo + e0 + u] : 0.0;
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int e = e0 + u;
-                        if (e >= e_n) break;
-                        const int q = e / br, p = e - q * br;
-                        ss = fma(v[u], v[u], ss);
-                        finite = finite && isfinite(v[u]);
-                        H32[vo + e] = __double2float_rn(v[u]);
-#pragma unroll
-                        for (int qq = 0; qq < kFastFilterB; ++qq)
-                            if (qq == q) bs[qq] += fabs(v[u]);
-                        if (r == j && p == q) {
-#pragma unroll
-                            for (int qq = 0; qq < kFastFilterB; ++qq)
-                                if (qq == q) dg[qq] = v[u];
-                        }
-                    }
-                }
-                const bool kept = r == j || !(sqrt(ss) < eps);
-                keep[k] = kept ? 1 : 0;
-                if (keep_prev && kept != (keep_prev[k] != 0)) changed = true;
-                if (kept) {
-#pragma unroll
-                    for (int q = 0; q < kFastFilterB; ++q) cs[q] += bs[q];
-                }
-                if (r == j) has_diag = 1;
-            }
-        }
-        if (__any_sync(0xffffffffu, changed) && lane == 0) atomicOr(&sc->changed, 1);
-        if (!__all_sync(0xffffffffu, finite) && lane == 0) atomicCAS(&sc->status, kOk, kErrNonfinite);
-        const unsigned dmask = __ballot_sync(0xffffffffu, has_diag);
-        const int dlane = dmask ? __ffs(dmask) - 1 : 0;
-        double lo = INFINITY, hi = -INFINITY;
-#pragma unroll
-        for (int q = 0; q < kFastFilterB; ++q) {
-            if (q >= bc) break;
-            const double tot = warp_sum(cs[q]);
-            const double d = __shfl_sync(0xffffffffu, dg[q], dlane), rad = tot - fabs(d);
-            lo = fmin(lo, d - rad);
-            hi = fmax(hi, d + rad);
-        }
-        if (lane == 0) {
-            lohi[2 * j] = lo;
-            lohi[2 * j + 1] = hi;
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last_s = atomicAdd(&sc->filter_done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last_s) return;
-    __threadfence();
-    double lo = INFINITY, hi = -INFINITY;
-    for (int c = threadIdx.x; c < n_cols; c += blockDim.x) {
-        lo = fmin(lo, __ldcg(lohi + 2 * c));
-        hi = fmax(hi, __ldcg(lohi + 2 * c + 1));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    }
-    if (lane == 0) {
-        mm_s[0][warp] = lo;
-        mm_s[1][warp] = hi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
-            lo = fmin(lo, mm_s[0][w]);
-            hi = fmax(hi, mm_s[1][w]);
-        }
-        sc->br_lo = lo;
-        sc->br_hi = hi;
-        sc->mu0 = 0.5 * (lo + hi);
-        sc->filter_done = 0u;
-    }
-}
-
 cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int32_t* bcol,
                                      const int64_t* voff, const int32_t* bsize, int n_cols, int64_t nnzb, int bmax,
                                      double eps, uint8_t* keep, const uint8_t* keep_prev, float* H32, double* csum,
                                      double* diag, double* lohi, DevScalars* sc, cudaStream_t st) {
     if (n_cols <= 0) return cudaSuccess;
-    if (bmax <= kFastFilterB) {
-        const int g = static_cast<int>((static_cast<int64_t>(n_cols) * 32 + 255) / 256);
-        k_filter_fast<<<g, 256, 0, st>>>(H, col_ptr, voff, row_idx, bsize, n_cols, eps, keep, keep_prev, H32, lohi, sc);
-        return cudaGetLastError();
-    }
     const int64_t g1 = (nnzb * 8 + 255) / 256;
     k_filter_blocks<<<static_cast<unsigned>(g1), 256, 0, st>>>(H, voff, row_idx, bcol, bsize, nnzb, bmax, eps, keep, keep_prev,
                                                                H32, csum, diag, sc);
@@ -308,103 +186,6 @@ cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, co
 // R_r, f5 mean_r R_r (R_r = sum_{c != r} |A_rc|), f6 n/256, f7 mean A_rr, f8
 // the previous step's ratio; then the 9 -> 64 -> 64 -> 2 tanh network with the
 // parameters rounded to FP16, and b_j = G clamp(rho_hat/G, 0.02, 1) (1 + margin)/1.2.
-// The end of a gather CTA: the block-wide Gershgorin bound G_j from the warps' row-sum maxima,
-// the learned-bound features from their statistics (F2, Da, Ds, Dq, Rs sums; Dm, Rm maxima of
-// this warp's rows) and, with parameters, the network's prediction and b_j; all threads call it.
-template <class R>
-__device__ __forceinline__ void gather_finish(const SubDesc& s, const GatherExtras& ex, double* __restrict__ bound,
-                                              double m, float f2, float da, float ds, float dq, float rs, float dm,
-                                              float rm) {
-    __shared__ double warp_max_s[8];
-    __shared__ float stat_s[8][7];  // per warp: F2, Da, Ds, Dq, Rs (sums), Dm, Rm (maxima)
-    __shared__ float x_s[kModelFeatures], h1_s[kModelHidden], y_s[2][2];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (lane == 0) {
-        warp_max_s[warp] = m;
-        stat_s[warp][0] = f2;
-        stat_s[warp][1] = da;
-        stat_s[warp][2] = ds;
-        stat_s[warp][3] = dq;
-        stat_s[warp][4] = rs;
-        stat_s[warp][5] = dm;
-        stat_s[warp][6] = rm;
-    }
-    __syncthreads();
-    double g = 0.0;
-    for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
-    const double graw = g;
-    // in FP32 the row sums carry a relative error below n 2^-24, covered by the 1e-5 margin
-    if (sizeof(R) == 4) g *= 1.0 + 1e-5;
-    if (!(g > 0.0)) g = 1.0;
-    if (ex.feat || ex.params) {
-        if (tid == 0) {
-            float F2 = 0.f, Da = 0.f, Ds = 0.f, Dq = 0.f, Rs = 0.f, Dm = 0.f, Rm = 0.f;
-            for (int w = 0; w < 8; ++w) {
-                F2 += stat_s[w][0];
-                Da += stat_s[w][1];
-                Ds += stat_s[w][2];
-                Dq += stat_s[w][3];
-                Rs += stat_s[w][4];
-                Dm = fmaxf(Dm, stat_s[w][5]);
-                Rm = fmaxf(Rm, stat_s[w][6]);
-            }
-            const float n = static_cast<float>(s.n), G = static_cast<float>(graw);
-            const float ig = G > 0.f ? 1.f / G : 0.f, mean = Ds / n;
-            x_s[0] = sqrtf(F2 / n) * ig;
-            x_s[1] = Dm * ig;
-            x_s[2] = Da / n * ig;
-            x_s[3] = sqrtf(fmaxf(Dq / n - mean * mean, 0.f)) * ig;
-            x_s[4] = Rm * ig;
-            x_s[5] = Rs / n * ig;
-            x_s[6] = n / 256.f;
-            x_s[7] = mean * ig;
-            x_s[8] = ex.prev_ratio ? ex.prev_ratio[blockIdx.x] : 0.f;
-            if (ex.feat)
-                for (int k = 0; k < kModelFeatures; ++k) ex.feat[static_cast<int64_t>(blockIdx.x) * kModelFeatures + k] = x_s[k];
-        }
-        __syncthreads();
-    }
-    double b = g;
-    if (ex.params) {
-        // the network, weights rounded to FP16 (threads 0..63: one hidden unit each)
-        const float* p = ex.params;
-        auto w16 = [](float v) { return __half2float(__float2half_rn(v)); };
-        if (tid < kModelHidden) {
-            float acc = w16(p[kOffB1 + tid]);
-            for (int k = 0; k < kModelFeatures; ++k) acc = fmaf(w16(p[tid * kModelFeatures + k]), x_s[k], acc);
-            h1_s[tid] = tanhf(acc);
-        }
-        __syncthreads();
-        if (tid < kModelHidden) {
-            float acc = w16(p[kOffB2 + tid]);
-            for (int k = 0; k < kModelHidden; ++k) acc = fmaf(w16(p[kOffW2 + tid * kModelHidden + k]), h1_s[k], acc);
-            const float h2 = tanhf(acc);
-            float y0 = w16(p[kOffW3 + tid]) * h2, y1 = w16(p[kOffW3 + kModelHidden + tid]) * h2;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                y0 += __shfl_xor_sync(0xffffffffu, y0, o);
-                y1 += __shfl_xor_sync(0xffffffffu, y1, o);
-            }
-            if (lane == 0) {
-                y_s[warp][0] = y0;
-                y_s[warp][1] = y1;
-            }
-        }
-        __syncthreads();
-        const float y0 = (y_s[0][0] + y_s[1][0]) + w16(p[kOffB3]);
-        const float y1 = (y_s[0][1] + y_s[1][1]) + w16(p[kOffB3 + 1]);
-        if (tid == 0 && ex.pred) {
-            ex.pred[2 * static_cast<int64_t>(blockIdx.x)] = y0;
-            ex.pred[2 * static_cast<int64_t>(blockIdx.x) + 1] = y1;
-        }
-        b = g * fmin(fmax(static_cast<double>(y0), 0.02), 1.0) * (1.0 + ex.margin) / 1.2;
-    }
-    if (tid == 0) {
-        bound[blockIdx.x] = b;
-        if (ex.gersh) ex.gersh[blockIdx.x] = g;
-    }
-}
-
 constexpr int kGatherRows = 8;  // rows of a block row written together
 
 template <class R>
@@ -413,6 +194,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(co
                                                       double* __restrict__ bound, int nblk_max, int n_max,
                                                       GatherExtras ex) {
     extern __shared__ __align__(16) unsigned char gsm[];
+    __shared__ double warp_max_s[8];
+    __shared__ float stat_s[8][7];  // per warp: F2, Da, Ds, Dq, Rs (sums), Dm, Rm (maxima)
+    __shared__ float x_s[kModelFeatures], h1_s[kModelHidden], y_s[2][2];
     const R mu = static_cast<R>(ex.mu_dev ? *ex.mu_dev : mu_d);
     const SubDesc s = subs[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -523,143 +307,95 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(co
         }
         __syncwarp();
     }
-    gather_finish<R>(s, ex, bound, m, f2, da, ds, dq, rs, dm, rm);
-}
-
-// The same for block sizes up to 8 (one CTA per submatrix, 256 threads).  All tables first:
-// tab[c][a] = value offset of block (R_j[a], R_j[c]) (-1 when the filter dropped it), a warp
-// per block column c.  Then warp w writes the rows of block rows c = w, w + 8, ...: row
-// x = start(c) + q of T_j is column x (T_j symmetric), i.e. column q of the blocks
-// (R_j[a], R_j[c]) stacked over a, and lane a copies the br contiguous values of block a's
-// column q (a warp covers 32 blocks of a row at once, writing 32 consecutive segments), with
-// the loads of all rows of the block row issued before their stores.
-constexpr int kSmallB = 8;
-template <class R>
-__global__ void __launch_bounds__(256, 2) k_gather_small(const SubDesc* __restrict__ subs, PatternView pv,
-                                                      const R* __restrict__ H, double mu_d, R* __restrict__ T,
-                                                      double* __restrict__ bound, int nblk_max, GatherExtras ex) {
-    extern __shared__ __align__(16) unsigned char gsm[];
-    const R mu = static_cast<R>(ex.mu_dev ? *ex.mu_dev : mu_d);
-    const SubDesc s = subs[blockIdx.x];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nb = s.nblk;
-    int64_t* tab = reinterpret_cast<int64_t*>(gsm);  // [nblk_max][nblk_max]
-    int* rows = reinterpret_cast<int*>(tab + static_cast<size_t>(nblk_max) * nblk_max);
-    int* ls = rows + nblk_max;  // local starts, nblk + 1 entries
-    for (int a = tid; a < nb; a += blockDim.x) {
-        rows[a] = pv.frow_idx[s.fptr + a];
-        ls[a] = pv.lstart[s.fptr + a];
-    }
-    if (tid == 0) ls[nb] = s.n;
-    for (int e = tid; e < nb * nb; e += blockDim.x) tab[e] = -1;
-    __syncthreads();
-    for (int c = warp; c < nb; c += 8) {
-        const int col = rows[c];
-        const int64_t k0 = pv.fcol_ptr[col], k1 = pv.fcol_ptr[col + 1];
-        for (int64_t k = k0 + lane; k < k1; k += 32) {
-            const int r = pv.frow_idx[k];
-            int lo = 0, hi = nb - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (rows[mid] < r) lo = mid + 1; else hi = mid;
-            }
-            if (rows[lo] == r) tab[static_cast<size_t>(c) * nb + lo] = pv.fvoff[k];
-        }
+    if (lane == 0) {
+        warp_max_s[warp] = m;
+        stat_s[warp][0] = f2;
+        stat_s[warp][1] = da;
+        stat_s[warp][2] = ds;
+        stat_s[warp][3] = dq;
+        stat_s[warp][4] = rs;
+        stat_s[warp][5] = dm;
+        stat_s[warp][6] = rm;
     }
     __syncthreads();
-
-    R* t = T + s.t_off;
-    double m = 0.0;
-    float f2 = 0.f, da = 0.f, ds = 0.f, dq = 0.f, rs = 0.f, dm = 0.f, rm = 0.f;  // feature statistics
-    constexpr int kQB = 4;  // rows of a block row loaded together
-    for (int c = warp; c < nb; c += 8) {
-        const int bc = ls[c + 1] - ls[c];
-        for (int q0 = 0; q0 < bc; q0 += kQB) {
-            R racc[kQB], rdg[kQB];
-            float rsq[kQB];
-#pragma unroll
-            for (int qq = 0; qq < kQB; ++qq) {
-                racc[qq] = rdg[qq] = R(0);
-                rsq[qq] = 0.f;
+    double g = 0.0;
+    for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
+    const double graw = g;
+    // in FP32 the row sums carry a relative error below n 2^-24, covered by the 1e-5 margin
+    if (sizeof(R) == 4) g *= 1.0 + 1e-5;
+    if (!(g > 0.0)) g = 1.0;
+    if (ex.feat || ex.params) {
+        if (tid == 0) {
+            float F2 = 0.f, Da = 0.f, Ds = 0.f, Dq = 0.f, Rs = 0.f, Dm = 0.f, Rm = 0.f;
+            for (int w = 0; w < 8; ++w) {
+                F2 += stat_s[w][0];
+                Da += stat_s[w][1];
+                Ds += stat_s[w][2];
+                Dq += stat_s[w][3];
+                Rs += stat_s[w][4];
+                Dm = fmaxf(Dm, stat_s[w][5]);
+                Rm = fmaxf(Rm, stat_s[w][6]);
             }
-            // passes of 32 blocks; lane a == nb of the last pass writes the zero padding [n, ld)
-            for (int a0 = 0; a0 < nb || (a0 == nb && s.ld > s.n); a0 += 32) {
-                const int a = a0 + lane;
-                const bool blk = a < nb;
-                const int64_t vo = blk ? tab[static_cast<size_t>(c) * nb + a] : -1;
-                const int y0 = blk ? ls[a] : s.n;
-                const int br = blk ? ls[a + 1] - y0 : (a == nb ? s.ld - s.n : 0);
-                R v[kQB][kSmallB];
+            const float n = static_cast<float>(s.n), G = static_cast<float>(graw);
+            const float ig = G > 0.f ? 1.f / G : 0.f, mean = Ds / n;
+            x_s[0] = sqrtf(F2 / n) * ig;
+            x_s[1] = Dm * ig;
+            x_s[2] = Da / n * ig;
+            x_s[3] = sqrtf(fmaxf(Dq / n - mean * mean, 0.f)) * ig;
+            x_s[4] = Rm * ig;
+            x_s[5] = Rs / n * ig;
+            x_s[6] = n / 256.f;
+            x_s[7] = mean * ig;
+            x_s[8] = ex.prev_ratio ? ex.prev_ratio[blockIdx.x] : 0.f;
+            if (ex.feat)
+                for (int k = 0; k < kModelFeatures; ++k) ex.feat[static_cast<int64_t>(blockIdx.x) * kModelFeatures + k] = x_s[k];
+        }
+        __syncthreads();
+    }
+    double b = g;
+    if (ex.params) {
+        // the network, weights rounded to FP16 (threads 0..63: one hidden unit each)
+        const float* p = ex.params;
+        auto w16 = [](float v) { return __half2float(__float2half_rn(v)); };
+        if (tid < kModelHidden) {
+            float acc = w16(p[kOffB1 + tid]);
+            for (int k = 0; k < kModelFeatures; ++k) acc = fmaf(w16(p[tid * kModelFeatures + k]), x_s[k], acc);
+            h1_s[tid] = tanhf(acc);
+        }
+        __syncthreads();
+        if (tid < kModelHidden) {
+            float acc = w16(p[kOffB2 + tid]);
+            for (int k = 0; k < kModelHidden; ++k) acc = fmaf(w16(p[kOffW2 + tid * kModelHidden + k]), h1_s[k], acc);
+            const float h2 = tanhf(acc);
+            float y0 = w16(p[kOffW3 + tid]) * h2, y1 = w16(p[kOffW3 + kModelHidden + tid]) * h2;
 #pragma unroll
-                for (int qq = 0; qq < kQB; ++qq)
-#pragma unroll
-                    for (int p = 0; p < kSmallB; ++p)
-                        v[qq][p] = (vo >= 0 && q0 + qq < bc && p < br) ? H[vo + static_cast<int64_t>(q0 + qq) * br + p] : R(0);
-#pragma unroll
-                for (int qq = 0; qq < kQB; ++qq) {
-                    const int q = q0 + qq;
-                    if (q >= bc) break;
-                    const int64_t xo = static_cast<int64_t>(ls[c] + q) * s.ld + y0;
-                    R acc = R(0), dsel = R(0);
-                    float sq = 0.f;
-#pragma unroll
-                    for (int p = 0; p < kSmallB; ++p) {
-                        if (p >= br) break;
-                        R w = v[qq][p];
-                        if (a == c && p == q) {
-                            w -= mu;
-                            dsel = w;
-                        }
-                        t[xo + p] = w;
-                        acc += fabs(w);
-                        sq = fmaf(static_cast<float>(w), static_cast<float>(w), sq);
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                        sq += __shfl_xor_sync(0xffffffffu, sq, o);
-                    }
-                    racc[qq] += acc;
-                    rsq[qq] += sq;
-                    if ((c >> 5) == (a0 >> 5)) rdg[qq] = __shfl_sync(0xffffffffu, dsel, c & 31);
-                }
+            for (int o = 16; o > 0; o >>= 1) {
+                y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+                y1 += __shfl_xor_sync(0xffffffffu, y1, o);
             }
-#pragma unroll
-            for (int qq = 0; qq < kQB; ++qq) {
-                if (q0 + qq >= bc) break;
-                const float d = static_cast<float>(rdg[qq]);
-                m = fmax(m, static_cast<double>(racc[qq]));
-                const float ad = fabsf(d), rr = static_cast<float>(racc[qq]) - ad;
-                f2 += rsq[qq];
-                da += ad;
-                ds += d;
-                dq = fmaf(d, d, dq);
-                rs += rr;
-                dm = fmaxf(dm, ad);
-                rm = fmaxf(rm, rr);
+            if (lane == 0) {
+                y_s[warp][0] = y0;
+                y_s[warp][1] = y1;
             }
         }
+        __syncthreads();
+        const float y0 = (y_s[0][0] + y_s[1][0]) + w16(p[kOffB3]);
+        const float y1 = (y_s[0][1] + y_s[1][1]) + w16(p[kOffB3 + 1]);
+        if (tid == 0 && ex.pred) {
+            ex.pred[2 * static_cast<int64_t>(blockIdx.x)] = y0;
+            ex.pred[2 * static_cast<int64_t>(blockIdx.x) + 1] = y1;
+        }
+        b = g * fmin(fmax(static_cast<double>(y0), 0.02), 1.0) * (1.0 + ex.margin) / 1.2;
     }
-    gather_finish<R>(s, ex, bound, m, f2, da, ds, dq, rs, dm, rm);
+    if (tid == 0) {
+        bound[blockIdx.x] = b;
+        if (ex.gersh) ex.gersh[blockIdx.x] = g;
+    }
 }
 
 template <class R>
 static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
                                  const R* H, double mu, R* T, double* bound, const GatherExtras& ex, cudaStream_t st) {
-    if (ex.bmax > 0 && ex.bmax <= kSmallB) {
-        // the block tables of all block columns, R_j and the local starts
-        const size_t smem = static_cast<size_t>(max_nblk) * max_nblk * sizeof(int64_t) +
-                            static_cast<size_t>(2 * max_nblk + 1) * sizeof(int);
-        if (smem <= (200u << 10)) {
-            if (smem > (48u << 10)) {
-                cudaError_t e = cudaFuncSetAttribute(k_gather_small<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     static_cast<int>(smem));
-                if (e != cudaSuccess) return e;
-            }
-            k_gather_small<R><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound, max_nblk, ex);
-            return cudaGetLastError();
-        }
-    }
     // per-warp block tables, R_j, local starts and the local block of every column
     const size_t smem = static_cast<size_t>(8) * max_nblk * sizeof(int64_t) +
                         (static_cast<size_t>(2 * max_nblk + 1) + static_cast<size_t>(max_n)) * sizeof(int);

@@ -426,10 +426,8 @@ static smx_status ns_event_pair(smx_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
 
 // One build at chemical potential mu (a3 - a8).
 // a3 + a4 for block columns [j0, j0 + m) into the staging buffer.
-static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const GatherExtras& ex_in) {
+static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const GatherExtras& ex) {
     const PatternView pv = pattern_view(c);
-    GatherExtras ex = ex_in;
-    ex.bmax = c->bmax;
     SubDesc* subs = dp<SubDesc>(c->d_subs);
     if (c->precision == SMX_FP64) {
         SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, c->max_n, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),

@@ -28,24 +28,26 @@ __device__ void finish_column(const SubDesc& s, const PatternView& pv, const dou
     if (threadIdx.x == 0) smem_ls[s.nblk] = s.n;
     __syncthreads();
     double tr = 0.0, en = 0.0;
-    // one work item per (block a of R_j, column q of block j): the br contiguous values of that
-    // column of block (R_j[a], j) (column-major blocks), consecutive items on consecutive
-    // columns of a block, so a warp writes whole blocks
-    const int items = s.nblk * s.bown;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int a = it / s.bown, q = it - a * s.bown;
-        const int i0 = smem_ls[a], br = smem_ls[a + 1] - i0;
-        const int64_t off = pv.fvoff[s.fptr + a] + static_cast<int64_t>(q) * br;
-        const int idiag = s.own + q - i0;  // row of the diagonal entry inside this chunk, if 0 <= idiag < br
-        for (int p = 0; p < br; ++p) {
-            const bool diag = p == idiag;
-            const double x = xrow(q, i0 + p);
-            const double d = density ? 0.5 * ((diag ? 1.0 : 0.0) - x) : x;
-            D[off + p] = d;
-            if (trace_weight) tr += d * trace_weight[off + p];
-            else if (diag) tr += d;
-            en += d * H[off + p];
+    const int total = s.n * s.bown;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int q = e / s.n;
+        const int i = e - q * s.n;
+        // block a of R_j that contains local row i
+        int lo = 0, hi = s.nblk - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (smem_ls[mid] <= i) lo = mid; else hi = mid - 1;
         }
+        const int64_t k = s.fptr + lo;
+        const int br = smem_ls[lo + 1] - smem_ls[lo];
+        const int p = i - smem_ls[lo];
+        const int64_t off = pv.fvoff[k] + static_cast<int64_t>(q) * br + p;
+        const bool diag = (i == s.own + q);
+        const double d = density ? 0.5 * ((diag ? 1.0 : 0.0) - xrow(q, i)) : xrow(q, i);
+        D[off] = d;
+        if (trace_weight) tr += d * trace_weight[off];
+        else if (diag) tr += d;
+        en += d * H[off];
     }
     tr = block_sum(tr, red_scratch);
     en = block_sum(en, red_scratch);

@@ -43,7 +43,6 @@ struct GatherExtras {
     float* pred = nullptr;               // ... and its two predictions
     float margin = 0.0f;                 // ... b_j = G_j clamp(pred_0, 0.02, 1) (1 + margin) / 1.2
     const double* mu_dev = nullptr;      // when set, mu is read from here (on the device) instead
-    int bmax = 0;                        // largest block size (0: unknown), selects the small-block kernel
 };
 
 // a3 + a4: T_j = H[R_j, R_j] - mu I into the FP64 staging buffer, then the
