@@ -471,8 +471,10 @@ def train_heldout_model(args, w, stream):
         # two rounds per system: the second sees the previous-step feature of the first
         for _ in range(2):
             ctx.set_values(sysm.values)
-            if _fixed_mu(w):
-                ctx.set_mu(float(w["mu"]))
+            if _fixed_mu(w) or args.per_build:
+                # fixed mu; for the per-build runs of the heavy bisection workloads the mid-gap
+                # mu = 0 of these generators stands in for a full solve
+                ctx.set_mu(float(w["mu"]) if _fixed_mu(w) else 0.0)
                 ctx.build_density()
             else:
                 ctx.set_electron_count(w["n_e"], max_steps=30, tol=1e-2)
@@ -603,10 +605,49 @@ def run_ours(args):
     if model_path:
         ctx.bound_model_init(0)
 
+    # --per-build: a step is one build at the solved mu (a density matrix at a given mu); the full
+    # bisection is timed once beside it
+    mu_fixed = float(w["mu"]) if fixed else None
+    solve_once = None
+    if args.per_build and not fixed:
+        ctx.set_precision(args.precision)
+        if model_path:
+            ctx.set_bound_model(args.bound_mode, model_path if args.bound_mode != "off" else None)
+        ctx.set_values(h_dev, on_device=True)
+        ctx.set_mu(0.0)
+        ctx.build_density()  # warm (pattern analysis, workspace)
+        torch.cuda.synchronize()
+        ctx.set_values(h_dev, on_device=True)
+        ctx.reset_counters()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.solve_mu()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sst = ctx.get_stats()
+        mu_fixed = ctx.get_trace()[2]
+        solve_once = {"seconds": e0.elapsed_time(e1) / 1e3, "bisection_builds": sst["bisection_steps"],
+                      "mu": mu_fixed, "trace": ctx.get_trace()[0], "iters_mean_last_build": sst["iters_mean"],
+                      "host_reads": sst["bisection_steps"] + 1}
+        if args.mu_device:
+            # the same solve with the bisection's decisions on the device (one host read)
+            ctx.set_values(h_dev, on_device=True)
+            ctx.set_mu(0.0)
+            ctx.build_density()  # the filter of the new values (not part of the solve)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ctx.solve_mu_device()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            solve_once["device_loop"] = {"seconds": e0.elapsed_time(e1) / 1e3,
+                                         "bisection_builds": ctx.get_stats()["bisection_steps"],
+                                         "mu": ctx.get_trace()[2], "same_mu": ctx.get_trace()[2] == mu_fixed,
+                                         "host_reads": 1}
+
     def step():
         ctx.set_values(h_dev, on_device=True)
-        if fixed:
-            ctx.set_mu(float(w["mu"]))
+        if mu_fixed is not None:
+            ctx.set_mu(mu_fixed)
             ctx.build_density()
         else:
             ctx.solve_mu()
@@ -647,7 +688,7 @@ def run_ours(args):
 
     # -- the other spectral-bound modes (same form, same workload) -----------------
     modes = {}
-    if model_path:
+    if model_path and args.mode_steps > 0:
         for mode in ["off", "rho", "gap"]:
             if mode != args.bound_mode:
                 m0, s0, _ = timed(args.mode_steps, args.precision, mode, warmup=1)
@@ -691,8 +732,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.set_values(h_np)
-        if fixed:
-            ctx.set_mu(float(w["mu"]))
+        if mu_fixed is not None:
+            ctx.set_mu(mu_fixed)
             ctx.build_density()
         else:
             ctx.solve_mu()
@@ -701,7 +742,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         if k >= args.warmup:
             e2e_times.append(t1 - t0)
-            bis_steps.append(ctx.get_stats()["bisection_steps"] if not fixed else 1)
+            bis_steps.append(ctx.get_stats()["bisection_steps"] if mu_fixed is None else 1)
     e2e_s = sum(e2e_times)
     if pg:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
@@ -770,6 +811,43 @@ def run_ours(args):
                "sample": f"{len(cols)} of {sysm.n_blocks} block columns at the GPU's final mu, "
                          f"time x{scale:.1f} (sum n_j^3 all / sample) x{builds} bisection build(s)"}
 
+    # -- precision study: single-pass bulk forms and FP64 finishing steps, same mu, same columns --
+    study = None
+    if rank == 0 and cpu is not None and not args.no_study and not big:
+        from paper_2205_14741_gb300 import SmxError
+
+        study = []
+        if model_path:
+            ctx.set_bound_model("off")
+        for prec, final in [("fp16x3", 0), ("fp16x3", 1), ("fp16", 0), ("fp16", 2), ("bf16", 0), ("bf16", 2)]:
+            row = {"bulk": prec, "fp64_final_iters": final}
+            try:
+                ctx.set_precision(prec, final)
+                ctx.set_mu(mu)
+                for _ in range(2):
+                    ctx.build_density()
+                torch.cuda.synchronize()
+                ctx.reset_counters()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(5):
+                    ctx.build_density()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                sst = ctx.get_stats()
+                dv = ctx.get_density()
+                err = 0.0
+                for j in cols:
+                    for k in range(sysm.col_ptr[j], sysm.col_ptr[j + 1]):
+                        a_ = dv[off[k]:off[k + 1]]
+                        b_ = res.values[off_f[kf[k]]:off_f[kf[k] + 1]] if keep[k] else np.zeros_like(a_)
+                        err = max(err, float(np.max(np.abs(a_ - b_))))
+                row.update(ms_per_build=e0.elapsed_time(e1) / 5, iters_mean=sst["iters_mean"], d_max_abs_err=err)
+            except SmxError as e:
+                row["status"] = str(e)
+            study.append(row)
+        ctx.set_precision(args.precision)
+
     learned = None
     if rank == 0 and world == 1 and args.learned_snapshots > 0 and args.workload == "water1024":
         learned = learned_scaling(args, stream)
@@ -786,7 +864,8 @@ def run_ours(args):
                                           "rho": "learned rho_hat (held-out training), plain steps",
                                           "gap": "learned rho_hat and gap (held-out training), scaled steps"}[
                            args.bound_mode],
-                       "mu": "fixed" if fixed else "bisection (tol 1e-2)",
+                       "mu": ("fixed" if fixed else "one build per step at the mu of a full bisection "
+                              "(timed once: mu_solve)" if args.per_build else "bisection (tol 1e-2)"),
                        "bisection_builds_per_step": float(np.mean(bis_steps)) if bis_steps else None,
                        "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
             "submatrix_tflops": submatrix_tflops,
@@ -807,6 +886,10 @@ def run_ours(args):
                                                                       * max(1.0, float(np.mean(bis_steps))))}
                             if model_path else None),
             "learned_scaling": learned,
+            "mu_solve": solve_once,
+            "precision_study": ({"note": "builds at the headline's mu, a-posteriori Gershgorin start, 5 builds "
+                                         "timed after 2; D error on the CPU-baseline columns",
+                                 "rows": study} if study else None),
         }
         print(json.dumps(out))
     ctx.close()
@@ -830,6 +913,10 @@ def main():
     ap.add_argument("--mode-steps", type=int, default=5, help="timed steps of each non-headline bound mode")
     ap.add_argument("--e2e-steps", type=int, default=None, help="end-to-end steps (default: --steps)")
     ap.add_argument("--max-steps", type=int, default=30, help="bisection steps at most")
+    ap.add_argument("--mu-device", action="store_true",
+                    help="with --per-build: also time the solve with the bisection's decisions on the device")
+    ap.add_argument("--per-build", action="store_true",
+                    help="a step is one build at the solved mu; the full bisection is timed once")
     ap.add_argument("--shard", action="store_true",
                     help="one system split over the ranks by block columns (strong scaling)")
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -837,6 +924,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-functions", action="store_true", help="skip the A^-1/2 and non-orthogonal (FP64) legs")
+    ap.add_argument("--no-study", action="store_true", help="skip the precision study (single-pass, FP64 finish)")
     ap.add_argument("--function-steps", type=int, default=3)
     ap.add_argument("--learned-snapshots", type=int, default=200,
                     help="trajectory length of the learned-bound report (0 skips it)")

@@ -89,12 +89,20 @@ typedef enum {
  *                   sign iteration of the Eq. 12 block matrix [[0, A], [I, 0]]
  *                   written per block (coupled Newton-Schulz);
  *   SMX_FN_INV      (H - mu I)^(-1) for the same inputs: the square of the
- *                   iteration's (H - mu I)^(-1/2), owner columns only. */
+ *                   iteration's (H - mu I)^(-1/2), owner columns only;
+ *   SMX_FN_FERMI    the finite-temperature Fermi function
+ *                   (I + exp(beta (H - mu I)))^(-1) = 1/2 (I - tanh(beta (H - mu I)/2)),
+ *                   the finite-temperature counterpart of Eq. 14 (beta from
+ *                   smx_set_fermi_beta): per submatrix, tanh by a Taylor start at
+ *                   a small argument and k doublings tanh(2x) = 2 tanh(x)/(1 + tanh^2 x),
+ *                   each with a Newton-Schulz inverse of I + T^2 (products only;
+ *                   about 7 + 11 k products, k = log2(8 beta G_j)). */
 typedef enum {
     SMX_FN_DENSITY = 0,
     SMX_FN_INV_SQRT = 1,
     SMX_FN_SQRT = 2,
-    SMX_FN_INV = 3
+    SMX_FN_INV = 3,
+    SMX_FN_FERMI = 4
 } smx_function;
 
 /* Statistics of the last build (or the last bisection step). */
@@ -191,8 +199,14 @@ smx_status smx_set_mu(smx_ctx* ctx, double mu);
  * Errors: SMX_ERR_ARG. */
 smx_status smx_set_electron_count(smx_ctx* ctx, double n_e, int32_t max_steps, double tol);
 
-/* Arithmetic of the Newton-Schulz iteration; fp64_final_iters (0..4) FP64
- * iterations follow the bulk phase when bulk != SMX_FP64.  Errors: SMX_ERR_ARG. */
+/* Arithmetic of the Newton-Schulz iteration (Eq. 13; Section 3's low-precision
+ * units).  fp64_final_iters (0..4): when bulk != SMX_FP64, that many plain
+ * Newton-Schulz steps in FP64 (CUDA cores) follow the bulk phase's stopping
+ * rule, on its last iterate, before the owner columns are scattered (the
+ * density matrix only; ignored for SMX_FP64).  Note that they restore
+ * X^2 = I but not the occupied subspace a single-pass bulk phase has rotated
+ * (a rounding error that anticommutes with the sign persists through later
+ * steps), so D keeps an error of the bulk's order.  Errors: SMX_ERR_ARG. */
 smx_status smx_set_precision(smx_ctx* ctx, smx_precision bulk, int32_t fp64_final_iters);
 
 /* The matrix function of the following builds.  The function forms run in
@@ -203,6 +217,10 @@ smx_status smx_set_precision(smx_ctx* ctx, smx_precision bulk, int32_t fp64_fina
  * SMX_ERR_NOCONV or SMX_ERR_NONFINITE.  smx_solve_mu needs SMX_FN_DENSITY
  * (SMX_ERR_STATE otherwise).  Errors: SMX_ERR_ARG (unknown f). */
 smx_status smx_set_function(smx_ctx* ctx, smx_function f);
+
+/* Inverse temperature beta >= 0 (in inverse units of H) of SMX_FN_FERMI.
+ * Default 0 (F = I/2).  Errors: SMX_ERR_ARG (negative or non-finite). */
+smx_status smx_set_fermi_beta(smx_ctx* ctx, double beta);
 
 /* Non-orthogonal basis (Eq. 14 with an overlap S != I).  values: S on the
  * block pattern given to smx_create, in the same layout as H (n_values
@@ -241,6 +259,18 @@ smx_status smx_build_density(smx_ctx* ctx);
  * Errors: as smx_build_density, plus SMX_ERR_STATE (no electron count set),
  * SMX_ERR_NOBRACKET, and latched device errors. */
 smx_status smx_solve_mu(smx_ctx* ctx);
+
+/* The same bisection as smx_solve_mu with its decisions taken on the device
+ * (Eq. 14's mu; a device-side loop): the bracket and the current midpoint live
+ * in device memory, every step is a build reading mu from there followed by a
+ * one-thread update, and all max_steps steps are enqueued at once; once the
+ * stopping rule holds (or after max_steps builds) the later steps' kernels
+ * return at once.  The result (mu, D, trace) is that of smx_solve_mu from the
+ * same state, bit for bit, and the host waits once (plus once for the filter
+ * when the values are new: the filtered pattern must be known before the
+ * builds are enqueued).  Not for the non-orthogonal form
+ * (SMX_ERR_UNSUPPORTED).  Errors: as smx_solve_mu. */
+smx_status smx_solve_mu_device(smx_ctx* ctx);
 
 /* trace(D), trace(D H) (the band-structure energy, unshifted H) and mu of the
  * last build, D being Eq. 14's density matrix assembled by Fig. 2 (trace(D)

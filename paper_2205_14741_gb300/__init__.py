@@ -121,10 +121,14 @@ class SubmatrixDensity:
         check(self._lib.smx_set_precision(self._ctx, p, int(fp64_final_iters)), "smx_set_precision")
 
     def set_function(self, f="density"):
-        """Matrix function of the following builds: "density" (default), "inv_sqrt", "sqrt" or "inv"
-        (FP64 form; see smx_set_function)."""
+        """Matrix function of the following builds: "density" (default), "inv_sqrt", "sqrt", "inv" or
+        "fermi" (FP64 form; see smx_set_function and smx_set_fermi_beta)."""
         check(self._lib.smx_set_function(self._ctx, FUNCTIONS[f] if isinstance(f, str) else int(f)),
               "smx_set_function")
+
+    def set_fermi_beta(self, beta: float):
+        """Inverse temperature of the "fermi" function form (smx_set_fermi_beta)."""
+        check(self._lib.smx_set_fermi_beta(self._ctx, float(beta)), "smx_set_fermi_beta")
 
     def set_overlap(self, values=None, on_device: bool = False):
         """Overlap S on the input pattern (non-orthogonal form of Eq. 14; see smx_set_overlap);
@@ -143,6 +147,10 @@ class SubmatrixDensity:
 
     def solve_mu(self):
         check(self._lib.smx_solve_mu(self._ctx), "smx_solve_mu")
+
+    def solve_mu_device(self):
+        """The bisection with its decisions on the device (smx_solve_mu_device)."""
+        check(self._lib.smx_solve_mu_device(self._ctx), "smx_solve_mu_device")
 
     # -- results ------------------------------------------------------------
     def get_trace(self):

@@ -19,8 +19,8 @@ OK, ERR_ARG, ERR_PATTERN, ERR_NONFINITE, ERR_CUDA, ERR_OOM, ERR_NOCONV, ERR_NOBR
 FP64, FP16X3, FP16, BF16 = range(4)
 PRECISIONS = {"fp64": FP64, "fp16x3": FP16X3, "fp16": FP16, "bf16": BF16}
 # smx_function: matrix function of a build
-FN_DENSITY, FN_INV_SQRT, FN_SQRT, FN_INV = 0, 1, 2, 3
-FUNCTIONS = {"density": FN_DENSITY, "inv_sqrt": FN_INV_SQRT, "sqrt": FN_SQRT, "inv": FN_INV}
+FN_DENSITY, FN_INV_SQRT, FN_SQRT, FN_INV, FN_FERMI = 0, 1, 2, 3, 4
+FUNCTIONS = {"density": FN_DENSITY, "inv_sqrt": FN_INV_SQRT, "sqrt": FN_SQRT, "inv": FN_INV, "fermi": FN_FERMI}
 # learned spectral bound
 BOUND_MODEL_FEATURES = 9
 BOUND_MODEL_PARAMS = 4930
@@ -70,6 +70,7 @@ SIGNATURES = {
     "smx_set_electron_count": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_double]),
     "smx_set_precision": (C.c_int, [C.c_void_p, C.c_int, C.c_int32]),
     "smx_set_function": (C.c_int, [C.c_void_p, C.c_int]),
+    "smx_set_fermi_beta": (C.c_int, [C.c_void_p, C.c_double]),
     "smx_set_overlap": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "smx_build_density": (C.c_int, [C.c_void_p]),
     "smx_solve_mu": (C.c_int, [C.c_void_p]),
@@ -87,6 +88,7 @@ SIGNATURES = {
     "smx_bound_model_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     "smx_set_bound_model": (C.c_int, [C.c_void_p, C.c_int32, C.c_char_p]),
     "smx_bound_model_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "smx_solve_mu_device": (C.c_int, [C.c_void_p]),
     "smx_selftest_wait_timeout": (C.c_int, [C.c_void_p, C.c_uint32]),
     "smx_reset_counters": (C.c_int, [C.c_void_p]),
     "smx_get_submatrix_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

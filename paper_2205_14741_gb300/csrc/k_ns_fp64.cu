@@ -116,6 +116,108 @@ __device__ int coupled_ns(double*& Yb, double*& Zb, double*& Tb, double*& Nb, in
     return done;
 }
 
+// The finite-temperature Fermi function F = (I + exp(beta A))^-1 = 1/2 (I - tanh(beta A / 2)) of
+// a symmetric A, from X = A / g (g >= the spectral radius of A), in products only:
+//   B = (beta g / 2) X / 2^k with k such that ||B|| <= 1/16;
+//   T = tanh(B) by its odd Taylor series to degree 11 (the next term is below 1e-18 there);
+//   k doublings tanh(2x) = 2 tanh(x) / (1 + tanh(x)^2): T <- 2 T (I + T^2)^-1, the inverse by
+//   Newton-Schulz V <- V + V (I - M V) from V = 4/3 I - 4/9 M (the first step from 2/3 I in
+//   closed form; M = I + T^2 has its eigenvalues in [1, 2], so the residual I - M V starts
+//   below 1/9 and squares every step) until ||I - M V||_F <= 1e-15 sqrt(n);
+//   F = 1/2 (I - T).
+// A doubling at most doubles an error in T, so k doublings cost about 2^k rounding errors
+// (k = 11 at beta g = 150).  Five n x n buffers (X first); returns the one holding F and counts
+// the products in nprod.
+__device__ double* fermi_tanh(double* X, double* B1, double* B2, double* B3, double* B4, int n, int ld, double beta_g,
+                              double (*As)[kTile + 1], double (*Bs)[kTile + 1], double* scratch, int& nprod, bool& bad) {
+    int k = 0;
+    double sc = 0.5 * beta_g;
+    while (sc > 1.0 / 16.0 && k < 60) {
+        sc *= 0.5;
+        ++k;
+    }
+    // M <- alpha M + d I
+    auto axpy_diag = [&](double* M, double alpha, double d) {
+        for (int r = threadIdx.x / 32; r < n; r += 8)
+            for (int c = threadIdx.x & 31; c < n; c += 32) {
+                double& v = M[static_cast<int64_t>(r) * ld + c];
+                v = alpha * v + (r == c ? d : 0.0);
+            }
+        __syncthreads();
+    };
+    auto prod = [&](const double* A, const double* B, double* C) {
+        gemm_fp64(A, B, C, n, ld, 2, As, Bs);
+        __syncthreads();
+        ++nprod;
+    };
+    nprod = 0;
+    bad = false;
+    // T = tanh(B): X <- B in place, Y = B^2, Horner in Y, T = B p(B^2)
+    axpy_diag(X, sc, 0.0);
+    double* Y = B1;
+    double* P = B2;
+    double* Q = B3;
+    prod(X, X, Y);
+    const double c[6] = {1.0, -1.0 / 3.0, 2.0 / 15.0, -17.0 / 315.0, 62.0 / 2835.0, -1382.0 / 155925.0};
+    for (int r = threadIdx.x / 32; r < n; r += 8)
+        for (int cc = threadIdx.x & 31; cc < n; cc += 32) {
+            const int64_t o = static_cast<int64_t>(r) * ld + cc;
+            P[o] = c[5] * Y[o] + (r == cc ? c[4] : 0.0);
+        }
+    __syncthreads();
+    for (int i = 3; i >= 0; --i) {
+        prod(P, Y, Q);
+        axpy_diag(Q, 1.0, c[i]);
+        double* t = P; P = Q; Q = t;
+    }
+    prod(X, P, Q);
+    double* T = Q;
+    double* fr[4] = {X, Y, P, B4};  // free buffers
+    for (int d = 0; d < k && !bad; ++d) {
+        double *M = fr[0], *V = fr[1], *R = fr[2], *Vn = fr[3];
+        prod(T, T, M);  // M = I + T^2
+        axpy_diag(M, 1.0, 1.0);
+        for (int r = threadIdx.x / 32; r < n; r += 8)
+            for (int cc = threadIdx.x & 31; cc < n; cc += 32) {
+                const int64_t o = static_cast<int64_t>(r) * ld + cc;
+                V[o] = (r == cc ? 4.0 / 3.0 : 0.0) - 4.0 / 9.0 * M[o];
+            }
+        __syncthreads();
+        for (int m = 0; m < 12; ++m) {
+            prod(M, V, R);  // R = I - M V
+            double r2 = 0.0;
+            for (int r = threadIdx.x / 32; r < n; r += 8)
+                for (int cc = threadIdx.x & 31; cc < n; cc += 32) {
+                    const int64_t o = static_cast<int64_t>(r) * ld + cc;
+                    const double e = (r == cc ? 1.0 : 0.0) - R[o];
+                    R[o] = e;
+                    r2 += e * e;
+                }
+            r2 = block_sum(r2, scratch);
+            if (!isfinite(r2)) { bad = true; break; }
+            if (sqrt(r2) <= 1e-15 * sqrt(static_cast<double>(n))) break;
+            prod(V, R, Vn);  // V <- V + V R
+            for (int r = threadIdx.x / 32; r < n; r += 8)
+                for (int cc = threadIdx.x & 31; cc < n; cc += 32) {
+                    const int64_t o = static_cast<int64_t>(r) * ld + cc;
+                    Vn[o] += V[o];
+                }
+            __syncthreads();
+            double* t = V; V = Vn; Vn = t;
+        }
+        prod(T, V, R);  // T <- 2 T V
+        axpy_diag(R, 2.0, 0.0);
+        double* oldT = T;
+        T = R;
+        fr[0] = oldT;
+        fr[1] = M;
+        fr[2] = V;
+        fr[3] = Vn;
+    }
+    axpy_diag(T, -0.5, 0.5);  // F = 1/2 (I - T)
+    return T;
+}
+
 // Gershgorin interval (lo, hi) of an n x n matrix held row by row.
 __device__ double2 gershgorin_interval(const double* M, int n, int ld, double* scratch) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
@@ -183,6 +285,7 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
     __shared__ double Bs[kKc][kTile + 1];
     __shared__ double scratch[32];
     extern __shared__ int ls_smem[];
+    if (a.skip && *a.skip) return;
     const SubDesc s = a.subs[blockIdx.x];
     const int n = s.n, ld = s.ld;
     double* X = a.T + s.t_off;
@@ -215,6 +318,28 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
         }
         __syncthreads();
     }
+    if (a.finish_iters > 0) {
+        // FP64 finishing steps after a low-precision bulk phase: X (in T) is that phase's last
+        // iterate; plain Newton-Schulz steps in FP64, then the scatter of the owner columns
+        bool bad = false;
+        for (int it = 0; it < a.finish_iters; ++it) {
+            double r2 = gemm_fp64(X, X, Y, n, ld, 1, As, Bs);  // Y = 3/2 I - 1/2 X^2
+            r2 = block_sum(r2, scratch);
+            gemm_fp64(X, Y, Z, n, ld, 2, As, Bs);
+            __syncthreads();
+            double* tmp = X; X = Z; Z = tmp;
+            if (!isfinite(r2)) bad = true;
+        }
+        if (threadIdx.x == 0) {
+            a.iters[s.col] += a.finish_iters;
+            atomicAdd(a.work_n3, static_cast<unsigned long long>(n) * n * n * a.finish_iters);
+            if (bad) atomicCAS(a.status, kOk, kErrNonfinite);
+        }
+        const double* Xf = X;
+        auto xrow = [&](int q, int i) -> double { return Xf[static_cast<int64_t>(s.own + q) * ld + i]; };
+        finish_column(s, a.pv, a.H, a.D, a.partial, xrow, ls_smem, scratch);
+        return;
+    }
     const double inv_b = 1.0 / a.bound[blockIdx.x];
     // learned bound: the predicted smallest |eigenvalue| of X0 = (T_j - mu I) / b_j (negative:
     // no prediction), and the lower end the scaled schedule assumes (1 = plain steps)
@@ -226,6 +351,21 @@ __global__ void __launch_bounds__(256) k_ns_fp64(NsFp64Args a) {
 
     int done = 0;
     bool conv = false, bad = false;
+    if (a.function == kFnFermi) {
+        // the Fermi function of A = T_j - mu I (now A / b in X, b its Gershgorin bound)
+        int nprod = 0;
+        bool bad = false;
+        const double* F = fermi_tanh(X, Y, Z, a.W3 + s.t_off, a.W4 + s.t_off, n, ld,
+                                     a.beta * a.bound[blockIdx.x], As, Bs, scratch, nprod, bad);
+        if (threadIdx.x == 0) {
+            a.iters[s.col] = nprod;
+            atomicAdd(a.work_n3, static_cast<unsigned long long>(n) * n * n * nprod);
+            if (bad) atomicCAS(a.status, kOk, kErrNonfinite);
+        }
+        auto frow = [&](int q, int i) -> double { return F[static_cast<int64_t>(s.own + q) * ld + i]; };
+        finish_column(s, a.pv, a.H, a.D, a.partial, frow, ls_smem, scratch, false);
+        return;
+    }
     if (a.function != kFnDensity) {
         // f = A^-1/2 or A^1/2 for a symmetric positive definite A = T_j - mu I (now A/b in X)
         double* Yb = X;

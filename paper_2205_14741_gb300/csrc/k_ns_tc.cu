@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     using C = TcCfg<PREC>;
     constexpr int NB = C::kNb, S = C::kStages, NT = C::kNmax;
     extern __shared__ uint8_t smem_raw[];
+    if (a.skip && *a.skip) return;  // a skipped step of a device-side bisection (uniform: set before launch)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
 
     __shared__ uint64_t full_bar[S], empty_bar[S], tfull[2], tempty[2], drain_bar;
@@ -1406,6 +1407,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             atomicAdd(a.work_n3, static_cast<unsigned long long>(s.n) * s.n * s.n * done);
             if (bad_s) atomicCAS(a.status, kOk, kErrNonfinite);
             else if (!conv_s) atomicCAS(a.status, kOk, kErrNoconv);
+        }
+        // the whole final X for FP64 finishing steps
+        if (a.xfull) {
+            double* xf = a.xfull + s.t_off;
+            for (int e = tid; e < s.n * s.n; e += blockDim.x) {
+                const int r = e / s.n, c = e - r * s.n;
+                float x;
+                if (resident) {
+                    const uint32_t off = img_offset(r, c, RB);
+                    x = from16<PREC>(*reinterpret_cast<const uint16_t*>(smem + hi_off + off));
+                    if constexpr (NB == 2) x += from16<PREC>(*reinterpret_cast<const uint16_t*>(smem + lo_off + off));
+                } else {
+                    const int64_t o = static_cast<int64_t>(r) * a.ld + c;
+                    const uint16_t* fh = ws + static_cast<int64_t>(cur ? zx1 : zx0) * buf;
+                    x = from16<PREC>(fh[o]);
+                    if constexpr (NB == 2) x += from16<PREC>(fh[buf + o]);
+                }
+                xf[static_cast<int64_t>(r) * s.ld + c] = static_cast<double>(x);
+            }
         }
         // save columns own .. own + b_j of the final X (the method keeps the
         // columns; the iterate is symmetric only up to rounding) for the scatter

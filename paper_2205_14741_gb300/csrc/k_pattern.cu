@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(co
     __shared__ double warp_max_s[8];
     __shared__ float stat_s[8][7];  // per warp: F2, Da, Ds, Dq, Rs (sums), Dm, Rm (maxima)
     __shared__ float x_s[kModelFeatures], h1_s[kModelHidden], y_s[2][2];
+    if (ex.skip && *ex.skip) return;
     const R mu = static_cast<R>(ex.mu_dev ? *ex.mu_dev : mu_d);
     const SubDesc s = subs[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -441,7 +442,8 @@ __device__ void sum_partials(const double2* partial, int n_cols, DevScalars* sc,
 __global__ void __launch_bounds__(256) k_scatter_owner(const SubDesc* __restrict__ subs, PatternView pv,
                                                        const float* __restrict__ xown, const double* __restrict__ H,
                                                        double* __restrict__ D, double2* __restrict__ partial, int n_cols,
-                                                       DevScalars* sc) {
+                                                       DevScalars* sc, const int* skip) {
+    if (skip && *skip) return;
     extern __shared__ int ls_smem[];
     __shared__ double scratch[32];
     __shared__ bool last_s;
@@ -464,19 +466,54 @@ __global__ void __launch_bounds__(256) k_scatter_owner(const SubDesc* __restrict
 
 cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
                                  const float* xown, const double* H, double* D, double2* partial, int n_cols,
-                                 DevScalars* sc, cudaStream_t st) {
+                                 DevScalars* sc, cudaStream_t st, const int* skip) {
     const size_t smem = sizeof(int) * (static_cast<size_t>(max_nblk) + 1);
-    k_scatter_owner<<<n_subs, 256, smem, st>>>(subs, pv, xown, H, D, partial, n_cols, sc);
+    k_scatter_owner<<<n_subs, 256, smem, st>>>(subs, pv, xown, H, D, partial, n_cols, sc, skip);
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(1024) k_reduce(const double2* __restrict__ partial, int n_cols, DevScalars* sc) {
+__global__ void __launch_bounds__(1024) k_reduce(const double2* __restrict__ partial, int n_cols, DevScalars* sc,
+                                                 const int* skip) {
+    if (skip && *skip) return;
     __shared__ double scratch[32];
     sum_partials(partial, n_cols, sc, scratch);
 }
 
-cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cudaStream_t st) {
-    k_reduce<<<1, 256, 0, st>>>(partial, n_cols, sc);
+cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cudaStream_t st, const int* skip) {
+    k_reduce<<<1, 256, 0, st>>>(partial, n_cols, sc, skip);
+    return cudaGetLastError();
+}
+
+// a9 on the device: the bisection's state lives in the device scalars, so a whole mu solve is
+// enqueued at once (the same decisions as the host loop, in the same FP64 arithmetic).
+__global__ void k_bisect_init(DevScalars* sc, double lo, double hi) {
+    sc->bis_lo = lo;
+    sc->bis_hi = hi;
+    sc->bis_mid = 0.5 * (lo + hi);
+    sc->bis_done = 0;
+    sc->bis_steps = 0;
+}
+
+__global__ void k_bisect_step(DevScalars* sc, double n_e, double tol, int max_steps) {
+    if (sc->bis_done) return;
+    const int steps = ++sc->bis_steps;
+    const double tr = sc->trace, mid = sc->bis_mid;
+    if (sc->status != kOk || fabs(tr - n_e) <= tol || steps >= max_steps) {
+        sc->bis_done = 1;  // the result is the last evaluated mu (and its D)
+        return;
+    }
+    if (tr < n_e) sc->bis_lo = mid;
+    else sc->bis_hi = mid;
+    sc->bis_mid = 0.5 * (sc->bis_lo + sc->bis_hi);
+}
+
+cudaError_t launch_bisect_init(DevScalars* sc, double lo, double hi, cudaStream_t st) {
+    k_bisect_init<<<1, 1, 0, st>>>(sc, lo, hi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bisect_step(DevScalars* sc, double n_e, double tol, int max_steps, cudaStream_t st) {
+    k_bisect_step<<<1, 1, 0, st>>>(sc, n_e, tol, max_steps);
     return cudaGetLastError();
 }
 

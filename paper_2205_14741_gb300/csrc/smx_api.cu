@@ -83,7 +83,7 @@ struct smx_ctx {
     DevBuf d_sc;                      // DevScalars: status, flags, bracket, trace and energy
     DevScalars* h_sc = nullptr;       // pinned copy, filled by fetch()
     DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order;
-    DevBuf d_T, d_W1, d_W2, d_W3, d_ws, d_D, d_xown;
+    DevBuf d_T, d_W1, d_W2, d_W3, d_W4, d_ws, d_D, d_xown;
     DevBuf d_bound, d_iters, d_partial, d_lohi, d_work_n3;
     uint8_t* h_keep_pinned = nullptr;
 
@@ -118,6 +118,7 @@ struct smx_ctx {
     // learned spectral bound
     bool model_ready = false, model_on = false, sq_valid = false;
     bool model_gap = false;  // the learned gap drives the scaled Newton-Schulz schedule
+    double beta = 0.0;       // inverse temperature of SMX_FN_FERMI
     int adam_t = 0;
     int64_t n_samples = 0, cap_samples = 0;
     DevBuf d_params, d_mst, d_vst, d_partial_mlp, d_feat, d_pred, d_labels, d_gersh, d_prev_ratio, d_sq_ratio,
@@ -498,11 +499,13 @@ static smx_status nonorth_setup(smx_ctx* c) {
     return SMX_OK;
 }
 
-// mu_on_device: the gather reads mu from the device scalars (the midpoint the
-// filter just computed) instead of the argument.
-static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
+// mu_dev: when set, the gather reads mu from this device address (the midpoint the filter just
+// computed, or the device-side bisection's current one) instead of the argument.  skip: when
+// set, every kernel of the build returns at once if *skip is non-zero at its launch (the steps
+// after the stopping step of a device-side bisection).
+static smx_status build_at(smx_ctx* c, double mu, const double* mu_dev = nullptr, const int* skip = nullptr) {
     if (c->function != SMX_FN_DENSITY && c->precision != SMX_FP64) return SMX_ERR_UNSUPPORTED;
-    if (c->have_S && (c->function != SMX_FN_DENSITY || c->precision != SMX_FP64 || mu_on_device))
+    if (c->have_S && (c->function != SMX_FN_DENSITY || c->precision != SMX_FP64 || mu_dev))
         return SMX_ERR_UNSUPPORTED;  // the non-orthogonal form: density matrix, FP64
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
     if (c->have_S && !c->nonorth_ready) SMX_TRY(nonorth_setup(c));
@@ -516,9 +519,15 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
         SMX_TRY(ensure(c->d_W1, c->d_T.bytes));
         SMX_TRY(ensure(c->d_W2, c->d_T.bytes));
         if (c->function != SMX_FN_DENSITY) SMX_TRY(ensure(c->d_W3, c->d_T.bytes));
+        if (c->function == SMX_FN_FERMI) SMX_TRY(ensure(c->d_W4, c->d_T.bytes));
     } else {
         SMX_TRY(prepare_tc_workspace(c));
         SMX_TRY(ensure(c->d_xown, static_cast<size_t>(c->x_elems) * sizeof(float)));
+        if (c->fp64_final > 0) {  // the bulk phase's last iterate in FP64, and two work buffers
+            SMX_TRY(ensure(c->d_W1, c->d_T.bytes));
+            SMX_TRY(ensure(c->d_W2, c->d_T.bytes));
+            SMX_TRY(ensure(c->d_W3, c->d_T.bytes));
+        }
     }
     SubDesc* subs = dp<SubDesc>(c->d_subs);
     // one pass of a3-a7 per chunk of block columns (the staging of T_j is reused)
@@ -526,7 +535,8 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
         const int j0 = c->chunk_start[k], m = c->chunk_start[k + 1] - j0;
         GatherExtras ex;
         ex.gersh = dp<double>(c->d_gersh) + j0;
-        if (mu_on_device) ex.mu_dev = &sc->mu0;
+        ex.mu_dev = mu_dev;
+        ex.skip = skip;
         if (model) {  // learned bound: features and prediction inside the gather (checked in the NS kernel)
             ex.prev_ratio = dp<float>(c->d_prev_ratio) + j0;
             ex.params = dp<float>(c->d_params);
@@ -544,6 +554,8 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             a.W1 = dp<double>(c->d_W1);
             a.W2 = dp<double>(c->d_W2);
             a.W3 = c->function != SMX_FN_DENSITY ? dp<double>(c->d_W3) : nullptr;
+            a.W4 = c->function == SMX_FN_FERMI ? dp<double>(c->d_W4) : nullptr;
+            a.beta = c->beta;
             a.function = c->function;
             a.bound = dp<double>(c->d_bound) + j0;
             a.tau = tau_for(SMX_FP64);
@@ -554,6 +566,7 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             a.sq_ratio = dp<float>(c->d_sq_ratio) + j0;
             a.use_model = model ? 1 : 0;
             if (model && c->model_gap) a.pred = dp<float>(c->d_pred) + 2 * j0;
+            a.skip = skip;
             a.fallbacks = &sc->fallbacks;
             a.status = &sc->status;
             a.pv = pv;
@@ -588,6 +601,7 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             a.sq_ratio = dp<float>(c->d_sq_ratio);
             a.use_model = model ? 1 : 0;
             if (model && c->model_gap) a.pred = dp<float>(c->d_pred);
+            a.skip = skip;
             a.fallbacks = &sc->fallbacks;
             a.status = &sc->status;
             a.pv = pv;
@@ -595,18 +609,54 @@ static smx_status build_at(smx_ctx* c, double mu, bool mu_on_device = false) {
             a.D = dp<double>(c->d_D);
             a.partial = dp<double2>(c->d_partial);
             a.xown = dp<float>(c->d_xown);
+            const bool finish = c->fp64_final > 0 && c->function == SMX_FN_DENSITY;
+            if (finish) a.xfull = dp<double>(c->d_W1);
             SMX_CUDA(cudaEventRecord(ns0, st));
             SMX_CUDA(launch_ns_tc(a, c->precision, c->tmap, c->max_nblk, st));
+            if (finish) {
+                // FP64 finishing steps on the bulk phase's last iterate, then the scatter (the
+                // tensor-core scatter, which also resets the job counter, is not run)
+                SMX_CUDA(cudaMemsetAsync(&sc->ns_counter, 0, sizeof(int), st));
+                NsFp64Args f;
+                f.subs = subs + j0;
+                f.n_subs = m;
+                f.T = dp<double>(c->d_W1);
+                f.W1 = dp<double>(c->d_W2);
+                f.W2 = dp<double>(c->d_W3);
+                f.W3 = nullptr;
+                f.function = SMX_FN_DENSITY;
+                f.bound = dp<double>(c->d_bound) + j0;
+                f.tau = tau_for(SMX_FP64);
+                f.max_iter = c->fp64_final;
+                f.iters = dp<int32_t>(c->d_iters);
+                f.work_n3 = dp<unsigned long long>(c->d_work_n3);
+                f.gersh = dp<double>(c->d_gersh) + j0;
+                f.sq_ratio = dp<float>(c->d_sq_ratio) + j0;
+                f.use_model = 0;
+                f.fallbacks = &sc->fallbacks;
+                f.status = &sc->status;
+                f.pv = pv;
+                f.H = dp<double>(c->d_H);
+                f.D = dp<double>(c->d_D);
+                f.partial = dp<double2>(c->d_partial);
+                f.finish_iters = c->fp64_final;
+                f.skip = skip;
+                SMX_CUDA(launch_ns_fp64(f, c->max_nblk, st));
+                c->kernel_launches += 1;
+            }
             SMX_CUDA(cudaEventRecord(ns1, st));
-            SMX_CUDA(launch_scatter_owner(subs + j0, m, c->max_nblk, pv, dp<float>(c->d_xown), dp<double>(c->d_H),
-                                          dp<double>(c->d_D), dp<double2>(c->d_partial), B, sc, st));
-            c->kernel_launches += 1;
+            if (!finish) {
+                SMX_CUDA(launch_scatter_owner(subs + j0, m, c->max_nblk, pv, dp<float>(c->d_xown), dp<double>(c->d_H),
+                                              dp<double>(c->d_D), dp<double2>(c->d_partial), B, sc, st, skip));
+                c->kernel_launches += 1;
+            }
         }
         c->kernel_launches += 1;
         c->ns_launches += 1;
     }
-    if (c->precision == SMX_FP64) {  // the tensor-core scatter sums the partials itself
-        SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), B, sc, st));
+    if (c->precision == SMX_FP64 || (c->fp64_final > 0 && c->function == SMX_FN_DENSITY)) {
+        // the tensor-core scatter sums the partials itself
+        SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), B, sc, st, skip));
         c->kernel_launches += 1;
     }
     SMX_CUDA(cudaEventRecord(c->ev1, st));
@@ -808,7 +858,7 @@ smx_status smx_set_precision(smx_ctx* c, smx_precision bulk, int32_t fp64_final_
     if (!c) return SMX_ERR_ARG;
     if (bulk != SMX_FP64 && bulk != SMX_FP16X3 && bulk != SMX_FP16 && bulk != SMX_BF16) return SMX_ERR_ARG;
     if (fp64_final_iters < 0 || fp64_final_iters > 4) return SMX_ERR_ARG;
-    if (fp64_final_iters != 0) return SMX_ERR_UNSUPPORTED;
+    if (bulk == SMX_FP64) fp64_final_iters = 0;  // the plain form is FP64 throughout
     c->precision = bulk;
     c->fp64_final = fp64_final_iters;
     return SMX_OK;
@@ -836,8 +886,16 @@ smx_status smx_set_overlap(smx_ctx* c, const double* values, int32_t on_device) 
 }
 
 smx_status smx_set_function(smx_ctx* c, smx_function f) {
-    if (!c || (f != SMX_FN_DENSITY && f != SMX_FN_INV_SQRT && f != SMX_FN_SQRT && f != SMX_FN_INV)) return SMX_ERR_ARG;
+    if (!c || (f != SMX_FN_DENSITY && f != SMX_FN_INV_SQRT && f != SMX_FN_SQRT && f != SMX_FN_INV &&
+               f != SMX_FN_FERMI))
+        return SMX_ERR_ARG;
     c->function = f;
+    return SMX_OK;
+}
+
+smx_status smx_set_fermi_beta(smx_ctx* c, double beta) {
+    if (!c || !std::isfinite(beta) || beta < 0.0) return SMX_ERR_ARG;
+    c->beta = beta;
     return SMX_OK;
 }
 
@@ -866,7 +924,7 @@ smx_status smx_solve_mu(smx_ctx* c) {
         // the step is discarded and taken again on the new one.
         SMX_TRY(launch_filter(c));
         c->dirty = false;  // the build below runs on the current filtered pattern
-        SMX_TRY(build_at(c, 0.0, true));
+        SMX_TRY(build_at(c, 0.0, &scalars(c)->mu0));
         SMX_TRY(fetch(c));
         const bool changed = c->filter_compared && c->h_sc->changed != 0;
         SMX_TRY(after_filter(c));  // errors of the filter, bracket, compaction when changed
@@ -905,6 +963,31 @@ smx_status smx_solve_mu(smx_ctx* c) {
         if (tr < c->n_e) lo = mid; else hi = mid;
     }
     return SMX_OK;
+}
+
+smx_status smx_solve_mu_device(smx_ctx* c) {
+    if (!c) return SMX_ERR_ARG;
+    if (!c->have_ne || c->col_hi >= 0) return SMX_ERR_STATE;
+    if (c->function != SMX_FN_DENSITY) return SMX_ERR_STATE;
+    if (c->have_S) return SMX_ERR_UNSUPPORTED;  // the non-orthogonal form: smx_solve_mu
+    DeviceGuard g(c->device);
+    if (c->n_e < 0.0 || c->n_e > static_cast<double>(c->N)) return SMX_ERR_NOBRACKET;
+    SMX_TRY(reset_flags(c));
+    c->bisection_steps = 0;
+    // the filtered pattern and its bracket first (one read when the values are new)
+    if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
+    DevScalars* sc = scalars(c);
+    SMX_CUDA(launch_bisect_init(sc, c->br_lo, c->br_hi, c->stream));
+    c->kernel_launches += 1;
+    for (int step = 0; step < c->max_steps; ++step) {
+        SMX_TRY(build_at(c, 0.0, &sc->bis_mid, &sc->bis_done));
+        SMX_CUDA(launch_bisect_step(sc, c->n_e, c->tol, c->max_steps, c->stream));
+        c->kernel_launches += 1;
+    }
+    SMX_TRY(fetch(c));  // the one read of the solve
+    c->bisection_steps = c->h_sc->bis_steps;
+    c->last_mu = c->h_sc->bis_mid;
+    return static_cast<smx_status>(c->h_sc->status);
 }
 
 smx_status smx_get_trace(smx_ctx* c, double* trace_D, double* trace_DH, double* mu) {
@@ -978,7 +1061,8 @@ smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
         dsum += n;
         isum += it[j];
         // two products per step for the sign iteration, three for the coupled one of the function forms
-        flops += (c->function == SMX_FN_DENSITY ? 4.0 : 6.0) * n * static_cast<double>(n) * n * it[j];
+        flops += (c->function == SMX_FN_DENSITY ? 4.0 : c->function == SMX_FN_FERMI ? 2.0 : 6.0) * n *
+                 static_cast<double>(n) * n * it[j];
         if (it[j] >= 100) ++noconv;
     }
     out->dim_mean = dsum / (hi - lo);
@@ -1274,7 +1358,7 @@ void smx_destroy(smx_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep_prev, &c->d_sc, &c->d_bcol, &c->d_csum, &c->d_diag, &c->d_keep, &c->d_fcol_ptr,
                       &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
-                      &c->d_W2, &c->d_W3, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
+                      &c->d_W2, &c->d_W3, &c->d_W4, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
                       &c->d_work_n3,
                       &c->d_params, &c->d_mst, &c->d_vst, &c->d_partial_mlp, &c->d_feat, &c->d_pred, &c->d_labels,
                       &c->d_gersh, &c->d_prev_ratio, &c->d_sq_ratio, &c->d_loss, &c->d_sx, &c->d_st,

@@ -14,14 +14,23 @@ struct DevScalars {
     double trace, energy;  // a8: trace(D) and trace(D H) of the last build
     double br_lo, br_hi;   // Gershgorin bracket of the filtered H (a9)
     double mu0;            // 0.5 (br_lo + br_hi): the first bisection step
-    double pad0;
+    double bis_mid;        // device-side bisection: the mu of the current step
+    double bis_lo, bis_hi; // ... and its bracket
     int status;            // first error recorded by a kernel (kOk = 0)
     int changed;           // the keep flags differ from the current filtered pattern
     int fallbacks;         // learned-bound fallbacks since the last reset
     int ns_counter;        // job counter of the tensor-core Newton-Schulz kernel (reset by the scatter)
     unsigned int filter_done, scatter_done;  // last-block tickets (each reset by its last block)
-    int pad1[2];
+    int bis_done;          // device-side bisection: stopped (the later builds are skipped)
+    int bis_steps;         // ... builds evaluated
 };
+
+// Device-side bisection for mu (a9): start at the bracket's midpoint (one thread).
+cudaError_t launch_bisect_init(DevScalars* sc, double lo, double hi, cudaStream_t st);
+// After a build at sc->bis_mid: stop when |trace - n_e| <= tol or after max_steps builds (the
+// result is the last evaluated mu), else halve the bracket and set the next midpoint.  Once
+// stopped, the following steps change nothing (and the kernels of their builds return early).
+cudaError_t launch_bisect_step(DevScalars* sc, double n_e, double tol, int max_steps, cudaStream_t st);
 
 // a1 + bracket: keep flags of every block (Frobenius norm >= eps, diagonal
 // always), non-finite check (sc->status), FP32 copy of H and the Gershgorin
@@ -43,6 +52,7 @@ struct GatherExtras {
     float* pred = nullptr;               // ... and its two predictions
     float margin = 0.0f;                 // ... b_j = G_j clamp(pred_0, 0.02, 1) (1 + margin) / 1.2
     const double* mu_dev = nullptr;      // when set, mu is read from here (on the device) instead
+    const int* skip = nullptr;           // when set and non-zero at launch, the kernel does nothing
 };
 
 // a3 + a4: T_j = H[R_j, R_j] - mu I into the FP64 staging buffer, then the
@@ -59,7 +69,8 @@ cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nbl
 
 // a8 (FP64 form): deterministic sums of the per-column partials ->
 // sc->trace = trace(D), sc->energy = trace(D H).
-cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cudaStream_t st);
+cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cudaStream_t st,
+                          const int* skip = nullptr);
 
 // Failure-detection self-test: a wait on an mbarrier nothing arrives at, given up after
 // poll_limit polls (records kErrTimeout in *status; *polls_out, if set, the polls made).
@@ -68,7 +79,7 @@ cudaError_t launch_wait_selftest(int* status, uint32_t poll_limit, int* polls_ou
 // a5/a6 (FP64 plain form) + a7: Newton-Schulz in FP64, then scatter.
 // Matrix function of a build (values of smx_function): 0 = the density matrix
 // 1/2 (I - sign(A)), 1 = A^-1/2, 2 = A^1/2 (A = T_j - mu I symmetric positive definite).
-enum : int { kFnDensity = 0, kFnInvSqrt = 1, kFnSqrt = 2, kFnInv = 3 };
+enum : int { kFnDensity = 0, kFnInvSqrt = 1, kFnSqrt = 2, kFnInv = 3, kFnFermi = 4 };
 
 struct NsFp64Args {
     const SubDesc* subs;
@@ -77,6 +88,7 @@ struct NsFp64Args {
     double* W1;  // FP64 work buffers laid out like T
     double* W2;
     double* W3;  // a third one for the function forms (coupled iteration), else unused
+    double* W4 = nullptr;  // a fourth one for the Fermi function
     int function;  // kFnDensity, kFnInvSqrt or kFnSqrt
     double* bound;  // in: initial bound b_j; out: effective bound after the a-posteriori rescale
     double tau;
@@ -102,6 +114,12 @@ struct NsFp64Args {
     // learned bound: predictions of this chunk ([2 i + 1] = delta_hat / G for the i-th
     // submatrix); see NsTcArgs::pred
     const float* pred = nullptr;
+    // FP64 finishing steps after a low-precision bulk phase (> 0): T holds the bulk phase's last
+    // iterate X (not T_j - mu I); exactly this many plain steps in FP64, then the scatter; the
+    // steps are added to iters
+    int finish_iters = 0;
+    const int* skip = nullptr;  // when set and non-zero at launch, the kernel does nothing
+    double beta = 0.0;          // kFnFermi: the inverse temperature (in inverse units of H)
 };
 cudaError_t launch_ns_fp64(const NsFp64Args& a, int max_nblk, cudaStream_t st);
 
@@ -154,6 +172,10 @@ struct NsTcArgs {
     // prediction accepted, the steps follow the scaled schedule from the lower bound
     // delta_hat / (b_j s) (null: plain steps after the a-posteriori start)
     const float* pred = nullptr;
+    // when set, the final X of every submatrix (n_j x n_j, row-major with leading dimension
+    // SubDesc::ld at SubDesc::t_off, as FP64) for FP64 finishing steps
+    double* xfull = nullptr;
+    const int* skip = nullptr;  // when set and non-zero at launch, the kernel does nothing
 };
 // precision: 1 = FP16 split hi/lo (3 products), 2 = FP16, 3 = BF16 (values of smx_precision)
 cudaError_t launch_ns_tc(const NsTcArgs& a, int precision, const CUtensorMap& tmap, int max_nblk, cudaStream_t st);
@@ -164,7 +186,7 @@ cudaError_t launch_ns_tc(const NsTcArgs& a, int precision, const CUtensorMap& tm
 // sc->energy and resets sc->ns_counter for the next Newton-Schulz launch.
 cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
                                  const float* xown, const double* H, double* D, double2* partial, int n_cols,
-                                 DevScalars* sc, cudaStream_t st);
+                                 DevScalars* sc, cudaStream_t st, const int* skip = nullptr);
 
 // ---------------------------------------------------------------------------
 // learned spectral bound (k_bound_model.cu)
