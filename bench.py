@@ -708,7 +708,10 @@ def run_ours(args):
     peaks, peak_kind = _peaks()
     passes = 3 if args.precision == "fp16x3" else 1
     peak = peaks["bf16_tflops"] / passes
-    form = "on-chip form (kpad <= 192)" if int(np.max(dims_all)) <= 192 else "streamed form (kpad > 192)"
+    d3 = dims_all.astype(np.float64) ** 3
+    onchip = float(d3[((dims_all + 31) // 32) * 32 <= 192].sum() / max(d3.sum(), 1.0))
+    form = (f"on-chip form (kpad <= 192) for {100 * onchip:.0f}% of the n^3 work"
+            if onchip >= 0.5 else f"streamed form (kpad > 192) for {100 * (1 - onchip):.0f}% of the n^3 work")
     roofline = {
         "bound": "tensor", "kernel": f"k_ns_tc<{args.precision}>, {form}", "achieved": achieved, "peak": peak,
         "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,

@@ -1063,7 +1063,10 @@ smx_status smx_get_stats(smx_ctx* c, smx_stats* out) {
         // two products per step for the sign iteration, three for the coupled one of the function forms
         flops += (c->function == SMX_FN_DENSITY ? 4.0 : c->function == SMX_FN_FERMI ? 2.0 : 6.0) * n *
                  static_cast<double>(n) * n * it[j];
-        if (it[j] >= 100) ++noconv;
+        // the iteration cap of the sign and coupled iterations (the Fermi form counts products;
+        // FP64 finishing steps come on top of the bulk phase's count)
+        const int capped = it[j] - (c->precision != SMX_FP64 && c->function == SMX_FN_DENSITY ? c->fp64_final : 0);
+        if (c->function != SMX_FN_FERMI && capped >= 100) ++noconv;
     }
     out->dim_mean = dsum / (hi - lo);
     out->iters_mean = isum / (hi - lo);
