@@ -107,9 +107,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _profiled_traffic(workload: str, precision: str):
-    """DRAM bytes per launch of the Newton-Schulz kernel from the committed ncu
-    record, or None when that record was taken on a different kernel source."""
+def _profiled_traffic(workload: str, precision: str, gemms_per_launch: float):
+    """DRAM bytes per launch of the Newton-Schulz kernel from the committed ncu record, or None
+    when that record was taken on a different kernel source or workload.  A record captured on a
+    column shard (a small case) is scaled to the launch by its number of GEMMs (two per step),
+    which the traffic of the streamed form follows."""
     import hashlib
 
     try:
@@ -119,9 +121,18 @@ def _profiled_traffic(workload: str, precision: str):
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
     except Exception:
         return None, "no ncu record"
-    if sha != rec["sha256_16"] or workload != rec["workload"] or precision != "fp16x3":
+    if sha != rec["sha256_16"]:
         return None, "kernel changed since the ncu capture"
-    return rec["dram_bytes_read"] + rec["dram_bytes_write"], "ncu dram__bytes_read+write of one launch"
+    if precision != "fp16x3":
+        return None, "no ncu record for this precision"
+    for r in rec["records"]:
+        if r["workload"] == workload:
+            t = r["dram_bytes_read"] + r["dram_bytes_write"]
+            if "gemms" in r:
+                return t * gemms_per_launch / r["gemms"], ("ncu dram__bytes_read+write of a 152-column launch, "
+                                                           "scaled by the launch's GEMM count")
+            return t, "ncu dram__bytes_read+write of one launch"
+    return None, "no ncu record for this workload"
 
 
 def _dist():
@@ -600,6 +611,11 @@ def run_ours(args):
     ctx = SubmatrixDensity.from_system(sysm, stream=stream.cuda_stream)
     ctx.set_filter_threshold(w["eps"])
     ctx.set_electron_count(n_e, max_steps=w.get("max_steps", args.max_steps), tol=1e-2)
+    if args.columns:
+        # a column shard only (a small case for profiling one launch); needs a fixed mu
+        if not fixed:
+            raise SystemExit("--columns needs a fixed-mu workload")
+        ctx.set_column_range(0, args.columns)
     h_dev = torch.from_numpy(sysm.values).to("cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     if model_path:
@@ -721,7 +737,11 @@ def run_ours(args):
                 + (" / 3 (three fp16 products per multiply-add in the split form)" if passes == 3 else ""),
         "ns_share_of_step": (st["ns_ms_total"] / ms) if ms > 0 else None,
     }
-    roofline["traffic"], roofline["traffic_note"] = _profiled_traffic(args.workload, args.precision)
+    n_cols = int(dims_all.shape[0]) if not args.columns else args.columns
+    builds_timed = args.steps * (1 if mu_fixed is not None else max(1, st["bisection_steps"]))
+    launches_per_build = max(1.0, st["ns_launches"] / builds_timed)
+    gemms = 2.0 * st["iters_mean"] * n_cols / launches_per_build  # two GEMMs per step
+    roofline["traffic"], roofline["traffic_note"] = _profiled_traffic(args.workload, args.precision, gemms)
     gpu_launches = int(st["kernel_launches"])
 
     # -- e2e through the C ABI with host buffers -------------------------------
@@ -752,8 +772,8 @@ def run_ours(args):
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e_s = float(t.item())
     nbytes = sysm.values.shape[0] * 8
-    e2e = {"value": args.e2e_steps * world / e2e_s, "unit": "density matrices/s", "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes + 24 * int(np.mean(bis_steps)) + 16}
+    e2e = ({"value": args.e2e_steps * world / e2e_s, "unit": "density matrices/s", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes + 24 * int(np.mean(bis_steps)) + 16} if args.e2e_steps > 0 else None)
 
     # -- the plain FP64 form on the same workload ------------------------------
     fp64 = None
@@ -920,6 +940,8 @@ def main():
                     help="with --per-build: also time the solve with the bisection's decisions on the device")
     ap.add_argument("--per-build", action="store_true",
                     help="a step is one build at the solved mu; the full bisection is timed once")
+    ap.add_argument("--columns", type=int, default=0,
+                    help="restrict the timed context to block columns [0, N) (a small case for profiling)")
     ap.add_argument("--shard", action="store_true",
                     help="one system split over the ranks by block columns (strong scaling)")
     ap.add_argument("--fp64-steps", type=int, default=2)

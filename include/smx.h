@@ -166,9 +166,11 @@ smx_status smx_set_filter_threshold(smx_ctx* ctx, double eps);
 
 /* Upper bound (bytes, >= 1 MiB) on the device staging of the gathered
  * submatrices T_j - mu I (counted as FP64).  Block columns are processed in
- * consecutive chunks whose staging fits; one chunk when everything fits
- * (default 24 GiB).  Results do not depend on the chunking.  Errors:
- * SMX_ERR_ARG. */
+ * consecutive chunks whose staging fits; one chunk when everything fits.
+ * Default (no call): automatic, a tenth of the device memory for each FP64
+ * staging buffer of the plain form (which keeps up to five of that size) and
+ * half of it for the FP32 staging of the tensor-core forms (which keep one).
+ * Results do not depend on the chunking.  Errors: SMX_ERR_ARG. */
 smx_status smx_set_staging_limit(smx_ctx* ctx, uint64_t bytes);
 
 /* Restricts the context to block columns [j0, j1) (one shard of a multi-GPU

@@ -11,8 +11,22 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "smx.h"
 #include "smx_kernels.h"
+
+namespace {
+// NVTX range over a host scope (filter, each build and its phases, each bisection step), so that
+// profiler timelines group the library's launches; free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
+
 
 using namespace smx;
 
@@ -105,7 +119,9 @@ struct smx_ctx {
     size_t ns_pending = 0;
 
     // staging of the submatrices T_j in chunks of consecutive block columns
-    size_t staging_limit = size_t(24) << 30;  // bytes (FP64 elements)
+    size_t staging_limit = 0;  // bytes counted as FP64 elements; 0 = automatic from the device memory
+    size_t mem_total = 0;      // device memory at creation
+    size_t chunk_elem = 0;     // element size the chunks were laid out for (automatic limit)
     std::vector<int32_t> chunk_start;         // chunk c = block columns [chunk_start[c], chunk_start[c + 1])
     int32_t col_lo = 0, col_hi = -1;          // block columns this context builds (a shard); col_hi < 0: all
     int64_t t_chunk_max = 0;                  // elements of the largest chunk
@@ -244,6 +260,7 @@ static smx_status fetch(smx_ctx* c) {
 // a1 on the device (asynchronous): keep flags, FP32 copy of H, the bracket and,
 // against the current filtered pattern, the change flag.
 static smx_status launch_filter(smx_ctx* c) {
+    NvtxRange nv("smx filter");
     c->filter_compared = c->analysed && c->eps > 0.0;  // without a threshold every block is kept
     SMX_CUDA(launch_filter_gershgorin(dp<double>(c->d_H), dp<int64_t>(c->d_col_ptr), dp<int32_t>(c->d_row_idx),
                                       dp<int32_t>(c->d_bcol), dp<int64_t>(c->d_voff), dp<int32_t>(c->d_bs), c->B, c->nnzb,
@@ -279,6 +296,24 @@ static smx_status analyse(smx_ctx* c) {
     return after_filter(c);
 }
 
+// Bytes per staged element: FP64 for the plain form, FP32 for the tensor-core forms.
+static size_t staging_elem(const smx_ctx* c) { return c->precision == SMX_FP64 ? sizeof(double) : sizeof(float); }
+
+// Elements of staging per chunk.  An explicit limit counts bytes as FP64 elements.  The
+// automatic one takes a tenth of the device memory for each FP64 staging buffer (the plain form
+// keeps up to five of that size) and half of it for the FP32 staging of the tensor-core forms,
+// which keep one; it follows the precision (the chunks are laid out again when it changes).
+static int64_t staging_chunk_elems(smx_ctx* c) {
+    if (c->staging_limit) {
+        c->chunk_elem = 0;
+        return static_cast<int64_t>(c->staging_limit / sizeof(double));
+    }
+    const size_t elem = staging_elem(c);
+    c->chunk_elem = elem;
+    const size_t mem = c->mem_total ? c->mem_total : (size_t(24) << 30) * 4;
+    return static_cast<int64_t>((elem == sizeof(double) ? mem / 10 : mem / 2) / elem);
+}
+
 // a2: the filtered pattern from the keep flags on the device, symbolic sets of
 // every submatrix, chunks and processing order (host), uploaded.
 static smx_status compact(smx_ctx* c) {
@@ -305,7 +340,7 @@ static smx_status compact(smx_ctx* c) {
     c->max_nblk = 0;
     c->max_n = 0;
     int64_t t_off = 0, x_off = 0;
-    const int64_t chunk_elems = std::max<int64_t>(1, static_cast<int64_t>(c->staging_limit / sizeof(double)));
+    const int64_t chunk_elems = std::max<int64_t>(1, staging_chunk_elems(c));
     const int32_t lo = c->col_lo, hi = c->col_hi < 0 ? B : c->col_hi;
     c->chunk_start.assign(1, lo);
     c->t_chunk_max = 0;
@@ -358,7 +393,7 @@ static smx_status compact(smx_ctx* c) {
     SMX_TRY(upload(c->d_lstart, c->lstart, st));
     SMX_TRY(upload(c->d_subs, c->subs, st));
     SMX_TRY(upload(c->d_order, c->order, st));
-    SMX_TRY(ensure(c->d_T, static_cast<size_t>(c->t_elems) * sizeof(double)));
+    SMX_TRY(ensure(c->d_T, static_cast<size_t>(c->t_elems) * staging_elem(c)));
     SMX_CUDA(cudaMemsetAsync(c->d_D.p, 0, c->n_values * sizeof(double), st));
     SMX_CUDA(cudaMemsetAsync(c->d_partial.p, 0, sizeof(double2) * B, st));  // columns outside the shard add zero
     SMX_CUDA(cudaMemsetAsync(c->d_iters.p, 0, sizeof(int32_t) * B, st));
@@ -428,6 +463,7 @@ static smx_status ns_event_pair(smx_ctx* c, cudaEvent_t* e0, cudaEvent_t* e1) {
 // One build at chemical potential mu (a3 - a8).
 // a3 + a4 for block columns [j0, j0 + m) into the staging buffer.
 static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const GatherExtras& ex) {
+    SMX_TRY(ensure(c->d_T, static_cast<size_t>(c->t_elems) * staging_elem(c)));  // after a precision change
     const PatternView pv = pattern_view(c);
     SubDesc* subs = dp<SubDesc>(c->d_subs);
     if (c->precision == SMX_FP64) {
@@ -451,6 +487,7 @@ static smx_status nonorth_setup(smx_ctx* c) {
     if (c->chunk_start.size() != 2) return SMX_ERR_UNSUPPORTED;  // L_j and M_j of every column stay resident
     cudaStream_t st = c->stream;
     const size_t tb = static_cast<size_t>(c->t_elems) * sizeof(double);
+    SMX_TRY(ensure(c->d_T, tb));
     SMX_TRY(ensure(c->d_W1, tb));
     SMX_TRY(ensure(c->d_W2, tb));
     SMX_TRY(ensure(c->d_W3, tb));
@@ -504,6 +541,7 @@ static smx_status nonorth_setup(smx_ctx* c) {
 // set, every kernel of the build returns at once if *skip is non-zero at its launch (the steps
 // after the stopping step of a device-side bisection).
 static smx_status build_at(smx_ctx* c, double mu, const double* mu_dev = nullptr, const int* skip = nullptr) {
+    NvtxRange nv("smx build");
     if (c->function != SMX_FN_DENSITY && c->precision != SMX_FP64) return SMX_ERR_UNSUPPORTED;
     if (c->have_S && (c->function != SMX_FN_DENSITY || c->precision != SMX_FP64 || mu_dev))
         return SMX_ERR_UNSUPPORTED;  // the non-orthogonal form: density matrix, FP64
@@ -516,17 +554,20 @@ static smx_status build_at(smx_ctx* c, double mu, const double* mu_dev = nullptr
     SMX_CUDA(cudaEventRecord(c->ev0, st));
     const PatternView pv = pattern_view(c);
     if (c->precision == SMX_FP64) {
-        SMX_TRY(ensure(c->d_W1, c->d_T.bytes));
-        SMX_TRY(ensure(c->d_W2, c->d_T.bytes));
-        if (c->function != SMX_FN_DENSITY) SMX_TRY(ensure(c->d_W3, c->d_T.bytes));
-        if (c->function == SMX_FN_FERMI) SMX_TRY(ensure(c->d_W4, c->d_T.bytes));
+        const size_t tb = static_cast<size_t>(c->t_elems) * sizeof(double);
+        SMX_TRY(ensure(c->d_T, tb));
+        SMX_TRY(ensure(c->d_W1, tb));
+        SMX_TRY(ensure(c->d_W2, tb));
+        if (c->function != SMX_FN_DENSITY) SMX_TRY(ensure(c->d_W3, tb));
+        if (c->function == SMX_FN_FERMI) SMX_TRY(ensure(c->d_W4, tb));
     } else {
         SMX_TRY(prepare_tc_workspace(c));
         SMX_TRY(ensure(c->d_xown, static_cast<size_t>(c->x_elems) * sizeof(float)));
         if (c->fp64_final > 0) {  // the bulk phase's last iterate in FP64, and two work buffers
-            SMX_TRY(ensure(c->d_W1, c->d_T.bytes));
-            SMX_TRY(ensure(c->d_W2, c->d_T.bytes));
-            SMX_TRY(ensure(c->d_W3, c->d_T.bytes));
+            const size_t tb = static_cast<size_t>(c->t_elems) * sizeof(double);
+            SMX_TRY(ensure(c->d_W1, tb));
+            SMX_TRY(ensure(c->d_W2, tb));
+            SMX_TRY(ensure(c->d_W3, tb));
         }
     }
     SubDesc* subs = dp<SubDesc>(c->d_subs);
@@ -704,6 +745,10 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if (!c) return SMX_ERR_OOM;
     cudaGetDevice(&c->device);
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) c->mem_total = total_b;
+    }
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->B = n_block_cols;
     c->bs.assign(block_size, block_size + n_block_cols);
@@ -861,6 +906,8 @@ smx_status smx_set_precision(smx_ctx* c, smx_precision bulk, int32_t fp64_final_
     if (bulk == SMX_FP64) fp64_final_iters = 0;  // the plain form is FP64 throughout
     c->precision = bulk;
     c->fp64_final = fp64_final_iters;
+    // with the automatic staging limit the chunks follow the staged element size
+    if (!c->staging_limit && c->chunk_elem && c->chunk_elem != staging_elem(c)) c->analysed = false;
     return SMX_OK;
 }
 
@@ -953,6 +1000,7 @@ smx_status smx_solve_mu(smx_ctx* c) {
         }
     }
     for (; step < c->max_steps; ++step) {
+        NvtxRange nv("smx bisection step");
         const double mid = 0.5 * (lo + hi);
         SMX_TRY(build_at(c, mid));
         ++c->bisection_steps;
