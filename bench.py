@@ -826,7 +826,19 @@ def run_ours(args):
                 a = d_gpu[off[k]:off[k + 1]]
                 b = res.values[off_f[kf[k]]:off_f[kf[k] + 1]] if keep[k] else np.zeros_like(a)
                 err = max(err, float(np.max(np.abs(a - b))))
-        acc = {"d_max_abs_err_sampled_columns": err, "columns": len(cols), "trace": tr, "energy": en, "mu": mu}
+        # the asymmetry of D (the submatrix D is not symmetric; a diagnostic, not a check): block (i, j)
+        # of a sampled column against the transpose of block (j, i)
+        asym = 0.0
+        bs = np.asarray(sysm.block_size, dtype=np.int64)
+        for j in cols:
+            for k in range(sysm.col_ptr[j], sysm.col_ptr[j + 1]):
+                i = int(sysm.row_idx[k])
+                kk = sysm.col_ptr[i] + int(np.searchsorted(sysm.row_idx[sysm.col_ptr[i]:sysm.col_ptr[i + 1]], j))
+                a_ = d_gpu[off[k]:off[k + 1]].reshape(bs[j], bs[i])      # block (i, j), column-major
+                b_ = d_gpu[off[kk]:off[kk + 1]].reshape(bs[i], bs[j])    # block (j, i), column-major
+                asym = max(asym, float(np.max(np.abs(a_ - b_.T))))
+        acc = {"d_max_abs_err_sampled_columns": err, "columns": len(cols), "trace": tr, "energy": en, "mu": mu,
+               "d_asymmetry_max_sampled_columns": asym}
         builds = int(round(np.mean(bis_steps))) if bis_steps else 1
         scale = _work_scale(sysm.block_size, cp_f, ri_f, cols)
         per_dm = dt * scale * builds
