@@ -55,6 +55,8 @@ constexpr uint32_t kStageOff = 144u * 1024u;
 // iterations; the prologue's staging buffers are dead by then)
 constexpr uint32_t kXsOff = 96u * 1024u;  // times the operand count NB
 constexpr uint32_t kXsWarp = 32 * 80;
+// The streamed form's products with K >= kSplitKpad accumulate in two chains (see gemm).
+constexpr int kSplitKpad = 2048;
 // A step with factor a maps an eigenvalue at 1 to p(a) ~ 1 - 1.5 (a - 1)^2: the last step may
 // use a up to 1 + kStopSlack (a shift of at most 1.4e-7, far below the split form's error).
 constexpr float kStopSlack = 3e-4f;
@@ -325,8 +327,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
 
     // role-local pipeline positions, continuous over all GEMMs of the CTA
     uint32_t p_it = 0;              // producer: K chunks issued
-    uint32_t m_it = 0, m_tile = 0;  // MMA: K chunks consumed, tiles issued
-    uint32_t e_tile = 0;            // epilogue: tiles drained
+    uint32_t m_it = 0;              // MMA: K chunks consumed
+    // the two TMEM accumulator buffers: tiles alternate between them (the epilogue of one
+    // overlaps the products of the next), except in the two-chain mode, where a tile takes both
+    uint32_t m_use0 = 0, m_use1 = 0;    // MMA: tiles issued into buffer 0 / 1
+    uint32_t m_nb = 0;                  // MMA: the buffer of the next single-chain tile
+    uint32_t e_full0 = 0, e_full1 = 0;  // epilogue: tiles drained from buffer 0's / 1's commits
+    uint32_t e_nb = 0;                  // epilogue: the buffer of the next single-chain tile
     const int64_t buf = static_cast<int64_t>(a.ld) * a.ld;
     uint16_t* ws = static_cast<uint16_t*>(a.ws);
     const int slot_z = blockIdx.x * 6;
@@ -347,6 +354,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     // mode 2: zo = oscale * A B.
     auto gemm = [&](int kpad, int n, int mode, int za, int zb, int zo, float oscale, float dg = 1.5f) {
         const int mtiles = (kpad + 127) / 128, kchunks = (kpad + 63) / 64;
+        // Long K: two accumulation chains over the two halves of K in the two TMEM buffers, summed
+        // in FP32 by the epilogue (the tensor cores' FP32 accumulation loses accuracy with the
+        // length of a chain: at n ~ 2800 one chain puts about 1.2e-5 on D, two about 7.6e-6); a
+        // tile then holds both buffers, so its epilogue no longer overlaps the next tile's products.
+        const bool split = kpad >= kSplitKpad;
         // row tile mt: N tiles of up to NT columns from column 128 mt
         auto ntiles_of = [&](int mt) { return (kpad - 128 * mt + NT - 1) / NT; };
         if (warp == 0) {
@@ -380,10 +392,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 for (int mt = 0; mt < mtiles && !*abortp; ++mt)
                     for (int nt = 0; nt < ntiles_of(mt) && !*abortp; ++nt) {
                         const int nn = min(NT, kpad - 128 * mt - NT * nt);
-                        const uint32_t abuf = m_tile & 1, around = m_tile >> 1;
-                        if (around > 0 && !mbar_wait(&tempty[abuf], (around - 1) & 1, &abort_s, a.status)) break;
+                        // the buffer(s) of this tile, released by the epilogue of their previous tiles
+                        const uint32_t abuf = split ? 0u : m_nb;
+                        if (!split) m_nb ^= 1u;
+                        bool freed = true;
+                        if (abuf == 0 || split) {
+                            if (m_use0 > 0 && !mbar_wait(&tempty[0], (m_use0 - 1) & 1, &abort_s, a.status)) freed = false;
+                            ++m_use0;
+                        }
+                        if (abuf == 1 || split) {
+                            if (freed && m_use1 > 0 && !mbar_wait(&tempty[1], (m_use1 - 1) & 1, &abort_s, a.status)) freed = false;
+                            ++m_use1;
+                        }
+                        if (!freed) break;
                         tc_fence_after();
-                        const uint32_t d = tmem_base + abuf * 256;
+                        const int khalf = split ? kchunks / 2 : kchunks;  // the second chain's first K chunk
                         const uint32_t idesc = idesc_f16(128, nn, C::kFmt) | idesc_b_mn;
                         bool ok = true;
                         for (int kc = 0; kc < kchunks; ++kc) {
@@ -396,8 +419,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                             const uint32_t b_hi = base + NB * kABytes, b_lo = b_hi + C::kBBytes;
                             // K steps beyond kpad (the tail of the last 64-wide chunk) are not issued
                             const int ksteps = min(4, (kpad - 64 * kc) / 16);
+                            const uint32_t d = tmem_base + (kc >= khalf ? 256u : abuf * 256u);
                             for (int kk = 0; kk < ksteps; ++kk) {
-                                const uint32_t acc = (kc | kk) ? 1u : 0u;
+                                const uint32_t acc = ((kc == 0 || kc == khalf) && kk == 0) ? 0u : 1u;
                                 const uint64_t ah = sdesc_sw128(a_hi + kk * 32), bh = sdesc_mn_sw128(b_hi + kk * 2048);
                                 tc_mma_f16(d, ah, bh, idesc, acc);
                                 if constexpr (NB == 2) {
@@ -410,7 +434,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                         }
                         if (!ok) break;
                         tc_commit(&tfull[abuf]);
-                        ++m_tile;
                     }
                 m_consumed_s = static_cast<int>(m_it);
             }
@@ -425,9 +448,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             for (int mt = 0; mt < mtiles; ++mt)
                 for (int nt = 0; nt < ntiles_of(mt); ++nt) {
                     const int n0 = 128 * mt + NT * nt, nn = min(NT, kpad - n0);
-                    const uint32_t abuf = e_tile & 1, around = e_tile >> 1;
+                    const uint32_t abuf = split ? 0u : e_nb;
+                    if (!split) e_nb ^= 1u;
+                    const uint32_t ph = (abuf ? e_full1++ : e_full0++) & 1u;
                     int ok = 1;
-                    if (lane == 0) ok = mbar_wait(&tfull[abuf], around & 1, &abort_s, a.status) ? 1 : 0;
+                    if (lane == 0) ok = mbar_wait(&tfull[abuf], ph, &abort_s, a.status) ? 1 : 0;
                     ok = __shfl_sync(0xffffffffu, ok, 0);
                     if (!ok) { mt = mtiles; break; }
                     tc_fence_after();
@@ -438,7 +463,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     for (int c0 = 32 * half; c0 < nn; c0 += 64) {
                         uint32_t raw[32];
                         tmem_ld32_issue(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + abuf * 256 + c0, raw);
-                        tmem_wait_ld();
+                        if (split) {  // the second chain, added in FP32
+                            uint32_t raw1[32];
+                            tmem_ld32_issue(tmem_base + (static_cast<uint32_t>(q * 32) << 16) + 256 + c0, raw1);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) raw[i] = __float_as_uint(__uint_as_float(raw[i]) + __uint_as_float(raw1[i]));
+                        } else {
+                            tmem_wait_ld();
+                        }
                         const int r0 = row - lane;  // the warp's first row
                         const int col0 = n0 + c0;
                         // chunks left of the warp's diagonal chunk are not written: the transposes of
@@ -533,8 +566,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     }
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&tempty[abuf]);
-                    ++e_tile;
+                    if (lane == 0) {
+                        mbar_arrive(&tempty[abuf]);
+                        if (split) mbar_arrive(&tempty[1]);
+                    }
                 }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
