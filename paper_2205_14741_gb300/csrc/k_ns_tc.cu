@@ -388,6 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         // lower end of the interval the scaled schedule assumes for the current iterate's
         // |eigenvalues| (1 = plain steps), and the factor a of the current step
         float lsch = 1.0f, acur = 1.0f;
+        float rprev = INFINITY;  // tid 0: the previous step's residual (rounding-floor stop)
 
         const int zx0 = slot_z + 0, zx1 = slot_z + 2, zy = slot_z + 4;
 
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             }
             cp_async_wait<0>();
             fence_proxy_async_smem();
-            if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; }
+            if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; rprev = INFINITY; }
             __syncthreads();
         } else {
             const float inv_b = static_cast<float>(1.0 / a.bound[j]);
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
             }
             fence_proxy_async_global();
-            if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; }
+            if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; rprev = INFINITY; }
             __syncthreads();
         }
 
@@ -541,10 +542,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         // stop after this step when the residual is <= tau, unless the step is a scaled one
         // whose factor would move converged eigenvalues off 1 (p(a) = 1 - 1.5 (a - 1)^2 + ...);
         // then the schedule ends and the next steps are plain.
-        auto converged = [&](double resid) {
+        auto converged = [&]() {
             if (acur - 1.0f <= kStopSlack) conv_s = 1;
             else plain_s = 1;
-            (void)resid;
+        };
+        // tid 0, with the residual r = ||X^2 - I||_F of the current step: the stopping rule,
+        // or (single-pass forms) the rounding floor: r below a.stall_level and not half of
+        // the previous step's residual
+        auto check_stop = [&](double r) {
+            if (!isfinite(r)) bad_s = 1;
+            else if (r <= a.tau || (r < a.stall_level && r > 0.5 * rprev)) converged();
+            rprev = static_cast<float>(r);
         };
         int cur = 0, done = 0;
         if (resident) {
@@ -932,8 +940,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             auto decide = [&]() {
                 double rr = 0.0;
                 for (int w = 0; w < kThreads / 32; ++w) rr += resid_s2[w];
-                if (!isfinite(rr)) bad_s = 1;
-                else if (sqrt(rr) <= a.tau) converged(sqrt(rr));
+                check_stop(sqrt(rr));
             };
 
             if (mtiles == 1) {
@@ -1208,8 +1215,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 if (tid == 0) {
                     double r2 = 0.0;
                     for (int w = 0; w < kEpiWarps; ++w) r2 += resid_s[w];
-                    if (!isfinite(r2)) bad_s = 1;
-                    else if (sqrt(r2) <= a.tau) converged(sqrt(r2));
+                    check_stop(sqrt(r2));
                 }
                 gemm(kpad, s.n, 2, zx, zy, zn, 1.0f);  // X' = X Y
             }

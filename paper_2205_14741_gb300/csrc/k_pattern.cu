@@ -14,158 +14,254 @@
 
 namespace smx {
 
-// a1 + the Gershgorin bracket of a9 in two passes.
-//
-// Pass 1, eight threads per block k of the input pattern (thread q takes the
-// block's columns q, q + 8, ...): the column's values are checked for
-// finiteness and copied to FP32, its sum of squares and of absolute values
-// taken; the block's Frobenius norm (squares summed over its columns in a
-// fixed tree) decides whether it is kept (diagonal blocks always), against
-// keep_prev when given.  The column absolute sums of a kept block (zero for a
-// dropped one) go to csum[k][q] (stride bmax), the diagonal block's diagonal
-// to diag[j][q].
-__global__ void __launch_bounds__(256) k_filter_blocks(const double* __restrict__ H, const int64_t* __restrict__ voff,
-                                                       const int32_t* __restrict__ row_idx,
-                                                       const int32_t* __restrict__ bcol,
-                                                       const int32_t* __restrict__ bsize, int64_t nnzb, int bmax,
-                                                       double eps, uint8_t* __restrict__ keep,
-                                                       const uint8_t* __restrict__ keep_prev, float* __restrict__ H32,
-                                                       double* __restrict__ csum, double* __restrict__ diag,
-                                                       DevScalars* sc) {
-    const int64_t k = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 3;
-    const int q0 = threadIdx.x & 7;
-    const bool on = k < nnzb;  // the 8-lane group is uniform
-    int j = 0, r = 0, br = 0, bc = 0;
-    if (on) {
-        j = bcol[k];
-        r = row_idx[k];
-        br = bsize[r];
-        bc = bsize[j];
-    }
-    double ss = 0.0;
+// a1 + the Gershgorin bracket of a9 in one pass: one CTA of 64 threads per
+// block column j of the input pattern, eight groups of eight lanes, group g
+// taking the column's blocks k = k0 + g, k0 + g + 8, ... and lane q0 of a group
+// the block's columns q0, q0 + 8, ...  Per (block, column): the values are
+// checked for finiteness and copied to FP32, their sum of squares and of
+// absolute values taken; the block's Frobenius norm (squares summed over its
+// columns in a fixed tree over the group) decides whether it is kept (diagonal
+// blocks always), against keep_prev when given.  The absolute column sums of
+// the kept blocks go into per-group accumulators in shared memory (each lane
+// owns its entries), then are summed over the groups in order: with the
+// diagonal block's diagonal d_q, column q's Gershgorin interval is
+// [d_q - r_q, d_q + r_q], r_q = sum - |d_q| (H symmetric: column sums are row
+// sums).  The column's minimum and maximum reach the bracket through atomic
+// maxima of order-preserving integer images (independent of the order of the
+// CTAs), and the last CTA writes the bracket and its midpoint.
+constexpr int kFilterThreads = 64;
+
+// Order-preserving image of a double in the unsigned integers: x < y <=> enc(x) < enc(y)
+// for non-NaN x, y, and enc(x) > 0 for every x, so 0 is below every value.
+__device__ __forceinline__ unsigned long long ord_enc(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double ord_dec(unsigned long long e) {
+    const unsigned long long b = (e >> 63) ? (e & 0x7fffffffffffffffull) : ~e;
+    return __longlong_as_double(static_cast<long long>(b));
+}
+
+__global__ void __launch_bounds__(kFilterThreads) k_filter(const double* __restrict__ H, const int64_t* __restrict__ col_ptr,
+                                                           const int32_t* __restrict__ row_idx,
+                                                           const int64_t* __restrict__ voff,
+                                                           const int32_t* __restrict__ bsize, int bmax, double eps,
+                                                           uint8_t* __restrict__ keep, const uint8_t* __restrict__ keep_prev,
+                                                           float* __restrict__ H32, DevScalars* sc) {
+    extern __shared__ double fsm[];  // cs[8][bmax] kept column sums, ca[8][bmax] this block's, dg[bmax], mm[2][2]
+    __shared__ bool last_s;
+    double* cs = fsm;
+    double* ca = cs + 8 * bmax;
+    double* dg = ca + 8 * bmax;
+    const int j = blockIdx.x, tid = threadIdx.x, g = tid >> 3, q0 = tid & 7;
+    const int bc = bsize[j];
+    const int64_t k0 = col_ptr[j], k1 = col_ptr[j + 1];
+    const unsigned gmask = 0xffu << (tid & 24);  // this group's lanes (groups differ in their block counts)
+    // keep decisions: sum of squares in FP32 unless it lies within its rounding bound of eps^2
+    // (then again in FP64, as the oracle takes it); eps <= 0 keeps every block
+    const bool keep_all = !(eps > 0.0);
+    const float eps2f = keep_all ? 0.0f : d2f_rn(eps * eps);
+    const bool fp32_ok = eps2f >= 1e-30f;  // far from FP32 underflow
+    for (int i = tid; i < 8 * bmax; i += kFilterThreads) cs[i] = 0.0;
+    for (int q = tid; q < bc; q += kFilterThreads) dg[q] = 0.0;
+    __syncthreads();
     bool finite = true;
-    for (int q = q0; q < bc; q += 8) {
-        const double* col = H + voff[k] + static_cast<int64_t>(q) * br;
-        float* col32 = H32 + voff[k] + static_cast<int64_t>(q) * br;
-        double cs = 0.0;
-        for (int p0 = 0; p0 < br; p0 += 8) {  // eight loads in flight, then their use
-            double v[8];
+    for (int64_t k = k0 + g; k < k1; k += 8) {  // the group is uniform
+        const int r = row_idx[k];
+        const int br = bsize[r];
+        const double* blk = H + voff[k];
+        float* blk32 = H32 + voff[k];
+        float ss = 0.0f;
+        for (int q = q0; q < bc; q += 8) {
+            const double* col = blk + static_cast<int64_t>(q) * br;
+            float* col32 = blk32 + static_cast<int64_t>(q) * br;
+            double a = 0.0;  // FP64: the Gershgorin bracket
+            for (int p0 = 0; p0 < br; p0 += 8) {  // eight loads in flight, then their use
+                double v[8];
 #pragma unroll
-            for (int p = 0; p < 8; ++p) v[p] = p0 + p < br ? col[p0 + p] : 0.0;
+                for (int p = 0; p < 8; ++p) v[p] = p0 + p < br ? col[p0 + p] : 0.0;
 #pragma unroll
-            for (int p = 0; p < 8; ++p) {
-                if (p0 + p >= br) break;
-                ss = fma(v[p], v[p], ss);
-                cs += fabs(v[p]);
-                finite = finite && isfinite(v[p]);
-                col32[p0 + p] = __double2float_rn(v[p]);
+                for (int p = 0; p < 8; ++p) {
+                    if (p0 + p >= br) break;
+                    const float f = d2f_rn(v[p]);
+                    ss = fmaf(f, f, ss);
+                    a += fabs(v[p]);
+                    finite = finite && finite_bits(v[p]);
+                    col32[p0 + p] = f;
+                }
+            }
+            ca[g * bmax + q] = a;
+            if (r == j) dg[q] = col[q];
+        }
+        // the block's sum of squares over its eight lanes (a fixed tree: every lane ends
+        // with the same bits, so the decision is uniform over the group)
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) ss += __shfl_xor_sync(gmask, ss, o, 8);
+        bool kept = keep_all || r == j;
+        if (!kept) {
+            // |ss - sum v^2| <= (n_elem + 5) 2^-24 sum v^2 (conversion, FMA chain, tree); twice that
+            const float tol = static_cast<float>(br * bc + 8) * 0x1p-23f * eps2f;
+            if (fp32_ok && fabsf(ss - eps2f) > tol) {
+                kept = !(ss < eps2f);
+            } else {
+                double sd = 0.0;
+                for (int q = q0; q < bc; q += 8)
+                    for (int p = 0; p < br; ++p) {
+                        const double x = blk[static_cast<int64_t>(q) * br + p];
+                        sd = fma(x, x, sd);
+                    }
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1) sd += __shfl_xor_sync(gmask, sd, o, 8);
+                kept = !(sqrt(sd) < eps);
             }
         }
-        csum[k * bmax + q] = cs;  // masked below once the block's fate is known
-        if (r == j) diag[static_cast<int64_t>(j) * bmax + q] = col[q];
-    }
-    // the block's sum of squares over its eight lanes (a fixed tree)
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    const bool kept = on && (r == j || !(sqrt(ss) < eps));
-    if (on) {
-        if (!kept)
-            for (int q = q0; q < bc; q += 8) csum[k * bmax + q] = 0.0;
+        if (kept)
+            for (int q = q0; q < bc; q += 8) cs[g * bmax + q] += ca[g * bmax + q];
         if (q0 == 0) {
             keep[k] = kept ? 1 : 0;
             if (keep_prev && kept != (keep_prev[k] != 0)) atomicOr(&sc->changed, 1);
         }
-        if (!finite) atomicCAS(&sc->status, kOk, kErrNonfinite);
     }
-}
-
-// Pass 2, a warp per block column j: per column q the sum over the column's
-// blocks of csum (lane-strided, then a fixed tree), the Gershgorin interval
-// [min_q (d_q - r_q), max_q (d_q + r_q)] (H symmetric: column sums are row
-// sums; r_q without the diagonal entry d_q) into lohi; the last block takes the
-// minimum and maximum over the columns: the bracket of the filtered H and its
-// midpoint.
-__global__ void __launch_bounds__(256) k_filter_columns(const int64_t* __restrict__ col_ptr,
-                                                        const int32_t* __restrict__ bsize, int n_cols, int bmax,
-                                                        const double* __restrict__ csum, const double* __restrict__ diag,
-                                                        double* __restrict__ lohi, DevScalars* sc) {
-    __shared__ double mm_s[2][8];
-    __shared__ bool last_s;
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (j < n_cols) {
-        const int bc = bsize[j];
-        const int64_t k0 = col_ptr[j], k1 = col_ptr[j + 1];
-        double lo = INFINITY, hi = -INFINITY;
-        for (int q0 = 0; q0 < bc; q0 += 8) {  // eight columns' loads in flight
-            double cs[8];
-#pragma unroll
-            for (int qq = 0; qq < 8; ++qq) cs[qq] = 0.0;
-            for (int64_t k = k0 + lane; k < k1; k += 32) {
-#pragma unroll
-                for (int qq = 0; qq < 8; ++qq)
-                    if (q0 + qq < bc) cs[qq] += csum[k * bmax + q0 + qq];
-            }
-#pragma unroll
-            for (int qq = 0; qq < 8; ++qq) {
-                if (q0 + qq >= bc) break;
-                const double c_ = warp_sum(cs[qq]);
-                const double d = diag[static_cast<int64_t>(j) * bmax + q0 + qq], rad = c_ - fabs(d);
-                lo = fmin(lo, d - rad);
-                hi = fmax(hi, d + rad);
-            }
-        }
-        if (lane == 0) {
-            lohi[2 * j] = lo;
-            lohi[2 * j + 1] = hi;
-        }
-    }
-    __threadfence();
+    if (!finite) atomicCAS(&sc->status, kOk, kErrNonfinite);
     __syncthreads();
-    if (threadIdx.x == 0) last_s = atomicAdd(&sc->filter_done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!last_s) return;
-    __threadfence();
+    // column q: the kept blocks' sums over the groups in order, then its interval
     double lo = INFINITY, hi = -INFINITY;
-    for (int c = threadIdx.x; c < n_cols; c += blockDim.x) {
-        lo = fmin(lo, __ldcg(lohi + 2 * c));
-        hi = fmax(hi, __ldcg(lohi + 2 * c + 1));
+    for (int q = tid; q < bc; q += kFilterThreads) {
+        double c_ = 0.0;
+        for (int gg = 0; gg < 8; ++gg) c_ += cs[gg * bmax + q];
+        const double d = dg[q], rad = c_ - fabs(d);
+        lo = fmin(lo, d - rad);
+        hi = fmax(hi, d + rad);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    if (lane == 0) {
-        mm_s[0][warp] = lo;
-        mm_s[1][warp] = hi;
+    if ((tid & 31) == 0 && lo <= hi) {  // a warp without columns has nothing to add
+        atomicMax(&sc->nlo_enc, ord_enc(-lo));
+        atomicMax(&sc->hi_enc, ord_enc(hi));
     }
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
-            lo = fmin(lo, mm_s[0][w]);
-            hi = fmax(hi, mm_s[1][w]);
-        }
-        sc->br_lo = lo;
-        sc->br_hi = hi;
-        sc->mu0 = 0.5 * (lo + hi);
-        sc->filter_done = 0u;
-    }
+    if (tid == 0) last_s = atomicAdd(&sc->filter_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last_s || tid != 0) return;
+    __threadfence();
+    const double blo = -ord_dec(atomicExch(&sc->nlo_enc, 0ull)), bhi = ord_dec(atomicExch(&sc->hi_enc, 0ull));
+    sc->br_lo = blo;
+    sc->br_hi = bhi;
+    sc->mu0 = 0.5 * (blo + bhi);
+    sc->filter_done = 0u;
 }
 
-cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int32_t* bcol,
-                                     const int64_t* voff, const int32_t* bsize, int n_cols, int64_t nnzb, int bmax,
-                                     double eps, uint8_t* keep, const uint8_t* keep_prev, float* H32, double* csum,
-                                     double* diag, double* lohi, DevScalars* sc, cudaStream_t st) {
+cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
+                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep,
+                                     const uint8_t* keep_prev, float* H32, DevScalars* sc, cudaStream_t st) {
     if (n_cols <= 0) return cudaSuccess;
-    const int64_t g1 = (nnzb * 8 + 255) / 256;
-    k_filter_blocks<<<static_cast<unsigned>(g1), 256, 0, st>>>(H, voff, row_idx, bcol, bsize, nnzb, bmax, eps, keep, keep_prev,
-                                                               H32, csum, diag, sc);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int g2 = static_cast<int>((static_cast<int64_t>(n_cols) * 32 + 255) / 256);
-    k_filter_columns<<<g2, 256, 0, st>>>(col_ptr, bsize, n_cols, bmax, csum, diag, lohi, sc);
+    const size_t smem = sizeof(double) * static_cast<size_t>(17) * bmax;
+    if (smem > (48u << 10)) {
+        cudaError_t e = cudaFuncSetAttribute(k_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    k_filter<<<n_cols, kFilterThreads, smem, st>>>(H, col_ptr, row_idx, voff, bsize, bmax, eps, keep, keep_prev, H32, sc);
     return cudaGetLastError();
+}
+
+// The end of both gather forms: the per-warp row statistics (Gershgorin maximum
+// m and the feature sums of this warp's rows) reduced over the 8 warps in
+// order, the bound b_j (Gershgorin, or the learned model's), the features and
+// predictions.  All 256 threads call it.
+__device__ void gather_finish(const SubDesc& s, double m, float f2, float da, float ds, float dq, float rs, float dm,
+                              float rm, bool fp32_rows, double* __restrict__ bound, const GatherExtras& ex) {
+    __shared__ double warp_max_s[8];
+    __shared__ float stat_s[8][7];  // per warp: F2, Da, Ds, Dq, Rs (sums), Dm, Rm (maxima)
+    __shared__ float x_s[kModelFeatures], h1_s[kModelHidden], y_s[2][2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (lane == 0) {
+        warp_max_s[warp] = m;
+        stat_s[warp][0] = f2;
+        stat_s[warp][1] = da;
+        stat_s[warp][2] = ds;
+        stat_s[warp][3] = dq;
+        stat_s[warp][4] = rs;
+        stat_s[warp][5] = dm;
+        stat_s[warp][6] = rm;
+    }
+    __syncthreads();
+    double g = 0.0;
+    for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
+    const double graw = g;
+    // in FP32 the row sums carry a relative error below n 2^-24, covered by the 1e-5 margin
+    if (fp32_rows) g *= 1.0 + 1e-5;
+    if (!(g > 0.0)) g = 1.0;
+    if (ex.feat || ex.params) {
+        if (tid == 0) {
+            float F2 = 0.f, Da = 0.f, Ds = 0.f, Dq = 0.f, Rs = 0.f, Dm = 0.f, Rm = 0.f;
+            for (int w = 0; w < 8; ++w) {
+                F2 += stat_s[w][0];
+                Da += stat_s[w][1];
+                Ds += stat_s[w][2];
+                Dq += stat_s[w][3];
+                Rs += stat_s[w][4];
+                Dm = fmaxf(Dm, stat_s[w][5]);
+                Rm = fmaxf(Rm, stat_s[w][6]);
+            }
+            const float n = static_cast<float>(s.n), G = static_cast<float>(graw);
+            const float ig = G > 0.f ? 1.f / G : 0.f, mean = Ds / n;
+            x_s[0] = sqrtf(F2 / n) * ig;
+            x_s[1] = Dm * ig;
+            x_s[2] = Da / n * ig;
+            x_s[3] = sqrtf(fmaxf(Dq / n - mean * mean, 0.f)) * ig;
+            x_s[4] = Rm * ig;
+            x_s[5] = Rs / n * ig;
+            x_s[6] = n / 256.f;
+            x_s[7] = mean * ig;
+            x_s[8] = ex.prev_ratio ? ex.prev_ratio[blockIdx.x] : 0.f;
+            if (ex.feat)
+                for (int k = 0; k < kModelFeatures; ++k) ex.feat[static_cast<int64_t>(blockIdx.x) * kModelFeatures + k] = x_s[k];
+        }
+        __syncthreads();
+    }
+    double b = g;
+    if (ex.params) {
+        // the network, weights rounded to FP16 (threads 0..63: one hidden unit each)
+        const float* p = ex.params;
+        auto w16 = [](float v) { return __half2float(__float2half_rn(v)); };
+        if (tid < kModelHidden) {
+            float acc = w16(p[kOffB1 + tid]);
+            for (int k = 0; k < kModelFeatures; ++k) acc = fmaf(w16(p[tid * kModelFeatures + k]), x_s[k], acc);
+            h1_s[tid] = tanhf(acc);
+        }
+        __syncthreads();
+        if (tid < kModelHidden) {
+            float acc = w16(p[kOffB2 + tid]);
+            for (int k = 0; k < kModelHidden; ++k) acc = fmaf(w16(p[kOffW2 + tid * kModelHidden + k]), h1_s[k], acc);
+            const float h2 = tanhf(acc);
+            float y0 = w16(p[kOffW3 + tid]) * h2, y1 = w16(p[kOffW3 + kModelHidden + tid]) * h2;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+                y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+            }
+            if (lane == 0) {
+                y_s[warp][0] = y0;
+                y_s[warp][1] = y1;
+            }
+        }
+        __syncthreads();
+        const float y0 = (y_s[0][0] + y_s[1][0]) + w16(p[kOffB3]);
+        const float y1 = (y_s[0][1] + y_s[1][1]) + w16(p[kOffB3 + 1]);
+        if (tid == 0 && ex.pred) {
+            ex.pred[2 * static_cast<int64_t>(blockIdx.x)] = y0;
+            ex.pred[2 * static_cast<int64_t>(blockIdx.x) + 1] = y1;
+        }
+        b = g * fmin(fmax(static_cast<double>(y0), 0.02), 1.0) * (1.0 + ex.margin) / 1.2;
+    }
+    if (tid == 0) {
+        bound[blockIdx.x] = b;
+        if (ex.gersh) ex.gersh[blockIdx.x] = g;
+    }
 }
 
 // One CTA per submatrix; T_j is row-major with leading dimension s.ld (zero
@@ -194,9 +290,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(co
                                                       double* __restrict__ bound, int nblk_max, int n_max,
                                                       GatherExtras ex) {
     extern __shared__ __align__(16) unsigned char gsm[];
-    __shared__ double warp_max_s[8];
-    __shared__ float stat_s[8][7];  // per warp: F2, Da, Ds, Dq, Rs (sums), Dm, Rm (maxima)
-    __shared__ float x_s[kModelFeatures], h1_s[kModelHidden], y_s[2][2];
     if (ex.skip && *ex.skip) return;
     const R mu = static_cast<R>(ex.mu_dev ? *ex.mu_dev : mu_d);
     const SubDesc s = subs[blockIdx.x];
@@ -222,7 +315,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(co
     __syncthreads();
 
     R* t = T + s.t_off;
-    double m = 0.0;
+    R m = R(0);  // largest row sum so far (in the staging type: no FP64 work per row in FP32)
     float f2 = 0.f, da = 0.f, ds = 0.f, dq = 0.f, rs = 0.f, dm = 0.f, rm = 0.f;  // feature statistics
     for (int c = warp; c < s.nblk; c += 8) {
         const int col = rows[c];
@@ -295,7 +388,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(co
                     s_ += __shfl_xor_sync(0xffffffffu, s_, o);
                 }
                 const float d = static_cast<float>(__shfl_sync(0xffffffffu, dsel, (dcol + qq) & 31));
-                m = fmax(m, static_cast<double>(a_));
+                m = fmax(m, a_);
                 const float ad = fabsf(d), rr = static_cast<float>(a_) - ad;
                 f2 += s_;
                 da += ad;
@@ -308,95 +401,189 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(co
         }
         __syncwarp();
     }
-    if (lane == 0) {
-        warp_max_s[warp] = m;
-        stat_s[warp][0] = f2;
-        stat_s[warp][1] = da;
-        stat_s[warp][2] = ds;
-        stat_s[warp][3] = dq;
-        stat_s[warp][4] = rs;
-        stat_s[warp][5] = dm;
-        stat_s[warp][6] = rm;
+    gather_finish(s, static_cast<double>(m), f2, da, ds, dq, rs, dm, rm, sizeof(R) == 4, bound, ex);
+}
+
+// Staged form of the same gather, for patterns whose block rows fit a per-warp
+// shared-memory buffer (bmax x round_up(max n, 4) elements) and whose
+// submatrices have at most kStagedMaxBlocks blocks; one CTA per submatrix,
+// same outputs bit for bit (same values, same per-lane and per-warp orders of
+// the row sums and feature sums).
+//
+// 1. The block map of T_j in shared memory, built once for the submatrix by
+//    all warps: map[a][c] = value offset of block (R_j[c], R_j[a]), the block
+//    of H's column R_j[a] in block row R_j[c] (-1 when the filter dropped it).
+//    T_j is symmetric, so block row a of T_j is that column transposed: the
+//    column-major block (R_j[c], R_j[a]) holds tile (a, c) of T_j row-major.
+// 2. Warp w assembles block rows a = w, w + 8, ... in its buffer: up to eight
+//    rows at once, 32 columns per lane-step and four lane-steps per batch
+//    (all loads of a batch issued before its shared-memory stores), -mu on the
+//    diagonal, row sums and feature sums as the values go in.
+// 3. The block row's b_a x ld elements are one contiguous, 16-byte aligned
+//    range of the staging buffer: one lane writes it with a bulk copy
+//    (cp.async.bulk shared -> global) and the warp goes on to the next block
+//    row; the buffer is reused once that copy has read it.
+constexpr int kStagedMaxBlocks = 64;
+constexpr size_t kStagedSmemLimit = 100u << 10;  // at least two CTAs per SM
+constexpr int kStagedBatch = 4;  // lane-steps of 32 columns whose loads are issued together
+
+template <class R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_gather_staged(const SubDesc* __restrict__ subs, PatternView pv,
+                                                       const R* __restrict__ H, double mu_d, R* __restrict__ T,
+                                                       double* __restrict__ bound, int nblk_max, int stage_elems,
+                                                       GatherExtras ex) {
+    extern __shared__ __align__(128) unsigned char gsm[];
+    if (ex.skip && *ex.skip) return;
+    const R mu = static_cast<R>(ex.mu_dev ? *ex.mu_dev : mu_d);
+    const SubDesc s = subs[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nb = s.nblk, ld = s.ld;
+    R* stage = reinterpret_cast<R*>(gsm) + static_cast<size_t>(warp) * stage_elems;  // this warp's block-row buffer
+    int64_t* map = reinterpret_cast<int64_t*>(gsm + static_cast<size_t>(8) * stage_elems * sizeof(R));
+    int64_t* kcol = map + static_cast<size_t>(nblk_max) * nblk_max;  // filtered blocks of column R_j[a]: [kcol[2a], kcol[2a + 1])
+    int* rows = reinterpret_cast<int*>(kcol + 2 * nblk_max);  // R_j
+    int* ls = rows + nblk_max;        // local starts, nb + 1 entries
+    int* cinfo = ls + nblk_max + 1;   // per local column y: local block (bits 16-31), its size (8-15), y - start (0-7)
+    for (int a = tid; a < nb; a += blockDim.x) {
+        const int r = pv.frow_idx[s.fptr + a];
+        rows[a] = r;
+        ls[a] = pv.lstart[s.fptr + a];
+        kcol[2 * a] = pv.fcol_ptr[r];
+        kcol[2 * a + 1] = pv.fcol_ptr[r + 1];
+    }
+    for (int i = tid; i < nb * nb; i += blockDim.x) map[i] = -1;
+    if (tid == 0) ls[nb] = s.n;
+    __syncthreads();
+    for (int y = tid; y < s.n; y += blockDim.x) {
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (ls[mid] <= y) lo = mid; else hi = mid - 1;
+        }
+        cinfo[y] = (lo << 16) | ((ls[lo + 1] - ls[lo]) << 8) | (y - ls[lo]);
+    }
+    for (int a = warp; a < nb; a += 8) {
+        for (int64_t k = kcol[2 * a] + lane; k < kcol[2 * a + 1]; k += 32) {
+            const int r = pv.frow_idx[k];
+            const int64_t vo = pv.fvoff[k];
+            int lo = 0, hi = nb - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (rows[mid] < r) lo = mid + 1; else hi = mid;
+            }
+            if (rows[lo] == r) map[a * nb + lo] = vo;
+        }
     }
     __syncthreads();
-    double g = 0.0;
-    for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
-    const double graw = g;
-    // in FP32 the row sums carry a relative error below n 2^-24, covered by the 1e-5 margin
-    if (sizeof(R) == 4) g *= 1.0 + 1e-5;
-    if (!(g > 0.0)) g = 1.0;
-    if (ex.feat || ex.params) {
-        if (tid == 0) {
-            float F2 = 0.f, Da = 0.f, Ds = 0.f, Dq = 0.f, Rs = 0.f, Dm = 0.f, Rm = 0.f;
-            for (int w = 0; w < 8; ++w) {
-                F2 += stat_s[w][0];
-                Da += stat_s[w][1];
-                Ds += stat_s[w][2];
-                Dq += stat_s[w][3];
-                Rs += stat_s[w][4];
-                Dm = fmaxf(Dm, stat_s[w][5]);
-                Rm = fmaxf(Rm, stat_s[w][6]);
-            }
-            const float n = static_cast<float>(s.n), G = static_cast<float>(graw);
-            const float ig = G > 0.f ? 1.f / G : 0.f, mean = Ds / n;
-            x_s[0] = sqrtf(F2 / n) * ig;
-            x_s[1] = Dm * ig;
-            x_s[2] = Da / n * ig;
-            x_s[3] = sqrtf(fmaxf(Dq / n - mean * mean, 0.f)) * ig;
-            x_s[4] = Rm * ig;
-            x_s[5] = Rs / n * ig;
-            x_s[6] = n / 256.f;
-            x_s[7] = mean * ig;
-            x_s[8] = ex.prev_ratio ? ex.prev_ratio[blockIdx.x] : 0.f;
-            if (ex.feat)
-                for (int k = 0; k < kModelFeatures; ++k) ex.feat[static_cast<int64_t>(blockIdx.x) * kModelFeatures + k] = x_s[k];
-        }
-        __syncthreads();
-    }
-    double b = g;
-    if (ex.params) {
-        // the network, weights rounded to FP16 (threads 0..63: one hidden unit each)
-        const float* p = ex.params;
-        auto w16 = [](float v) { return __half2float(__float2half_rn(v)); };
-        if (tid < kModelHidden) {
-            float acc = w16(p[kOffB1 + tid]);
-            for (int k = 0; k < kModelFeatures; ++k) acc = fmaf(w16(p[tid * kModelFeatures + k]), x_s[k], acc);
-            h1_s[tid] = tanhf(acc);
-        }
-        __syncthreads();
-        if (tid < kModelHidden) {
-            float acc = w16(p[kOffB2 + tid]);
-            for (int k = 0; k < kModelHidden; ++k) acc = fmaf(w16(p[kOffW2 + tid * kModelHidden + k]), h1_s[k], acc);
-            const float h2 = tanhf(acc);
-            float y0 = w16(p[kOffW3 + tid]) * h2, y1 = w16(p[kOffW3 + kModelHidden + tid]) * h2;
+
+    R* tj = T + s.t_off;
+    R m = R(0);  // largest row sum so far (in the staging type: no FP64 work per row in FP32)
+    float f2 = 0.f, da = 0.f, ds = 0.f, dq = 0.f, rs = 0.f, dm = 0.f, rm = 0.f;  // feature statistics
+    for (int a = warp; a < nb; a += 8) {
+        const int x0 = ls[a], ba = ls[a + 1] - x0;
+        const int64_t* mrow = map + a * nb;
+        if (lane == 0) bulk_wait_read_all();  // the buffer's previous bulk copy has read it
+        __syncwarp();
+        for (int q0 = 0; q0 < ba; q0 += kGatherRows) {
+            const int nq = min(kGatherRows, ba - q0);
+            R acc[kGatherRows];
+            float sq[kGatherRows];
+            R dsel = R(0);  // this lane's diagonal entry of the group, if it holds one
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                y0 += __shfl_xor_sync(0xffffffffu, y0, o);
-                y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+            for (int qq = 0; qq < kGatherRows; ++qq) {
+                acc[qq] = R(0);
+                sq[qq] = 0.f;
             }
-            if (lane == 0) {
-                y_s[warp][0] = y0;
-                y_s[warp][1] = y1;
+            const int dcol = x0 + q0;  // column of row q0's diagonal entry
+            R* srow = stage + static_cast<size_t>(q0) * ld;
+            for (int y0 = 0; y0 < ld; y0 += 32 * kStagedBatch) {
+                R v[kStagedBatch][kGatherRows];
+#pragma unroll
+                for (int i = 0; i < kStagedBatch; ++i) {
+                    const int y = y0 + lane + 32 * i;
+                    const R* src = nullptr;
+                    int br = 0;
+                    if (y < s.n) {
+                        const int ci = cinfo[y];
+                        const int64_t vo = mrow[ci >> 16];
+                        if (vo >= 0) {
+                            br = (ci >> 8) & 0xff;
+                            src = H + vo + (ci & 0xff) + q0 * br;
+                        }
+                    }
+#pragma unroll
+                    for (int qq = 0; qq < kGatherRows; ++qq) v[i][qq] = (src != nullptr && qq < nq) ? src[qq * br] : R(0);
+                }
+#pragma unroll
+                for (int i = 0; i < kStagedBatch; ++i) {
+                    const int y = y0 + lane + 32 * i;
+                    if (y >= ld) break;
+                    const int dq_ = y - dcol;  // row of the group whose diagonal is column y
+#pragma unroll
+                    for (int qq = 0; qq < kGatherRows; ++qq) {
+                        if (qq >= nq) break;
+                        R val = v[i][qq];
+                        if (qq == dq_) {
+                            val -= mu;
+                            dsel = val;
+                        }
+                        srow[qq * ld + y] = val;
+                        acc[qq] += fabs(val);
+                        sq[qq] = fmaf(static_cast<float>(val), static_cast<float>(val), sq[qq]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int qq = 0; qq < kGatherRows; ++qq) {
+                if (qq >= nq) break;
+                R a_ = acc[qq];
+                float s_ = sq[qq];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a_ += __shfl_xor_sync(0xffffffffu, a_, o);
+                    s_ += __shfl_xor_sync(0xffffffffu, s_, o);
+                }
+                const float d = static_cast<float>(__shfl_sync(0xffffffffu, dsel, (dcol + qq) & 31));
+                m = fmax(m, a_);
+                const float ad = fabsf(d), rr = static_cast<float>(a_) - ad;
+                f2 += s_;
+                da += ad;
+                ds += d;
+                dq = fmaf(d, d, dq);
+                rs += rr;
+                dm = fmaxf(dm, ad);
+                rm = fmaxf(rm, rr);
             }
         }
-        __syncthreads();
-        const float y0 = (y_s[0][0] + y_s[1][0]) + w16(p[kOffB3]);
-        const float y1 = (y_s[0][1] + y_s[1][1]) + w16(p[kOffB3 + 1]);
-        if (tid == 0 && ex.pred) {
-            ex.pred[2 * static_cast<int64_t>(blockIdx.x)] = y0;
-            ex.pred[2 * static_cast<int64_t>(blockIdx.x) + 1] = y1;
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            bulk_store(tj + static_cast<int64_t>(x0) * ld, stage, static_cast<uint32_t>(ba * ld * sizeof(R)));
+            bulk_commit();
         }
-        b = g * fmin(fmax(static_cast<double>(y0), 0.02), 1.0) * (1.0 + ex.margin) / 1.2;
     }
-    if (tid == 0) {
-        bound[blockIdx.x] = b;
-        if (ex.gersh) ex.gersh[blockIdx.x] = g;
-    }
+    if (lane == 0) bulk_wait_all();
+    gather_finish(s, static_cast<double>(m), f2, da, ds, dq, rs, dm, rm, sizeof(R) == 4, bound, ex);
 }
 
 template <class R>
-static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
+static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, const PatternView& pv,
                                  const R* H, double mu, R* T, double* bound, const GatherExtras& ex, cudaStream_t st) {
+    if (n_subs <= 0) return cudaSuccess;
+    // staged form: eight block-row buffers, the block map, R_j, local starts, column ranges, column info
+    const int stage_elems = static_cast<int>((static_cast<int64_t>(bmax) * ((max_n + 3) / 4 * 4) + 31) / 32 * 32);
+    const size_t staged_smem = static_cast<size_t>(8) * stage_elems * sizeof(R) +
+                               (static_cast<size_t>(max_nblk) * max_nblk + 2 * max_nblk) * sizeof(int64_t) +
+                               (static_cast<size_t>(2 * max_nblk + 1) + static_cast<size_t>(max_n)) * sizeof(int);
+    if (max_nblk <= kStagedMaxBlocks && staged_smem <= kStagedSmemLimit) {
+        if (staged_smem > (48u << 10)) {
+            cudaError_t e = cudaFuncSetAttribute(k_gather_staged<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(staged_smem));
+            if (e != cudaSuccess) return e;
+        }
+        k_gather_staged<R><<<n_subs, 256, staged_smem, st>>>(subs, pv, H, mu, T, bound, max_nblk, stage_elems, ex);
+        return cudaGetLastError();
+    }
     // per-warp block tables, R_j, local starts and the local block of every column
     const size_t smem = static_cast<size_t>(8) * max_nblk * sizeof(int64_t) +
                         (static_cast<size_t>(2 * max_nblk + 1) + static_cast<size_t>(max_n)) * sizeof(int);
@@ -408,16 +595,16 @@ static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, const PatternView& pv,
                                 const double* H, double mu, double* T, double* bound, const GatherExtras& ex,
                                 cudaStream_t st) {
-    return launch_gather<double>(subs, n_subs, max_nblk, max_n, pv, H, mu, T, bound, ex, st);
+    return launch_gather<double>(subs, n_subs, max_nblk, max_n, bmax, pv, H, mu, T, bound, ex, st);
 }
 
-cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, const PatternView& pv,
                                     const float* H32, double mu, float* T32, double* bound, const GatherExtras& ex,
                                     cudaStream_t st) {
-    return launch_gather<float>(subs, n_subs, max_nblk, max_n, pv, H32, mu, T32, bound, ex, st);
+    return launch_gather<float>(subs, n_subs, max_nblk, max_n, bmax, pv, H32, mu, T32, bound, ex, st);
 }
 
 // Deterministic sums of partial[0, n_cols) by one block (each thread adds a fixed
@@ -437,38 +624,134 @@ __device__ void sum_partials(const double2* partial, int n_cols, DevScalars* sc,
     }
 }
 
-// One CTA per submatrix: scatter of the saved owner columns (Fig. 2 step (iii)),
-// then (the last CTA) the sums of a8.
+// One CTA per submatrix: scatter of the saved owner columns (Fig. 2 step (iii);
+// Eq. 14: D[R_j, j] = 1/2 (E_j - X[:, own]), X symmetric, so the saved column q
+// is X's row own + q), then (the last CTA) the sums of a8.
+//
+// The elements are taken in the order of D's own layout: the kept blocks
+// (R_j[a], j) of column j, each column-major b_a x b_j, so element e of the
+// packed column lies in block a = blk[e / b_j] (the blocks' packed starts are
+// ls[a] b_j) at e' = e - ls[a] b_j, row p = e' mod b_a of column q = e' / b_a.
+// Consecutive threads store consecutive D entries and read runs of b_a
+// consecutive saved values; each thread issues the loads of up to
+// kScatterBatch elements before their stores.
+//
+// Arithmetic (GB300's FP64 pipe is narrow): an off-diagonal entry -x/2 is exact
+// in FP32 and widened on the integer pipes; a diagonal entry (1 - x)/2 is
+// formed in FP64.  The trace (diagonal entries) is summed in FP64; the energy
+// sum trace(D H) takes FP32 products of D and the FP32 copy of H, summed in
+// FP32 per thread and warp, then in FP64 over the warps and the columns.
+constexpr int kScatterBatch = 4;
+
 __global__ void __launch_bounds__(256) k_scatter_owner(const SubDesc* __restrict__ subs, PatternView pv,
-                                                       const float* __restrict__ xown, const double* __restrict__ H,
+                                                       const float* __restrict__ xown, const float* __restrict__ H32,
                                                        double* __restrict__ D, double2* __restrict__ partial, int n_cols,
                                                        DevScalars* sc, const int* skip) {
     if (skip && *skip) return;
-    extern __shared__ int ls_smem[];
+    extern __shared__ __align__(16) unsigned char ssm[];
     __shared__ double scratch[32];
+    __shared__ double tr_s[8];
+    __shared__ float en_s[8];
     __shared__ bool last_s;
     const SubDesc s = subs[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nb = s.nblk, n = s.n, bj = s.bown;
+    int64_t* fvo = reinterpret_cast<int64_t*>(ssm);  // value offset of block (R_j[a], j)
+    int* ls = reinterpret_cast<int*>(fvo + nb);      // local starts, nb + 1 entries
+    int* blk = ls + nb + 1;                          // local block of every row of T_j
+    for (int a = tid; a < nb; a += blockDim.x) {
+        fvo[a] = pv.fvoff[s.fptr + a];
+        ls[a] = pv.lstart[s.fptr + a];
+    }
+    if (tid == 0) ls[nb] = n;
+    __syncthreads();
+    for (int a = warp; a < nb; a += 8)
+        for (int r = ls[a] + lane; r < ls[a + 1]; r += 32) blk[r] = a;
+    __syncthreads();
     const float* x = xown + s.x_off;
-    auto xcol = [&](int q, int i) -> double { return static_cast<double>(x[static_cast<int64_t>(q) * s.n + i]); };
-    finish_column(s, pv, H, D, partial, xcol, ls_smem, scratch);
+    double tr = 0.0;
+    float en = 0.0f;
+    bool any_diag = false;
+    const int total = n * bj;
+    for (int e0 = tid; e0 < total; e0 += kScatterBatch * 256) {
+        float xv[kScatterBatch], hv[kScatterBatch];
+        int64_t off[kScatterBatch];
+        bool dg[kScatterBatch];
+#pragma unroll
+        for (int i = 0; i < kScatterBatch; ++i) {
+            const int e = e0 + i * 256;
+            off[i] = -1;
+            dg[i] = false;
+            xv[i] = 0.f;
+            hv[i] = 0.f;
+            if (e < total) {
+                const int a = blk[e / bj];
+                const int ba = ls[a + 1] - ls[a];
+                const int ep = e - ls[a] * bj;
+                const int q = ep / ba, row = ls[a] + (ep - q * ba);
+                off[i] = fvo[a] + ep;
+                dg[i] = row == s.own + q;
+                xv[i] = x[static_cast<int64_t>(q) * n + row];
+                hv[i] = H32[off[i]];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kScatterBatch; ++i) {
+            if (off[i] < 0) break;
+            float d32;
+            if (dg[i]) {
+                const double d = 0.5 * (1.0 - f2d(xv[i]));
+                D[off[i]] = d;
+                tr += d;
+                any_diag = true;
+                d32 = d2f_rn(d);
+            } else {
+                d32 = -0.5f * xv[i];
+                D[off[i]] = f2d(d32);
+            }
+            en = fmaf(d32, hv[i], en);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) en += __shfl_xor_sync(0xffffffffu, en, o);
+    if (__any_sync(0xffffffffu, any_diag)) tr = warp_sum(tr);  // warps without diagonal entries add zero
+    if (lane == 0) {
+        tr_s[warp] = tr;
+        en_s[warp] = en;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0, e = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            t += tr_s[w];
+            e += f2d(en_s[w]);
+        }
+        partial[s.col] = make_double2(t, e);
+    }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last_s = atomicAdd(&sc->scatter_done, 1u) == gridDim.x - 1;
+    if (tid == 0) last_s = atomicAdd(&sc->scatter_done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last_s) return;
     __threadfence();
     sum_partials(partial, n_cols, sc, scratch);
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         sc->scatter_done = 0u;
         sc->ns_counter = 0;  // the Newton-Schulz launch before this one is complete
     }
 }
 
-cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
-                                 const float* xown, const double* H, double* D, double2* partial, int n_cols,
+cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
+                                 const float* xown, const float* H32, double* D, double2* partial, int n_cols,
                                  DevScalars* sc, cudaStream_t st, const int* skip) {
-    const size_t smem = sizeof(int) * (static_cast<size_t>(max_nblk) + 1);
-    k_scatter_owner<<<n_subs, 256, smem, st>>>(subs, pv, xown, H, D, partial, n_cols, sc, skip);
+    if (n_subs <= 0) return cudaSuccess;
+    const size_t smem = sizeof(int64_t) * static_cast<size_t>(max_nblk) +
+                        sizeof(int) * (static_cast<size_t>(max_nblk) + 1 + static_cast<size_t>(max_n));
+    if (smem > (48u << 10)) {
+        cudaError_t e = cudaFuncSetAttribute(k_scatter_owner, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    k_scatter_owner<<<n_subs, 256, smem, st>>>(subs, pv, xown, H32, D, partial, n_cols, sc, skip);
     return cudaGetLastError();
 }
 

@@ -69,7 +69,7 @@ struct smx_ctx {
     int32_t B = 0;
     int32_t bmax = 0;  // largest block size
     int64_t N = 0, nnzb = 0, n_values = 0;
-    std::vector<int32_t> bs, row_idx, bcol;
+    std::vector<int32_t> bs, row_idx;
     std::vector<int64_t> col_ptr, voff, row_start;
 
     // settings
@@ -91,14 +91,14 @@ struct smx_ctx {
     int64_t t_elems = 0, x_elems = 0;
 
     // device buffers
-    DevBuf d_H, d_H32, d_voff, d_row_idx, d_col_ptr, d_bs, d_keep, d_keep_prev, d_bcol, d_csum, d_diag;
+    DevBuf d_H, d_H32, d_voff, d_row_idx, d_col_ptr, d_bs, d_keep, d_keep_prev;
     double br_lo = 0.0, br_hi = 0.0;  // Gershgorin bracket of the filtered H (from the last filter)
     bool filter_compared = false;     // the last filter launch compared its flags with the current pattern
     DevBuf d_sc;                      // DevScalars: status, flags, bracket, trace and energy
     DevScalars* h_sc = nullptr;       // pinned copy, filled by fetch()
     DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order;
     DevBuf d_T, d_W1, d_W2, d_W3, d_W4, d_ws, d_D, d_xown;
-    DevBuf d_bound, d_iters, d_partial, d_lohi, d_work_n3;
+    DevBuf d_bound, d_iters, d_partial, d_work_n3;
     uint8_t* h_keep_pinned = nullptr;
 
     // tensor-core workspace
@@ -263,12 +263,10 @@ static smx_status launch_filter(smx_ctx* c) {
     NvtxRange nv("smx filter");
     c->filter_compared = c->analysed && c->eps > 0.0;  // without a threshold every block is kept
     SMX_CUDA(launch_filter_gershgorin(dp<double>(c->d_H), dp<int64_t>(c->d_col_ptr), dp<int32_t>(c->d_row_idx),
-                                      dp<int32_t>(c->d_bcol), dp<int64_t>(c->d_voff), dp<int32_t>(c->d_bs), c->B, c->nnzb,
-                                      c->bmax, c->eps, dp<uint8_t>(c->d_keep),
-                                      c->filter_compared ? dp<uint8_t>(c->d_keep_prev) : nullptr, dp<float>(c->d_H32),
-                                      dp<double>(c->d_csum), dp<double>(c->d_diag), dp<double>(c->d_lohi), scalars(c),
-                                      c->stream));
-    c->kernel_launches += 2;
+                                      dp<int64_t>(c->d_voff), dp<int32_t>(c->d_bs), c->B, c->bmax, c->eps,
+                                      dp<uint8_t>(c->d_keep), c->filter_compared ? dp<uint8_t>(c->d_keep_prev) : nullptr,
+                                      dp<float>(c->d_H32), scalars(c), c->stream));
+    c->kernel_launches += 1;
     return SMX_OK;
 }
 
@@ -428,6 +426,11 @@ static smx_status prepare_tc_workspace(smx_ctx* c) {
     return SMX_OK;
 }
 
+// Single-pass forms stop at their rounding floor: once ||X^2 - I||_F < 1/2 every eigenvalue
+// of X^2 lies within 1/2 of 1, where a Newton-Schulz step shrinks each |lambda^2 - 1| at least
+// 2.5-fold; a residual there that does not halve is rounding, not progress.
+constexpr float kStallLevel = 0.5f;
+
 static double tau_for(int precision) {
     switch (precision) {
         case SMX_FP64: return 1e-7;
@@ -467,10 +470,10 @@ static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const Gathe
     const PatternView pv = pattern_view(c);
     SubDesc* subs = dp<SubDesc>(c->d_subs);
     if (c->precision == SMX_FP64) {
-        SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, c->max_n, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
+        SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, c->max_n, c->bmax, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
                                      dp<double>(c->d_bound) + j0, ex, c->stream));
     } else {
-        SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, c->max_n, pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
+        SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, c->max_n, c->bmax, pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
                                          dp<double>(c->d_bound) + j0, ex, c->stream));
     }
     c->kernel_launches += 1;
@@ -499,9 +502,9 @@ static smx_status nonorth_setup(smx_ctx* c) {
     const PatternView pv = pattern_view(c);
     SubDesc* subs = dp<SubDesc>(c->d_subs) + j0;
     GatherExtras ex;
-    SMX_CUDA(launch_gather_bound(subs, m, c->max_nblk, c->max_n, pv, dp<double>(c->d_S), 0.0, dp<double>(c->d_Lc),
+    SMX_CUDA(launch_gather_bound(subs, m, c->max_nblk, c->max_n, c->bmax, pv, dp<double>(c->d_S), 0.0, dp<double>(c->d_Lc),
                                  dp<double>(c->d_bound) + j0, ex, st));
-    SMX_CUDA(launch_gather_bound(subs, m, c->max_nblk, c->max_n, pv, dp<double>(c->d_H), 0.0, dp<double>(c->d_Mc),
+    SMX_CUDA(launch_gather_bound(subs, m, c->max_nblk, c->max_n, c->bmax, pv, dp<double>(c->d_H), 0.0, dp<double>(c->d_Mc),
                                  dp<double>(c->d_gersh) + j0, ex, st));
     NonorthSetupArgs a;
     a.subs = subs;
@@ -635,6 +638,7 @@ static smx_status build_at(smx_ctx* c, double mu, const double* mu_dev = nullptr
             a.ld = c->ws_ld;
             a.n_slots = std::min(c->ws_slots, m);
             a.tau = static_cast<float>(tau_for(c->precision));
+            a.stall_level = (c->precision == SMX_FP16 || c->precision == SMX_BF16) ? kStallLevel : 0.0f;
             a.max_iter = 100;
             a.iters = dp<int32_t>(c->d_iters);
             a.work_n3 = dp<unsigned long long>(c->d_work_n3);
@@ -687,7 +691,7 @@ static smx_status build_at(smx_ctx* c, double mu, const double* mu_dev = nullptr
             }
             SMX_CUDA(cudaEventRecord(ns1, st));
             if (!finish) {
-                SMX_CUDA(launch_scatter_owner(subs + j0, m, c->max_nblk, pv, dp<float>(c->d_xown), dp<double>(c->d_H),
+                SMX_CUDA(launch_scatter_owner(subs + j0, m, c->max_nblk, c->max_n, pv, dp<float>(c->d_xown), dp<float>(c->d_H32),
                                               dp<double>(c->d_D), dp<double2>(c->d_partial), B, sc, st, skip));
                 c->kernel_launches += 1;
             }
@@ -756,16 +760,13 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     c->col_ptr.assign(col_ptr, col_ptr + n_block_cols + 1);
     c->nnzb = col_ptr[n_block_cols];
     c->row_idx.assign(row_idx, row_idx + c->nnzb);
-    c->bcol.resize(c->nnzb);
     c->voff.assign(c->nnzb + 1, 0);
     c->row_start.assign(n_block_cols + 1, 0);
     for (int32_t j = 0; j < n_block_cols; ++j) c->row_start[j + 1] = c->row_start[j] + block_size[j];
     c->N = c->row_start[n_block_cols];
     for (int32_t j = 0; j < n_block_cols; ++j)
-        for (int64_t k = col_ptr[j]; k < col_ptr[j + 1]; ++k) {
-            c->bcol[k] = j;
+        for (int64_t k = col_ptr[j]; k < col_ptr[j + 1]; ++k)
             c->voff[k + 1] = c->voff[k] + static_cast<int64_t>(block_size[row_idx[k]]) * block_size[j];
-        }
     c->n_values = c->voff[c->nnzb];
     smx_status s = SMX_OK;
     auto fail = [&](smx_status e) {
@@ -777,9 +778,6 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if ((s = upload(c->d_row_idx, c->row_idx, c->stream)) != SMX_OK) return fail(s);
     if ((s = upload(c->d_col_ptr, c->col_ptr, c->stream)) != SMX_OK) return fail(s);
     if ((s = upload(c->d_bs, c->bs, c->stream)) != SMX_OK) return fail(s);
-    if ((s = upload(c->d_bcol, c->bcol, c->stream)) != SMX_OK) return fail(s);
-    if ((s = ensure(c->d_csum, sizeof(double) * std::max<int64_t>(1, c->nnzb) * c->bmax)) != SMX_OK) return fail(s);
-    if ((s = ensure(c->d_diag, sizeof(double) * static_cast<size_t>(n_block_cols) * c->bmax)) != SMX_OK) return fail(s);
     const size_t vb = static_cast<size_t>(c->n_values) * sizeof(double);
     if ((s = ensure(c->d_H, vb)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_H32, vb / 2)) != SMX_OK) return fail(s);
@@ -792,7 +790,6 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     if ((s = ensure(c->d_bound, sizeof(double) * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_iters, sizeof(int32_t) * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_partial, sizeof(double2) * n_block_cols)) != SMX_OK) return fail(s);
-    if ((s = ensure(c->d_lohi, sizeof(double) * 2 * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_work_n3, sizeof(unsigned long long))) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_gersh, sizeof(double) * n_block_cols)) != SMX_OK) return fail(s);
     if ((s = ensure(c->d_sq_ratio, sizeof(float) * n_block_cols)) != SMX_OK) return fail(s);
@@ -1407,9 +1404,9 @@ void smx_destroy(smx_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep_prev, &c->d_sc, &c->d_bcol, &c->d_csum, &c->d_diag, &c->d_keep, &c->d_fcol_ptr,
+    DevBuf* bufs[] = {&c->d_H, &c->d_H32, &c->d_voff, &c->d_row_idx, &c->d_col_ptr, &c->d_bs, &c->d_keep_prev, &c->d_sc, &c->d_keep, &c->d_fcol_ptr,
                       &c->d_frow_idx, &c->d_fvoff, &c->d_lstart, &c->d_subs, &c->d_order, &c->d_T, &c->d_W1,
-                      &c->d_W2, &c->d_W3, &c->d_W4, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial, &c->d_lohi,
+                      &c->d_W2, &c->d_W3, &c->d_W4, &c->d_ws, &c->d_D, &c->d_xown, &c->d_bound, &c->d_iters, &c->d_partial,
                       &c->d_work_n3,
                       &c->d_params, &c->d_mst, &c->d_vst, &c->d_partial_mlp, &c->d_feat, &c->d_pred, &c->d_labels,
                       &c->d_gersh, &c->d_prev_ratio, &c->d_sq_ratio, &c->d_loss, &c->d_sx, &c->d_st,

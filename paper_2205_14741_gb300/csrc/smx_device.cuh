@@ -36,6 +36,37 @@ struct PatternView {
     const int32_t* bsize;     // [B] block sizes
 };
 
+// Conversions between FP64 and FP32 on the integer pipes.  GB300's FP64 pipe
+// takes about 16 cycles per warp instruction per SM, and conversions with an
+// FP64 operand run on it; these give the same results as the conversion
+// instructions for normal values (round to nearest even for FP64 -> FP32) and
+// leave the others (zero, subnormal, overflow, inf, NaN) to them.
+__device__ __forceinline__ float d2f_rn(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const uint32_t hi = static_cast<uint32_t>(b >> 32), lo = static_cast<uint32_t>(b);
+    const int ef = static_cast<int>((hi >> 20) & 0x7ffu) - 896;  // FP32 exponent field (1023 - 127)
+    if (ef >= 1 && ef <= 254) {
+        uint32_t r = (hi & 0x80000000u) | (static_cast<uint32_t>(ef) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const uint32_t rem = lo & 0x1fffffffu;  // the 29 bits dropped; half = 2^28
+        if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ++r;  // a carry may reach inf: correct
+        return __uint_as_float(r);
+    }
+    return __double2float_rn(x);
+}
+__device__ __forceinline__ double f2d(float f) {
+    const uint32_t u = __float_as_uint(f), e = (u >> 23) & 0xffu;
+    if (e != 0u && e != 0xffu) {
+        const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+        return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(hi) << 32) | (u << 29)));
+    }
+    return static_cast<double>(f);
+}
+// false for inf and NaN (the exponent field of the high word)
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (static_cast<uint32_t>(static_cast<unsigned long long>(__double_as_longlong(x)) >> 32) & 0x7ff00000u) !=
+           0x7ff00000u;
+}
+
 // Bounded waits: every spin in the library gives up after this many polls,
 // records kErrTimeout and returns false.
 constexpr uint32_t kSpinLimit = 1u << 26;
@@ -88,6 +119,24 @@ __device__ __forceinline__ void fence_barrier_init() {
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
+
+// Orders this thread's generic-proxy shared-memory writes before later
+// async-proxy reads of them (tensor-core operands, bulk copies) issued after a
+// barrier.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Untiled bulk copy shared -> global (both addresses 16-byte aligned, bytes a
+// multiple of 16), tracked by this thread's bulk async-groups.
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until this thread's committed bulk copies have read their shared-memory source.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Waits until this thread's committed bulk copies are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // 3-D tiled TMA load (box given by the tensor map) into shared memory,
 // completing on an mbarrier transaction count.

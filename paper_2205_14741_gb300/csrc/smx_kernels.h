@@ -21,6 +21,7 @@ struct DevScalars {
     int fallbacks;         // learned-bound fallbacks since the last reset
     int ns_counter;        // job counter of the tensor-core Newton-Schulz kernel (reset by the scatter)
     unsigned int filter_done, scatter_done;  // last-block tickets (each reset by its last block)
+    unsigned long long nlo_enc, hi_enc;      // filter: running bracket as order-preserving images (reset by its last block)
     int bis_done;          // device-side bisection: stopped (the later builds are skipped)
     int bis_steps;         // ... builds evaluated
 };
@@ -33,15 +34,13 @@ cudaError_t launch_bisect_init(DevScalars* sc, double lo, double hi, cudaStream_
 cudaError_t launch_bisect_step(DevScalars* sc, double n_e, double tol, int max_steps, cudaStream_t st);
 
 // a1 + bracket: keep flags of every block (Frobenius norm >= eps, diagonal
-// always), non-finite check (sc->status), FP32 copy of H and the Gershgorin
-// interval of every filtered column (lohi[2j], lohi[2j + 1]); with keep_prev,
-// sc->changed = 1 when a flag differs from it.  The bracket (min and max over
-// the columns) and its midpoint go to sc->br_lo, br_hi, mu0.  csum (nnzb x
-// bmax) and diag (n_cols x bmax) are scratch.
-cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int32_t* bcol,
-                                     const int64_t* voff, const int32_t* bsize, int n_cols, int64_t nnzb, int bmax,
-                                     double eps, uint8_t* keep, const uint8_t* keep_prev, float* H32, double* csum,
-                                     double* diag, double* lohi, DevScalars* sc, cudaStream_t st);
+// always), non-finite check (sc->status), FP32 copy of H; with keep_prev,
+// sc->changed = 1 when a flag differs from it.  The Gershgorin bracket of the
+// filtered H (minimum and maximum over its columns' intervals) and its
+// midpoint go to sc->br_lo, br_hi, mu0.
+cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
+                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep,
+                                     const uint8_t* keep_prev, float* H32, DevScalars* sc, cudaStream_t st);
 
 // Optional outputs of the gather, per submatrix (pointers offset like subs; null = not wanted).
 struct GatherExtras {
@@ -58,12 +57,12 @@ struct GatherExtras {
 // a3 + a4: T_j = H[R_j, R_j] - mu I into the FP64 staging buffer, then the
 // Gershgorin bound b_j = max row abs-sum of T_j (>= spectral radius), or the
 // learned bound (extras.params).
-cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, const PatternView& pv,
                                 const double* H, double mu, double* T, double* bound, const GatherExtras& ex,
                                 cudaStream_t st);
 // The same in FP32 (tensor-core path): T32 from the FP32 copy of H; the bound
 // is enlarged by 1e-5 relative to cover FP32 summation.
-cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, const PatternView& pv,
                                     const float* H32, double mu, float* T32, double* bound, const GatherExtras& ex,
                                     cudaStream_t st);
 
@@ -155,6 +154,9 @@ struct NsTcArgs {
     int ld;                // multiple of 64, >= every padded n_j
     int n_slots;           // persistent CTAs (one per SM)
     float tau;
+    // single-pass forms: also stop after a step whose residual lies below this level but is
+    // more than half the previous one (the rounding floor; 0 = off)
+    float stall_level;
     int max_iter;
     int32_t* iters;
     unsigned long long* work_n3;  // += n_j^3 * iters_j per submatrix
@@ -181,11 +183,12 @@ struct NsTcArgs {
 cudaError_t launch_ns_tc(const NsTcArgs& a, int precision, const CUtensorMap& tmap, int max_nblk, cudaStream_t st);
 
 // a7 + a8 for the tensor-core path: D[R_j, j] = 1/2 (E_j - X[:, own]) from the
-// saved owner columns, with the per-column trace / energy partials (FP64);
-// the last block sums partial[0, n_cols) in a fixed order into sc->trace,
+// saved owner columns, with the per-column trace (FP64) and energy (FP32 terms
+// against the FP32 copy H32 of H, FP64 over warps and columns) partials; the
+// last block sums partial[0, n_cols) in a fixed order into sc->trace,
 // sc->energy and resets sc->ns_counter for the next Newton-Schulz launch.
-cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, const PatternView& pv,
-                                 const float* xown, const double* H, double* D, double2* partial, int n_cols,
+cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
+                                 const float* xown, const float* H32, double* D, double2* partial, int n_cols,
                                  DevScalars* sc, cudaStream_t st, const int* skip = nullptr);
 
 // ---------------------------------------------------------------------------

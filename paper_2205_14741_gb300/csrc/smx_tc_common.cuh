@@ -184,10 +184,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Orders this thread's generic shared-memory writes before later async-proxy
-// (tensor-core) reads issued after a barrier.
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 // Byte offset of element (r, c) in a row-major matrix image held as 64 x 64
 // boxes in the 128-byte-swizzled layout (what a TMA box load writes), box
 // (row block rb, column block cb) at (cb * RB + rb) * 8 KB.
