@@ -18,6 +18,8 @@ on the same workload instead (bounded column samples, extrapolated).
 from __future__ import annotations
 
 import argparse
+import contextlib
+import gc
 import json
 import os
 import statistics
@@ -42,6 +44,19 @@ WORKLOAD_TEXT = {
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_TFLOPS = 1.2  # DFMA throughput measured on this machine's GB300 (register-resident FMA loop)
 METRIC = "density matrices/s (mu-solved), mixed precision vs FP64 plain at <=1e-5 error on D"
+
+
+@contextlib.contextmanager
+def no_gc():
+    """Timed loops run with Python's cyclic garbage collector paused (as timeit does), so that a
+    collection pause of the interpreter does not land inside a sub-millisecond step."""
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
 
 
 def _peaks():
@@ -682,12 +697,13 @@ def run_ours(args):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
         clocks = ClockSampler(local)
         clocks.start()
-        for k in range(n_steps):
-            flush.zero_()  # write > L2 between timed steps (outside the events)
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
+        with no_gc():
+            for k in range(n_steps):
+                flush.zero_()  # write > L2 between timed steps (outside the events)
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
         clk = clocks.stop()
         ms = sum(a.elapsed_time(b) for a, b in ev)
         stats = ctx.get_stats()
@@ -750,22 +766,23 @@ def run_ours(args):
     h_np, d_np = h_host.numpy(), d_host.numpy()
     e2e_times = []
     bis_steps = []
-    for k in range(args.warmup + args.e2e_steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ctx.set_values(h_np)
-        if mu_fixed is not None:
-            ctx.set_mu(mu_fixed)
-            ctx.build_density()
-        else:
-            ctx.solve_mu()
-        ctx.get_density(d_np)
-        ctx.get_trace()
-        t1 = time.perf_counter()
-        if k >= args.warmup:
-            e2e_times.append(t1 - t0)
-            bis_steps.append(ctx.get_stats()["bisection_steps"] if mu_fixed is None else 1)
+    with no_gc():
+        for k in range(args.warmup + args.e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.set_values(h_np)
+            if mu_fixed is not None:
+                ctx.set_mu(mu_fixed)
+                ctx.build_density()
+            else:
+                ctx.solve_mu()
+            ctx.get_density(d_np)
+            ctx.get_trace()
+            t1 = time.perf_counter()
+            if k >= args.warmup:
+                e2e_times.append(t1 - t0)
+                bis_steps.append(ctx.get_stats()["bisection_steps"] if mu_fixed is None else 1)
     e2e_s = sum(e2e_times)
     if pg:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")

@@ -364,6 +364,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     // Jobs are claimed one ahead: while a submatrix iterates, its successor's staged
     // T_j is prefetched into L2 (the prologue then reads it from there).
     __shared__ int next_s;
+    // the job's scalars in FP32, formed once by thread 0 (FP64 arithmetic on every thread would
+    // queue twelve warps on the narrow FP64 pipe): 1 / b_j and the predicted smallest
+    // |eigenvalue| of X0 = (T_j - mu I) / b_j (negative when there is no prediction)
+    __shared__ float inv_b_s, dhat_s;
     if (tid == 0) next_s = atomicAdd(a.work_counter, 1);
     for (;;) {
         if (tid == 0) {
@@ -375,6 +379,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 const uint32_t len = static_cast<uint32_t>(bytes < (4u << 20) ? bytes : (4u << 20)) & ~15u;
                 if (len) prefetch_l2_bulk(a.T + sn.t_off, len);
             }
+            if (job_s < a.n_subs) {
+                const int jj = a.order[job_s];
+                const double b = a.bound[jj];  // the gather's b_j (this job rewrites it later)
+                inv_b_s = static_cast<float>(1.0 / b);
+                dhat_s = a.pred ? a.pred[2 * jj + 1] * static_cast<float>(a.gersh[jj] / b) : -1.0f;
+            }
         }
         __syncthreads();
         const int job = job_s;
@@ -384,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         const int kpad = (s.n + 31) & ~31;  // MMA extent; TMA moves 64-wide boxes
         // learned bound: the predicted smallest |eigenvalue| of X0 = (T_j - mu I) / b_j (read
         // before this job rewrites b_j; negative when there is no prediction)
-        const float dhat = a.pred ? a.pred[2 * j + 1] * static_cast<float>(a.gersh[j] / a.bound[j]) : -1.0f;
+        const float dhat = dhat_s;
         // lower end of the interval the scaled schedule assumes for the current iterate's
         // |eigenvalues| (1 = plain steps), and the factor a of the current step
         float lsch = 1.0f, acur = 1.0f;
@@ -403,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         if (resident) {
             // rows of T_j through two shared-memory buffers by asynchronous 16-byte copies: the
             // copy of a batch of rows overlaps the split of the batch before
-            const float inv_b = static_cast<float>(1.0 / a.bound[j]);
+            const float inv_b = inv_b_s;
             const float* t = a.T + s.t_off;
             const int row_chunks = s.ld / 4;  // 16-byte chunks per row of T_j
             const int per = max(1, min(s.n, static_cast<int>(C::kStageBuf / (16u * row_chunks))));  // rows per batch
@@ -458,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; rprev = INFINITY; }
             __syncthreads();
         } else {
-            const float inv_b = static_cast<float>(1.0 / a.bound[j]);
+            const float inv_b = inv_b_s;
             const float* t = a.T + s.t_off;
             uint16_t* xh = ws + static_cast<int64_t>(zx0) * buf;
             uint16_t* xl = xh + buf;
@@ -579,7 +589,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             // two row tiles (kpad in (128, 192]): tile 1 holds the wc = kpad - 128 last rows
             const int wc = kpad - 128;
             const uint32_t idesc_w = idesc_f16(128, wc > 0 ? wc : 32, C::kFmt) | idesc_b_mn;
-            const uint32_t idesc_128 = idesc_f16(128, 128, C::kFmt) | idesc_b_mn;
             // Bz = (Z - shift I)[:, 128 ..] as an MN-major B operand (kpad K rows, one 64-column
             // block; hi boxes, then lo boxes) after the images; iteration 0's row-sum scratch at
             // 160 KB is used only before Bz is written
@@ -588,6 +597,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             float* rpart_s = reinterpret_cast<float*>(smem + 160 * 1024);  // [3][kResKpad], iteration 0 only
             float* rsum_s = rpart_s + 3 * kResKpad;
             float* rs2_s = rsum_s + kResKpad;
+            float* csum_s = rs2_s + kResKpad;  // [4][64]: rows 128 .. over columns 0 .. 127, per lane quadrant
+            float* tbsum_s = csum_s + 4 * 64;  // [64]: rows 128 .. over columns 128 .. (the corner)
             const uint32_t lbo = static_cast<uint32_t>(RB) * 8192u;
             const int q = warp & 3, part = warp >> 2;
             const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
@@ -881,51 +892,124 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                     if (kMirror) mirror_chunk(hw, lw, 128 + crow0, 128 + c0, c0 == crow0);
                 }
             };
-            // scan: rpart_s[part, row] = sum_c |C_rc| w_c over this thread's columns (w = 1 when null)
-            // (with acc_hi != 0 the columns >= 128 come from acc_hi instead: the two-tile form's tile 1)
-            auto scan = [&](int t, uint32_t acc, const float* w, uint32_t acc_hi = 0u) {
-                const int row = 128 * t + 32 * q + lane;
+            // Row sums sum_c |Z_rc| w_c of the first product Z (w = 1 when null), for the bound.
+            // Rows 0 .. 127 (tile 0, accumulator acc): each warp adds its columns into
+            // rpart_s[part, row].  Rows 128 .. (kpad > 128): Z is symmetric, so their columns
+            // 0 .. 127 are tile 0's columns 128 .. summed over the rows (w of the row): the warp
+            // holding such a 32-column chunk reduces it over its 32 lanes into csum_s[quadrant]
+            // (a transpose-reduce: after five exchange steps lane L holds column L's sum);
+            // their columns 128 .. are the corner product (scan_corner).
+            auto colsum32 = [&](float (&v)[32]) -> float {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const bool up = lane & 16;
+                    const float send = up ? v[i] : v[i + 16], keep = up ? v[i + 16] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const bool up = lane & 8;
+                    const float send = up ? v[i] : v[i + 8], keep = up ? v[i + 8] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const bool up = lane & 4;
+                    const float send = up ? v[i] : v[i + 4], keep = up ? v[i + 4] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const bool up = lane & 2;
+                    const float send = up ? v[i] : v[i + 2], keep = up ? v[i + 2] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+                }
+                const bool up = lane & 1;
+                const float send = up ? v[0] : v[1], keep = up ? v[1] : v[0];
+                return keep + __shfl_xor_sync(0xffffffffu, send, 1);
+            };
+            auto scan = [&](uint32_t acc, const float* w) {
+                const int row = 32 * q + lane;
+                const float wr = (w && row < s.n) ? w[row] : 1.0f;
                 float sum = 0.0f;
 #pragma unroll 1
                 for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
                     uint32_t raw[32];
-                    tmem_ld32_issue((acc_hi != 0u && c0 >= 128 ? acc_hi + (c0 - 128) : acc + c0) + lane_off, raw);
+                    tmem_ld32_issue(acc + c0 + lane_off, raw);
                     tmem_wait_ld();
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int c = c0 + i;
                         if (row < s.n && c < s.n) sum = fmaf(fabsf(__uint_as_float(raw[i])), w ? w[c] : 1.0f, sum);
                     }
+                    if (c0 >= 128) {  // warp-uniform
+                        float v[32];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            v[i] = (row < s.n && c0 + i < s.n) ? fabsf(__uint_as_float(raw[i])) * wr : 0.0f;
+                        csum_s[q * 64 + (c0 - 128) + lane] = colsum32(v);
+                    }
                 }
                 if (row < s.n) rpart_s[part * kResKpad + row] = sum;
             };
-            // out[r] = sum of the parts' partials, in part order (deterministic); after a barrier
-            auto gather_parts = [&](float* out) {
+            // rows 128 + 32 q + lane over the corner's columns 128 .. (warps of part 0, quadrants
+            // holding corner rows)
+            auto scan_corner = [&](uint32_t acc, const float* w) {
+                if (part != 0 || 32 * q >= wc) return;
+                const int row = 128 + 32 * q + lane;
+                float sum = 0.0f;
+#pragma unroll 1
+                for (int c0 = 0; c0 < wc; c0 += 32) {
+                    uint32_t raw[32];
+                    tmem_ld32_issue(acc + c0 + lane_off, raw);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int c = 128 + c0 + i;
+                        if (row < s.n && c < s.n) sum = fmaf(fabsf(__uint_as_float(raw[i])), w ? w[c] : 1.0f, sum);
+                    }
+                }
+                if (row < s.n) tbsum_s[row - 128] = sum;
+            };
+            // out[r] = the sum of r's parts in a fixed order (after a barrier), and the block's
+            // maximum of out[r] (of out[r] / div[r] with div); every thread gets it
+            auto gather_max = [&](float* out, const float* div) -> float {
                 __syncthreads();
-                for (int r = tid; r < s.n; r += kThreads) out[r] = (rpart_s[r] + rpart_s[kResKpad + r]) + rpart_s[2 * kResKpad + r];
+                float mx = 0.0f;
+                for (int r = tid; r < s.n; r += kThreads) {
+                    float v;
+                    if (r < 128) {
+                        v = (rpart_s[r] + rpart_s[kResKpad + r]) + rpart_s[2 * kResKpad + r];
+                    } else {
+                        const int c = r - 128;
+                        v = ((csum_s[c] + csum_s[64 + c]) + (csum_s[128 + c] + csum_s[192 + c])) + tbsum_s[c];
+                    }
+                    out[r] = v;
+                    mx = fmaxf(mx, div ? v / div[r] : v);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if (lane == 0) red_s[0][warp] = mx;
                 __syncthreads();
+                float m = 0.0f;
+                for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, red_s[0][w]);
+                return m;
             };
 
-            // it = 0: the bound on rho(Z) from the first products' row sums (tile 0 in z0, tile 1
-            // in z1; after a barrier) and the a-posteriori scaling c = 1.2/s (every thread gets c)
-            auto start_scale = [&](uint32_t z0, uint32_t z1, uint32_t z1_hi = 0u) -> float {
-                scan(0, z0, nullptr);
-                if (mtiles > 1) scan(1, z1, nullptr, z1_hi);
-                gather_parts(rsum_s);
-                float rmax = 0.0f;
-                for (int r = tid; r < s.n; r += kThreads) rmax = fmaxf(rmax, rsum_s[r]);
-                rmax = block_max2(rmax, 0.0f).x;
+            // it = 0: the bound on rho(Z) from the first product's row sums (tile 0 in z0, the
+            // corner in zc; after a barrier) and the a-posteriori scaling c = 1.2/s (every thread gets c)
+            auto start_scale = [&](uint32_t z0, uint32_t zc) -> float {
+                scan(z0, nullptr);
+                if (mtiles > 1) scan_corner(zc, nullptr);
+                const float rmax = gather_max(rsum_s, nullptr);
                 float best = rmax;
                 if (a.use_model && rmax > 0.0f) {
                     // one power step: w = the row sums (floored to stay positive)
                     for (int r = tid; r < s.n; r += kThreads) rsum_s[r] = fmaxf(rsum_s[r], 1e-12f * rmax);
                     __syncthreads();
-                    scan(0, z0, rsum_s);
-                    if (mtiles > 1) scan(1, z1, rsum_s, z1_hi);
-                    gather_parts(rs2_s);
-                    float qm = 0.0f;
-                    for (int r = tid; r < s.n; r += kThreads) qm = fmaxf(qm, rs2_s[r] / rsum_s[r]);
-                    best = fminf(best, block_max2(qm, 0.0f).x);
+                    scan(z0, rsum_s);
+                    if (mtiles > 1) scan_corner(zc, rsum_s);
+                    best = fminf(best, gather_max(rs2_s, rsum_s));
                 }
                 const float smax = sqrtf(best * (1.0f + 1e-4f));  // margin for FP32 summation
                 const float scale = start_factor(smax);
@@ -1010,27 +1094,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 //   rows 128 .. of the image and Bz; its A tile's rows past kpad, whose results are
                 //   dropped, may see the new values), then tile 0's columns 128 .. as rows 128 ..
                 //   (transposed) and the corner.
-                // Iteration 0 also forms tile 1's columns 0 .. 127 (-> R1, N = 128) for the
-                // row sums of the bound.  Tensor memory: TA, TB, R1 and TC = the last kpad
-                // columns (TC overlaps R1 only when kpad = 192, and R1 is dead by then).
-                const uint32_t TA = tmem_base, TB = tmem_base + kpad, R1 = TB + wc, TC = tmem_base + 512 - kpad;
+                // Iteration 0's row sums of the bound take rows 128 .. from tile 0's columns by
+                // symmetry (no product for tile 1's columns 0 .. 127).  Tensor memory: TA, TB and
+                // TC = the last kpad columns.
+                const uint32_t TA = tmem_base, TB = tmem_base + kpad, TC = tmem_base + 512 - kpad;
                 for (int it = 0; it < a.max_iter; ++it) {
                     float alpha = -0.5f, shift = 3.0f;
                     if (it > 0) next_step(shift, alpha);
                     if (it == 0 && warp == 1 && lane == 0) {  // later iterations: issued at the end of the previous one
                         tc_fence_after();
                         issue_xx(0, TA);
-                        issue_xx_cols(1, R1, 0, idesc_128);
                         tc_commit(&mma_bar);
                         issue_xx_cols(1, TB, 128, idesc_w);
                         tc_commit(&mma_bar2);
                     }
-                    mma_wait();  // Z_0 (and R1)
+                    mma_wait();  // Z_0
                     if (it == 0) {
                         mma_wait2();  // Z_c
                         __syncthreads();
                         if (*abortp) break;
-                        const float c = start_scale(TA, R1, TB);
+                        const float c = start_scale(TA, TB);
                         shift = 3.0f / (c * c);
                         alpha = -0.5f * c * c * c;
                         tc_fence_before();

@@ -14,22 +14,24 @@
 
 namespace smx {
 
-// a1 + the Gershgorin bracket of a9 in one pass: one CTA of 64 threads per
-// block column j of the input pattern, eight groups of eight lanes, group g
-// taking the column's blocks k = k0 + g, k0 + g + 8, ... and lane q0 of a group
-// the block's columns q0, q0 + 8, ...  Per (block, column): the values are
-// checked for finiteness and copied to FP32, their sum of squares and of
-// absolute values taken; the block's Frobenius norm (squares summed over its
-// columns in a fixed tree over the group) decides whether it is kept (diagonal
-// blocks always), against keep_prev when given.  The absolute column sums of
-// the kept blocks go into per-group accumulators in shared memory (each lane
-// owns its entries), then are summed over the groups in order: with the
-// diagonal block's diagonal d_q, column q's Gershgorin interval is
-// [d_q - r_q, d_q + r_q], r_q = sum - |d_q| (H symmetric: column sums are row
-// sums).  The column's minimum and maximum reach the bracket through atomic
-// maxima of order-preserving integer images (independent of the order of the
-// CTAs), and the last CTA writes the bracket and its midpoint.
-constexpr int kFilterThreads = 64;
+// a1 + the Gershgorin bracket of a9 in one pass: one CTA per block column j of
+// the input pattern, G groups of eight lanes (G = blockDim / 8).  The column's
+// block rows, block sizes and value offsets are first staged in shared memory
+// (one round of dependent loads for the whole column); then group g takes the
+// blocks k0 + g, k0 + g + G, ... and lane q0 of a group the block's columns q0,
+// q0 + 8, ...  Per (block, column): the values are checked for finiteness and
+// copied to FP32, their sum of squares and of absolute values taken; the
+// block's Frobenius norm (squares summed over its columns in a fixed tree over
+// the group) decides whether it is kept (diagonal blocks always), against
+// keep_prev when given.  The absolute column sums of the kept blocks go into
+// per-group accumulators in shared memory (each lane owns its entries), then
+// are summed over the groups in order: with the diagonal block's diagonal d_q,
+// column q's Gershgorin interval is [d_q - r_q, d_q + r_q], r_q = sum - |d_q|
+// (H symmetric: column sums are row sums).  The column's minimum and maximum
+// reach the bracket through atomic maxima of order-preserving integer images
+// (independent of the order of the CTAs), and the last CTA writes the bracket
+// and its midpoint.
+constexpr int kFilterGroups = 8;
 
 // Order-preserving image of a double in the unsigned integers: x < y <=> enc(x) < enc(y)
 // for non-NaN x, y, and enc(x) > 0 for every x, so 0 is below every value.
@@ -42,35 +44,50 @@ __device__ __forceinline__ double ord_dec(unsigned long long e) {
     return __longlong_as_double(static_cast<long long>(b));
 }
 
-__global__ void __launch_bounds__(kFilterThreads) k_filter(const double* __restrict__ H, const int64_t* __restrict__ col_ptr,
-                                                           const int32_t* __restrict__ row_idx,
-                                                           const int64_t* __restrict__ voff,
-                                                           const int32_t* __restrict__ bsize, int bmax, double eps,
-                                                           uint8_t* __restrict__ keep, const uint8_t* __restrict__ keep_prev,
-                                                           float* __restrict__ H32, DevScalars* sc) {
-    extern __shared__ double fsm[];  // cs[8][bmax] kept column sums, ca[8][bmax] this block's, dg[bmax], mm[2][2]
+__global__ void __launch_bounds__(8 * kFilterGroups) k_filter(const double* __restrict__ H, const int64_t* __restrict__ col_ptr,
+                                                              const int32_t* __restrict__ row_idx,
+                                                              const int64_t* __restrict__ voff,
+                                                              const int32_t* __restrict__ bsize, int bmax, int max_col_blocks,
+                                                              double eps, uint8_t* __restrict__ keep,
+                                                              const uint8_t* __restrict__ keep_prev, float* __restrict__ H32,
+                                                              DevScalars* sc) {
+    // cs[G][bmax] kept column sums, ca[G][bmax] this block's, dg[bmax]; the column's block
+    // offsets, rows and sizes
+    extern __shared__ double fsm[];
     __shared__ bool last_s;
+    const int G = blockDim.x >> 3, nt = blockDim.x;
     double* cs = fsm;
-    double* ca = cs + 8 * bmax;
-    double* dg = ca + 8 * bmax;
+    double* ca = cs + G * bmax;
+    double* dg = ca + G * bmax;
+    int64_t* mvo = reinterpret_cast<int64_t*>(dg + bmax);
+    int* mr = reinterpret_cast<int*>(mvo + max_col_blocks);
+    int* mbr = mr + max_col_blocks;
     const int j = blockIdx.x, tid = threadIdx.x, g = tid >> 3, q0 = tid & 7;
     const int bc = bsize[j];
     const int64_t k0 = col_ptr[j], k1 = col_ptr[j + 1];
+    const int nk = static_cast<int>(k1 - k0);
+    for (int i = tid; i < nk; i += nt) {
+        const int r = row_idx[k0 + i];
+        mr[i] = r;
+        mvo[i] = voff[k0 + i];
+        mbr[i] = bsize[r];
+    }
     const unsigned gmask = 0xffu << (tid & 24);  // this group's lanes (groups differ in their block counts)
     // keep decisions: sum of squares in FP32 unless it lies within its rounding bound of eps^2
     // (then again in FP64, as the oracle takes it); eps <= 0 keeps every block
     const bool keep_all = !(eps > 0.0);
     const float eps2f = keep_all ? 0.0f : d2f_rn(eps * eps);
     const bool fp32_ok = eps2f >= 1e-30f;  // far from FP32 underflow
-    for (int i = tid; i < 8 * bmax; i += kFilterThreads) cs[i] = 0.0;
-    for (int q = tid; q < bc; q += kFilterThreads) dg[q] = 0.0;
+    for (int i = tid; i < G * bmax; i += nt) cs[i] = 0.0;
+    for (int q = tid; q < bc; q += nt) dg[q] = 0.0;
     __syncthreads();
     bool finite = true;
-    for (int64_t k = k0 + g; k < k1; k += 8) {  // the group is uniform
-        const int r = row_idx[k];
-        const int br = bsize[r];
-        const double* blk = H + voff[k];
-        float* blk32 = H32 + voff[k];
+    for (int i = g; i < nk; i += G) {  // the group is uniform
+        const int64_t k = k0 + i;
+        const int r = mr[i];
+        const int br = mbr[i];
+        const double* blk = H + mvo[i];
+        float* blk32 = H32 + mvo[i];
         float ss = 0.0f;
         for (int q = q0; q < bc; q += 8) {
             const double* col = blk + static_cast<int64_t>(q) * br;
@@ -126,9 +143,9 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(const double* __restr
     __syncthreads();
     // column q: the kept blocks' sums over the groups in order, then its interval
     double lo = INFINITY, hi = -INFINITY;
-    for (int q = tid; q < bc; q += kFilterThreads) {
+    for (int q = tid; q < bc; q += nt) {
         double c_ = 0.0;
-        for (int gg = 0; gg < 8; ++gg) c_ += cs[gg * bmax + q];
+        for (int gg = 0; gg < G; ++gg) c_ += cs[gg * bmax + q];
         const double d = dg[q], rad = c_ - fabs(d);
         lo = fmin(lo, d - rad);
         hi = fmax(hi, d + rad);
@@ -156,25 +173,32 @@ __global__ void __launch_bounds__(kFilterThreads) k_filter(const double* __restr
 }
 
 cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
-                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep,
-                                     const uint8_t* keep_prev, float* H32, DevScalars* sc, cudaStream_t st) {
+                                     const int32_t* bsize, int n_cols, int bmax, int max_col_blocks, double eps,
+                                     uint8_t* keep, const uint8_t* keep_prev, float* H32, DevScalars* sc, cudaStream_t st) {
     if (n_cols <= 0) return cudaSuccess;
-    const size_t smem = sizeof(double) * static_cast<size_t>(17) * bmax;
+    // as many groups as fit 48 KB of column sums next to the staged block information
+    const size_t meta = static_cast<size_t>(max_col_blocks) * (sizeof(int64_t) + 2 * sizeof(int));
+    int groups = kFilterGroups;
+    while (groups > 1 && sizeof(double) * static_cast<size_t>(2 * groups + 1) * bmax + meta > (48u << 10)) groups >>= 1;
+    const size_t smem = sizeof(double) * static_cast<size_t>(2 * groups + 1) * bmax + meta;
     if (smem > (48u << 10)) {
         cudaError_t e = cudaFuncSetAttribute(k_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
-    k_filter<<<n_cols, kFilterThreads, smem, st>>>(H, col_ptr, row_idx, voff, bsize, bmax, eps, keep, keep_prev, H32, sc);
+    k_filter<<<n_cols, 8 * groups, smem, st>>>(H, col_ptr, row_idx, voff, bsize, bmax, max_col_blocks, eps, keep, keep_prev,
+                                               H32, sc);
     return cudaGetLastError();
 }
 
 // The end of both gather forms: the per-warp row statistics (Gershgorin maximum
 // m and the feature sums of this warp's rows) reduced over the 8 warps in
 // order, the bound b_j (Gershgorin, or the learned model's), the features and
-// predictions.  All 256 threads call it.
-__device__ void gather_finish(const SubDesc& s, double m, float f2, float da, float ds, float dq, float rs, float dm,
-                              float rm, bool fp32_rows, double* __restrict__ bound, const GatherExtras& ex) {
-    __shared__ double warp_max_s[8];
+// predictions.  All 256 threads call it; the FP64 scalar work is thread 0's
+// (on every thread it would queue eight warps on the narrow FP64 pipe).
+template <class R>
+__device__ void gather_finish(const SubDesc& s, R m, float f2, float da, float ds, float dq, float rs, float dm,
+                              float rm, double* __restrict__ bound, const GatherExtras& ex) {
+    __shared__ R warp_max_s[8];
     __shared__ float stat_s[8][7];  // per warp: F2, Da, Ds, Dq, Rs (sums), Dm, Rm (maxima)
     __shared__ float x_s[kModelFeatures], h1_s[kModelHidden], y_s[2][2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -189,12 +213,12 @@ __device__ void gather_finish(const SubDesc& s, double m, float f2, float da, fl
         stat_s[warp][6] = rm;
     }
     __syncthreads();
-    double g = 0.0;
-    for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
-    const double graw = g;
-    // in FP32 the row sums carry a relative error below n 2^-24, covered by the 1e-5 margin
-    if (fp32_rows) g *= 1.0 + 1e-5;
-    if (!(g > 0.0)) g = 1.0;
+    // G = the largest row sum (the maximum is exact in the staging type)
+    auto gmax = [&]() -> double {
+        R g = R(0);
+        for (int w = 0; w < 8; ++w) g = fmax(g, warp_max_s[w]);
+        return static_cast<double>(g);
+    };
     if (ex.feat || ex.params) {
         if (tid == 0) {
             float F2 = 0.f, Da = 0.f, Ds = 0.f, Dq = 0.f, Rs = 0.f, Dm = 0.f, Rm = 0.f;
@@ -207,7 +231,7 @@ __device__ void gather_finish(const SubDesc& s, double m, float f2, float da, fl
                 Dm = fmaxf(Dm, stat_s[w][5]);
                 Rm = fmaxf(Rm, stat_s[w][6]);
             }
-            const float n = static_cast<float>(s.n), G = static_cast<float>(graw);
+            const float n = static_cast<float>(s.n), G = static_cast<float>(gmax());
             const float ig = G > 0.f ? 1.f / G : 0.f, mean = Ds / n;
             x_s[0] = sqrtf(F2 / n) * ig;
             x_s[1] = Dm * ig;
@@ -223,11 +247,10 @@ __device__ void gather_finish(const SubDesc& s, double m, float f2, float da, fl
         }
         __syncthreads();
     }
-    double b = g;
-    if (ex.params) {
+    const float* p = ex.params;
+    auto w16 = [](float v) { return __half2float(__float2half_rn(v)); };
+    if (p) {
         // the network, weights rounded to FP16 (threads 0..63: one hidden unit each)
-        const float* p = ex.params;
-        auto w16 = [](float v) { return __half2float(__float2half_rn(v)); };
         if (tid < kModelHidden) {
             float acc = w16(p[kOffB1 + tid]);
             for (int k = 0; k < kModelFeatures; ++k) acc = fmaf(w16(p[tid * kModelFeatures + k]), x_s[k], acc);
@@ -250,15 +273,22 @@ __device__ void gather_finish(const SubDesc& s, double m, float f2, float da, fl
             }
         }
         __syncthreads();
-        const float y0 = (y_s[0][0] + y_s[1][0]) + w16(p[kOffB3]);
-        const float y1 = (y_s[0][1] + y_s[1][1]) + w16(p[kOffB3 + 1]);
-        if (tid == 0 && ex.pred) {
-            ex.pred[2 * static_cast<int64_t>(blockIdx.x)] = y0;
-            ex.pred[2 * static_cast<int64_t>(blockIdx.x) + 1] = y1;
-        }
-        b = g * fmin(fmax(static_cast<double>(y0), 0.02), 1.0) * (1.0 + ex.margin) / 1.2;
     }
     if (tid == 0) {
+        double g = gmax();
+        // in FP32 the row sums carry a relative error below n 2^-24, covered by the 1e-5 margin
+        if (sizeof(R) == 4) g *= 1.0 + 1e-5;
+        if (!(g > 0.0)) g = 1.0;
+        double b = g;
+        if (p) {
+            const float y0 = (y_s[0][0] + y_s[1][0]) + w16(p[kOffB3]);
+            const float y1 = (y_s[0][1] + y_s[1][1]) + w16(p[kOffB3 + 1]);
+            if (ex.pred) {
+                ex.pred[2 * static_cast<int64_t>(blockIdx.x)] = y0;
+                ex.pred[2 * static_cast<int64_t>(blockIdx.x) + 1] = y1;
+            }
+            b = g * fmin(fmax(static_cast<double>(y0), 0.02), 1.0) * (1.0 + ex.margin) / 1.2;
+        }
         bound[blockIdx.x] = b;
         if (ex.gersh) ex.gersh[blockIdx.x] = g;
     }
@@ -401,7 +431,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(co
         }
         __syncwarp();
     }
-    gather_finish(s, static_cast<double>(m), f2, da, ds, dq, rs, dm, rm, sizeof(R) == 4, bound, ex);
+    gather_finish<R>(s, m, f2, da, ds, dq, rs, dm, rm, bound, ex);
 }
 
 // Staged form of the same gather, for patterns whose block rows fit a per-warp
@@ -426,8 +456,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(co
 constexpr int kStagedMaxBlocks = 64;
 constexpr size_t kStagedSmemLimit = 100u << 10;  // at least two CTAs per SM
 constexpr int kStagedBatch = 4;  // lane-steps of 32 columns whose loads are issued together
+constexpr int kPairBatch = 2;    // uniform 6 x 6 blocks: lane-steps of 32 pairs whose loads are issued together
 
-template <class R>
+template <class R> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
+// BS = 6: every block is 6 x 6 (the water workloads): a block row is taken as pairs of
+// consecutive elements (float2 / double2 loads and stores), six rows per pair of columns;
+// BS = 0: any block sizes, one element per lane and row group of up to eight rows.
+template <class R, int BS>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_gather_staged(const SubDesc* __restrict__ subs, PatternView pv,
                                                        const R* __restrict__ H, double mu_d, R* __restrict__ T,
                                                        double* __restrict__ bound, int nblk_max, int stage_elems,
@@ -454,13 +492,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_gather_staged(c
     for (int i = tid; i < nb * nb; i += blockDim.x) map[i] = -1;
     if (tid == 0) ls[nb] = s.n;
     __syncthreads();
-    for (int y = tid; y < s.n; y += blockDim.x) {
-        int lo = 0, hi = nb - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (ls[mid] <= y) lo = mid; else hi = mid - 1;
+    if constexpr (BS == 0) {
+        for (int y = tid; y < s.n; y += blockDim.x) {
+            int lo = 0, hi = nb - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ls[mid] <= y) lo = mid; else hi = mid - 1;
+            }
+            cinfo[y] = (lo << 16) | ((ls[lo + 1] - ls[lo]) << 8) | (y - ls[lo]);
         }
-        cinfo[y] = (lo << 16) | ((ls[lo + 1] - ls[lo]) << 8) | (y - ls[lo]);
     }
     for (int a = warp; a < nb; a += 8) {
         for (int64_t k = kcol[2 * a] + lane; k < kcol[2 * a + 1]; k += 32) {
@@ -484,6 +524,75 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_gather_staged(c
         const int64_t* mrow = map + a * nb;
         if (lane == 0) bulk_wait_read_all();  // the buffer's previous bulk copy has read it
         __syncwarp();
+        if constexpr (BS == 6) {
+            // pair unit t of a row: tile c = t / 3, columns 6c + p2, p2 + 1 (p2 = 2 (t mod 3)); tile
+            // (a, c) is H's block (R_j[c], R_j[a]) holding the 6 x 6 tile row-major, so row q of
+            // the pair is at vo + 6q + p2; pairs past the 3 nb of data are the zero padding
+            using V2 = typename Pair<R>::type;
+            const int units = ld >> 1, uvalid = 3 * nb;
+            R acc[6];
+            float sq[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                acc[q] = R(0);
+                sq[q] = 0.f;
+            }
+            for (int t0 = 0; t0 < units; t0 += 32 * kPairBatch) {
+                V2 v[kPairBatch][6];
+#pragma unroll
+                for (int i = 0; i < kPairBatch; ++i) {
+                    const int t = t0 + lane + 32 * i;
+                    const int c = t / 3, p2 = 2 * (t - 3 * c);
+                    const int64_t vo = t < uvalid ? mrow[c] : -1;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        v[i][q].x = R(0);
+                        v[i][q].y = R(0);
+                        if (vo >= 0) v[i][q] = *reinterpret_cast<const V2*>(H + vo + 6 * q + p2);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < kPairBatch; ++i) {
+                    const int t = t0 + lane + 32 * i;
+                    if (t >= units) break;
+                    const int c = t / 3, p2 = 2 * (t - 3 * c);
+                    const bool dtile = c == a;  // the diagonal tile of block row a
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        V2 w = v[i][q];
+                        if (dtile && p2 == (q & ~1)) {
+                            if (q & 1) w.y -= mu;
+                            else w.x -= mu;
+                        }
+                        *reinterpret_cast<V2*>(stage + q * ld + 2 * t) = w;
+                        acc[q] += fabs(w.x) + fabs(w.y);
+                        sq[q] = fmaf(static_cast<float>(w.x), static_cast<float>(w.x), sq[q]);
+                        sq[q] = fmaf(static_cast<float>(w.y), static_cast<float>(w.y), sq[q]);
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                R a_ = acc[q];
+                float s_ = sq[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a_ += __shfl_xor_sync(0xffffffffu, a_, o);
+                    s_ += __shfl_xor_sync(0xffffffffu, s_, o);
+                }
+                const float d = static_cast<float>(stage[q * ld + x0 + q]);  // the diagonal entry of row x0 + q
+                m = fmax(m, a_);
+                const float ad = fabsf(d), rr = static_cast<float>(a_) - ad;
+                f2 += s_;
+                da += ad;
+                ds += d;
+                dq = fmaf(d, d, dq);
+                rs += rr;
+                dm = fmaxf(dm, ad);
+                rm = fmaxf(rm, rr);
+            }
+        } else
         for (int q0 = 0; q0 < ba; q0 += kGatherRows) {
             const int nq = min(kGatherRows, ba - q0);
             R acc[kGatherRows];
@@ -563,12 +672,26 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_gather_staged(c
         }
     }
     if (lane == 0) bulk_wait_all();
-    gather_finish(s, static_cast<double>(m), f2, da, ds, dq, rs, dm, rm, sizeof(R) == 4, bound, ex);
+    gather_finish<R>(s, m, f2, da, ds, dq, rs, dm, rm, bound, ex);
+}
+
+template <class R, int BS>
+static cudaError_t launch_staged(const SubDesc* subs, int n_subs, int max_nblk, int stage_elems, size_t smem,
+                                 const PatternView& pv, const R* H, double mu, R* T, double* bound, const GatherExtras& ex,
+                                 cudaStream_t st) {
+    if (smem > (48u << 10)) {
+        cudaError_t e = cudaFuncSetAttribute(k_gather_staged<R, BS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    k_gather_staged<R, BS><<<n_subs, 256, smem, st>>>(subs, pv, H, mu, T, bound, max_nblk, stage_elems, ex);
+    return cudaGetLastError();
 }
 
 template <class R>
-static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, const PatternView& pv,
-                                 const R* H, double mu, R* T, double* bound, const GatherExtras& ex, cudaStream_t st) {
+static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, bool uniform,
+                                 const PatternView& pv, const R* H, double mu, R* T, double* bound, const GatherExtras& ex,
+                                 cudaStream_t st) {
     if (n_subs <= 0) return cudaSuccess;
     // staged form: eight block-row buffers, the block map, R_j, local starts, column ranges, column info
     const int stage_elems = static_cast<int>((static_cast<int64_t>(bmax) * ((max_n + 3) / 4 * 4) + 31) / 32 * 32);
@@ -576,13 +699,9 @@ static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, 
                                (static_cast<size_t>(max_nblk) * max_nblk + 2 * max_nblk) * sizeof(int64_t) +
                                (static_cast<size_t>(2 * max_nblk + 1) + static_cast<size_t>(max_n)) * sizeof(int);
     if (max_nblk <= kStagedMaxBlocks && staged_smem <= kStagedSmemLimit) {
-        if (staged_smem > (48u << 10)) {
-            cudaError_t e = cudaFuncSetAttribute(k_gather_staged<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(staged_smem));
-            if (e != cudaSuccess) return e;
-        }
-        k_gather_staged<R><<<n_subs, 256, staged_smem, st>>>(subs, pv, H, mu, T, bound, max_nblk, stage_elems, ex);
-        return cudaGetLastError();
+        if (uniform && bmax == 6)
+            return launch_staged<R, 6>(subs, n_subs, max_nblk, stage_elems, staged_smem, pv, H, mu, T, bound, ex, st);
+        return launch_staged<R, 0>(subs, n_subs, max_nblk, stage_elems, staged_smem, pv, H, mu, T, bound, ex, st);
     }
     // per-warp block tables, R_j, local starts and the local block of every column
     const size_t smem = static_cast<size_t>(8) * max_nblk * sizeof(int64_t) +
@@ -595,16 +714,16 @@ static cudaError_t launch_gather(const SubDesc* subs, int n_subs, int max_nblk, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, const PatternView& pv,
-                                const double* H, double mu, double* T, double* bound, const GatherExtras& ex,
-                                cudaStream_t st) {
-    return launch_gather<double>(subs, n_subs, max_nblk, max_n, bmax, pv, H, mu, T, bound, ex, st);
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, bool uniform,
+                                const PatternView& pv, const double* H, double mu, double* T, double* bound,
+                                const GatherExtras& ex, cudaStream_t st) {
+    return launch_gather<double>(subs, n_subs, max_nblk, max_n, bmax, uniform, pv, H, mu, T, bound, ex, st);
 }
 
-cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, const PatternView& pv,
-                                    const float* H32, double mu, float* T32, double* bound, const GatherExtras& ex,
-                                    cudaStream_t st) {
-    return launch_gather<float>(subs, n_subs, max_nblk, max_n, bmax, pv, H32, mu, T32, bound, ex, st);
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, bool uniform,
+                                    const PatternView& pv, const float* H32, double mu, float* T32, double* bound,
+                                    const GatherExtras& ex, cudaStream_t st) {
+    return launch_gather<float>(subs, n_subs, max_nblk, max_n, bmax, uniform, pv, H32, mu, T32, bound, ex, st);
 }
 
 // Deterministic sums of partial[0, n_cols) by one block (each thread adds a fixed

@@ -68,6 +68,8 @@ struct smx_ctx {
     // input pattern
     int32_t B = 0;
     int32_t bmax = 0;  // largest block size
+    bool bsize_uniform = false;  // every block has size bmax
+    int32_t max_col_blocks = 0;  // most blocks in one column of the input pattern
     int64_t N = 0, nnzb = 0, n_values = 0;
     std::vector<int32_t> bs, row_idx;
     std::vector<int64_t> col_ptr, voff, row_start;
@@ -263,7 +265,7 @@ static smx_status launch_filter(smx_ctx* c) {
     NvtxRange nv("smx filter");
     c->filter_compared = c->analysed && c->eps > 0.0;  // without a threshold every block is kept
     SMX_CUDA(launch_filter_gershgorin(dp<double>(c->d_H), dp<int64_t>(c->d_col_ptr), dp<int32_t>(c->d_row_idx),
-                                      dp<int64_t>(c->d_voff), dp<int32_t>(c->d_bs), c->B, c->bmax, c->eps,
+                                      dp<int64_t>(c->d_voff), dp<int32_t>(c->d_bs), c->B, c->bmax, c->max_col_blocks, c->eps,
                                       dp<uint8_t>(c->d_keep), c->filter_compared ? dp<uint8_t>(c->d_keep_prev) : nullptr,
                                       dp<float>(c->d_H32), scalars(c), c->stream));
     c->kernel_launches += 1;
@@ -470,10 +472,10 @@ static smx_status gather_chunk(smx_ctx* c, int j0, int m, double mu, const Gathe
     const PatternView pv = pattern_view(c);
     SubDesc* subs = dp<SubDesc>(c->d_subs);
     if (c->precision == SMX_FP64) {
-        SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, c->max_n, c->bmax, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
+        SMX_CUDA(launch_gather_bound(subs + j0, m, c->max_nblk, c->max_n, c->bmax, c->bsize_uniform, pv, dp<double>(c->d_H), mu, dp<double>(c->d_T),
                                      dp<double>(c->d_bound) + j0, ex, c->stream));
     } else {
-        SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, c->max_n, c->bmax, pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
+        SMX_CUDA(launch_gather_bound_f32(subs + j0, m, c->max_nblk, c->max_n, c->bmax, c->bsize_uniform, pv, dp<float>(c->d_H32), mu, dp<float>(c->d_T),
                                          dp<double>(c->d_bound) + j0, ex, c->stream));
     }
     c->kernel_launches += 1;
@@ -502,9 +504,9 @@ static smx_status nonorth_setup(smx_ctx* c) {
     const PatternView pv = pattern_view(c);
     SubDesc* subs = dp<SubDesc>(c->d_subs) + j0;
     GatherExtras ex;
-    SMX_CUDA(launch_gather_bound(subs, m, c->max_nblk, c->max_n, c->bmax, pv, dp<double>(c->d_S), 0.0, dp<double>(c->d_Lc),
+    SMX_CUDA(launch_gather_bound(subs, m, c->max_nblk, c->max_n, c->bmax, c->bsize_uniform, pv, dp<double>(c->d_S), 0.0, dp<double>(c->d_Lc),
                                  dp<double>(c->d_bound) + j0, ex, st));
-    SMX_CUDA(launch_gather_bound(subs, m, c->max_nblk, c->max_n, c->bmax, pv, dp<double>(c->d_H), 0.0, dp<double>(c->d_Mc),
+    SMX_CUDA(launch_gather_bound(subs, m, c->max_nblk, c->max_n, c->bmax, c->bsize_uniform, pv, dp<double>(c->d_H), 0.0, dp<double>(c->d_Mc),
                                  dp<double>(c->d_gersh) + j0, ex, st));
     NonorthSetupArgs a;
     a.subs = subs;
@@ -757,6 +759,7 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
     c->B = n_block_cols;
     c->bs.assign(block_size, block_size + n_block_cols);
     c->bmax = *std::max_element(c->bs.begin(), c->bs.end());
+    c->bsize_uniform = *std::min_element(c->bs.begin(), c->bs.end()) == c->bmax;
     c->col_ptr.assign(col_ptr, col_ptr + n_block_cols + 1);
     c->nnzb = col_ptr[n_block_cols];
     c->row_idx.assign(row_idx, row_idx + c->nnzb);
@@ -768,6 +771,8 @@ smx_status smx_create(smx_ctx** out, int32_t n_block_cols, const int32_t* block_
         for (int64_t k = col_ptr[j]; k < col_ptr[j + 1]; ++k)
             c->voff[k + 1] = c->voff[k] + static_cast<int64_t>(block_size[row_idx[k]]) * block_size[j];
     c->n_values = c->voff[c->nnzb];
+    for (int32_t j = 0; j < n_block_cols; ++j)
+        c->max_col_blocks = std::max(c->max_col_blocks, static_cast<int32_t>(col_ptr[j + 1] - col_ptr[j]));
     smx_status s = SMX_OK;
     auto fail = [&](smx_status e) {
         smx_destroy(c);

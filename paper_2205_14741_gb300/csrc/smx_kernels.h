@@ -38,9 +38,10 @@ cudaError_t launch_bisect_step(DevScalars* sc, double n_e, double tol, int max_s
 // sc->changed = 1 when a flag differs from it.  The Gershgorin bracket of the
 // filtered H (minimum and maximum over its columns' intervals) and its
 // midpoint go to sc->br_lo, br_hi, mu0.
+// max_col_blocks: the largest number of blocks in a column of the input pattern.
 cudaError_t launch_filter_gershgorin(const double* H, const int64_t* col_ptr, const int32_t* row_idx, const int64_t* voff,
-                                     const int32_t* bsize, int n_cols, int bmax, double eps, uint8_t* keep,
-                                     const uint8_t* keep_prev, float* H32, DevScalars* sc, cudaStream_t st);
+                                     const int32_t* bsize, int n_cols, int bmax, int max_col_blocks, double eps,
+                                     uint8_t* keep, const uint8_t* keep_prev, float* H32, DevScalars* sc, cudaStream_t st);
 
 // Optional outputs of the gather, per submatrix (pointers offset like subs; null = not wanted).
 struct GatherExtras {
@@ -57,14 +58,15 @@ struct GatherExtras {
 // a3 + a4: T_j = H[R_j, R_j] - mu I into the FP64 staging buffer, then the
 // Gershgorin bound b_j = max row abs-sum of T_j (>= spectral radius), or the
 // learned bound (extras.params).
-cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, const PatternView& pv,
-                                const double* H, double mu, double* T, double* bound, const GatherExtras& ex,
-                                cudaStream_t st);
+// bmax: the largest block size; uniform: every block has that size.
+cudaError_t launch_gather_bound(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, bool uniform,
+                                const PatternView& pv, const double* H, double mu, double* T, double* bound,
+                                const GatherExtras& ex, cudaStream_t st);
 // The same in FP32 (tensor-core path): T32 from the FP32 copy of H; the bound
 // is enlarged by 1e-5 relative to cover FP32 summation.
-cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, const PatternView& pv,
-                                    const float* H32, double mu, float* T32, double* bound, const GatherExtras& ex,
-                                    cudaStream_t st);
+cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, bool uniform,
+                                    const PatternView& pv, const float* H32, double mu, float* T32, double* bound,
+                                    const GatherExtras& ex, cudaStream_t st);
 
 // a8 (FP64 form): deterministic sums of the per-column partials ->
 // sc->trace = trace(D), sc->energy = trace(D H).
