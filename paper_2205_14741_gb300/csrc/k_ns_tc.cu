@@ -368,23 +368,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     // queue twelve warps on the narrow FP64 pipe): 1 / b_j and the predicted smallest
     // |eigenvalue| of X0 = (T_j - mu I) / b_j (negative when there is no prediction)
     __shared__ float inv_b_s, dhat_s;
-    if (tid == 0) next_s = atomicAdd(a.work_counter, 1);
+    // thread 0 claims job `job` and, one ahead, its successor: prefetches the successor's staged
+    // T_j into L2 and forms its scalars from the gather's b_j (a job rewrites its own b_j later)
+    float next_inv_b = 0.0f, next_dhat = -1.0f;
+    auto claim_next = [&]() {
+        next_s = atomicAdd(a.work_counter, 1);
+        if (next_s < a.n_subs) {
+            const int jj = a.order[next_s];
+            const SubDesc sn = a.subs[jj];
+            const double b = a.bound[jj];
+            const float pr = a.pred ? a.pred[2 * jj + 1] : -1.0f;
+            const double g = a.gersh[jj];
+            const uint64_t bytes = static_cast<uint64_t>(sn.n) * sn.ld * sizeof(float);
+            const uint32_t len = static_cast<uint32_t>(bytes < (4u << 20) ? bytes : (4u << 20)) & ~15u;
+            if (len) prefetch_l2_bulk(a.T + sn.t_off, len);
+            next_inv_b = static_cast<float>(1.0 / b);
+            next_dhat = a.pred ? pr * static_cast<float>(g / b) : -1.0f;
+        }
+    };
+    if (tid == 0) claim_next();
     for (;;) {
         if (tid == 0) {
             job_s = next_s;
-            next_s = atomicAdd(a.work_counter, 1);
-            if (next_s < a.n_subs) {
-                const SubDesc sn = a.subs[a.order[next_s]];
-                const uint64_t bytes = static_cast<uint64_t>(sn.n) * sn.ld * sizeof(float);
-                const uint32_t len = static_cast<uint32_t>(bytes < (4u << 20) ? bytes : (4u << 20)) & ~15u;
-                if (len) prefetch_l2_bulk(a.T + sn.t_off, len);
-            }
-            if (job_s < a.n_subs) {
-                const int jj = a.order[job_s];
-                const double b = a.bound[jj];  // the gather's b_j (this job rewrites it later)
-                inv_b_s = static_cast<float>(1.0 / b);
-                dhat_s = a.pred ? a.pred[2 * jj + 1] * static_cast<float>(a.gersh[jj] / b) : -1.0f;
-            }
+            inv_b_s = next_inv_b;
+            dhat_s = next_dhat;
+            claim_next();
         }
         __syncthreads();
         const int job = job_s;

@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_gather_bound(co
 constexpr int kStagedMaxBlocks = 64;
 constexpr size_t kStagedSmemLimit = 100u << 10;  // at least two CTAs per SM
 constexpr int kStagedBatch = 4;  // lane-steps of 32 columns whose loads are issued together
-constexpr int kPairBatch = 2;    // uniform 6 x 6 blocks: lane-steps of 32 pairs whose loads are issued together
+constexpr int kPairBatch = 1;    // uniform 6 x 6 blocks: lane-steps of 32 pairs whose loads are issued together
 
 template <class R> struct Pair;
 template <> struct Pair<float> { using type = float2; };
@@ -466,7 +466,7 @@ template <> struct Pair<double> { using type = double2; };
 // consecutive elements (float2 / double2 loads and stores), six rows per pair of columns;
 // BS = 0: any block sizes, one element per lane and row group of up to eight rows.
 template <class R, int BS>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_gather_staged(const SubDesc* __restrict__ subs, PatternView pv,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? (BS == 6 ? 4 : 3) : 2) k_gather_staged(const SubDesc* __restrict__ subs, PatternView pv,
                                                        const R* __restrict__ H, double mu_d, R* __restrict__ T,
                                                        double* __restrict__ bound, int nblk_max, int stage_elems,
                                                        GatherExtras ex) {
@@ -749,19 +749,22 @@ __device__ void sum_partials(const double2* partial, int n_cols, DevScalars* sc,
 //
 // The elements are taken in the order of D's own layout: the kept blocks
 // (R_j[a], j) of column j, each column-major b_a x b_j, so element e of the
-// packed column lies in block a = blk[e / b_j] (the blocks' packed starts are
-// ls[a] b_j) at e' = e - ls[a] b_j, row p = e' mod b_a of column q = e' / b_a.
-// Consecutive threads store consecutive D entries and read runs of b_a
-// consecutive saved values; each thread issues the loads of up to
-// kScatterBatch elements before their stores.
+// packed column lies in block a (the blocks' packed starts are ls[a] b_j) at
+// e' = e - ls[a] b_j, row p = e' mod b_a of column q = e' / b_a.  With uniform
+// b x b blocks (BS = b) a = e / b^2 and no tables are needed; otherwise block
+// a = blk[e / b_j] from shared-memory tables.  Consecutive threads store
+// consecutive D entries and read runs of b_a consecutive saved values; each
+// thread issues the loads of up to kScatterBatch elements before their stores.
 //
 // Arithmetic (GB300's FP64 pipe is narrow): an off-diagonal entry -x/2 is exact
-// in FP32 and widened on the integer pipes; a diagonal entry (1 - x)/2 is
-// formed in FP64.  The trace (diagonal entries) is summed in FP64; the energy
-// sum trace(D H) takes FP32 products of D and the FP32 copy of H, summed in
-// FP32 per thread and warp, then in FP64 over the warps and the columns.
+// in FP32 and widened on the integer pipes; the b_j diagonal entries (1 - x)/2
+// are formed in FP64 by the first b_j threads after the sweep (which skips
+// them), and only they add to the trace (FP64).  The energy sum trace(D H)
+// takes FP32 products of D and the FP32 copy of H, summed in FP32 per thread
+// and warp, then in FP64 over the warps and the columns.
 constexpr int kScatterBatch = 4;
 
+template <int BS>
 __global__ void __launch_bounds__(256) k_scatter_owner(const SubDesc* __restrict__ subs, PatternView pv,
                                                        const float* __restrict__ xown, const float* __restrict__ H32,
                                                        double* __restrict__ D, double2* __restrict__ partial, int n_cols,
@@ -775,68 +778,80 @@ __global__ void __launch_bounds__(256) k_scatter_owner(const SubDesc* __restrict
     const SubDesc s = subs[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nb = s.nblk, n = s.n, bj = s.bown;
-    int64_t* fvo = reinterpret_cast<int64_t*>(ssm);  // value offset of block (R_j[a], j)
-    int* ls = reinterpret_cast<int*>(fvo + nb);      // local starts, nb + 1 entries
-    int* blk = ls + nb + 1;                          // local block of every row of T_j
-    for (int a = tid; a < nb; a += blockDim.x) {
-        fvo[a] = pv.fvoff[s.fptr + a];
-        ls[a] = pv.lstart[s.fptr + a];
+    const int64_t* fvoff = pv.fvoff + s.fptr;
+    int64_t* fvo = reinterpret_cast<int64_t*>(ssm);  // generic form: value offset of block (R_j[a], j)
+    int* ls = reinterpret_cast<int*>(fvo + nb);      // ... local starts, nb + 1 entries
+    int* blk = ls + nb + 1;                          // ... local block of every row of T_j
+    if constexpr (BS == 0) {
+        for (int a = tid; a < nb; a += blockDim.x) {
+            fvo[a] = fvoff[a];
+            ls[a] = pv.lstart[s.fptr + a];
+        }
+        if (tid == 0) ls[nb] = n;
+        __syncthreads();
+        for (int a = warp; a < nb; a += 8)
+            for (int r = ls[a] + lane; r < ls[a + 1]; r += 32) blk[r] = a;
+        __syncthreads();
     }
-    if (tid == 0) ls[nb] = n;
-    __syncthreads();
-    for (int a = warp; a < nb; a += 8)
-        for (int r = ls[a] + lane; r < ls[a + 1]; r += 32) blk[r] = a;
-    __syncthreads();
     const float* x = xown + s.x_off;
-    double tr = 0.0;
     float en = 0.0f;
-    bool any_diag = false;
     const int total = n * bj;
     for (int e0 = tid; e0 < total; e0 += kScatterBatch * 256) {
         float xv[kScatterBatch], hv[kScatterBatch];
         int64_t off[kScatterBatch];
-        bool dg[kScatterBatch];
 #pragma unroll
         for (int i = 0; i < kScatterBatch; ++i) {
             const int e = e0 + i * 256;
             off[i] = -1;
-            dg[i] = false;
             xv[i] = 0.f;
             hv[i] = 0.f;
             if (e < total) {
-                const int a = blk[e / bj];
-                const int ba = ls[a + 1] - ls[a];
-                const int ep = e - ls[a] * bj;
-                const int q = ep / ba, row = ls[a] + (ep - q * ba);
-                off[i] = fvo[a] + ep;
-                dg[i] = row == s.own + q;
-                xv[i] = x[static_cast<int64_t>(q) * n + row];
-                hv[i] = H32[off[i]];
+                int a, ba, ep, row0;
+                if constexpr (BS > 0) {
+                    a = e / (BS * BS);
+                    ba = BS;
+                    ep = e - a * (BS * BS);
+                    row0 = BS * a;
+                } else {
+                    a = blk[e / bj];
+                    ba = ls[a + 1] - ls[a];
+                    ep = e - ls[a] * bj;
+                    row0 = ls[a];
+                }
+                const int q = ep / ba, row = row0 + (ep - q * ba);
+                if (row != s.own + q) {  // diagonal entries after the sweep
+                    off[i] = (BS > 0 ? fvoff[a] : fvo[a]) + ep;
+                    xv[i] = x[static_cast<int64_t>(q) * n + row];
+                    hv[i] = H32[off[i]];
+                }
             }
         }
 #pragma unroll
         for (int i = 0; i < kScatterBatch; ++i) {
-            if (off[i] < 0) break;
-            float d32;
-            if (dg[i]) {
-                const double d = 0.5 * (1.0 - f2d(xv[i]));
-                D[off[i]] = d;
-                tr += d;
-                any_diag = true;
-                d32 = d2f_rn(d);
-            } else {
-                d32 = -0.5f * xv[i];
-                D[off[i]] = f2d(d32);
-            }
+            if (off[i] < 0) continue;
+            const float d32 = -0.5f * xv[i];
+            D[off[i]] = f2d(d32);
             en = fmaf(d32, hv[i], en);
         }
     }
+    double tr = 0.0;
+    int a_own;
+    if constexpr (BS > 0) a_own = s.own / BS;
+    else a_own = blk[s.own];
+    const int64_t own_off = BS > 0 ? fvoff[a_own] : fvo[a_own];
+    for (int q = tid; q < bj; q += blockDim.x) {  // the diagonal entry of the owner block's column q
+        const int64_t off = own_off + static_cast<int64_t>(q) * bj + q;
+        const double d = 0.5 * (1.0 - f2d(x[static_cast<int64_t>(q) * n + s.own + q]));
+        D[off] = d;
+        tr += d;
+        en = fmaf(d2f_rn(d), H32[off], en);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) en += __shfl_xor_sync(0xffffffffu, en, o);
-    if (__any_sync(0xffffffffu, any_diag)) tr = warp_sum(tr);  // warps without diagonal entries add zero
+    if (warp * 32 < bj) tr = warp_sum(tr);  // only the warps holding diagonal entries (warp-uniform)
     if (lane == 0) {
-        tr_s[warp] = tr;
         en_s[warp] = en;
+        tr_s[warp] = tr;
     }
     __syncthreads();
     if (tid == 0) {
@@ -860,17 +875,21 @@ __global__ void __launch_bounds__(256) k_scatter_owner(const SubDesc* __restrict
     }
 }
 
-cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
-                                 const float* xown, const float* H32, double* D, double2* partial, int n_cols,
-                                 DevScalars* sc, cudaStream_t st, const int* skip) {
+cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, bool uniform,
+                                 const PatternView& pv, const float* xown, const float* H32, double* D, double2* partial,
+                                 int n_cols, DevScalars* sc, cudaStream_t st, const int* skip) {
     if (n_subs <= 0) return cudaSuccess;
+    if (uniform && bmax == 6) {
+        k_scatter_owner<6><<<n_subs, 256, 0, st>>>(subs, pv, xown, H32, D, partial, n_cols, sc, skip);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(int64_t) * static_cast<size_t>(max_nblk) +
                         sizeof(int) * (static_cast<size_t>(max_nblk) + 1 + static_cast<size_t>(max_n));
     if (smem > (48u << 10)) {
-        cudaError_t e = cudaFuncSetAttribute(k_scatter_owner, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        cudaError_t e = cudaFuncSetAttribute(k_scatter_owner<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
     }
-    k_scatter_owner<<<n_subs, 256, smem, st>>>(subs, pv, xown, H32, D, partial, n_cols, sc, skip);
+    k_scatter_owner<0><<<n_subs, 256, smem, st>>>(subs, pv, xown, H32, D, partial, n_cols, sc, skip);
     return cudaGetLastError();
 }
 

@@ -693,7 +693,7 @@ static smx_status build_at(smx_ctx* c, double mu, const double* mu_dev = nullptr
             }
             SMX_CUDA(cudaEventRecord(ns1, st));
             if (!finish) {
-                SMX_CUDA(launch_scatter_owner(subs + j0, m, c->max_nblk, c->max_n, pv, dp<float>(c->d_xown), dp<float>(c->d_H32),
+                SMX_CUDA(launch_scatter_owner(subs + j0, m, c->max_nblk, c->max_n, c->bmax, c->bsize_uniform, pv, dp<float>(c->d_xown), dp<float>(c->d_H32),
                                               dp<double>(c->d_D), dp<double2>(c->d_partial), B, sc, st, skip));
                 c->kernel_launches += 1;
             }

@@ -189,8 +189,8 @@ cudaError_t launch_ns_tc(const NsTcArgs& a, int precision, const CUtensorMap& tm
 // against the FP32 copy H32 of H, FP64 over warps and columns) partials; the
 // last block sums partial[0, n_cols) in a fixed order into sc->trace,
 // sc->energy and resets sc->ns_counter for the next Newton-Schulz launch.
-cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, int max_n, const PatternView& pv,
-                                 const float* xown, const float* H32, double* D, double2* partial, int n_cols,
+cudaError_t launch_scatter_owner(const SubDesc* subs, int n_subs, int max_nblk, int max_n, int bmax, bool uniform,
+                                 const PatternView& pv, const float* xown, const float* H32, double* D, double2* partial, int n_cols,
                                  DevScalars* sc, cudaStream_t st, const int* skip = nullptr);
 
 // ---------------------------------------------------------------------------
