@@ -364,35 +364,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
     // Jobs are claimed one ahead: while a submatrix iterates, its successor's staged
     // T_j is prefetched into L2 (the prologue then reads it from there).
     __shared__ int next_s;
-    // the job's scalars in FP32, formed once by thread 0 (FP64 arithmetic on every thread would
-    // queue twelve warps on the narrow FP64 pipe): 1 / b_j and the predicted smallest
-    // |eigenvalue| of X0 = (T_j - mu I) / b_j (negative when there is no prediction)
-    __shared__ float inv_b_s, dhat_s;
-    // thread 0 claims job `job` and, one ahead, its successor: prefetches the successor's staged
-    // T_j into L2 and forms its scalars from the gather's b_j (a job rewrites its own b_j later)
-    float next_inv_b = 0.0f, next_dhat = -1.0f;
+    __shared__ float rprev_s;  // the previous step's residual (rounding-floor stop)
+    // the job's scalars in FP32: 1 / b_j, the predicted smallest |eigenvalue| of
+    // X0 = (T_j - mu I) / b_j (negative when there is no prediction), and b_j / G_j; with b_j
+    // itself (FP64), which the job rescales by its a-posteriori factor
+    __shared__ float inv_b_s, dhat_s, bg_s;
+    __shared__ double b_s;
+    __shared__ float next_inv_b_s, next_dhat_s, next_bg_s;
+    __shared__ double next_b_s;
+    // Claims the successor of the current job: one atomic, its descriptors, a prefetch of its
+    // staged T_j into L2, and its scalars (FP32 divisions: FP64 division is slow on this GPU's
+    // FP64 pipe).  Run by one thread: thread 0 for the first job, then warp 11's first lane
+    // while the job's first product is multiplied, so that no CTA barrier waits for its
+    // memory round trips; the loop head takes the results from shared memory.
     auto claim_next = [&]() {
-        next_s = atomicAdd(a.work_counter, 1);
-        if (next_s < a.n_subs) {
-            const int jj = a.order[next_s];
+        const int nx = atomicAdd(a.work_counter, 1);
+        next_s = nx;
+        if (nx < a.n_subs) {
+            const int jj = a.order[nx];
             const SubDesc sn = a.subs[jj];
             const double b = a.bound[jj];
             const float pr = a.pred ? a.pred[2 * jj + 1] : -1.0f;
-            const double g = a.gersh[jj];
+            const float g = static_cast<float>(a.gersh[jj]);
             const uint64_t bytes = static_cast<uint64_t>(sn.n) * sn.ld * sizeof(float);
             const uint32_t len = static_cast<uint32_t>(bytes < (4u << 20) ? bytes : (4u << 20)) & ~15u;
             if (len) prefetch_l2_bulk(a.T + sn.t_off, len);
-            next_inv_b = static_cast<float>(1.0 / b);
-            next_dhat = a.pred ? pr * static_cast<float>(g / b) : -1.0f;
+            const float bf = static_cast<float>(b);
+            next_b_s = b;
+            next_inv_b_s = 1.0f / bf;
+            next_bg_s = bf / g;
+            next_dhat_s = a.pred ? pr * (g / bf) : -1.0f;
         }
     };
     if (tid == 0) claim_next();
+    __syncthreads();
     for (;;) {
         if (tid == 0) {
             job_s = next_s;
-            inv_b_s = next_inv_b;
-            dhat_s = next_dhat;
-            claim_next();
+            inv_b_s = next_inv_b_s;
+            dhat_s = next_dhat_s;
+            bg_s = next_bg_s;
+            b_s = next_b_s;
         }
         __syncthreads();
         const int job = job_s;
@@ -406,7 +418,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
         // lower end of the interval the scaled schedule assumes for the current iterate's
         // |eigenvalues| (1 = plain steps), and the factor a of the current step
         float lsch = 1.0f, acur = 1.0f;
-        float rprev = INFINITY;  // tid 0: the previous step's residual (rounding-floor stop)
 
         const int zx0 = slot_z + 0, zx1 = slot_z + 2, zy = slot_z + 4;
 
@@ -473,8 +484,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             }
             cp_async_wait<0>();
             fence_proxy_async_smem();
-            if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; rprev = INFINITY; }
+            if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; rprev_s = INFINITY; }
             __syncthreads();
+            if (warp == 11 && lane == 0) claim_next();  // while the first product runs
         } else {
             const float inv_b = inv_b_s;
             const float* t = a.T + s.t_off;
@@ -512,8 +524,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
             }
             fence_proxy_async_global();
-            if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; rprev = INFINITY; }
+            if (tid == 0) { conv_s = 0; bad_s = 0; plain_s = 0; rprev_s = INFINITY; }
             __syncthreads();
+            if (warp == 11 && lane == 0) claim_next();  // while the first product runs
         }
 
         // The factor c of the first step X1 = p(c X0), p(x) = x (3 - x^2) / 2, from the guaranteed
@@ -564,13 +577,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
             if (acur - 1.0f <= kStopSlack) conv_s = 1;
             else plain_s = 1;
         };
-        // tid 0, with the residual r = ||X^2 - I||_F of the current step: the stopping rule,
-        // or (single-pass forms) the rounding floor: r below a.stall_level and not half of
-        // the previous step's residual
-        auto check_stop = [&](double r) {
+        // one thread, with the residual r = ||X^2 - I||_F of the current step: the stopping
+        // rule, or (single-pass forms) the rounding floor: r below a.stall_level and not half
+        // of the previous step's residual.  FP32 throughout: FP64 arithmetic on the thread
+        // that decides would hold a warp of the next pass for microseconds.
+        auto check_stop = [&](float r) {
             if (!isfinite(r)) bad_s = 1;
-            else if (r <= a.tau || (r < a.stall_level && r > 0.5 * rprev)) converged();
-            rprev = static_cast<float>(r);
+            else if (r <= a.tau || (r < a.stall_level && r > 0.5f * rprev_s)) converged();
+            rprev_s = r;
         };
         int cur = 0, done = 0;
         if (resident) {
@@ -1021,18 +1035,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
                 const float smax = sqrtf(best * (1.0f + 1e-4f));  // margin for FP32 summation
                 const float scale = start_factor(smax);
-                if (tid == 0) {
-                    const double s0 = sqrt(static_cast<double>(rmax) * (1.0 + 1e-5));
-                    a.sq_ratio[j] = static_cast<float>(s0 * a.bound[j] / a.gersh[j]);
-                    a.bound[j] = a.bound[j] / static_cast<double>(scale);
+                if (tid == 0) {  // next-step feature sqrt(rmax) b_j / G_j, and b_j / c
+                    a.sq_ratio[j] = sqrtf(rmax * (1.0f + 1e-5f)) * bg_s;
+                    a.bound[j] = b_s * static_cast<double>(1.0f / scale);
                 }
                 return scale;
             };
             // convergence of this step from ||X^2 - I||_F (the residual partials of every warp)
             auto decide = [&]() {
-                double rr = 0.0;
+                float rr = 0.0f;
                 for (int w = 0; w < kThreads / 32; ++w) rr += resid_s2[w];
-                check_stop(sqrt(rr));
+                check_stop(sqrtf(rr));
             };
 
             if (mtiles == 1) {
@@ -1154,7 +1167,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                         issue_cyx(TB);
                         tc_commit(&mma_bar2);
                     }
-                    if (tid == 0 && it > 0) decide();
+                    if (warp == 8 && lane == 0 && it > 0) decide();  // a warp without corner chunks
                     mma_wait();   // Q_0
                     drain(0, TC, alpha, hi_off, true);
                     fence_proxy_async_smem();  // rows 0 .. 127 of the image (read by the next Z_0)
@@ -1291,10 +1304,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 }
                 fence_proxy_async_global();
                 if (tid == 0) {
-                    // feature of the next snapshot: the Gershgorin bound of A^2, over G
-                    const double s0 = sqrt(static_cast<double>(rmax) * (1.0 + 1e-5));
-                    a.sq_ratio[j] = static_cast<float>(s0 * a.bound[j] / a.gersh[j]);
-                    a.bound[j] = a.bound[j] / static_cast<double>(scale);  // effective scaling of X0'
+                    // feature of the next snapshot: the Gershgorin bound of A^2, over G; and the
+                    // effective scaling b_j / c of X0'
+                    a.sq_ratio[j] = sqrtf(rmax * (1.0f + 1e-5f)) * bg_s;
+                    a.bound[j] = b_s * static_cast<double>(1.0f / scale);
                 }
                 __syncthreads();
                 gemm(kpad, s.n, 2, zx, zy, zn, -0.5f * scale * scale * scale);  // X1 = -c^3/2 X0 (Z - 3/c^2 I)
@@ -1304,9 +1317,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 // Y = a (3/2 I - a^2/2 X^2) = alpha X^2 - alpha shift I: the scaled step X' = X Y
                 gemm(kpad, s.n, 1, zx, zx, zy, alpha, -alpha * shift);  // Y = 3/2 I - 1/2 X^2 when plain
                 if (tid == 0) {
-                    double r2 = 0.0;
+                    float r2 = 0.0f;
                     for (int w = 0; w < kEpiWarps; ++w) r2 += resid_s[w];
-                    check_stop(sqrt(r2));
+                    check_stop(sqrtf(r2));
                 }
                 gemm(kpad, s.n, 2, zx, zy, zn, 1.0f);  // X' = X Y
             }
