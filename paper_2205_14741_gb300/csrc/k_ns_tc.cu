@@ -950,25 +950,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 const float send = up ? v[0] : v[1], keep = up ? v[1] : v[0];
                 return keep + __shfl_xor_sync(0xffffffffu, send, 1);
             };
+            // No masks: the columns of Z past n are exactly zero, rows past n hold zeros (or, past
+            // kpad, finite values of an earlier job whose sums are not kept), and w is zero past n.
             auto scan = [&](uint32_t acc, const float* w) {
                 const int row = 32 * q + lane;
-                const float wr = (w && row < s.n) ? w[row] : 1.0f;
+                const float wr = w ? w[row] : 1.0f;
                 float sum = 0.0f;
 #pragma unroll 1
                 for (int c0 = 32 * part; c0 < kpad; c0 += 96) {
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + c0 + lane_off, raw);
                     tmem_wait_ld();
+                    if (w) {
+                        const float4* w4 = reinterpret_cast<const float4*>(w + c0);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int c = c0 + i;
-                        if (row < s.n && c < s.n) sum = fmaf(fabsf(__uint_as_float(raw[i])), w ? w[c] : 1.0f, sum);
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 wv = w4[i];
+                            sum = fmaf(fabsf(__uint_as_float(raw[4 * i])), wv.x, sum);
+                            sum = fmaf(fabsf(__uint_as_float(raw[4 * i + 1])), wv.y, sum);
+                            sum = fmaf(fabsf(__uint_as_float(raw[4 * i + 2])), wv.z, sum);
+                            sum = fmaf(fabsf(__uint_as_float(raw[4 * i + 3])), wv.w, sum);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) sum += fabsf(__uint_as_float(raw[i]));
                     }
                     if (c0 >= 128) {  // warp-uniform
                         float v[32];
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            v[i] = (row < s.n && c0 + i < s.n) ? fabsf(__uint_as_float(raw[i])) * wr : 0.0f;
+                        for (int i = 0; i < 32; ++i) v[i] = fabsf(__uint_as_float(raw[i])) * wr;
                         csum_s[q * 64 + (c0 - 128) + lane] = colsum32(v);
                     }
                 }
@@ -981,14 +991,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 const int row = 128 + 32 * q + lane;
                 float sum = 0.0f;
 #pragma unroll 1
-                for (int c0 = 0; c0 < wc; c0 += 32) {
+                for (int c0 = 0; c0 < wc; c0 += 32) {  // unmasked, as in scan
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + c0 + lane_off, raw);
                     tmem_wait_ld();
+                    if (w) {
+                        const float4* w4 = reinterpret_cast<const float4*>(w + 128 + c0);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const int c = 128 + c0 + i;
-                        if (row < s.n && c < s.n) sum = fmaf(fabsf(__uint_as_float(raw[i])), w ? w[c] : 1.0f, sum);
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 wv = w4[i];
+                            sum = fmaf(fabsf(__uint_as_float(raw[4 * i])), wv.x, sum);
+                            sum = fmaf(fabsf(__uint_as_float(raw[4 * i + 1])), wv.y, sum);
+                            sum = fmaf(fabsf(__uint_as_float(raw[4 * i + 2])), wv.z, sum);
+                            sum = fmaf(fabsf(__uint_as_float(raw[4 * i + 3])), wv.w, sum);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) sum += fabsf(__uint_as_float(raw[i]));
                     }
                 }
                 if (row < s.n) tbsum_s[row - 128] = sum;
@@ -1026,8 +1045,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 const float rmax = gather_max(rsum_s, nullptr);
                 float best = rmax;
                 if (a.use_model && rmax > 0.0f) {
-                    // one power step: w = the row sums (floored to stay positive)
-                    for (int r = tid; r < s.n; r += kThreads) rsum_s[r] = fmaxf(rsum_s[r], 1e-12f * rmax);
+                    // one power step: w = the row sums (floored to stay positive), zero past n
+                    for (int r = tid; r < kResKpad; r += kThreads) rsum_s[r] = r < s.n ? fmaxf(rsum_s[r], 1e-12f * rmax) : 0.0f;
                     __syncthreads();
                     scan(z0, rsum_s);
                     if (mtiles > 1) scan_corner(zc, rsum_s);
