@@ -136,12 +136,12 @@ def _profiled_traffic(workload: str, precision: str, gemms_per_launch: float):
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
     except Exception:
         return None, "no ncu record"
-    if sha != rec["sha256_16"]:
-        return None, "kernel changed since the ncu capture"
     if precision != "fp16x3":
         return None, "no ncu record for this precision"
     for r in rec["records"]:
         if r["workload"] == workload:
+            if sha != r["sha256_16"]:  # each record names the kernel source it was captured on
+                return None, "kernel changed since the ncu capture"
             t = r["dram_bytes_read"] + r["dram_bytes_write"]
             if "gemms" in r:
                 return t * gemms_per_launch / r["gemms"], ("ncu dram__bytes_read+write of a 152-column launch, "
