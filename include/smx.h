@@ -224,6 +224,20 @@ smx_status smx_set_function(smx_ctx* ctx, smx_function f);
  * Default 0 (F = I/2).  Errors: SMX_ERR_ARG (negative or non-finite). */
 smx_status smx_set_fermi_beta(smx_ctx* ctx, double beta);
 
+/* Symmetrised result (off by default).  Fig. 2 keeps only the owner columns of
+ * each submatrix's f(T_j), so the assembled D is not symmetric (each block
+ * D_ij comes from column j's submatrix, D_ji from column i's).  With enable != 0
+ * every later build returns 1/2 (D + D^T) on the filtered pattern: both blocks
+ * of a pair (i, j), (j, i) get the mean of D_ij and D_ji^T, a diagonal block its
+ * symmetric part, and blocks the filter dropped stay zero.  The trace and
+ * energy of smx_get_trace stay those of D as built (for the symmetric pattern
+ * of a symmetric H they are unchanged).  The pair list of the input pattern is
+ * built on the first enable (host work and one upload, synchronous).
+ * Errors: SMX_ERR_UNSUPPORTED with a column range set (smx_set_column_range:
+ * a shard holds only its own columns of D; also returned by a build if a range
+ * is set later). */
+smx_status smx_set_symmetrize(smx_ctx* ctx, int32_t enable);
+
 /* Non-orthogonal basis (Eq. 14 with an overlap S != I).  values: S on the
  * block pattern given to smx_create, in the same layout as H (n_values
  * doubles, host or device memory per on_device; copied, the caller keeps

@@ -130,6 +130,10 @@ class SubmatrixDensity:
         """Inverse temperature of the "fermi" function form (smx_set_fermi_beta)."""
         check(self._lib.smx_set_fermi_beta(self._ctx, float(beta)), "smx_set_fermi_beta")
 
+    def set_symmetrize(self, enable: bool = True):
+        """Return 1/2 (D + D^T) on the filtered pattern from later builds (smx_set_symmetrize)."""
+        check(self._lib.smx_set_symmetrize(self._ctx, 1 if enable else 0), "smx_set_symmetrize")
+
     def set_overlap(self, values=None, on_device: bool = False):
         """Overlap S on the input pattern (non-orthogonal form of Eq. 14; see smx_set_overlap);
         None returns to S = I."""

@@ -71,6 +71,7 @@ SIGNATURES = {
     "smx_set_precision": (C.c_int, [C.c_void_p, C.c_int, C.c_int32]),
     "smx_set_function": (C.c_int, [C.c_void_p, C.c_int]),
     "smx_set_fermi_beta": (C.c_int, [C.c_void_p, C.c_double]),
+    "smx_set_symmetrize": (C.c_int, [C.c_void_p, C.c_int32]),
     "smx_set_overlap": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "smx_build_density": (C.c_int, [C.c_void_p]),
     "smx_solve_mu": (C.c_int, [C.c_void_p]),

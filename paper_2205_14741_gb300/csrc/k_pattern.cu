@@ -905,6 +905,50 @@ cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cu
     return cudaGetLastError();
 }
 
+// The symmetrised D (the option of taking 1/2 (D + D^T): the submatrix method's D is not
+// symmetric).  Warp w of the grid takes pair w; its lanes stride over the pair's elements.
+__global__ void __launch_bounds__(256) k_symmetrize(const SymPair* __restrict__ pairs, int n_pairs,
+                                                    const uint8_t* __restrict__ keep, double* __restrict__ D,
+                                                    const int* skip) {
+    if (skip && *skip) return;
+    const int w = static_cast<int>((blockIdx.x * static_cast<unsigned>(blockDim.x) + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= n_pairs) return;
+    const SymPair p = pairs[w];
+    const int br = p.br, bj = p.bj;
+    if (p.k == p.kt) {  // a diagonal block (br == bj): element (r, c) with r < c and its mirror (c, r)
+        if (!keep[p.k]) return;
+        double* blk = D + p.off_k;
+        for (int e = lane; e < br * br; e += 32) {
+            const int c = e / br, r = e - c * br;  // column-major: element (r, c) at c br + r
+            if (r < c) {
+                const double v = 0.5 * (blk[e] + blk[r * br + c]);
+                blk[e] = v;
+                blk[r * br + c] = v;
+            }
+        }
+        return;
+    }
+    const bool kk = keep[p.k] != 0, kt = keep[p.kt] != 0;
+    double* bk = D + p.off_k;    // br x bj: rows of block row r, columns of block column j
+    double* bt = D + p.off_kt;   // bj x br: its transpose position
+    for (int e = lane; e < br * bj; e += 32) {
+        const int c = e / br, r = e - c * br;  // element (r, c) of block k; (c, r) of block kt
+        const int et = r * bj + c;
+        const double v = 0.5 * (bk[e] + bt[et]);  // a dropped block holds zeros
+        bk[e] = kk ? v : 0.0;
+        bt[et] = kt ? v : 0.0;
+    }
+}
+
+cudaError_t launch_symmetrize(const SymPair* pairs, int n_pairs, const uint8_t* keep, double* D, cudaStream_t st,
+                              const int* skip) {
+    if (n_pairs <= 0) return cudaSuccess;
+    const int blocks = (n_pairs + 7) / 8;  // eight warps (pairs) per CTA
+    k_symmetrize<<<blocks, 256, 0, st>>>(pairs, n_pairs, keep, D, skip);
+    return cudaGetLastError();
+}
+
 // a9 on the device: the bisection's state lives in the device scalars, so a whole mu solve is
 // enqueued at once (the same decisions as the host loop, in the same FP64 arithmetic).
 __global__ void k_bisect_init(DevScalars* sc, double lo, double hi) {

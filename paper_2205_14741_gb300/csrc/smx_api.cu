@@ -137,6 +137,10 @@ struct smx_ctx {
     bool model_ready = false, model_on = false, sq_valid = false;
     bool model_gap = false;  // the learned gap drives the scaled Newton-Schulz schedule
     double beta = 0.0;       // inverse temperature of SMX_FN_FERMI
+    // the symmetrised D: the block pairs of the input pattern (built on first use)
+    bool symmetrize = false;
+    int32_t n_pairs = -1;
+    DevBuf d_pairs;
     int adam_t = 0;
     int64_t n_samples = 0, cap_samples = 0;
     DevBuf d_params, d_mst, d_vst, d_partial_mlp, d_feat, d_pred, d_labels, d_gersh, d_prev_ratio, d_sq_ratio,
@@ -550,6 +554,7 @@ static smx_status build_at(smx_ctx* c, double mu, const double* mu_dev = nullptr
     if (c->function != SMX_FN_DENSITY && c->precision != SMX_FP64) return SMX_ERR_UNSUPPORTED;
     if (c->have_S && (c->function != SMX_FN_DENSITY || c->precision != SMX_FP64 || mu_dev))
         return SMX_ERR_UNSUPPORTED;  // the non-orthogonal form: density matrix, FP64
+    if (c->symmetrize && c->col_hi >= 0) return SMX_ERR_UNSUPPORTED;  // a shard holds only its columns of D
     if (c->dirty || !c->analysed) SMX_TRY(analyse(c));
     if (c->have_S && !c->nonorth_ready) SMX_TRY(nonorth_setup(c));
     cudaStream_t st = c->stream;
@@ -704,6 +709,11 @@ static smx_status build_at(smx_ctx* c, double mu, const double* mu_dev = nullptr
     if (c->precision == SMX_FP64 || (c->fp64_final > 0 && c->function == SMX_FN_DENSITY)) {
         // the tensor-core scatter sums the partials itself
         SMX_CUDA(launch_reduce(dp<double2>(c->d_partial), B, sc, st, skip));
+        c->kernel_launches += 1;
+    }
+    if (c->symmetrize) {  // after the sums: trace and energy are those of D as built
+        SMX_CUDA(launch_symmetrize(dp<SymPair>(c->d_pairs), c->n_pairs, dp<uint8_t>(c->d_keep), dp<double>(c->d_D), st,
+                                   skip));
         c->kernel_launches += 1;
     }
     SMX_CUDA(cudaEventRecord(c->ev1, st));
@@ -945,6 +955,41 @@ smx_status smx_set_function(smx_ctx* c, smx_function f) {
 smx_status smx_set_fermi_beta(smx_ctx* c, double beta) {
     if (!c || !std::isfinite(beta) || beta < 0.0) return SMX_ERR_ARG;
     c->beta = beta;
+    return SMX_OK;
+}
+
+smx_status smx_set_symmetrize(smx_ctx* c, int32_t enable) {
+    if (!c) return SMX_ERR_ARG;
+    if (enable && c->col_hi >= 0) return SMX_ERR_UNSUPPORTED;  // a shard holds only its own columns of D
+    if (enable && c->n_pairs < 0) {
+        // block k = (r, j) with r <= j and its transpose; the input pattern is symmetric with
+        // sorted rows (checked at creation), so the partner is found by bisection
+        std::vector<SymPair> pairs;
+        for (int32_t j = 0; j < c->B; ++j) {
+            for (int64_t k = c->col_ptr[j]; k < c->col_ptr[j + 1]; ++k) {
+                const int32_t r = c->row_idx[k];
+                if (r > j) break;
+                const int32_t* b0 = c->row_idx.data() + c->col_ptr[r];
+                const int32_t* b1 = c->row_idx.data() + c->col_ptr[r + 1];
+                const int32_t* f = std::lower_bound(b0, b1, j);
+                if (f == b1 || *f != j) return SMX_ERR_PATTERN;
+                SymPair p;
+                p.k = static_cast<int32_t>(k);
+                p.kt = static_cast<int32_t>(f - c->row_idx.data());
+                p.off_k = c->voff[k];
+                p.off_kt = c->voff[p.kt];
+                p.br = c->bs[r];
+                p.bj = c->bs[j];
+                pairs.push_back(p);
+            }
+        }
+        DeviceGuard g(c->device);
+        SMX_TRY(upload(c->d_pairs, pairs, c->stream));
+        SMX_CUDA(cudaStreamSynchronize(c->stream));
+        c->n_pairs = static_cast<int32_t>(pairs.size());
+    }
+    c->symmetrize = enable != 0;
+    c->built = false;
     return SMX_OK;
 }
 

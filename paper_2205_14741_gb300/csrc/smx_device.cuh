@@ -27,6 +27,15 @@ struct SubDesc {
     int64_t x_off;  // offset of the saved owner columns (n x bown, column by column)
 };
 
+// One block pair of the symmetric input pattern for the symmetrised D: block k = (row r,
+// column j) with r <= j and its transpose kt = (row j, column r) (kt == k on the diagonal);
+// value offsets of both in the input layout (column-major blocks of br x bj and bj x br).
+struct SymPair {
+    int64_t off_k, off_kt;
+    int32_t k, kt;
+    int32_t br, bj;
+};
+
 // Filtered pattern and value addressing shared by gather and scatter.
 struct PatternView {
     const int64_t* fcol_ptr;  // [B+1] filtered block-CSC column pointers

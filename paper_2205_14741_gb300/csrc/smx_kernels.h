@@ -73,6 +73,13 @@ cudaError_t launch_gather_bound_f32(const SubDesc* subs, int n_subs, int max_nbl
 cudaError_t launch_reduce(const double2* partial, int n_cols, DevScalars* sc, cudaStream_t st,
                           const int* skip = nullptr);
 
+// D <- 1/2 (D + D^T) on the filtered pattern, in place, in the input layout: for each block
+// pair both blocks get the mean of the block and the transpose of its partner, and a block the
+// filter dropped (keep[k] == 0) stays zero.  One warp per pair; every element is read and
+// written by one thread.
+cudaError_t launch_symmetrize(const SymPair* pairs, int n_pairs, const uint8_t* keep, double* D, cudaStream_t st,
+                              const int* skip = nullptr);
+
 // Failure-detection self-test: a wait on an mbarrier nothing arrives at, given up after
 // poll_limit polls (records kErrTimeout in *status; *polls_out, if set, the polls made).
 cudaError_t launch_wait_selftest(int* status, uint32_t poll_limit, int* polls_out, cudaStream_t st);

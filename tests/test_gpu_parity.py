@@ -382,3 +382,39 @@ def test_second_row_tile_edges(n, prec, bound):
         _check(d, tr, en, d_or, res, prec)
     else:
         assert float(np.max(np.abs(d - d_or))) <= bound
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x3"])
+def test_symmetrize_matches_oracle(prec):
+    # The option 1/2 (D + D^T) on the filtered pattern against the oracle's: ragged blocks
+    # (1..7) give pairs of unequal block sizes, and the threshold drops 166 of 1022 blocks.
+    sizes = np.random.default_rng(11).integers(1, 8, 48)
+    s = make_mixed_block_system(sizes, r_c=5.5, ell=1.5, seed=12)
+    eps, mu = 1e-2, 0.02
+    with _ctx(s, prec, eps) as c:
+        c.set_mu(mu)
+        c.build_density()
+        d_plain = c.get_density()
+        c.set_symmetrize(True)
+        c.build_density()
+        d = c.get_density()
+        tr, en, _ = c.get_trace()
+        c.set_symmetrize(False)
+        c.build_density()
+        d_again = c.get_density()
+    d_or, res, keep = oracle_in_input_layout(s, eps, mu, symmetrize=True)
+    assert 0 < int(np.count_nonzero(~keep)) < keep.shape[0]
+    _check(d, tr, en, d_or, res, prec)
+    dense = O.to_dense(s.block_size, s.col_ptr, s.row_idx, d)
+    assert np.array_equal(dense, dense.T)  # exactly symmetric: both blocks of a pair get one value
+    plain = O.to_dense(s.block_size, s.col_ptr, s.row_idx, d_plain)
+    assert float(np.max(np.abs(plain - plain.T))) > 0.0  # the submatrix method's D is not
+    assert np.array_equal(d_again, d_plain)  # switched off: the plain D again, bit for bit
+
+
+def test_symmetrize_refused_on_a_shard():
+    s = make_workload("water32")
+    with _ctx(s, "fp64") as c:
+        c.set_column_range(0, 16)
+        with pytest.raises(Exception, match="smx_set_symmetrize"):
+            c.set_symmetrize(True)
