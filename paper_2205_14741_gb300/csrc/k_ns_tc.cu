@@ -865,32 +865,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_ns_tc(NsTcArgs a, const __grid_
                 if (keep_a) tmem_wait_st();
             };
             // two-tile form: the columns 128 .. of tile 0 of X' as rows 128 .. of the image (X' is
-            // symmetric), element by element, from the packed operand that drain left at acc
+            // symmetric), element by element, from the packed operand that drain left at acc.
+            // Warps of parts 0 and 1 only (part 2 drains the corner meanwhile): with two chunks
+            // (kpad 192) one each, with one (kpad 160) a half (16 columns) each.
             auto drain_t = [&](uint32_t acc) {
+                if (part == 2) return;
                 const int row = 32 * q + lane;
-#pragma unroll 1
-                for (int c0 = 128 + 32 * part; c0 < kpad; c0 += 96) {
-                    uint32_t w[32];
-                    tmem_ld32_issue(acc + lane_off + c0, w);
-                    tmem_wait_ld_regs(w);
+                const bool halves = wc <= 32;
+                const int c0 = 128 + (halves ? 0 : 32 * part);
+                if (c0 >= kpad) return;
+                const int i0 = halves ? 16 * part : 0;
+                uint32_t w[32];
+                tmem_ld32_issue(acc + lane_off + c0, w);
+                tmem_wait_ld_regs(w);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const uint32_t off = img_offset(c0 + i, row, RB);  // element (c0 + i, row)
-                        const int sh = (i & 1) * 16;                       // pairs hold the even column low
-                        *reinterpret_cast<uint16_t*>(smem + hi_off + off) = static_cast<uint16_t>(w[i >> 1] >> sh);
-                        if constexpr (NB == 2)
-                            *reinterpret_cast<uint16_t*>(smem + lo_off + off) = static_cast<uint16_t>(w[16 + (i >> 1)] >> sh);
-                    }
+                for (int ii = 0; ii < 32; ++ii) {
+                    if (halves && (ii < i0 || ii >= i0 + 16)) continue;  // warp-uniform
+                    const int i = ii;
+                    const uint32_t off = img_offset(c0 + i, row, RB);  // element (c0 + i, row)
+                    const int sh = (i & 1) * 16;                       // pairs hold the even column low
+                    *reinterpret_cast<uint16_t*>(smem + hi_off + off) = static_cast<uint16_t>(w[i >> 1] >> sh);
+                    if constexpr (NB == 2)
+                        *reinterpret_cast<uint16_t*>(smem + lo_off + off) = static_cast<uint16_t>(w[16 + (i >> 1)] >> sh);
                 }
             };
             // the corner of X' = alpha C (accumulator at acc, wc columns) into rows and columns
-            // 128 .., made exactly symmetric as the diagonal block of tile 0 in drain
+            // 128 .., made exactly symmetric as the diagonal block of tile 0 in drain; by the
+            // part-2 warps of the corner's lane quadrants (8, and 9 for wc = 64; never warp 10),
+            // all its chunks, while parts 0 and 1 run drain_t
             auto drain_corner = [&](uint32_t acc, float alpha) {
                 const int crow0 = 32 * q;
-                if (crow0 >= wc) return;
+                if (crow0 >= wc || part != 2) return;
                 const int row = 128 + crow0 + lane;
 #pragma unroll 1
-                for (int c0 = 32 * part; c0 < wc; c0 += 96) {
+                for (int c0 = 0; c0 < wc; c0 += 32) {
                     if (kMirror && c0 < crow0) continue;  // the mirror of another warp's chunk
                     uint32_t raw[32];
                     tmem_ld32_issue(acc + lane_off + c0, raw);
