@@ -18,12 +18,14 @@ def _need_cuda():
         pytest.skip("no CUDA device")
 
 
-def _solve(sysm, prec, n_e, max_steps, tol, device, eps=1e-5, repeat_values=False):
+def _solve(sysm, prec, n_e, max_steps, tol, device, eps=1e-5, repeat_values=False, symmetrize=False):
     from paper_2205_14741_gb300 import SubmatrixDensity
 
     with SubmatrixDensity.from_system(sysm) as c:
         c.set_precision(prec)
         c.set_filter_threshold(eps)
+        if symmetrize:
+            c.set_symmetrize(True)
         c.set_electron_count(n_e, max_steps=max_steps, tol=tol)
         if repeat_values:  # an analysed context given new values (the filter runs first)
             c.set_mu(0.0)
@@ -47,3 +49,20 @@ def test_device_bisection_matches_the_host_loop(prec, case):
     assert np.array_equal(dev[0], host[0])
     if case == "all_steps":
         assert host[4] == steps
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x3"])
+def test_device_bisection_with_symmetrised_result(prec):
+    # The symmetrisation runs after every build of the solve, and the skipped builds after
+    # the stopping step skip it too: the device loop's D is the host loop's, bit for bit,
+    # and it is exactly symmetric on the pattern.
+    import oracle as O
+
+    s = make_workload("water32")
+    host = _solve(s, prec, 96.0, 40, 1e-3, False, symmetrize=True)
+    dev = _solve(s, prec, 96.0, 40, 1e-3, True, symmetrize=True)
+    assert dev[3] == host[3] and dev[4] == host[4] and dev[4] < 40
+    assert np.array_equal(dev[0], host[0])
+    dense = O.to_dense(s.block_size, s.col_ptr, s.row_idx, dev[0])
+    assert np.array_equal(dense, dense.T)
+
