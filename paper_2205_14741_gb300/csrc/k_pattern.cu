@@ -482,14 +482,21 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (BS == 6 ? 4 : 3) : 2) k
     int* rows = reinterpret_cast<int*>(kcol + 2 * nblk_max);  // R_j
     int* ls = rows + nblk_max;        // local starts, nb + 1 entries
     int* cinfo = ls + nblk_max + 1;   // per local column y: local block (bits 16-31), its size (8-15), y - start (0-7)
-    for (int a = tid; a < nb; a += blockDim.x) {
-        const int r = pv.frow_idx[s.fptr + a];
-        rows[a] = r;
-        ls[a] = pv.lstart[s.fptr + a];
-        kcol[2 * a] = pv.fcol_ptr[r];
-        kcol[2 * a + 1] = pv.fcol_ptr[r + 1];
+    const bool premap = pv.maps != nullptr;  // the map built once per pattern: one coalesced read
+    if (premap) {
+        const int32_t* gm = pv.maps + pv.map_off[s.col];
+        for (int a = tid; a < nb; a += blockDim.x) ls[a] = pv.lstart[s.fptr + a];
+        for (int i = tid; i < nb * nb; i += blockDim.x) map[i] = gm[i];
+    } else {
+        for (int a = tid; a < nb; a += blockDim.x) {
+            const int r = pv.frow_idx[s.fptr + a];
+            rows[a] = r;
+            ls[a] = pv.lstart[s.fptr + a];
+            kcol[2 * a] = pv.fcol_ptr[r];
+            kcol[2 * a + 1] = pv.fcol_ptr[r + 1];
+        }
+        for (int i = tid; i < nb * nb; i += blockDim.x) map[i] = -1;
     }
-    for (int i = tid; i < nb * nb; i += blockDim.x) map[i] = -1;
     if (tid == 0) ls[nb] = s.n;
     __syncthreads();
     if constexpr (BS == 0) {
@@ -502,7 +509,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (BS == 6 ? 4 : 3) : 2) k
             cinfo[y] = (lo << 16) | ((ls[lo + 1] - ls[lo]) << 8) | (y - ls[lo]);
         }
     }
-    for (int a = warp; a < nb; a += 8) {
+    for (int a = premap ? nb : warp; a < nb; a += 8) {
         for (int64_t k = kcol[2 * a] + lane; k < kcol[2 * a + 1]; k += 32) {
             const int r = pv.frow_idx[k];
             const int64_t vo = pv.fvoff[k];

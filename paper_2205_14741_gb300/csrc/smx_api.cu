@@ -88,6 +88,8 @@ struct smx_ctx {
     std::vector<uint8_t> keep;
     std::vector<int64_t> fcol_ptr, fvoff;
     std::vector<int32_t> frow_idx, lstart, order;
+    std::vector<int32_t> maps;     // block maps of the submatrices (empty: built by the gather)
+    std::vector<int64_t> map_off;
     std::vector<SubDesc> subs;
     int max_nblk = 0, max_n = 0;
     int64_t t_elems = 0, x_elems = 0;
@@ -98,7 +100,7 @@ struct smx_ctx {
     bool filter_compared = false;     // the last filter launch compared its flags with the current pattern
     DevBuf d_sc;                      // DevScalars: status, flags, bracket, trace and energy
     DevScalars* h_sc = nullptr;       // pinned copy, filled by fetch()
-    DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order;
+    DevBuf d_fcol_ptr, d_frow_idx, d_fvoff, d_lstart, d_subs, d_order, d_maps, d_map_off;
     DevBuf d_T, d_W1, d_W2, d_W3, d_W4, d_ws, d_D, d_xown;
     DevBuf d_bound, d_iters, d_partial, d_work_n3;
     uint8_t* h_keep_pinned = nullptr;
@@ -205,6 +207,10 @@ static PatternView pattern_view(smx_ctx* c) {
     pv.fvoff = dp<int64_t>(c->d_fvoff);
     pv.lstart = dp<int32_t>(c->d_lstart);
     pv.bsize = dp<int32_t>(c->d_bs);
+    if (!c->maps.empty()) {
+        pv.maps = dp<int32_t>(c->d_maps);
+        pv.map_off = dp<int64_t>(c->d_map_off);
+    }
     return pv;
 }
 
@@ -391,6 +397,32 @@ static smx_status compact(smx_ctx* c) {
         std::stable_sort(c->order.begin() + c->chunk_start[k], c->order.begin() + c->chunk_start[k + 1],
                          [&](int32_t x, int32_t y) { return c->subs[x].n > c->subs[y].n; });
 
+    // The block maps of the submatrices (what the shared-memory gather would otherwise build at
+    // every gather from the pattern): for submatrices of at most 64 blocks (the gather's staged
+    // form), 32-bit value offsets, at most 2^26 entries in all
+    c->maps.clear();
+    c->map_off.assign(B + 1, 0);
+    for (int32_t j = 0; j < B; ++j) {
+        const int64_t nb = c->fcol_ptr[j + 1] - c->fcol_ptr[j];
+        c->map_off[j + 1] = c->map_off[j] + nb * nb;
+    }
+    if (c->max_nblk <= 64 && c->map_off[B] <= (int64_t(1) << 26) && c->n_values < (int64_t(1) << 31)) {
+        c->maps.assign(static_cast<size_t>(c->map_off[B]), -1);
+        for (int32_t j = 0; j < B; ++j) {
+            const int32_t* R = c->frow_idx.data() + c->fcol_ptr[j];
+            const int32_t nb = static_cast<int32_t>(c->fcol_ptr[j + 1] - c->fcol_ptr[j]);
+            int32_t* m = c->maps.data() + c->map_off[j];
+            for (int32_t a = 0; a < nb; ++a) {
+                const int32_t col = R[a];
+                for (int64_t k = c->fcol_ptr[col]; k < c->fcol_ptr[col + 1]; ++k) {
+                    const int32_t* f = std::lower_bound(R, R + nb, c->frow_idx[k]);
+                    if (f != R + nb && *f == c->frow_idx[k]) m[static_cast<int64_t>(a) * nb + (f - R)] = static_cast<int32_t>(c->fvoff[k]);
+                }
+            }
+        }
+        SMX_TRY(upload(c->d_maps, c->maps, st));
+        SMX_TRY(upload(c->d_map_off, c->map_off, st));
+    }
     SMX_TRY(upload(c->d_fcol_ptr, c->fcol_ptr, st));
     SMX_TRY(upload(c->d_frow_idx, c->frow_idx, st));
     SMX_TRY(upload(c->d_fvoff, c->fvoff, st));

@@ -43,6 +43,11 @@ struct PatternView {
     const int64_t* fvoff;     // [nnzb_f] offset of each filtered block in the input value array
     const int32_t* lstart;    // [nnzb_f] first row of the block inside its column's submatrix
     const int32_t* bsize;     // [B] block sizes
+    // Block maps of the submatrices, built once per filtered pattern (null: the gather builds
+    // them): for block column j, nblk_j x nblk_j value offsets from maps + map_off[j], entry
+    // (a, c) the offset of block (R_j[c], R_j[a]) of H, -1 when the filter dropped it
+    const int32_t* maps = nullptr;
+    const int64_t* map_off = nullptr;
 };
 
 // Conversions between FP64 and FP32 on the integer pipes.  GB300's FP64 pipe
