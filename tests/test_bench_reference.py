@@ -38,3 +38,32 @@ def test_reference_arm_other_ranks_print_nothing():
                         "--warmup", "0", "--workload", "water32"], capture_output=True, text=True, timeout=600,
                        cwd=ROOT, env=env)
     assert r.returncode == 0 and not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def _bench_module():
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_traffic_records_follow_the_kernel_source():
+    # The roofline's `traffic` comes from a committed ncu record only while the record's hash
+    # names the current kernel source; a shard record is scaled by the launch's GEMM count.
+    b = _bench_module()
+    rec = json.load(open(os.path.join(ROOT, "profiles", "ns_tc_traffic.json")))
+    by = {r["workload"]: r for r in rec["records"]}
+    t, note = b._profiled_traffic("water1024", "fp16x3", 1.0)
+    if t is not None:  # the record matches the source: the launch's bytes as recorded
+        assert t == by["water1024"]["dram_bytes_read"] + by["water1024"]["dram_bytes_write"]
+        c3 = by["water4096x23"]
+        t3, note3 = b._profiled_traffic("water4096x23", "fp16x3", 2.0 * c3["gemms"])
+        if t3 is not None:
+            assert abs(t3 - 2.0 * (c3["dram_bytes_read"] + c3["dram_bytes_write"])) <= 1e-6 * t3
+            assert "scaled" in note3
+    else:
+        assert note == "kernel changed since the ncu capture"
+    assert b._profiled_traffic("water1024", "fp16", 1.0) == (None, "no ncu record for this precision")
+    assert b._profiled_traffic("slab6000", "fp16x3", 1.0)[0] is None
