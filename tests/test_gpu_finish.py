@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # the bulk precision sets the error (the finishing steps do not repair a single-pass bulk's
-# rotated subspace); the split form keeps the benchmark spec's 1e-5
+# rotated subspace); the split form keeps the 1e-5 bound on D of the mixed forms
 BOUND = {"fp16x3": 1e-5, "fp16": 2e-2, "bf16": 1e-1}
 
 
